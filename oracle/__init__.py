@@ -1,0 +1,21 @@
+"""Plain double-precision CPU oracle for the truncated LJ force over a Verlet list.
+
+TEST INFRASTRUCTURE ONLY.  The CUDA library never imports, links or runs
+anything here; only the tests, the smoke check and the benchmark's CPU
+baseline do.  See ``lj_oracle.c`` for the passages of the paper each function
+follows and the readings taken where the paper is silent.
+
+Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
+
+* pairlist (brute, cells): pinned -- the two independent routes agree as
+  sets; mean row length against the closed-form sphere volume; the paper's
+  55-80 neighbours per atom.
+* force: pinned -- sympy's symbolic derivative of Eq. (1); two-body closed
+  forms (zero at 2^(1/6) sigma, 24 dt at r = sigma); Newton's third law;
+  F = -grad E by central differences; half list == full list; invariance
+  under permutation and translation; the eps/sigma scaling law.
+* energy: pinned -- V(2^(1/6) sigma) = -eps, V(sigma) = 0, the shift.
+* force_vjp: pinned -- central finite differences of the loss (h = 1e-6)
+  built from ``forces`` alone.
+"""
+from .oracle import build, energy, force, force_vjp, forces, pairlist  # noqa: F401
