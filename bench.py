@@ -1,0 +1,470 @@
+#!/usr/bin/env python3
+"""LJ pair interactions/s on one GB300: FP64 and mixed precision.
+
+Workload: the paper's benchmark (section "Benchmark Conditions"): an FCC
+crystal of N = 119,164 = 4*31^3 atoms at density 1.0, cutoff 3.0 sigma,
+search length 3.3 sigma (bookkeeping margin 0.3), jitter 0.05 sigma,
+particle order randomly permuted, half list (i < j), dt = 0.01.
+
+One step = one pass of the hot path: build the sorted CSR Verlet list on
+the GPU (cell binning, count, scan, fill) and then run the force 100 times
+on it, the paper's protocol ("the time to calculate the force 100 times").
+A pair interaction is one unique list entry processed in one force call,
+so each step credits 100 * nnz(half list).
+
+Timing: inputs resident in HBM; L2 flushed (256 MiB write) before every
+step, outside the timed events; each step timed with CUDA events on the
+launching stream; W warm-up steps; the max over ranks of the summed step
+times.  `e2e` repeats the step with the positions and momenta copied from
+pinned host memory and the momenta copied back inside the timed region.
+
+`--impl reference` times the CPU oracle (the plain double-precision C
+implementation the tests compare against) on the same workload: each step
+is one oracle cell-list build plus 10 oracle force calls, single thread.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "LJ pair interactions/s on 1 GB300, FP64 vs mixed at stated error; % HBM roofline"
+UNIT = "pair interactions/s"
+FORCE_CALLS = 100
+DT, RC, MARGIN = 0.01, 3.0, 0.3
+CPU_FORCE_CALLS = 10
+L2_FLUSH_BYTES = 256 << 20
+# FP64 peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM
+# (4 flop) x 2070 MHz (the nominal 1.25 TFLOP/s FP64 of GB300).
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
+# DRAM bytes per launch from an ncu capture of the kernel as it stands
+# (profiles/); None until captured for the current kernel source.
+TRAFFIC_PER_LAUNCH = {"force_stream_kernel": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--order", choices=["random", "cell"], default="random")
+    ap.add_argument("--no-variants", action="store_true", help="skip the per-variant table")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--profile", choices=["fp64", "fp64-full", "mixed", "mixed-full", "list"],
+                    help="no timing: build the list and run a few calls of one kernel (for ncu)")
+    ap.add_argument("--profile-atoms", choices=["paper", "million"], default="paper")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "fallback (profiling recipe)"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None or not self.path:
+            out["reasons"] = ["nvidia-smi unavailable"]
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(rank: int, order: str):
+    from paper_1806_05713_gb300 import inputs
+    return inputs.fcc_system(31, 1.0, 0.05, seed=rank, order=order, rc=RC, margin=MARGIN)
+
+
+def workload_name(order: str) -> str:
+    return f"fcc-31^3 N=119164 rho=1.0 rc=3.0 rs=3.3 jitter=0.05 {order}-order half-list dt=0.01"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(s, calls: int):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    rp, col = oracle.pairlist(s.q, s.box, s.rs, True, "cells")
+    p = np.zeros((s.n, 3))
+    for _ in range(calls):
+        p = oracle.force(s.q, p, rp, col, True, DT, s.rc, s.box)
+    dt = time.perf_counter() - t0
+    return dt, int(col.size)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    s = workload(0, args.order)
+    for _ in range(max(0, args.warmup)):
+        oracle_sample(s, 1)
+    times, nnz = [], 0
+    for _ in range(args.steps):
+        t, nnz = oracle_sample(s, CPU_FORCE_CALLS)
+        times.append(t)
+    total = sum(times)
+    value = args.steps * CPU_FORCE_CALLS * nnz / total
+    sample = (f"each step: 1 oracle cell-list build + {CPU_FORCE_CALLS} oracle force calls on "
+              f"N={s.n} ({nnz} half-list entries), single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_name(args.order)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def count_in_cutoff(q, pl, box, rc):
+    """Entries with r < r_c (for the flop count), with torch on the GPU at
+    set-up time; not part of the timed path."""
+    import torch
+    rp = pl.row_ptr.long()
+    rows = torch.repeat_interleave(torch.arange(pl.n, device=q.device), rp[1:] - rp[:-1])
+    col = pl.col_view.long()
+    d = q[col, :3] - q[rows, :3]
+    L = torch.tensor(box, device=q.device, dtype=torch.float64)
+    d = d - L * torch.round(d / L)
+    return int(((d * d).sum(1) < rc * rc).sum().item())
+
+
+def run_profile(args):
+    """A short, fixed launch sequence for a profiler: 2 list builds, then
+    5 calls of the chosen force kernel (or 3 more list builds)."""
+    import torch
+    from paper_1806_05713_gb300 import build as lib_build
+    from paper_1806_05713_gb300 import inputs, lj
+    lib_build.build()
+    k = 31 if args.profile_atoms == "paper" else 64
+    s = inputs.fcc_system(k, 1.0, 0.05, seed=0, order=args.order, rc=RC, margin=MARGIN)
+    box = [float(x) for x in s.box]
+    q = torch.from_numpy(s.q).cuda()
+    p = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
+    half = not args.profile.endswith("full")
+    pl = lj.lj_build_pairlist(q, box, s.rs, half)
+    pl = lj.lj_build_pairlist(q, box, s.rs, half, reuse=pl)
+    if args.profile == "list":
+        for _ in range(3):
+            lj.lj_build_pairlist(q, box, s.rs, half, reuse=pl)
+    else:
+        prec = lj.LJ_MIXED if args.profile.startswith("mixed") else lj.LJ_FP64
+        tpi = lj.LJ_TPI_AUTO
+        fn = lj.lj_force_prepared(q, p, pl, DT, s.rc, box, precision=prec, tpi=tpi)
+        for _ in range(5):
+            fn()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "n": s.n, "nnz": pl.nnz,
+                      "launches": int(lj.load().lj_kernel_launch_count())}))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    if args.profile:
+        run_profile(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1806_05713_gb300 import build as lib_build
+    from paper_1806_05713_gb300 import lj
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        lib_build.build()
+    if world > 1:
+        dist.barrier()
+    lib = lj.load()
+
+    s = workload(rank, args.order)
+    box = [float(x) for x in s.box]
+    q = torch.from_numpy(s.q).to(dev)
+    p = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    pl = lj.lj_build_pairlist(q, box, s.rs, True)
+    force = lj.lj_force_prepared(q, p, pl, DT, s.rc, box, precision=lj.LJ_FP64,
+                                 tpi=lj.LJ_SCHED_STREAM)
+    nnz = pl.nnz
+    n_cut = count_in_cutoff(q, pl, box, s.rc)
+
+    def one_step(ev):
+        lj.lj_build_pairlist(q, box, s.rs, True, reuse=pl)
+        ev[1].record(stream)
+        for c in range(FORCE_CALLS):
+            ev[2][c].record(stream)
+            force()
+            ev[3][c].record(stream)
+
+    def new_events():
+        return ([torch.cuda.Event(enable_timing=True) for _ in range(2)],
+                [torch.cuda.Event(enable_timing=True) for _ in range(2)],
+                [torch.cuda.Event(enable_timing=True) for _ in range(FORCE_CALLS)],
+                [torch.cuda.Event(enable_timing=True) for _ in range(FORCE_CALLS)])
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        ev = new_events()
+        ev[0][0].record(stream)
+        one_step((None, ev[1][0], ev[2], ev[3]))
+    torch.cuda.synchronize()
+
+    step_ms, list_ms, force_ms = [], [], []
+    launches0 = lib.lj_kernel_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev = new_events()
+            e0.record(stream)
+            one_step((None, ev[1][0], ev[2], ev[3]))
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            list_ms.append(e0.elapsed_time(ev[1][0]))
+            force_ms.extend(a.elapsed_time(b) for a, b in zip(ev[2], ev[3]))
+        torch.cuda.synchronize()
+    launches = lib.lj_kernel_launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    pairs = FORCE_CALLS * nnz * args.steps * world
+    value = pairs / (total_ms / 1e3)
+
+    # ---- end to end through the public API, host buffers --------------------
+    q_host = torch.from_numpy(s.q).pin_memory()
+    p_host = torch.zeros((s.n, 4), dtype=torch.float64).pin_memory()
+    p_back = torch.empty_like(p_host).pin_memory()
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        q.copy_(q_host, non_blocking=True)
+        p.copy_(p_host, non_blocking=True)
+        lj.lj_build_pairlist(q, box, s.rs, True, reuse=pl)
+        for _ in range(FORCE_CALLS):
+            force()
+        p_back.copy_(p, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = pairs / (e2e_total / 1e3)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (the FP64 force) -------------------
+    hbm_peak, hbm_src = measured_peaks()
+    t_force = statistics.mean(force_ms) / 1e3
+    flops = 28.0 * n_cut + 8.0 * (nnz - n_cut)     # paper: 27 add/mul + 1 div per pair
+    alg_bytes = 4.0 * nnz + 4.0 * (s.n + 1) + 32.0 * s.n + 64.0 * s.n
+    roof = {"bound": "alu", "achieved": flops / t_force / 1e12, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": flops / t_force / 1e12 / FP64_PEAK_TFLOPS,
+            "traffic": TRAFFIC_PER_LAUNCH["force_stream_kernel"],
+            "kernel": "force_stream_kernel (FP64, half list)",
+            "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+            "flops_per_launch": flops, "launch_ms": t_force * 1e3}
+    hbm_view = {"achieved": alg_bytes / t_force / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": alg_bytes / t_force / 1e9 / hbm_peak, "peak_source": hbm_src,
+                "bytes_per_pair": alg_bytes / nnz}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.order), "n_atoms": s.n, "pairs_per_call": nnz,
+                   "pairs_in_cutoff": n_cut, "force_calls_per_step": FORCE_CALLS,
+                   "list_builds_per_step": 1, "schedule": "pair-stream FP64",
+                   "l2": "flushed before every step (256 MiB write, outside the timed events)",
+                   "parallelism": f"replicas x{world}"},
+        "list_build_ms": statistics.mean(list_ms),
+        "force_ms_per_call": t_force * 1e3,
+        "force_only_pairs_per_s": nnz / t_force,
+        "roofline": roof, "hbm_roofline": hbm_view,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 32 * s.n,
+                "d2h_bytes_per_step": 32 * s.n},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+
+    if not args.no_variants:
+        out["variants"] = variants(lj, s, q, pl, box, dev, stream, flush)
+    if world == 1 and not args.no_cpu:
+        t, m = oracle_sample(s, CPU_FORCE_CALLS)
+        out["cpu_baseline"] = {
+            "value": CPU_FORCE_CALLS * m / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 oracle cell-list build + {CPU_FORCE_CALLS} oracle force calls on the "
+                      f"same N={s.n} system, single thread ({t:.1f} s)"}
+    print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def time_calls(fn, stream, flush, calls=20, warm=3):
+    import torch
+    for _ in range(warm):
+        fn()
+    ms = []
+    for _ in range(calls):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
+
+
+def variants(lj, s, q, pl_half, box, dev, stream, flush):
+    """Force-only time per call of each schedule, list kind, precision and
+    particle order (config 'paper size: two orderings, half and full'), with
+    L2 flushed before each call, plus list-build times and mixed-form error."""
+    import torch
+    from paper_1806_05713_gb300 import inputs
+    res = {}
+    for order in ("random", "cell"):
+        if order == "random":
+            qq, sys_ = q, s
+        else:
+            sys_ = inputs.fcc_system(31, 1.0, 0.05, seed=0, order="cell", rc=RC, margin=MARGIN)
+            qq = torch.from_numpy(sys_.q).to(dev)
+        for half in (True, False):
+            kind = "half" if half else "full"
+            t_list = time_calls(lambda: lj.lj_build_pairlist(qq, box, sys_.rs, half), stream, flush, 5, 1)
+            pl = lj.lj_build_pairlist(qq, box, sys_.rs, half)
+            m_half = pl.nnz if half else pl.nnz // 2
+            res[f"list_build_ms/{order}/{kind}"] = t_list
+            p64 = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
+            ref = None
+            for prec, tpis in ((lj.LJ_FP64, (64, 8, 32)), (lj.LJ_MIXED, (4, 8, 16))):
+                for tpi in tpis:
+                    pp = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
+                    fn = lj.lj_force_prepared(qq, pp, pl, DT, sys_.rc, box, precision=prec, tpi=tpi)
+                    ms = time_calls(fn, stream, flush)
+                    name = f"{'fp64' if prec == 0 else 'mixed'}/{order}/{kind}/tpi{tpi}"
+                    res[name] = {"ms": ms, "pairs_per_s": m_half / (ms / 1e3)}
+                    # error of one call vs the FP64 result (itself within 1e-12 of the oracle)
+                    pp.zero_()
+                    fn()
+                    if prec == lj.LJ_FP64 and ref is None:
+                        ref = pp[:, :3].clone()
+                    elif prec == lj.LJ_MIXED and ref is not None:
+                        err = pp[:, :3] - ref
+                        res[name]["max_err_rel"] = float(err.abs().max() / ref.abs().max())
+                        res[name]["rms_err_rel"] = float(err.pow(2).mean().sqrt() / ref.pow(2).mean().sqrt())
+            del p64
+    return res
+
+
+if __name__ == "__main__":
+    main()

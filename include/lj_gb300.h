@@ -1,0 +1,184 @@
+/*
+ * lj_gb300.h -- C ABI of the GB300 (sm_103a) Lennard-Jones force library.
+ *
+ * The library computes one step of the truncated Lennard-Jones momentum
+ * update over a sorted Verlet pair list (Watanabe & Nakagawa, arXiv
+ * 1806.05713): for each atom i it walks the j of its list row, forms the
+ * minimum-image displacement d = q_j - q_i, skips pairs with r^2 >= r_c^2,
+ * and applies
+ *
+ *     df = (24 eps sigma^6 r^6 - 48 eps sigma^12) dt / r^14,
+ *     p_i += df d,   p_j -= df d,
+ *
+ * which is Algorithm 1 (with the printed sign of the p_j update read as the
+ * opposite of p_i's, as Newton's third law requires) inside the sorted-list
+ * double loop of Algorithm 3, for the potential of Eq. (1).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are device pointers; every other pointer is host.
+ *  - Positions and momenta are "AoS4": n rows of 4 doubles {x, y, z, pad}
+ *    (the padded layout of the section "AoS with Padding"); their base
+ *    pointers must be 32-byte aligned (rows are read with 256-bit loads),
+ *    else LJ_ERR_ARG.  Workspaces must be 256-byte aligned.
+ *    The pad element of positions is ignored; that of momenta is never
+ *    written.
+ *  - Positions must lie in [0, L) per axis of the periodic box (L = box[a]),
+ *    and every box side must be at least 2 r_search (unique minimum image).
+ *  - The pair list is CSR with 32-bit indices: row_ptr[n+1], col[nnz]; row i
+ *    holds its j in ascending order; a "half" list holds only j > i, a
+ *    "full" list every j != i.
+ *  - Caller owns every buffer.  The library never allocates device memory:
+ *    scratch space is passed in as `workspace_dev` of at least the size the
+ *    matching *_workspace_bytes() function reports (256-byte aligned).
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  Entry points that must read a count back say so.
+ *  - Return value: LJ_OK (0) or one of the LJ_ERR_* codes; no exception or
+ *    abort crosses the ABI.  On error, outputs are unspecified unless stated.
+ *    lj_status_string() names each code.
+ */
+#ifndef LJ_GB300_H
+#define LJ_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LJ_OK 0
+#define LJ_ERR_ARG 1      /* null pointer, n < 0, bad flag, r_cut > r_search, ... */
+#define LJ_ERR_BOX 2      /* a box side is shorter than 2 r_search (or not finite) */
+#define LJ_ERR_RANGE 3    /* a position is outside [0, L) or not finite */
+#define LJ_ERR_CAPACITY 4 /* output or workspace too small, or nnz >= 2^31 */
+#define LJ_ERR_CUDA 5     /* a CUDA runtime call failed (see lj_last_cuda_error) */
+#define LJ_ERR_DEVICE 6   /* no usable sm_103 device for this library build */
+
+/* ---- arithmetic forms of the force kernels ----------------------------- */
+#define LJ_FP64 0  /* every step in IEEE double precision */
+#define LJ_MIXED 1 /* FP32 pair arithmetic; cell-relative displacement derived
+                      from the FP64 positions; compensated FP32 per-i sums and
+                      FP64 momentum updates */
+
+/* ---- schedules ---------------------------------------------------------- */
+/* `tpi` = threads per i-row: 1, 2, 4, 8, 16 or 32 lanes of one warp walk one
+ * row and reduce their partial sums with warp shuffles; 0 = library default
+ * for the list kind and precision. */
+#define LJ_TPI_AUTO 0
+/* LJ_SCHED_STREAM: the FP64 pair-stream schedule.  Each warp walks a
+ * contiguous block of rows as one flat stream of list entries, queues the
+ * in-cutoff pairs in shared memory and evaluates the force 32 pairs at a
+ * time, so no lane idles on a margin pair or a row tail. */
+#define LJ_SCHED_STREAM 64
+
+const char *lj_status_string(int status);
+/* Text of the last CUDA error seen by this library in this thread. */
+const char *lj_last_cuda_error(void);
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int lj_version(void);
+/* Number of CUDA kernels this library has enqueued since it was loaded
+ * (all threads; memsets and copies are not counted).  For accounting. */
+unsigned long long lj_kernel_launch_count(void);
+
+/* ======================================================================== */
+/* Pair list (section "Verlet List and Bookkeeping Method"; Fig. "Data      */
+/* layout of a pair list"; the counting sort of section "Sorting by        */
+/* Indices").                                                               */
+/* ======================================================================== */
+
+/* Bytes of device workspace lj_build_pairlist needs for n atoms. */
+size_t lj_pairlist_workspace_bytes(int64_t n, const double box[3], double r_search);
+
+/*
+ * Build the sorted CSR Verlet list of every pair closer than r_search:
+ * all (i, j), j != i (j > i if half != 0), with minimum-image
+ * r^2 < r_search^2, where r^2 = (dx*dx + dy*dy) + dz*dz in round-to-nearest
+ * double arithmetic without fused multiply-adds (the list is bit-exact
+ * against that definition).  Atoms are binned into cells of side >= r_search
+ * (the linked-list cell method), candidates are screened in FP32 with a
+ * proven error bound and decided in FP64, and each row is sorted.
+ *
+ *  q4_dev        n x 4 doubles, positions in [0, L).
+ *  n             number of atoms (>= 0; n = 0 gives an empty list).
+ *  box           host, 3 box sides, each >= 2 r_search.
+ *  r_search      search length r_s = r_c + margin (> 0).
+ *  half          nonzero: half list (j > i); zero: full list.
+ *  row_ptr_dev   out, n + 1 int32.
+ *  col_dev       out, col_capacity int32.
+ *  col_capacity  entries available in col_dev.
+ *  workspace_dev scratch of lj_pairlist_workspace_bytes(n, box, r_search).
+ *  nnz_out       host out: number of list entries.  On LJ_ERR_CAPACITY it
+ *                holds the number needed (row_ptr_dev is then valid and
+ *                col_dev unspecified); retry with a larger col_dev.
+ *  max_row_out   host out (may be NULL): longest row.
+ *  stream        cudaStream_t.
+ * Blocks the calling thread until the list size is known (one small
+ * device-to-host copy), then enqueues the fill and returns.
+ * Errors: LJ_ERR_ARG, LJ_ERR_BOX, LJ_ERR_RANGE (a position outside [0, L) or
+ * not finite), LJ_ERR_CAPACITY (col_capacity too small, nnz >= 2^31, or a
+ * row longer than the 56,000 entries one warp's shared memory can sort),
+ * LJ_ERR_CUDA.
+ */
+int lj_build_pairlist(const double *q4_dev, int64_t n, const double box[3], double r_search,
+                      int half, int32_t *row_ptr_dev, int32_t *col_dev, int64_t col_capacity,
+                      void *workspace_dev, size_t workspace_bytes, int64_t *nnz_out,
+                      int64_t *max_row_out, void *stream);
+
+/* ======================================================================== */
+/* Force (Algorithm 1 inside Algorithm 3)                                    */
+/* ======================================================================== */
+
+/* Bytes of device workspace lj_force needs (0 for LJ_FP64). */
+size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
+
+/*
+ * One momentum update p += impulses(q) over the list, Algorithms 1 and 3:
+ * for each list entry (i, j) with minimum-image r^2 < r_cut^2,
+ *   df = (24 eps sigma^6 r^6 - 48 eps sigma^12) dt / r^14,
+ *   p_i += df d and, for a half list, p_j -= df d (d = q_j - q_i).
+ * A full list applies only the p_i part (the pair appears again in row j).
+ * Entries with r_cut <= r < r_search (the bookkeeping margin) contribute
+ * nothing.  p4_dev is updated in place and is never zeroed.
+ *
+ *  q4_dev, p4_dev   n x 4 doubles (positions in [0, L); momenta).
+ *  row_ptr_dev, col_dev, nnz, half   the list from lj_build_pairlist.
+ *  dt, r_cut        time step and cutoff (0 < r_cut <= L/2).
+ *  box              host, 3 box sides.
+ *  eps, sigma       Eq. (1) parameters (> 0).
+ *  precision        LJ_FP64 or LJ_MIXED.
+ *  tpi              LJ_TPI_AUTO, 1..32 (power of two) or LJ_SCHED_STREAM
+ *                   (FP64 half or full list).
+ *  workspace_dev    scratch of lj_force_workspace_bytes() (NULL if 0).
+ * Half lists add p_j with FP64 atomics, so their rounding order (not their
+ * value beyond the last bits) varies between calls; full lists are
+ * deterministic.  Asynchronous.  Errors: LJ_ERR_ARG, LJ_ERR_BOX,
+ * LJ_ERR_CAPACITY (workspace too small), LJ_ERR_CUDA.
+ */
+int lj_force(const double *q4_dev, double *p4_dev, int64_t n, const int32_t *row_ptr_dev,
+             const int32_t *col_dev, int64_t nnz, int half, double dt, double r_cut,
+             const double box[3], double eps, double sigma, int precision, int tpi,
+             void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/* ======================================================================== */
+/* Energy (Eq. 1, truncated at r_c, optionally shifted)                     */
+/* ======================================================================== */
+
+size_t lj_energy_workspace_bytes(int64_t n);
+
+/*
+ * E = sum over unique pairs with r < r_cut of V(r) - shifted * V(r_cut),
+ * V(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6] (Eq. 1; the shift is the
+ * paper's "adding a constant so that V(r_c) = 0").  With a full list only
+ * entries with j > i are summed.  FP64, deterministic (fixed-order block
+ * reduction).  e_out_dev: one device double, overwritten.  Asynchronous.
+ */
+int lj_energy(const double *q4_dev, int64_t n, const int32_t *row_ptr_dev,
+              const int32_t *col_dev, int64_t nnz, int half, double r_cut, const double box[3],
+              double eps, double sigma, int shifted, double *e_out_dev, void *workspace_dev,
+              size_t workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LJ_GB300_H */

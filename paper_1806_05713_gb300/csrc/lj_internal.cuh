@@ -1,0 +1,143 @@
+// lj_internal.cuh -- helpers shared by the CUDA translation units of the
+// library (never by the CPU oracle, which is an independent program).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lj_gb300.h"
+
+namespace lj {
+
+// Records a CUDA error for lj_last_cuda_error() (thread-local text).
+void record_cuda_error(cudaError_t err, const char *where);
+
+// Counts kernels this library has enqueued (reported by
+// lj_kernel_launch_count); every launch site passes through LJ_TRY_LAUNCH.
+void count_launch();
+
+#define LJ_TRY_CUDA(call)                                   \
+    do {                                                    \
+        cudaError_t lj_err_ = (call);                       \
+        if (lj_err_ != cudaSuccess) {                       \
+            ::lj::record_cuda_error(lj_err_, #call);        \
+            return LJ_ERR_CUDA;                             \
+        }                                                   \
+    } while (0)
+
+#define LJ_TRY_LAUNCH(where)                                \
+    do {                                                    \
+        ::lj::count_launch();                               \
+        cudaError_t lj_err_ = cudaGetLastError();           \
+        if (lj_err_ != cudaSuccess) {                       \
+            ::lj::record_cuda_error(lj_err_, where);        \
+            return LJ_ERR_CUDA;                             \
+        }                                                   \
+    } while (0)
+
+// Host-side check of the shared preconditions on the box and the lengths.
+int check_box(const double box[3], double r_search);
+
+// Workspace carving: successive 256-byte-aligned sub-buffers of one block.
+struct Carver {
+    char *base;
+    size_t used = 0;
+    explicit Carver(void *b) : base(static_cast<char *>(b)) {}
+    template <class T>
+    T *take(size_t count) {
+        used = (used + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + used) : nullptr;
+        used += count * sizeof(T);
+        return p;
+    }
+};
+
+inline int num_sms()
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 152;
+    }
+    return sms;
+}
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+// Position x, y, z of atom i from the AoS4 array (one 16-byte and one
+// 8-byte read-only load of the same 32-byte record).
+__device__ __forceinline__ void load_xyz(const double *__restrict__ q4, int64_t i, double &x,
+                                         double &y, double &z)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(q4 + 4 * i));
+    x = a.x;
+    y = a.y;
+    z = __ldg(q4 + 4 * i + 2);
+}
+
+// Minimum image of one displacement component, exactly as
+//   if (d > L/2) d -= L; else if (d < -L/2) d += L;
+// but with the two comparisons done on the IEEE bit pattern (|d| > L/2 iff
+// the magnitude bits compare greater), so no FP64 compare instruction is
+// issued; the subtraction or addition of L is the same rounded operation.
+__device__ __forceinline__ double min_image(double d, double L, long long half_bits)
+{
+    const long long b = __double_as_longlong(d);
+    if ((b & 0x7fffffffffffffffLL) > half_bits)
+        d = __dadd_rn(d, b < 0 ? L : -L);
+    return d;
+}
+
+// r2 < c2 for r2 >= 0 and c2 >= 0, on the bit patterns (integer compare).
+__device__ __forceinline__ bool less_nonneg(double r2, long long c2_bits)
+{
+    return __double_as_longlong(r2) < c2_bits;
+}
+
+// Reciprocal of a in double precision for 2^-126 <= a < 2^126: an FP32 seed
+// (the double truncated to FP32 by bit manipulation, then the hardware
+// approximate reciprocal, rcp.approx.ftz.f32, relative error ~2^-22), then
+// one third-order correction.  With e = 1 - a x0, 1/a = x0 / (1 - e)
+// = x0 (1 + e + e^2 + ...), so x1 = x0 + x0 (e + e^2) has relative error
+// ~e^3 < 2^-64 before rounding; the result is within two ulps of 1/a.
+// This is the "reciprocal approximation plus correction" the paper's
+// summary proposes for AVX-512 (vrcp14pd / vrcp28pd), built on GB300's FP32
+// special-function unit.  Outside that range it divides.
+__device__ __forceinline__ double rcp_fp64(double a)
+{
+    const int hi = __double2hiint(a);
+    if (hi < 0x38100000 || hi >= 0x47d00000)
+        return 1.0 / a;
+    const unsigned lo = static_cast<unsigned>(__double2loint(a));
+    const unsigned fb = (static_cast<unsigned>(hi - 0x38000000) << 3) | (lo >> 29);
+    float xf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(xf) : "f"(__uint_as_float(fb)));
+    const unsigned g = __float_as_uint(xf);
+    const double x0 = __hiloint2double(static_cast<int>((g >> 3) + 0x38000000u),
+                                       static_cast<int>(g << 29));
+    const double e = fma(-a, x0, 1.0);
+    return fma(x0, fma(e, e, e), x0);
+}
+
+// FP32 reciprocal: hardware approximation plus one Newton step
+// x1 = x0 + x0 (1 - a x0), relative error about one ulp.
+__device__ __forceinline__ float rcp_fp32(float a)
+{
+    float x;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(x) : "f"(a));
+    const float e = fmaf(-a, x, 1.0f);
+    return fmaf(x, e, x);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace lj

@@ -1,0 +1,448 @@
+// lj_pairlist.cu -- GPU construction of the sorted CSR Verlet list.
+//
+// Paper basis (Watanabe & Nakagawa, arXiv 1806.05713): section "Verlet List
+// and Bookkeeping Method" (register every pair closer than the search length
+// r_s > r_c; the linked-list cell method makes this O(N)) and section
+// "Sorting by Indices" (group the j of each i with a counting sort; Fig.
+// "Data layout of a pair list" (b), (c) is this CSR).
+//
+// GB300 design:
+//   1. bin:      one thread per atom -> cell id (cells of side >= r_s) and a
+//                slot inside the cell (atomic counter); validates q in [0, L).
+//   2. scan:     exclusive prefix sum of the cell counts -> cell_start.
+//   3. scatter:  atoms in cell order, with an FP32 copy {x, y, z, id} so that
+//                the candidate loops below stream 16-byte records.
+//   4. count:    one warp per row (rows taken in cell order, so neighbouring
+//                warps share their 27 neighbour cells in L1/L2); candidates
+//                are screened in FP32 against r_s^2 (1 +- delta) with a proven
+//                error bound delta, and only the rare candidates inside the
+//                band are decided by the exact FP64 definition.
+//   5. scan:     row counts -> row_ptr; total and longest row read back.
+//   6. fill:     the same walk compacts the j of the row into shared memory
+//                (ballot + popc), ranks them (all j are distinct) and writes
+//                the sorted row.
+// The result is bit-exact against the FP64 definition because every
+// decision is either certain from the FP32 bound or taken with the exact
+// IEEE operations (d = q_j - q_i, minimum image, (dx*dx + dy*dy) + dz*dz,
+// no fused multiply-add).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "lj_internal.cuh"
+#include "lj_scan.cuh"
+
+namespace lj {
+namespace {
+
+constexpr int kWarpsPerBlock = 8;
+constexpr int kMaxRowSmem = 56000;  // longest row one warp can sort in shared memory
+
+struct ListStats {
+    int64_t nnz;
+    int max_row;
+    int err;
+};
+
+struct Grid {
+    int nc[3];
+    int noff[3];
+    int off[3][3];
+    double L[3];
+    long long half_bits[3];
+    float Lf[3];
+    float hLf[3];
+    double inv_h[3];
+    long long rs2_bits;
+    float lo, hi;  // FP32 screening band around r_s^2
+    int ncell;
+};
+
+int cells_per_axis(double L, double rs)
+{
+    int nc = static_cast<int>(std::floor(L / rs));
+    while (nc > 1 && L / nc < rs * (1.0 + 1e-12)) --nc;
+    return nc < 1 ? 1 : nc;
+}
+
+Grid make_grid(int64_t n, const double box[3], double rs)
+{
+    Grid g{};
+    for (int a = 0; a < 3; ++a) g.nc[a] = cells_per_axis(box[a], rs);
+    // Larger cells stay correct (side >= r_s); cap the cell count near 2n.
+    const long long limit = 2 * static_cast<long long>(n) + 64;
+    while (static_cast<long long>(g.nc[0]) * g.nc[1] * g.nc[2] > limit) {
+        int a = 0;
+        if (g.nc[1] > g.nc[a]) a = 1;
+        if (g.nc[2] > g.nc[a]) a = 2;
+        if (g.nc[a] <= 1) break;
+        --g.nc[a];
+    }
+    double Lmax = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const int nc = g.nc[a];
+        if (nc == 1) {
+            g.noff[a] = 1;
+            g.off[a][0] = 0;
+        } else if (nc == 2) {
+            g.noff[a] = 2;
+            g.off[a][0] = 0;
+            g.off[a][1] = 1;
+        } else {
+            g.noff[a] = 3;
+            g.off[a][0] = -1;
+            g.off[a][1] = 0;
+            g.off[a][2] = 1;
+        }
+        g.L[a] = box[a];
+        const double h = 0.5 * box[a];
+        std::memcpy(&g.half_bits[a], &h, sizeof(double));
+        g.Lf[a] = static_cast<float>(box[a]);
+        g.hLf[a] = 0.5f * g.Lf[a];
+        g.inv_h[a] = nc / box[a];
+        Lmax = std::max(Lmax, box[a]);
+    }
+    g.ncell = g.nc[0] * g.nc[1] * g.nc[2];
+    const double rs2 = rs * rs;
+    std::memcpy(&g.rs2_bits, &rs2, sizeof(double));
+    // |r2_fp32 - r2| <= ~8.3e-7 (L/r_s) r_s^2 + rounding of the FP32 sum;
+    // take four times that.
+    const double delta = 4e-6 + 4e-6 * (Lmax / rs);
+    g.lo = std::nextafter(static_cast<float>(rs2 * (1.0 - delta)), 0.0f);
+    if (!(g.lo > 0.0f)) g.lo = 0.0f;
+    g.hi = std::nextafter(static_cast<float>(rs2 * (1.0 + delta)), INFINITY);
+    return g;
+}
+
+struct Work {
+    int *cell_of;
+    int *slot;
+    int *cell_count;
+    int *cell_start;
+    int *cell_atoms;
+    float4 *pos_f;
+    int *row_cnt;
+    ListStats *stats;
+    int64_t *scan_scratch;
+};
+
+Work carve(void *base, int64_t n, int ncell)
+{
+    Carver c(base);
+    Work w;
+    const size_t nn = static_cast<size_t>(n > 0 ? n : 1);
+    w.cell_of = c.take<int>(nn);
+    w.slot = c.take<int>(nn);
+    w.cell_count = c.take<int>(size_t(ncell) + 1);
+    w.cell_start = c.take<int>(size_t(ncell) + 1);
+    w.cell_atoms = c.take<int>(nn);
+    w.pos_f = c.take<float4>(nn);
+    w.row_cnt = c.take<int>(nn);
+    w.stats = c.take<ListStats>(1);
+    const size_t words = std::max(scan_scratch_words(n), scan_scratch_words(ncell));
+    w.scan_scratch = c.take<int64_t>(words);
+    return w;
+}
+
+size_t carve_bytes(int64_t n, int ncell)
+{
+    Carver c(nullptr);
+    const size_t nn = static_cast<size_t>(n > 0 ? n : 1);
+    c.take<int>(nn);
+    c.take<int>(nn);
+    c.take<int>(size_t(ncell) + 1);
+    c.take<int>(size_t(ncell) + 1);
+    c.take<int>(nn);
+    c.take<float4>(nn);
+    c.take<int>(nn);
+    c.take<ListStats>(1);
+    c.take<int64_t>(std::max(scan_scratch_words(n), scan_scratch_words(ncell)));
+    return c.used + 256;
+}
+
+__global__ void bin_kernel(const double *__restrict__ q4, int n, Grid g, int *__restrict__ cell_of,
+                           int *__restrict__ slot, int *__restrict__ cell_count,
+                           ListStats *__restrict__ stats)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x[3];
+    load_xyz(q4, i, x[0], x[1], x[2]);
+    int c[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ok = ok && (x[a] >= 0.0) && (x[a] < g.L[a]);  // false for NaN
+        int ca = static_cast<int>(x[a] * g.inv_h[a]);
+        ca = ca < 0 ? 0 : (ca >= g.nc[a] ? g.nc[a] - 1 : ca);
+        c[a] = ca;
+    }
+    if (!ok) atomicOr(&stats->err, 1);
+    const int id = (c[2] * g.nc[1] + c[1]) * g.nc[0] + c[0];
+    cell_of[i] = id;
+    slot[i] = atomicAdd(&cell_count[id], 1);
+}
+
+__global__ void scatter_kernel(const double *__restrict__ q4, int n, int ncell,
+                               const int *__restrict__ cell_of, const int *__restrict__ slot,
+                               int *__restrict__ cell_start, int *__restrict__ cell_atoms,
+                               float4 *__restrict__ pos_f)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) cell_start[ncell] = n;
+    if (i >= n) return;
+    const int k = cell_start[cell_of[i]] + slot[i];
+    double x, y, z;
+    load_xyz(q4, i, x, y, z);
+    cell_atoms[k] = i;
+    pos_f[k] = make_float4(static_cast<float>(x), static_cast<float>(y), static_cast<float>(z),
+                           __int_as_float(i));
+}
+
+// Exact FP64 decision, identical operations to the definition.
+__device__ __forceinline__ bool exact_within(const double *__restrict__ q4, int j, double xi,
+                                             double yi, double zi, const Grid &g)
+{
+    double xj, yj, zj;
+    load_xyz(q4, j, xj, yj, zj);
+    const double dx = min_image(__dsub_rn(xj, xi), g.L[0], g.half_bits[0]);
+    const double dy = min_image(__dsub_rn(yj, yi), g.L[1], g.half_bits[1]);
+    const double dz = min_image(__dsub_rn(zj, zi), g.L[2], g.half_bits[2]);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return less_nonneg(r2, g.rs2_bits);
+}
+
+// Walks every candidate j of row i (the atoms of the distinct neighbour
+// cells), calling visit(in_mask) once per 32 candidates with the warp's
+// ballot of accepted j (and each lane's j in `jout`).
+template <bool HALF, class Visit>
+__device__ __forceinline__ void walk_row(const double *__restrict__ q4, const Grid &g,
+                                         const int *__restrict__ cell_start,
+                                         const float4 *__restrict__ pos_f, int i, float4 pi,
+                                         int cell_i, Visit visit)
+{
+    const int lane = threadIdx.x & 31;
+    const int cx = cell_i % g.nc[0];
+    const int cy = (cell_i / g.nc[0]) % g.nc[1];
+    const int cz = cell_i / (g.nc[0] * g.nc[1]);
+    bool have_exact = false;
+    double xi = 0.0, yi = 0.0, zi = 0.0;
+    for (int oz = 0; oz < g.noff[2]; ++oz) {
+        int nz = cz + g.off[2][oz];
+        nz = nz < 0 ? nz + g.nc[2] : (nz >= g.nc[2] ? nz - g.nc[2] : nz);
+        for (int oy = 0; oy < g.noff[1]; ++oy) {
+            int ny = cy + g.off[1][oy];
+            ny = ny < 0 ? ny + g.nc[1] : (ny >= g.nc[1] ? ny - g.nc[1] : ny);
+            for (int ox = 0; ox < g.noff[0]; ++ox) {
+                int nx = cx + g.off[0][ox];
+                nx = nx < 0 ? nx + g.nc[0] : (nx >= g.nc[0] ? nx - g.nc[0] : nx);
+                const int cell = (nz * g.nc[1] + ny) * g.nc[0] + nx;
+                const int s = cell_start[cell], e = cell_start[cell + 1];
+                for (int base = s; base < e; base += 32) {
+                    const int k = base + lane;
+                    bool in = false;
+                    int j = -1;
+                    if (k < e) {
+                        const float4 pj = pos_f[k];
+                        j = __float_as_int(pj.w);
+                        if (HALF ? (j > i) : (j != i)) {
+                            float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                            if (fabsf(dx) > g.hLf[0]) dx -= copysignf(g.Lf[0], dx);
+                            if (fabsf(dy) > g.hLf[1]) dy -= copysignf(g.Lf[1], dy);
+                            if (fabsf(dz) > g.hLf[2]) dz -= copysignf(g.Lf[2], dz);
+                            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                            if (r2 < g.lo) {
+                                in = true;
+                            } else if (r2 < g.hi) {
+                                if (!have_exact) {
+                                    load_xyz(q4, i, xi, yi, zi);
+                                    have_exact = true;
+                                }
+                                in = exact_within(q4, j, xi, yi, zi, g);
+                            }
+                        }
+                    }
+                    visit(__ballot_sync(0xffffffffu, in), in, j);
+                }
+            }
+        }
+    }
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+count_kernel(const double *__restrict__ q4, int n, Grid g, const int *__restrict__ cell_of,
+             const int *__restrict__ cell_start, const int *__restrict__ cell_atoms,
+             const float4 *__restrict__ pos_f, int *__restrict__ row_cnt,
+             ListStats *__restrict__ stats)
+{
+    const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (w >= n) return;
+    const int i = cell_atoms[w];
+    const float4 pi = pos_f[w];
+    int cnt = 0;
+    walk_row<HALF>(q4, g, cell_start, pos_f, i, pi, cell_of[i],
+                   [&](unsigned mask, bool, int) { cnt += __popc(mask); });
+    if ((threadIdx.x & 31) == 0) {
+        row_cnt[i] = cnt;
+        atomicMax(&stats->max_row, cnt);
+    }
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+fill_kernel(const double *__restrict__ q4, int n, Grid g, const int *__restrict__ cell_of,
+            const int *__restrict__ cell_start, const int *__restrict__ cell_atoms,
+            const float4 *__restrict__ pos_f, const int *__restrict__ row_ptr,
+            int *__restrict__ col, int cap, int warps_per_block, ListStats *__restrict__ stats)
+{
+    extern __shared__ int smem[];
+    const int wib = threadIdx.x >> 5;
+    const int w = blockIdx.x * warps_per_block + wib;
+    if (w >= n) return;
+    const int lane = threadIdx.x & 31;
+    int *buf = smem + size_t(wib) * cap;
+    const int i = cell_atoms[w];
+    const float4 pi = pos_f[w];
+    int cnt = 0;
+    walk_row<HALF>(q4, g, cell_start, pos_f, i, pi, cell_of[i],
+                   [&](unsigned mask, bool in, int j) {
+                       const int pos = cnt + __popc(mask & lanemask_lt());
+                       if (in && pos < cap) buf[pos] = j;
+                       cnt += __popc(mask);
+                   });
+    __syncwarp();
+    const int start = row_ptr[i];
+    const int len = row_ptr[i + 1] - start;
+    if (cnt != len || cnt > cap) {
+        if (lane == 0) atomicOr(&stats->err, 2);
+        return;
+    }
+    // Rank sort: the j of a row are distinct, so rank(v) = #{m : buf[m] < v}.
+    for (int e = lane; e < cnt; e += 32) {
+        const int v = buf[e];
+        int r = 0;
+        int m = 0;
+        for (; m + 4 <= cnt; m += 4)
+            r += (buf[m] < v) + (buf[m + 1] < v) + (buf[m + 2] < v) + (buf[m + 3] < v);
+        for (; m < cnt; ++m) r += buf[m] < v;
+        col[start + r] = v;
+    }
+}
+
+}  // namespace
+
+int build_pairlist_impl(const double *q4, int64_t n, const double box[3], double rs, int half,
+                        int32_t *row_ptr, int32_t *col, int64_t cap, void *ws, size_t ws_bytes,
+                        int64_t *nnz_out, int64_t *max_row_out, cudaStream_t st)
+{
+    if (nnz_out) *nnz_out = 0;
+    if (max_row_out) *max_row_out = 0;
+    if (!box || !row_ptr || !nnz_out || n < 0 || !(rs > 0.0) || !std::isfinite(rs) || cap < 0)
+        return LJ_ERR_ARG;
+    if (n > 0 && (!q4 || !ws)) return LJ_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(q4) & 31u) || (reinterpret_cast<uintptr_t>(ws) & 255u))
+        return LJ_ERR_ARG;
+    if (n >= (int64_t(1) << 31) - 1) return LJ_ERR_CAPACITY;
+    int rc = check_box(box, rs);
+    if (rc != LJ_OK) return rc;
+    if (n == 0) {
+        LJ_TRY_CUDA(cudaMemsetAsync(row_ptr, 0, sizeof(int32_t), st));
+        return LJ_OK;
+    }
+    const Grid g = make_grid(n, box, rs);
+    if (ws_bytes < carve_bytes(n, g.ncell)) return LJ_ERR_CAPACITY;
+    const Work w = carve(ws, n, g.ncell);
+    const int ni = static_cast<int>(n);
+
+    LJ_TRY_CUDA(cudaMemsetAsync(w.cell_count, 0, sizeof(int) * (size_t(g.ncell) + 1), st));
+    LJ_TRY_CUDA(cudaMemsetAsync(w.stats, 0, sizeof(ListStats), st));
+    const unsigned gb = unsigned((n + 255) / 256);
+    bin_kernel<<<gb, 256, 0, st>>>(q4, ni, g, w.cell_of, w.slot, w.cell_count, w.stats);
+    LJ_TRY_LAUNCH("bin_kernel");
+    rc = scan_exclusive<int, int>(w.cell_count, w.cell_start, g.ncell, &w.stats->nnz,
+                                  w.scan_scratch, st);
+    if (rc != LJ_OK) return rc;
+    scatter_kernel<<<gb, 256, 0, st>>>(q4, ni, g.ncell, w.cell_of, w.slot, w.cell_start,
+                                       w.cell_atoms, w.pos_f);
+    LJ_TRY_LAUNCH("scatter_kernel");
+    const unsigned gw = unsigned((n + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    if (half)
+        count_kernel<true><<<gw, kWarpsPerBlock * 32, 0, st>>>(q4, ni, g, w.cell_of, w.cell_start,
+                                                               w.cell_atoms, w.pos_f, w.row_cnt,
+                                                               w.stats);
+    else
+        count_kernel<false><<<gw, kWarpsPerBlock * 32, 0, st>>>(q4, ni, g, w.cell_of, w.cell_start,
+                                                                w.cell_atoms, w.pos_f, w.row_cnt,
+                                                                w.stats);
+    LJ_TRY_LAUNCH("count_kernel");
+    rc = scan_exclusive<int, int32_t>(w.row_cnt, row_ptr, n, &w.stats->nnz, w.scan_scratch, st);
+    if (rc != LJ_OK) return rc;
+    ListStats hs{};
+    LJ_TRY_CUDA(cudaMemcpyAsync(&hs, w.stats, sizeof(ListStats), cudaMemcpyDeviceToHost, st));
+    LJ_TRY_CUDA(cudaStreamSynchronize(st));
+    if (hs.err & 1) return LJ_ERR_RANGE;
+    *nnz_out = hs.nnz;
+    if (max_row_out) *max_row_out = hs.max_row;
+    if (hs.nnz >= (int64_t(1) << 31) - 1) return LJ_ERR_CAPACITY;
+    // row_ptr[n] = nnz (the scan writes only the first n entries).
+    const int32_t total32 = static_cast<int32_t>(hs.nnz);
+    LJ_TRY_CUDA(cudaMemcpyAsync(row_ptr + n, &total32, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (hs.nnz > cap || hs.max_row > kMaxRowSmem) {
+        LJ_TRY_CUDA(cudaStreamSynchronize(st));
+        return LJ_ERR_CAPACITY;
+    }
+    if (hs.nnz == 0) {
+        LJ_TRY_CUDA(cudaStreamSynchronize(st));
+        return LJ_OK;
+    }
+    const int cap_row = std::max(1, hs.max_row);
+    int wpb = kWarpsPerBlock;
+    while (wpb > 1 && size_t(wpb) * cap_row * sizeof(int) > 200 * 1024) wpb >>= 1;
+    const size_t smem = size_t(wpb) * cap_row * sizeof(int);
+    const unsigned gf = unsigned((n + wpb - 1) / wpb);
+    if (half) {
+        if (smem > 48 * 1024)
+            LJ_TRY_CUDA(cudaFuncSetAttribute(fill_kernel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        fill_kernel<true><<<gf, wpb * 32, smem, st>>>(q4, ni, g, w.cell_of, w.cell_start,
+                                                       w.cell_atoms, w.pos_f, row_ptr, col, cap_row,
+                                                       wpb, w.stats);
+    } else {
+        if (smem > 48 * 1024)
+            LJ_TRY_CUDA(cudaFuncSetAttribute(fill_kernel<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        fill_kernel<false><<<gf, wpb * 32, smem, st>>>(q4, ni, g, w.cell_of, w.cell_start,
+                                                        w.cell_atoms, w.pos_f, row_ptr, col, cap_row,
+                                                        wpb, w.stats);
+    }
+    LJ_TRY_LAUNCH("fill_kernel");
+    // The copy of the host-stack total above must finish before returning.
+    LJ_TRY_CUDA(cudaStreamSynchronize(st));
+    return LJ_OK;
+}
+
+size_t pairlist_workspace_bytes_impl(int64_t n, const double box[3], double rs)
+{
+    if (n < 0 || !box || !(rs > 0.0)) return 0;
+    if (check_box(box, rs) != LJ_OK) return 256;
+    const Grid g = make_grid(n, box, rs);
+    return carve_bytes(n, g.ncell);
+}
+
+}  // namespace lj
+
+extern "C" size_t lj_pairlist_workspace_bytes(int64_t n, const double box[3], double r_search)
+{
+    return lj::pairlist_workspace_bytes_impl(n, box, r_search);
+}
+
+extern "C" int lj_build_pairlist(const double *q4_dev, int64_t n, const double box[3],
+                                 double r_search, int half, int32_t *row_ptr_dev, int32_t *col_dev,
+                                 int64_t col_capacity, void *workspace_dev, size_t workspace_bytes,
+                                 int64_t *nnz_out, int64_t *max_row_out, void *stream)
+{
+    return lj::build_pairlist_impl(q4_dev, n, box, r_search, half, row_ptr_dev, col_dev,
+                                   col_capacity, workspace_dev, workspace_bytes, nnz_out,
+                                   max_row_out, static_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,256 @@
+"""Thin Python binding of the C ABI in ``include/lj_gb300.h``.
+
+Each function has the name of the C entry point it calls and only
+marshals arguments: torch CUDA tensors provide device memory and the
+current CUDA stream; every step of the computation runs in the library's
+kernels.  The library is loaded from the package's ``_build`` folder; if it
+is missing or no CUDA device is present the functions raise -- there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+LJ_OK = 0
+LJ_ERR_ARG = 1
+LJ_ERR_BOX = 2
+LJ_ERR_RANGE = 3
+LJ_ERR_CAPACITY = 4
+LJ_ERR_CUDA = 5
+LJ_ERR_DEVICE = 6
+
+LJ_FP64 = 0
+LJ_MIXED = 1
+LJ_TPI_AUTO = 0
+LJ_SCHED_STREAM = 64
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liblj_gb300.so")
+_lib = None
+
+_i64, _dbl, _int, _vp, _sz = ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+_dbl3 = ctypes.c_double * 3
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+# (name, restype, argtypes) of every exported entry point.
+SIGNATURES = {
+    "lj_status_string": (ctypes.c_char_p, [_int]),
+    "lj_last_cuda_error": (ctypes.c_char_p, []),
+    "lj_version": (_int, []),
+    "lj_kernel_launch_count": (ctypes.c_ulonglong, []),
+    "lj_pairlist_workspace_bytes": (_sz, [_i64, _dbl3, _dbl]),
+    "lj_build_pairlist": (_int, [_vp, _i64, _dbl3, _dbl, _int, _vp, _vp, _i64, _vp, _sz, _i64p,
+                                 _i64p, _vp]),
+    "lj_force_workspace_bytes": (_sz, [_i64, _dbl3, _int]),
+    "lj_force": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl, _dbl3, _dbl, _dbl, _int,
+                        _int, _vp, _sz, _vp]),
+    "lj_energy_workspace_bytes": (_sz, [_i64]),
+    "lj_energy": (_int, [_vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl3, _dbl, _dbl, _int, _vp, _vp,
+                         _sz, _vp]),
+}
+
+
+class LJError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = _lib
+        msg = lib.lj_status_string(status).decode() if lib else f"status {status}"
+        if status == LJ_ERR_CUDA and lib:
+            msg += " -- " + lib.lj_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"CUDA library not built ({_LIB_PATH} missing); "
+                           "run paper_1806_05713_gb300.build.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != LJ_OK:
+        raise LJError(status, where)
+
+
+def _box3(box) -> ctypes.Array:
+    b = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
+    return _dbl3(*[float(x) for x in b])
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str, shape=None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous {dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+@dataclass
+class PairList:
+    """CSR Verlet list on the device (row_ptr int32[n+1], col int32[nnz]).
+
+    ``workspace`` is the builder's scratch, kept so that a rebuild can reuse
+    every buffer (pass the list as ``reuse=``)."""
+    row_ptr: torch.Tensor
+    col: torch.Tensor
+    n: int
+    nnz: int
+    half: bool
+    r_search: float
+    max_row: int
+    workspace: torch.Tensor | None = None
+
+    @property
+    def col_view(self) -> torch.Tensor:
+        return self.col[: self.nnz]
+
+
+def lj_pairlist_workspace_bytes(n: int, box, r_search: float) -> int:
+    return int(load().lj_pairlist_workspace_bytes(int(n), _box3(box), float(r_search)))
+
+
+def lj_build_pairlist(q4: torch.Tensor, box, r_search: float, half: bool = True,
+                      col_capacity: int | None = None, stream=None,
+                      reuse: PairList | None = None) -> PairList:
+    """Build the sorted CSR list.  Buffers of ``reuse`` are used when large
+    enough; a too-small column buffer is regrown to the reported size and
+    the build retried once."""
+    lib = load()
+    n = int(q4.shape[0]) if q4.dim() == 2 else 0
+    qp = _dev(q4, torch.float64, "q4", (n, 4))
+    dev = q4.device
+    bx = _box3(box)
+    wsb = int(lib.lj_pairlist_workspace_bytes(n, bx, float(r_search)))
+    if reuse is not None and reuse.row_ptr.numel() == n + 1:
+        row_ptr = reuse.row_ptr
+    else:
+        row_ptr = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    if reuse is not None and reuse.workspace is not None and reuse.workspace.numel() >= wsb:
+        ws = reuse.workspace
+    else:
+        ws = _workspace(wsb, dev)
+    if col_capacity is None:
+        col_capacity = max(1, (90 if half else 180) * n)
+    col = reuse.col if reuse is not None else None
+    for _ in range(2):
+        if col is None or col.numel() < col_capacity:
+            col = torch.empty(max(1, int(col_capacity)), dtype=torch.int32, device=dev)
+        nnz = ctypes.c_int64(0)
+        mrow = ctypes.c_int64(0)
+        st = lib.lj_build_pairlist(qp, n, bx, float(r_search), int(bool(half)),
+                                   row_ptr.data_ptr(), col.data_ptr(), int(col.numel()),
+                                   ws.data_ptr(), ws.numel(), ctypes.byref(nnz), ctypes.byref(mrow),
+                                   _stream(stream))
+        if st == LJ_ERR_CAPACITY and nnz.value > col.numel():
+            col_capacity = nnz.value
+            col = None
+            continue
+        _check(st, "lj_build_pairlist")
+        return PairList(row_ptr, col, n, int(nnz.value), bool(half), float(r_search),
+                        int(mrow.value), ws)
+    raise LJError(LJ_ERR_CAPACITY, "lj_build_pairlist")
+
+
+def lj_force_workspace_bytes(n: int, box, precision: int = LJ_FP64) -> int:
+    return int(load().lj_force_workspace_bytes(int(n), _box3(box), int(precision)))
+
+
+def lj_force(q4: torch.Tensor, p4: torch.Tensor, plist: PairList, dt: float, r_cut: float, box,
+             eps: float = 1.0, sigma: float = 1.0, precision: int = LJ_FP64, tpi: int = LJ_TPI_AUTO,
+             workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """p4 += impulses (in place); returns p4."""
+    lib = load()
+    n = plist.n
+    qp = _dev(q4, torch.float64, "q4", (n, 4))
+    pp = _dev(p4, torch.float64, "p4", (n, 4))
+    need = lib.lj_force_workspace_bytes(n, _box3(box), int(precision))
+    if workspace is None and need > 0:
+        workspace = _workspace(need, q4.device)
+    wsp = workspace.data_ptr() if workspace is not None else None
+    wsb = workspace.numel() if workspace is not None else 0
+    st = lib.lj_force(qp, pp, n, plist.row_ptr.data_ptr(), plist.col.data_ptr(), plist.nnz,
+                      int(plist.half), float(dt), float(r_cut), _box3(box), float(eps),
+                      float(sigma), int(precision), int(tpi), wsp, wsb, _stream(stream))
+    _check(st, "lj_force")
+    return p4
+
+
+def lj_force_prepared(q4: torch.Tensor, p4: torch.Tensor, plist: PairList, dt: float,
+                      r_cut: float, box, eps: float = 1.0, sigma: float = 1.0,
+                      precision: int = LJ_FP64, tpi: int = LJ_TPI_AUTO,
+                      workspace: torch.Tensor | None = None, stream=None):
+    """lj_force with its arguments marshalled once; returns a no-argument
+    callable that enqueues the same call again (for tight loops)."""
+    lib = load()
+    n = plist.n
+    qp = _dev(q4, torch.float64, "q4", (n, 4))
+    pp = _dev(p4, torch.float64, "p4", (n, 4))
+    need = lib.lj_force_workspace_bytes(n, _box3(box), int(precision))
+    if workspace is None and need > 0:
+        workspace = _workspace(need, q4.device)
+    args = (qp, pp, n, plist.row_ptr.data_ptr(), plist.col.data_ptr(), plist.nnz,
+            int(plist.half), float(dt), float(r_cut), _box3(box), float(eps), float(sigma),
+            int(precision), int(tpi), workspace.data_ptr() if workspace is not None else None,
+            workspace.numel() if workspace is not None else 0, _stream(stream))
+    keep = (q4, p4, plist, workspace)
+    fn = lib.lj_force
+
+    def call():
+        st = fn(*args)
+        if st != LJ_OK:
+            raise LJError(st, "lj_force")
+        return keep[1]
+    return call
+
+
+def lj_energy_workspace_bytes(n: int) -> int:
+    return int(load().lj_energy_workspace_bytes(int(n)))
+
+
+def lj_energy(q4: torch.Tensor, plist: PairList, r_cut: float, box, eps: float = 1.0,
+              sigma: float = 1.0, shifted: bool = False, out: torch.Tensor | None = None,
+              workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Potential energy into a 1-element device tensor (returned)."""
+    lib = load()
+    n = plist.n
+    qp = _dev(q4, torch.float64, "q4", (n, 4))
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=q4.device)
+    if workspace is None:
+        workspace = _workspace(lib.lj_energy_workspace_bytes(n), q4.device)
+    st = lib.lj_energy(qp, n, plist.row_ptr.data_ptr(), plist.col.data_ptr(), plist.nnz,
+                       int(plist.half), float(r_cut), _box3(box), float(eps), float(sigma),
+                       int(bool(shifted)), _dev(out, torch.float64, "out"), workspace.data_ptr(),
+                       workspace.numel(), _stream(stream))
+    _check(st, "lj_energy")
+    return out

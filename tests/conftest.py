@@ -18,3 +18,23 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def cuda_lib():
+    """The built CUDA library and its binding (GPU tests only)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test selected but no CUDA device is visible")
+    from paper_1806_05713_gb300 import build, lj
+    build.build()
+    lj.load()
+    return lj
+
+
+def to_dev(a, dtype=None):
+    import torch
+    t = torch.from_numpy(a)
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda().contiguous()

@@ -1,0 +1,121 @@
+"""The C-ABI library builds, loads and exports every entry point its header
+declares; host-side argument checks return the documented status codes.
+No test here launches GPU work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1806_05713_gb300 import build as lj_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(lj_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = lj_build.build()
+    return ctypes.CDLL(path), path
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("lj_build_pairlist", "lj_force", "lj_energy", "lj_status_string"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    cdll, path = lib
+    for name in sorted(_declared()):
+        assert hasattr(cdll, name), f"{name} declared in include/ but not exported by {path}"
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1806_05713_gb300 import lj
+    assert _declared() == set(lj.SIGNATURES)
+
+
+def test_status_strings_and_version():
+    from paper_1806_05713_gb300 import lj
+    L = lj.load()
+    assert L.lj_version() >= 10000
+    for code in range(7):
+        assert L.lj_status_string(code).decode().startswith("LJ_")
+    assert b"unknown" in L.lj_status_string(99)
+
+
+def test_host_argument_checks_without_gpu():
+    from paper_1806_05713_gb300 import lj
+    L = lj.load()
+    box = lj._box3([10.0, 10.0, 10.0])
+    nnz, mrow = ctypes.c_int64(), ctypes.c_int64()
+    # n < 0
+    assert L.lj_build_pairlist(None, -1, box, 3.3, 1, None, None, 0, None, 0, ctypes.byref(nnz),
+                               ctypes.byref(mrow), None) == lj.LJ_ERR_ARG
+    # box shorter than 2 r_s
+    assert L.lj_build_pairlist(None, 0, lj._box3([6.0, 10, 10]), 3.3, 1, ctypes.c_void_p(16),
+                               None, 0, None, 0, ctypes.byref(nnz), ctypes.byref(mrow),
+                               None) == lj.LJ_ERR_BOX
+    # non-finite search length
+    assert L.lj_build_pairlist(None, 0, box, float("nan"), 1, ctypes.c_void_p(16), None, 0, None,
+                               0, ctypes.byref(nnz), ctypes.byref(mrow), None) == lj.LJ_ERR_ARG
+    # force: bad precision, bad cutoff, box too small, bad eps
+    fake = ctypes.c_void_p(256)
+    args = lambda **k: dict(dict(q=fake, p=fake, n=10, rp=fake, col=fake, nnz=10, half=1, dt=0.01,
+                                 rc=3.0, box=box, eps=1.0, sig=1.0, prec=0, tpi=0), **k)
+
+    def force(**k):
+        a = args(**k)
+        return L.lj_force(a["q"], a["p"], a["n"], a["rp"], a["col"], a["nnz"], a["half"], a["dt"],
+                          a["rc"], a["box"], a["eps"], a["sig"], a["prec"], a["tpi"], None, 0, None)
+    assert force(prec=7) == lj.LJ_ERR_ARG
+    assert force(rc=-1.0) == lj.LJ_ERR_ARG
+    assert force(rc=6.0) == lj.LJ_ERR_BOX
+    assert force(eps=0.0) == lj.LJ_ERR_ARG
+    assert force(q=None) == lj.LJ_ERR_ARG
+    assert force(tpi=3) == lj.LJ_ERR_ARG
+    assert force(prec=1, tpi=lj.LJ_SCHED_STREAM) == lj.LJ_ERR_ARG
+    # mixed precision without its workspace
+    assert force(prec=1, tpi=8) == lj.LJ_ERR_CAPACITY
+    # empty work is a no-op that succeeds
+    assert force(n=0, nnz=0) == lj.LJ_OK
+
+
+def test_workspace_sizes_are_sane():
+    from paper_1806_05713_gb300 import lj
+    L = lj.load()
+    b = lj._box3([49.2, 49.2, 49.2])
+    w1 = L.lj_pairlist_workspace_bytes(119164, b, 3.3)
+    assert 119164 * 32 <= w1 < 119164 * 200
+    assert L.lj_force_workspace_bytes(1000, b, 0) == 0
+    assert L.lj_force_workspace_bytes(1000, b, 1) >= 16000
+    assert L.lj_energy_workspace_bytes(1000) >= 8
+
+
+def test_product_path_has_no_cpu_fallback(monkeypatch):
+    """Without the built library the binding raises instead of computing."""
+    from paper_1806_05713_gb300 import lj
+    monkeypatch.setattr(lj, "_lib", None)
+    monkeypatch.setattr(lj, "_LIB_PATH", "/nonexistent/liblj_gb300.so")
+    with pytest.raises(RuntimeError, match="not built"):
+        lj.load()
+
+
+def test_package_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_1806_05713_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
+                assert "lj_oracle" not in text, f

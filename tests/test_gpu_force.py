@@ -1,0 +1,160 @@
+"""GPU force kernels vs the oracle (Algorithm 3 with Algorithm 1).
+
+FP64: every schedule, half and full lists, within 1e-12 of max|dp|.
+MIXED: within the stated error bound (max |dp error| <= 1e-5 max|dp|, RMS <= 2.5e-6)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1806_05713_gb300 import inputs
+from conftest import to_dev
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-5
+SCHEDULES = [1, 2, 4, 8, 16, 32, 64]   # 64 = LJ_SCHED_STREAM
+
+
+def _run(lj, s, half, precision, tpi, dt=0.01, eps=1.0, sigma=1.0, p0=None, rc=None, pl=None):
+    rc = s.rc if rc is None else rc
+    q = to_dev(s.q)
+    if pl is None:
+        pl = lj.lj_build_pairlist(q, s.box, s.rs, half)
+    p = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda") if p0 is None else to_dev(p0)
+    lj.lj_force(q, p, pl, dt, rc, s.box, eps, sigma, precision, tpi)
+    torch.cuda.synchronize()
+    return p.cpu().numpy()[:, :3], pl
+
+
+def _oracle(oracle_lib, s, half, dt=0.01, eps=1.0, sigma=1.0, p0=None, rc=None):
+    rc = s.rc if rc is None else rc
+    rp, col = oracle_lib.pairlist(s.q, s.box, s.rs, half)
+    p = np.zeros((s.n, 3)) if p0 is None else p0[:, :3]
+    return oracle_lib.force(s.q, p, rp, col, half, dt, rc, s.box, eps, sigma)
+
+
+def _relerr(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+@pytest.fixture(scope="module")
+def small():
+    return inputs.workload_small()
+
+
+@pytest.mark.parametrize("tpi", SCHEDULES)
+@pytest.mark.parametrize("half", [True, False])
+def test_fp64_small_all_schedules(cuda_lib, oracle_lib, small, tpi, half):
+    got, _ = _run(cuda_lib, small, half, cuda_lib.LJ_FP64, tpi)
+    want = _oracle(oracle_lib, small, half)
+    assert _relerr(got, want) <= FP64_TOL
+
+
+@pytest.mark.parametrize("tpi", [1, 4, 8, 32])
+@pytest.mark.parametrize("half", [True, False])
+def test_mixed_small(cuda_lib, oracle_lib, small, tpi, half):
+    got, _ = _run(cuda_lib, small, half, cuda_lib.LJ_MIXED, tpi)
+    want = _oracle(oracle_lib, small, half)
+    assert _relerr(got, want) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+def test_eps_sigma_dt_and_existing_momenta(cuda_lib, oracle_lib, precision, tol):
+    s = inputs.fcc_system(8, 0.9, 0.05, seed=3)
+    p0 = np.random.default_rng(2).normal(size=(s.n, 4))
+    kw = dict(dt=0.005, eps=1.3, sigma=1.1, rc=3.0)
+    for half in (True, False):
+        for tpi in ((64, 8) if precision == 0 else (8,)):
+            got, _ = _run(cuda_lib, s, half, precision, tpi, p0=p0, **kw)
+            want = _oracle(oracle_lib, s, half, p0=p0, **kw)
+            assert _relerr(got - p0[:, :3], want - p0[:, :3]) <= tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_two_body_closed_form(cuda_lib, precision):
+    """r = 1: dp = -+ 24 dt along d; r = 2^(1/6): dp ~ 0 (Algorithm 1)."""
+    lj = cuda_lib
+    dt = 0.01
+    for r, want in [(1.0, 24 * dt), (2.0 ** (1 / 6), 0.0)]:
+        q = np.zeros((2, 4))
+        q[:, :3] = 5.0
+        q[1, 0] += r
+        s = inputs.LJSystem(q=q, box=np.array([20.0] * 3), rho=0.0)
+        for half in (True, False):
+            for tpi in (1, 32) + ((64,) if precision == 0 else ()):
+                got, _ = _run(lj, s, half, precision, tpi, dt=dt)
+                tol = 1e-15 if precision == 0 else 1e-6
+                assert abs(got[1, 0] - want) <= tol * 24 * dt + 1e-14 * 48 * dt
+                assert abs(got[0, 0] + want) <= tol * 24 * dt + 1e-14 * 48 * dt
+                assert np.all(got[:, 1:] == 0.0)
+
+
+def test_wrap_across_boundary(cuda_lib):
+    lj = cuda_lib
+    q = np.zeros((2, 4))
+    q[0, :3] = [0.3, 5.0, 5.0]
+    q[1, :3] = [9.3, 5.0, 5.0]
+    s = inputs.LJSystem(q=q, box=np.array([10.0] * 3), rho=0.0)
+    for precision in (0, 1):
+        for half in (True, False):
+            got, _ = _run(lj, s, half, precision, 8)
+            assert abs(got[0, 0] - 0.24) < 1e-6 and abs(got[1, 0] + 0.24) < 1e-6
+
+
+def test_small_box_mixed_image_choice(cuda_lib, oracle_lib):
+    """L = 6.8 (2-3 cells): the mixed form picks the minimum image."""
+    s = inputs.fcc_system(4, 0.8, 0.1, seed=9)   # L = 6.84
+    s.rc, s.margin = 3.0, 0.3
+    for half in (True, False):
+        got, _ = _run(cuda_lib, s, half, 1, 8)
+        want = _oracle(oracle_lib, s, half)
+        assert _relerr(got, want) <= MIXED_TOL
+
+
+def test_newton_third_law_half_list(cuda_lib, small):
+    got, _ = _run(cuda_lib, small, True, 0, 64)
+    assert np.max(np.abs(got.sum(axis=0))) < 1e-12 * np.abs(got).sum()
+
+
+def test_pad_column_untouched(cuda_lib, small):
+    lj = cuda_lib
+    q = to_dev(small.q)
+    pl = lj.lj_build_pairlist(q, small.box, small.rs, True)
+    p = torch.full((small.n, 4), 7.0, dtype=torch.float64, device="cuda")
+    for prec, tpi in ((0, 64), (0, 8), (1, 8)):
+        lj.lj_force(q, p, pl, 0.01, 3.0, small.box, precision=prec, tpi=tpi)
+    torch.cuda.synchronize()
+    assert torch.all(p[:, 3] == 7.0)
+
+
+@pytest.mark.parametrize("order", ["random", "cell"])
+@pytest.mark.parametrize("half", [True, False])
+def test_fp64_paper_size(cuda_lib, oracle_lib, order, half):
+    """N = 119,164, both orderings and list kinds, the bench schedules."""
+    s = inputs.workload_paper(order=order)
+    want = _oracle(oracle_lib, s, half)
+    pl = None
+    for tpi in (64, 8, 32):
+        got, pl = _run(cuda_lib, s, half, 0, tpi, pl=pl)
+        assert _relerr(got, want) <= FP64_TOL, tpi
+
+
+@pytest.mark.parametrize("half", [True, False])
+def test_mixed_paper_size(cuda_lib, oracle_lib, half):
+    s = inputs.workload_paper(order="cell")
+    want = _oracle(oracle_lib, s, half)
+    got, _ = _run(cuda_lib, s, half, 1, 8)
+    err = got - want
+    assert np.max(np.abs(err)) / np.max(np.abs(want)) <= MIXED_TOL
+    assert np.sqrt(np.mean(err ** 2)) / np.sqrt(np.mean(want ** 2)) <= 2.5e-6
+
+
+@pytest.mark.slow
+def test_million_atoms_fp64_and_mixed(cuda_lib, oracle_lib):
+    s = inputs.workload_million()
+    want = _oracle(oracle_lib, s, True)
+    got, pl = _run(cuda_lib, s, True, 0, 64)
+    assert _relerr(got, want) <= FP64_TOL
+    got, _ = _run(cuda_lib, s, True, 1, 8, pl=pl)
+    assert _relerr(got, want) <= MIXED_TOL
