@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--profile", choices=["fp64", "fp64-full", "mixed", "mixed-full", "list"],
                     help="no timing: build the list and run a few calls of one kernel (for ncu)")
     ap.add_argument("--profile-atoms", choices=["paper", "million"], default="paper")
+    ap.add_argument("--profile-tpi", type=int, default=0, help="schedule for --profile (0 = auto)")
     return ap.parse_args()
 
 
@@ -231,7 +232,7 @@ def run_profile(args):
             lj.lj_build_pairlist(q, box, s.rs, half, reuse=pl)
     else:
         prec = lj.LJ_MIXED if args.profile.startswith("mixed") else lj.LJ_FP64
-        tpi = lj.LJ_TPI_AUTO
+        tpi = args.profile_tpi
         fn = lj.lj_force_prepared(q, p, pl, DT, s.rc, box, precision=prec, tpi=tpi)
         for _ in range(5):
             fn()

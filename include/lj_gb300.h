@@ -125,6 +125,34 @@ int lj_build_pairlist(const double *q4_dev, int64_t n, const double box[3], doub
                       void *workspace_dev, size_t workspace_bytes, int64_t *nnz_out,
                       int64_t *max_row_out, void *stream);
 
+/*
+ * lj_build_pairlist_static: the same list as lj_build_pairlist, for callers
+ * that cannot allocate device memory (no cudaMalloc in their context, no
+ * workspace from their host); the paper has no counterpart -- it is a
+ * deployment variant of the builder above.
+ *
+ * The builder's scratch lives in one fixed array of LJ_STATIC_SCRATCH_BYTES
+ * inside the library's device memory (every GPU that loads the library holds
+ * it until the process exits), so this call allocates nothing: no cudaMalloc,
+ * no cudaFree, no allocating library routine.  The caller still passes the
+ * positions and the row_ptr / col outputs, exactly as for lj_build_pairlist.
+ *  - n must not exceed LJ_STATIC_MAX_ATOMS (LJ_ERR_CAPACITY otherwise; no GPU
+ *    work is done).
+ *  - The first call on a device looks up the array's device address with that
+ *    device current; make that first call before any stream capture.
+ *  - All calls share the one array and each call clears what it needs zeroed:
+ *    calls whose GPU work overlaps (other streams or host threads) race on it
+ *    and must be serialised by the caller.
+ * Arguments, outputs, blocking behaviour and the other errors are those of
+ * lj_build_pairlist.
+ */
+#define LJ_STATIC_MAX_ATOMS 131072
+#define LJ_STATIC_SCRATCH_BYTES (8u << 20)
+int lj_build_pairlist_static(const double *q4_dev, int64_t n, const double box[3],
+                             double r_search, int half, int32_t *row_ptr_dev, int32_t *col_dev,
+                             int64_t col_capacity, int64_t *nnz_out, int64_t *max_row_out,
+                             void *stream);
+
 /* ======================================================================== */
 /* Force (Algorithm 1 inside Algorithm 3)                                    */
 /* ======================================================================== */

@@ -28,6 +28,7 @@ LJ_FP64 = 0
 LJ_MIXED = 1
 LJ_TPI_AUTO = 0
 LJ_SCHED_STREAM = 64
+LJ_STATIC_MAX_ATOMS = 131072
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liblj_gb300.so")
 _lib = None
@@ -45,6 +46,8 @@ SIGNATURES = {
     "lj_pairlist_workspace_bytes": (_sz, [_i64, _dbl3, _dbl]),
     "lj_build_pairlist": (_int, [_vp, _i64, _dbl3, _dbl, _int, _vp, _vp, _i64, _vp, _sz, _i64p,
                                  _i64p, _vp]),
+    "lj_build_pairlist_static": (_int, [_vp, _i64, _dbl3, _dbl, _int, _vp, _vp, _i64, _i64p, _i64p,
+                                        _vp]),
     "lj_force_workspace_bytes": (_sz, [_i64, _dbl3, _int]),
     "lj_force": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl, _dbl3, _dbl, _dbl, _int,
                         _int, _vp, _sz, _vp]),
@@ -179,6 +182,24 @@ def lj_build_pairlist(q4: torch.Tensor, box, r_search: float, half: bool = True,
         return PairList(row_ptr, col, n, int(nnz.value), bool(half), float(r_search),
                         int(mrow.value), ws)
     raise LJError(LJ_ERR_CAPACITY, "lj_build_pairlist")
+
+
+def lj_build_pairlist_static(q4: torch.Tensor, box, r_search: float, half: bool,
+                             row_ptr: torch.Tensor, col: torch.Tensor, stream=None):
+    """The allocation-free builder: scratch comes from the library's fixed
+    device array; the caller passes the row_ptr (n+1) and col outputs.
+    Returns (nnz, max_row)."""
+    lib = load()
+    n = int(q4.shape[0])
+    nnz = ctypes.c_int64(0)
+    mrow = ctypes.c_int64(0)
+    st = lib.lj_build_pairlist_static(_dev(q4, torch.float64, "q4", (n, 4)), n, _box3(box),
+                                      float(r_search), int(bool(half)),
+                                      _dev(row_ptr, torch.int32, "row_ptr", (n + 1,)),
+                                      _dev(col, torch.int32, "col"), int(col.numel()),
+                                      ctypes.byref(nnz), ctypes.byref(mrow), _stream(stream))
+    _check(st, "lj_build_pairlist_static")
+    return int(nnz.value), int(mrow.value)
 
 
 def lj_force_workspace_bytes(n: int, box, precision: int = LJ_FP64) -> int:
