@@ -52,7 +52,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
 # DRAM bytes per launch from an ncu capture of the kernel as it stands
 # (profiles/); None until captured for the current kernel source.
-TRAFFIC_PER_LAUNCH = {"force_stream_kernel": None}
+TRAFFIC_PER_LAUNCH = {"force_refill_kernel": None}
 
 
 def parse():
@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--order", choices=["random", "cell"], default="random")
     ap.add_argument("--no-variants", action="store_true", help="skip the per-variant table")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads (1M atoms, 512-system batch, 64-replica adjoint)")
     ap.add_argument("--profile", choices=["fp64", "fp64-full", "mixed", "mixed-full", "list"],
                     help="no timing: build the list and run a few calls of one kernel (for ncu)")
     ap.add_argument("--profile-atoms", choices=["paper", "million"], default="paper")
@@ -275,8 +277,9 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     pl = lj.lj_build_pairlist(q, box, s.rs, True)
-    force = lj.lj_force_prepared(q, p, pl, DT, s.rc, box, precision=lj.LJ_FP64,
-                                 tpi=lj.LJ_SCHED_STREAM)
+    # schedule picked by the library's autotuner on this system and list
+    best_tpi, _, tune_table = lj.lj_autotune_force(q, pl, DT, s.rc, box, reps=5)
+    force = lj.lj_force_prepared(q, p, pl, DT, s.rc, box, precision=lj.LJ_FP64, tpi=best_tpi)
     nnz = pl.nnz
     n_cut = count_in_cutoff(q, pl, box, s.rc)
 
@@ -369,8 +372,8 @@ def main():
     alg_bytes = 4.0 * nnz + 4.0 * (s.n + 1) + 32.0 * s.n + 64.0 * s.n
     roof = {"bound": "alu", "achieved": flops / t_force / 1e12, "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": flops / t_force / 1e12 / FP64_PEAK_TFLOPS,
-            "traffic": TRAFFIC_PER_LAUNCH["force_stream_kernel"],
-            "kernel": "force_stream_kernel (FP64, half list)",
+            "traffic": TRAFFIC_PER_LAUNCH["force_refill_kernel"],
+            "kernel": f"FP64 force kernel, {schedule_name(best_tpi)}, half list",
             "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
             "flops_per_launch": flops, "launch_ms": t_force * 1e3}
     hbm_view = {"achieved": alg_bytes / t_force / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -383,7 +386,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(args.order), "n_atoms": s.n, "pairs_per_call": nnz,
                    "pairs_in_cutoff": n_cut, "force_calls_per_step": FORCE_CALLS,
-                   "list_builds_per_step": 1, "schedule": "pair-stream FP64",
+                   "list_builds_per_step": 1, "schedule": schedule_name(best_tpi),
                    "l2": "flushed before every step (256 MiB write, outside the timed events)",
                    "parallelism": f"replicas x{world}"},
         "list_build_ms": statistics.mean(list_ms),
@@ -396,8 +399,17 @@ def main():
         "clocks": clk.summary(),
     }
 
+    out["autotune_ms"] = {schedule_name(k): v for k, v in tune_table.items()}
     if not args.no_variants:
         out["variants"] = variants(lj, s, q, pl, box, dev, stream, flush)
+    if not args.no_extra:
+        del p, q, pl, force
+        torch.cuda.empty_cache()
+        out["other_configs"] = {
+            "million_fp64_vs_mixed": extra_million(lj, dev, stream, flush),
+            "batched_512_systems": extra_batched(lj, dev, stream, flush),
+            "adjoint_64_replicas": extra_adjoint(lj, dev, stream, flush),
+        }
     if world == 1 and not args.no_cpu:
         t, m = oracle_sample(s, CPU_FORCE_CALLS)
         out["cpu_baseline"] = {
@@ -408,6 +420,114 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def schedule_name(tpi: int) -> str:
+    if tpi == 64:
+        return "lane-refill"
+    if tpi & 128:
+        return f"{tpi & 127} lanes/row, 2 entries/lane (software-pipelined)"
+    return f"{tpi} lanes/row"
+
+
+def extra_million(lj, dev, stream, flush):
+    """N = 1,048,576 (64^3 FCC): FP64 vs mixed, per call (L2 flushed), the
+    mixed error against the FP64 result."""
+    import torch
+    from paper_1806_05713_gb300 import inputs
+    s = inputs.workload_million()
+    box = [float(x) for x in s.box]
+    q = torch.from_numpy(s.q).to(dev)
+    t_list = time_calls(lambda: lj.lj_build_pairlist(q, box, s.rs, True), stream, flush, 3, 1)
+    pl = lj.lj_build_pairlist(q, box, s.rs, True)
+    res = {"n_atoms": s.n, "pairs_per_call": pl.nnz, "list_build_ms": t_list}
+    best, _, _ = lj.lj_autotune_force(q, pl, DT, s.rc, box, reps=3)
+    out = {}
+    for name, prec, tpis in (("fp64", lj.LJ_FP64, (best,)), ("mixed", lj.LJ_MIXED, (4, 8, 16))):
+        for t in tpis:
+            pp = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
+            fn = lj.lj_force_prepared(q, pp, pl, DT, s.rc, box, precision=prec, tpi=t)
+            ms = time_calls(fn, stream, flush, 10, 2)
+            pp.zero_()
+            fn()
+            out[(name, t)] = (ms, pp[:, :3].clone())
+    ms64, ref = out[("fp64", best)]
+    res["fp64"] = {"schedule": schedule_name(best), "ms": ms64, "pairs_per_s": pl.nnz / (ms64 / 1e3)}
+    mk = min((k for k in out if k[0] == "mixed"), key=lambda k: out[k][0])
+    msm, pm = out[mk]
+    err = pm - ref
+    res["mixed"] = {"schedule": schedule_name(mk[1]), "ms": msm, "pairs_per_s": pl.nnz / (msm / 1e3),
+                    "max_err_rel_vs_fp64": float(err.abs().max() / ref.abs().max()),
+                    "rms_err_rel_vs_fp64": float(err.pow(2).mean().sqrt() / ref.pow(2).mean().sqrt())}
+    res["speedup_mixed_vs_fp64"] = ms64 / msm
+    return res
+
+
+def extra_batched(lj, dev, stream, flush):
+    """512 systems, N log-uniform in 500..32000, rho in 0.8..1.2, rc 2.5 or
+    3.0: one persistent launch replayed from a CUDA graph vs one launch per
+    system, FP64 and mixed, half lists."""
+    import torch
+    from paper_1806_05713_gb300 import inputs
+    from paper_1806_05713_gb300.batch import Batch
+    systems = inputs.batched_systems(nsys=512, seed=0)
+    res = {"n_systems": len(systems), "total_atoms": int(sum(s.n for s in systems))}
+    for name, prec in (("fp64", lj.LJ_FP64), ("mixed", lj.LJ_MIXED)):
+        b = Batch(systems, DT, prec, True, tpi=8, rows_per_item=64, plan_rows_min=16)
+        tpi, rows, _ = b.autotune(tpis=(4, 8, 16), rows=(16, 32, 64, 128), reps=3)
+        g = b.capture_graph()
+        t_graph = time_calls(g.replay, stream, flush, 10, 2)
+        t_sep = time_calls(lambda: b.force_per_system(tpi=8 if prec == lj.LJ_MIXED else 136),
+                           stream, flush, 5, 1)
+        res[name] = {"tpi": tpi, "rows_per_item": rows, "pairs_per_call": b.pairs,
+                     "graph_persistent_ms": t_graph,
+                     "graph_persistent_pairs_per_s": b.pairs / (t_graph / 1e3),
+                     "per_system_launches_ms": t_sep,
+                     "per_system_pairs_per_s": b.pairs / (t_sep / 1e3),
+                     "speedup": t_sep / t_graph}
+        del b, g
+    return res
+
+
+def extra_adjoint(lj, dev, stream, flush):
+    """64 replicas of N = 16,384 (16^3 FCC, rho 1, jitter 0.1): forces with
+    (eps, sigma) = (1.1, 0.97) against targets at (1, 1), mean squared force
+    error, gradient w.r.t. positions, eps and sigma through the autograd
+    wrapper (forward kernel + hand-written adjoint kernel)."""
+    import torch
+    from paper_1806_05713_gb300 import inputs
+    from paper_1806_05713_gb300.autograd import lj_forces
+    reps = inputs.workload_replicas(64, 16, seed=0)
+    L = float(reps[0].box[0])
+    box = [L, L, L]
+    n1 = reps[0].n
+    q = torch.from_numpy(np.concatenate([r.q for r in reps])).to(dev)
+    rows, cols, off = [torch.zeros(1, dtype=torch.int32, device=dev)], [], 0
+    for k, r in enumerate(reps):  # block-diagonal list over replicas sharing one box size
+        pl = lj.lj_build_pairlist(q[k * n1:(k + 1) * n1].contiguous(), box, r.rs, False)
+        rows.append(pl.row_ptr[1:] + off)
+        cols.append(pl.col_view + k * n1)
+        off += pl.nnz
+    big = lj.PairList(torch.cat(rows).contiguous(), torch.cat(cols).contiguous(), q.shape[0], off,
+                      False, reps[0].rs, 0)
+    Ft = torch.zeros_like(q)
+    lj.lj_force(q, Ft, big, 1.0, reps[0].rc, box, 1.0, 1.0)
+    res = {"replicas": len(reps), "atoms": int(q.shape[0]), "pairs": off // 2}
+    for name, prec in (("fp64", lj.LJ_FP64), ("mixed", lj.LJ_MIXED)):
+        eps = torch.tensor(1.1, dtype=torch.float64, device=dev, requires_grad=True)
+        sig = torch.tensor(0.97, dtype=torch.float64, device=dev, requires_grad=True)
+
+        def step():
+            qq = q.detach().requires_grad_(True)
+            eps.grad = None
+            sig.grad = None
+            F = lj_forces(qq, eps, sig, big, reps[0].rc, box, prec)
+            loss = ((F - Ft) ** 2)[:, :3].mean()
+            loss.backward()
+            return qq.grad
+        ms = time_calls(step, stream, flush, 5, 1)
+        res[name] = {"forward_backward_ms": ms, "grad_eps": float(eps.grad), "grad_sigma": float(sig.grad)}
+    return res
 
 
 def time_calls(fn, stream, flush, calls=20, warm=3):
@@ -447,7 +567,7 @@ def variants(lj, s, q, pl_half, box, dev, stream, flush):
             res[f"list_build_ms/{order}/{kind}"] = t_list
             p64 = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
             ref = None
-            for prec, tpis in ((lj.LJ_FP64, (64, 8, 32)), (lj.LJ_MIXED, (4, 8, 16))):
+            for prec, tpis in ((lj.LJ_FP64, (136, 8, 144, 64)), (lj.LJ_MIXED, (4, 8, 16))):
                 for tpi in tpis:
                     pp = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
                     fn = lj.lj_force_prepared(qq, pp, pl, DT, sys_.rc, box, precision=prec, tpi=tpi)

@@ -64,13 +64,18 @@ extern "C" {
 /* ---- schedules ---------------------------------------------------------- */
 /* `tpi` = threads per i-row: 1, 2, 4, 8, 16 or 32 lanes of one warp walk one
  * row and reduce their partial sums with warp shuffles; 0 = library default
- * for the list kind and precision. */
+ * (8 lanes per row). */
 #define LJ_TPI_AUTO 0
-/* LJ_SCHED_STREAM: the FP64 pair-stream schedule.  Each warp walks a
- * contiguous block of rows as one flat stream of list entries, queues the
- * in-cutoff pairs in shared memory and evaluates the force 32 pairs at a
- * time, so no lane idles on a margin pair or a row tail. */
-#define LJ_SCHED_STREAM 64
+/* LJ_SCHED_REFILL: the FP64 lane-refill schedule (the FP64 default).  Each
+ * lane owns one row, keeps its q_i and p_i sum in registers, and takes the
+ * next row as soon as its own ends (rows are handed out to warps in chunks
+ * of 32 from a counter in the workspace), so no lane waits for a longer row
+ * of its warp; a persistent grid of one launch. */
+#define LJ_SCHED_REFILL 64
+/* LJ_SCHED_SWP2 | tpi (tpi = 4, 8 or 16; FP64 only): software pipelining,
+ * the paper's section "Software Pipelining" -- each lane carries two
+ * independent entries per iteration so that their FP64 chains overlap. */
+#define LJ_SCHED_SWP2 128
 
 const char *lj_status_string(int status);
 /* Text of the last CUDA error seen by this library in this thread. */
@@ -157,7 +162,9 @@ int lj_build_pairlist_static(const double *q4_dev, int64_t n, const double box[3
 /* Force (Algorithm 1 inside Algorithm 3)                                    */
 /* ======================================================================== */
 
-/* Bytes of device workspace lj_force needs (0 for LJ_FP64). */
+/* Bytes of device workspace lj_force needs: 256 for LJ_FP64 (a row counter
+ * of the lane-refill schedule), 16 n + 256 for LJ_MIXED (cell-relative FP32
+ * positions). */
 size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
 
 /*
@@ -175,8 +182,8 @@ size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
  *  box              host, 3 box sides.
  *  eps, sigma       Eq. (1) parameters (> 0).
  *  precision        LJ_FP64 or LJ_MIXED.
- *  tpi              LJ_TPI_AUTO, 1..32 (power of two) or LJ_SCHED_STREAM
- *                   (FP64 half or full list).
+ *  tpi              LJ_TPI_AUTO, 1..32 (power of two), LJ_SCHED_REFILL or
+ *                   LJ_SCHED_SWP2 | 4, 8, 16 (the last two FP64 only).
  *  workspace_dev    scratch of lj_force_workspace_bytes() (NULL if 0).
  * Half lists add p_j with FP64 atomics, so their rounding order (not their
  * value beyond the last bits) varies between calls; full lists are
@@ -205,6 +212,142 @@ int lj_energy(const double *q4_dev, int64_t n, const int32_t *row_ptr_dev,
               const int32_t *col_dev, int64_t nnz, int half, double r_cut, const double box[3],
               double eps, double sigma, int shifted, double *e_out_dev, void *workspace_dev,
               size_t workspace_bytes, void *stream);
+
+/* ======================================================================== */
+/* Batched systems: many independent LJ systems in one persistent launch    */
+/* (the Algorithm 3 loop of each system, work-shared across the GPU)        */
+/* ======================================================================== */
+
+/* One system of a batch.  Atoms of system s are rows atom_offset ..
+ * atom_offset + n - 1 of the packed q4/p4 arrays; its CSR list occupies
+ * row_ptr[row_offset .. row_offset + n] (entry indices local to the system,
+ * starting at 0) and col[entry_offset .. entry_offset + nnz - 1] (atom
+ * indices local to the system) -- exactly what lj_build_pairlist writes when
+ * given q4 + 4 atom_offset, row_ptr + row_offset and col + entry_offset. */
+typedef struct lj_system {
+    int64_t atom_offset;
+    int64_t n;
+    int64_t row_offset;
+    int64_t entry_offset;
+    int64_t nnz;
+    double box[3];
+    double r_cut;
+    double eps;
+    double sigma;
+    int32_t half;
+    int32_t reserved;
+} lj_system;
+
+/* A batch plan: host-side summary of a device buffer (caller-owned) that
+ * holds per-system parameters and the work-item table.  Filled by
+ * lj_batch_init; read by lj_force_batched. */
+typedef struct lj_batch {
+    void *plan_dev;
+    size_t plan_bytes;
+    int64_t nitems;
+    int64_t total_atoms;
+    double dt;
+    int32_t nsys;
+    int32_t precision;
+    int32_t tpi;           /* lanes per row: 1, 2, 4, 8, 16, 32 */
+    int32_t rows_per_item; /* rows per work item (>= 1) */
+    int32_t blocks;        /* persistent grid size */
+    int32_t reserved;
+} lj_batch;
+
+/* Bytes of the device plan for these systems and rows_per_item. */
+size_t lj_batch_plan_bytes(const lj_system *systems, int nsys, int rows_per_item);
+
+/*
+ * Validate the systems (each as lj_force would), build the work-item table
+ * (items of at most rows_per_item rows of one system, ordered by decreasing
+ * estimated cost nnz/n * rows, the longest-first rule), and copy it and the
+ * per-system constants of Algorithm 1 (dt, eps, sigma, cutoff, box) to
+ * plan_dev.  Blocks until the copy is done.  Errors: LJ_ERR_ARG, LJ_ERR_BOX,
+ * LJ_ERR_CAPACITY (plan_bytes too small), LJ_ERR_CUDA.
+ */
+int lj_batch_init(lj_batch *batch, const lj_system *systems, int nsys, double dt, int precision,
+                  int tpi, int rows_per_item, void *plan_dev, size_t plan_bytes, void *stream);
+
+/* Bytes of device workspace lj_force_batched needs (a work counter; for
+ * LJ_MIXED also 16 bytes per atom). */
+size_t lj_force_batched_workspace_bytes(const lj_batch *batch);
+
+/*
+ * p += impulses for every system of the batch (lj_force semantics per
+ * system) in one persistent launch: warps take work items from a counter in
+ * the workspace until none is left.  Enqueues a memset of the counter, (for
+ * LJ_MIXED) one pre-pass kernel and the force kernel; no host
+ * synchronisation and no allocation, so the call can be captured in a CUDA
+ * graph and replayed.  Errors: LJ_ERR_ARG, LJ_ERR_CAPACITY, LJ_ERR_CUDA.
+ */
+int lj_force_batched(const lj_batch *batch, const double *q4_dev, double *p4_dev,
+                     const int32_t *row_ptr_dev, const int32_t *col_dev, void *workspace_dev,
+                     size_t workspace_bytes, void *stream);
+
+/* ======================================================================== */
+/* Autotuning (host-side; times candidate schedules with CUDA events)       */
+/* ======================================================================== */
+
+/*
+ * Time lj_force over each candidate schedule in `tpis` (values accepted by
+ * lj_force's tpi argument) `reps` times on the given system and list, using
+ * p4_scratch_dev as the momentum output (its contents are overwritten), and
+ * return the fastest in *best_tpi with its median time in *best_ms.
+ * ms_out (host, n_tpi floats, may be NULL) receives every candidate's median.
+ * Candidates that the precision does not accept are skipped (time +inf).
+ * Synchronous.  Errors as lj_force.
+ */
+int lj_autotune_force(const double *q4_dev, double *p4_scratch_dev, int64_t n,
+                      const int32_t *row_ptr_dev, const int32_t *col_dev, int64_t nnz, int half,
+                      double dt, double r_cut, const double box[3], double eps, double sigma,
+                      int precision, const int *tpis, int n_tpi, int reps, void *workspace_dev,
+                      size_t workspace_bytes, int *best_tpi, float *best_ms, float *ms_out,
+                      void *stream);
+
+/*
+ * Time lj_force_batched for every (tpi, rows_per_item) pair of the
+ * candidate lists (re-initialising the plan in plan_dev for each), `reps`
+ * times each, on p4_scratch_dev; return the fastest pair and its median
+ * time.  plan_bytes must hold the plan for the smallest rows_per_item and
+ * the workspace must be sized for the batch.  Synchronous.
+ */
+int lj_autotune_batched(const lj_system *systems, int nsys, double dt, int precision,
+                        const int *tpis, int n_tpi, const int *rows_per_item, int n_rpi,
+                        const double *q4_dev, double *p4_scratch_dev, const int32_t *row_ptr_dev,
+                        const int32_t *col_dev, void *plan_dev, size_t plan_bytes,
+                        void *workspace_dev, size_t workspace_bytes, int reps, int *best_tpi,
+                        int *best_rows_per_item, float *best_ms, void *stream);
+
+/* ======================================================================== */
+/* Adjoint of the force map (derived from Eq. 1)                            */
+/* ======================================================================== */
+
+/* Bytes of device workspace lj_force_vjp needs. */
+size_t lj_force_vjp_workspace_bytes(int64_t n, int precision);
+
+/*
+ * Vector-Jacobian product of the force map F(q; eps, sigma), the impulse of
+ * lj_force with dt = 1 and p = 0: for each unique pair with
+ * s = r^2 < r_cut^2 and g(s) = 24 eps (2 sigma^12 s^-7 - sigma^6 s^-4),
+ * F_j += g d, F_i -= g d (d = q_j - q_i, minimum image).  Given
+ * R = dLoss/dF (gradF4_dev, n x 4, pad ignored) it writes, with w = R_j - R_i
+ * and c = g w + 2 g'(s) (d.w) d per pair:
+ *   gradq4_dev          n x 4, overwritten: dLoss/dq (pad set to 0);
+ *                       dLoss/dq_j += c, dLoss/dq_i -= c;
+ *   grad_eps_sigma_dev  2 device doubles, overwritten:
+ *                       dLoss/deps = sum (g/eps)(d.w),
+ *                       dLoss/dsigma = sum dg/dsigma (d.w).
+ * Full lists gather per row without atomics (deterministic); half lists
+ * scatter dLoss/dq_j with FP64 atomics.  The scalar sums use a fixed-order
+ * reduction.  precision: LJ_FP64 or LJ_MIXED (FP32 pair arithmetic,
+ * compensated FP32 sums, FP64 outputs).  Asynchronous.  Errors as lj_force.
+ */
+int lj_force_vjp(const double *q4_dev, const double *gradF4_dev, int64_t n,
+                 const int32_t *row_ptr_dev, const int32_t *col_dev, int64_t nnz, int half,
+                 double r_cut, const double box[3], double eps, double sigma, int precision,
+                 double *gradq4_dev, double *grad_eps_sigma_dev, void *workspace_dev,
+                 size_t workspace_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -106,21 +106,53 @@ __device__ __forceinline__ bool less_nonneg(double r2, long long c2_bits)
 // ~e^3 < 2^-64 before rounding; the result is within two ulps of 1/a.
 // This is the "reciprocal approximation plus correction" the paper's
 // summary proposes for AVX-512 (vrcp14pd / vrcp28pd), built on GB300's FP32
-// special-function unit.  Outside that range it divides.
-__device__ __forceinline__ double rcp_fp64(double a)
+// special-function unit: three FP64 instructions instead of a division.
+// `ok` is false outside that range (the caller divides there instead).
+__device__ __forceinline__ double rcp_fp64_fast(double a, bool &ok)
 {
     const int hi = __double2hiint(a);
-    if (hi < 0x38100000 || hi >= 0x47d00000)
-        return 1.0 / a;
+    ok = (hi >= 0x38100000) && (hi < 0x47d00000);
     const unsigned lo = static_cast<unsigned>(__double2loint(a));
     const unsigned fb = (static_cast<unsigned>(hi - 0x38000000) << 3) | (lo >> 29);
     float xf;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(xf) : "f"(__uint_as_float(fb)));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(xf) : "f"(__uint_as_float(ok ? fb : 0x3f800000u)));
     const unsigned g = __float_as_uint(xf);
     const double x0 = __hiloint2double(static_cast<int>((g >> 3) + 0x38000000u),
                                        static_cast<int>(g << 29));
     const double e = fma(-a, x0, 1.0);
     return fma(x0, fma(e, e, e), x0);
+}
+
+// rcp_fp64_fast with the out-of-range fallback taken only when some lane of
+// `mask` needs it (a warp-uniform branch, so the division's instructions are
+// not issued in the common case).
+__device__ __forceinline__ double rcp_fp64(double a, unsigned mask = 0xffffffffu)
+{
+    bool ok;
+    double x = rcp_fp64_fast(a, ok);
+    if (__any_sync(mask, !ok)) {
+        if (!ok) x = 1.0 / a;
+    }
+    return x;
+}
+
+// Minimum image of the three components of d, exactly as
+//   if (d > L/2) d -= L; else if (d < -L/2) d += L;
+// per axis, with the tests on IEEE bit patterns and the adds issued only
+// when some lane of `mask` needs a wrap.
+__device__ __forceinline__ void min_image3(double &dx, double &dy, double &dz, const double L[3],
+                                           const long long hb[3], unsigned mask = 0xffffffffu)
+{
+    const long long bx = __double_as_longlong(dx), by = __double_as_longlong(dy),
+                    bz = __double_as_longlong(dz);
+    const bool wx = (bx & 0x7fffffffffffffffLL) > hb[0];
+    const bool wy = (by & 0x7fffffffffffffffLL) > hb[1];
+    const bool wz = (bz & 0x7fffffffffffffffLL) > hb[2];
+    if (__any_sync(mask, wx || wy || wz)) {
+        if (wx) dx = __dadd_rn(dx, bx < 0 ? L[0] : -L[0]);
+        if (wy) dy = __dadd_rn(dy, by < 0 ? L[1] : -L[1]);
+        if (wz) dz = __dadd_rn(dz, bz < 0 ? L[2] : -L[2]);
+    }
 }
 
 // FP32 reciprocal: hardware approximation plus one Newton step

@@ -1,0 +1,175 @@
+// lj_rows.cuh -- one CSR row of the LJ momentum update (Algorithm 1 for
+// each entry of SortedList[i], Algorithm 3), in the FP64 and MIXED forms,
+// walked by a group of TPI lanes of one warp.  Shared by the single-system
+// kernels (lj_force.cu) and the batched persistent kernel (lj_batched.cu).
+#pragma once
+
+#include "lj_forms.cuh"
+
+namespace lj {
+namespace {
+
+// One row i of the FP64 form, walked by the TPI lanes of the calling group
+// (gm = their mask).  U independent entries per lane and iteration (U = 2 is
+// the paper's software pipelining, section "Software Pipelining": the loads
+// and distance work of one entry overlap the force arithmetic of the other,
+// so the long dependent FP64 chains of two pairs are in flight together).
+// Pointers are the system's own arrays (local indices).
+template <int TPI, bool HALF, int U>
+__device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *__restrict__ p4,
+                                         const int *__restrict__ row_ptr,
+                                         const int *__restrict__ col, int i, const Fp64Params &P,
+                                         unsigned gm)
+{
+    const int sub = threadIdx.x & (TPI - 1);
+    double xi, yi, zi;
+    load_q4_256(q4, i, xi, yi, zi);
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    const int kb = row_ptr[i], ke = row_ptr[i + 1];
+    for (int base = kb; base < ke; base += TPI * U) {
+        int j[U];
+        bool valid[U], in[U], near[U];
+        double dx[U], dy[U], dz[U], r2[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = base + sub + u * TPI;
+            valid[u] = k < ke;
+            j[u] = valid[u] ? col[k] : i;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            double xj, yj, zj;
+            load_q4_256(q4, j[u], xj, yj, zj);
+            dx[u] = xj - xi;
+            dy[u] = yj - yi;
+            dz[u] = zj - zi;
+        }
+        bool anynear = false, anyin = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            min_image3(dx[u], dy[u], dz[u], P.L, P.half_bits, gm);
+            r2[u] = fma(dz[u], dz[u], fma(dy[u], dy[u], dx[u] * dx[u]));
+            const long long rb = __double_as_longlong(r2[u]);
+            in[u] = valid[u] && rb < P.rc2_bits;
+            near[u] = valid[u] && static_cast<unsigned long long>(rb - P.rc2_bits + 64) < 128ull;
+            anynear |= near[u];
+        }
+        if (__any_sync(gm, anynear)) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (near[u]) in[u] = exact_in_cutoff(dx[u], dy[u], dz[u], P.rc2);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!valid[u]) r2[u] = 1.0;
+            anyin |= in[u];
+        }
+        if (__any_sync(gm, anyin)) {
+            double fn[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const double w = rcp_fp64(r2[u], gm);
+                const double w2 = w * w;
+                const double w4 = w2 * w2;
+                const double w3 = w2 * w;
+                fn[u] = w4 * fma(P.B, w3, -P.A);  // -df: p_i -= fn d, p_j += fn d
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (in[u]) {
+                    if (HALF) {
+                        const double fx = fn[u] * dx[u], fy = fn[u] * dy[u], fz = fn[u] * dz[u];
+                        atomicAdd(p4 + 4 * static_cast<int64_t>(j[u]) + 0, fx);
+                        atomicAdd(p4 + 4 * static_cast<int64_t>(j[u]) + 1, fy);
+                        atomicAdd(p4 + 4 * static_cast<int64_t>(j[u]) + 2, fz);
+                        ax -= fx;
+                        ay -= fy;
+                        az -= fz;
+                    } else {
+                        ax = fma(-fn[u], dx[u], ax);
+                        ay = fma(-fn[u], dy[u], ay);
+                        az = fma(-fn[u], dz[u], az);
+                    }
+                }
+            }
+        }
+    }
+    if (TPI > 1) {
+        ax = group_sum<TPI>(ax);
+        ay = group_sum<TPI>(ay);
+        az = group_sum<TPI>(az);
+    }
+    if (sub == 0) {
+        double *pi = p4 + 4 * static_cast<int64_t>(i);
+        atomicAdd(pi + 0, ax);
+        atomicAdd(pi + 1, ay);
+        atomicAdd(pi + 2, az);
+    }
+}
+
+// One row i of the MIXED form (see lj_force.cu), walked by a TPI group.
+template <int TPI, bool HALF>
+__device__ __forceinline__ void mixed_row(const double *__restrict__ q4,
+                                          const float4 *__restrict__ rel, double *__restrict__ p4,
+                                          const int *__restrict__ row_ptr,
+                                          const int *__restrict__ col, int i, const MixedParams &P)
+{
+    const int sub = threadIdx.x & (TPI - 1);
+    const float4 pi = rel[i];
+    const int ci = __float_as_int(pi.w);
+    const int cix = ci & 1023, ciy = (ci >> 10) & 1023, ciz = ci >> 20;
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    const int kb = row_ptr[i], ke = row_ptr[i + 1];
+    for (int k = kb + sub; k < ke; k += TPI) {
+        const int j = col[k];
+        const float4 pj = rel[j];
+        const int cj = __float_as_int(pj.w);
+        const float dx = mixed_disp(pj.x, pi.x, cj & 1023, cix, P.h[0], P.hLf[0], P.nc[0], P.nhalf[0], P.wrap_fix);
+        const float dy = mixed_disp(pj.y, pi.y, (cj >> 10) & 1023, ciy, P.h[1], P.hLf[1], P.nc[1], P.nhalf[1], P.wrap_fix);
+        const float dz = mixed_disp(pj.z, pi.z, cj >> 20, ciz, P.h[2], P.hLf[2], P.nc[2], P.nhalf[2], P.wrap_fix);
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        bool in = r2 < P.rc2f;
+        if (fabsf(r2 - P.rc2f) <= P.band) {
+            double xi, yi, zi, xj, yj, zj;
+            load_xyz(q4, i, xi, yi, zi);
+            load_xyz(q4, j, xj, yj, zj);
+            const double ex = min_image(__dsub_rn(xj, xi), P.L[0], P.half_bits[0]);
+            const double ey = min_image(__dsub_rn(yj, yi), P.L[1], P.half_bits[1]);
+            const double ez = min_image(__dsub_rn(zj, zi), P.L[2], P.half_bits[2]);
+            in = exact_in_cutoff(ex, ey, ez, P.rc2);
+        }
+        if (in) {
+            const float u = rcp_fp32(r2);
+            const float u2 = u * u;
+            const float u4 = u2 * u2;
+            const float u3 = u2 * u;
+            const float f = u4 * fmaf(-P.Bf, u3, P.Af);
+            const float fx = f * dx, fy = f * dy, fz = f * dz;
+            kahan_add(sx, cx, fx);
+            kahan_add(sy, cy, fy);
+            kahan_add(sz, cz, fz);
+            if (HALF) {
+                atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 0, -static_cast<double>(fx));
+                atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 1, -static_cast<double>(fy));
+                atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 2, -static_cast<double>(fz));
+            }
+        }
+    }
+    if (TPI > 1) {
+        group_kahan<TPI>(sx, cx);
+        group_kahan<TPI>(sy, cy);
+        group_kahan<TPI>(sz, cz);
+    }
+    if (sub == 0) {
+        const double ax = static_cast<double>(sx) - static_cast<double>(cx);
+        const double ay = static_cast<double>(sy) - static_cast<double>(cy);
+        const double az = static_cast<double>(sz) - static_cast<double>(cz);
+        double *pp = p4 + 4 * static_cast<int64_t>(i);
+        atomicAdd(pp + 0, ax);
+        atomicAdd(pp + 1, ay);
+        atomicAdd(pp + 2, az);
+    }
+}
+
+}  // namespace
+}  // namespace lj

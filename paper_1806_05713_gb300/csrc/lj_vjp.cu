@@ -1,0 +1,378 @@
+// lj_vjp.cu -- hand-written adjoint of the LJ force map.
+//
+// Forward map (Eq. (1) of Watanabe & Nakagawa differentiated once; the
+// impulse of Algorithm 1 divided by dt): with d = q_j - q_i (minimum image),
+// s = |d|^2 < r_c^2 and
+//     g(s) = 24 eps (2 sigma^12 s^-7 - sigma^6 s^-4),
+// each pair adds F_j += g d and F_i -= g d.
+//
+// Given R = dLoss/dF, the vector-Jacobian product per pair is, with
+// w = R_j - R_i,
+//     c        = g w + 2 g'(s) (d.w) d,     dLoss/dq_j += c, dLoss/dq_i -= c,
+//     dLoss/deps   += (g / eps) (d.w),
+//     dLoss/dsigma += (dg/dsigma) (d.w),
+//     g'(s)      = 24 eps (-14 sigma^12 s^-8 + 4 sigma^6 s^-5),
+//     dg/dsigma  = 24 eps (24 sigma^11 s^-7 - 6 sigma^5 s^-4).
+// A full list visits every pair from both ends; c is odd under i <-> j, so
+// row i gathers dLoss/dq_i = -sum_j c(d_ij, w_ij) with no atomics, and the
+// two scalar gradients take half of the sum over entries.  A half list
+// scatters c to q_j with FP64 atomics.
+//
+// Forms: FP64 (every step double), MIXED (cell-relative FP32 displacement
+// and FP32 pair arithmetic as in lj_force, Kahan-compensated FP32 row and
+// scalar sums, FP64 outputs).  Pairs within the error band of r_c^2 are
+// decided by the exact FP64 definition in both forms.
+#include <cmath>
+#include <cstring>
+
+#include "lj_forms.cuh"
+
+namespace lj {
+namespace {
+
+constexpr int kVjpTpi = 8;
+constexpr int kVjpThreads = 256;
+
+struct VjpCoef {
+    double G1, G2;  // g      = u^4 (G1 u^3 - G2)
+    double H1, H2;  // g'     = u^5 (H2 - H1 u^3)
+    double S1, S2;  // dg/ds  = u^4 (S1 u^3 - S2)   (s = sigma)
+    double inv_eps;
+};
+
+VjpCoef make_coef(double eps, double sigma)
+{
+    const double s2 = sigma * sigma, s5 = s2 * s2 * sigma, s6 = s5 * sigma, s11 = s5 * s6,
+                 s12 = s6 * s6;
+    VjpCoef C;
+    C.G1 = 48.0 * eps * s12;
+    C.G2 = 24.0 * eps * s6;
+    C.H1 = 336.0 * eps * s12;
+    C.H2 = 96.0 * eps * s6;
+    C.S1 = 576.0 * eps * s11;
+    C.S2 = 144.0 * eps * s5;
+    C.inv_eps = 1.0 / eps;
+    return C;
+}
+
+__device__ __forceinline__ void load_r3(const double *__restrict__ R4, int i, double &x, double &y,
+                                        double &z)
+{
+    double w;
+    asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+        : "=d"(x), "=d"(y), "=d"(z), "=d"(w)
+        : "l"(R4 + 4 * static_cast<int64_t>(i)));
+}
+
+// Block reduction of two doubles into partial[2 * blockIdx.x + {0, 1}].
+__device__ __forceinline__ void block_pair_sum(double a, double b, double *__restrict__ partial)
+{
+    __shared__ double red[2][kVjpThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = a;
+        red[1][threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int w = 0; w < kVjpThreads / 32; ++w) {
+            sa += red[0][w];
+            sb += red[1][w];
+        }
+        partial[2 * blockIdx.x + 0] = sa;
+        partial[2 * blockIdx.x + 1] = sb;
+    }
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(kVjpThreads)
+vjp_fp64_kernel(const double *__restrict__ q4, const double *__restrict__ R4, int n,
+                const int *__restrict__ row_ptr, const int *__restrict__ col, Fp64Params P,
+                VjpCoef C, double *__restrict__ gq4, double *__restrict__ partial)
+{
+    constexpr int TPI = kVjpTpi;
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
+    const int sub = threadIdx.x & (TPI - 1);
+    const unsigned gm = group_mask<TPI>();
+    double ge = 0.0, gs = 0.0;
+    if (gid < n) {
+        const int i = gid;
+        double xi, yi, zi, Rxi, Ryi, Rzi;
+        load_q4_256(q4, i, xi, yi, zi);
+        load_r3(R4, i, Rxi, Ryi, Rzi);
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        const int kb = row_ptr[i], ke = row_ptr[i + 1];
+        for (int base = kb; base < ke; base += TPI) {
+            const int k = base + sub;
+            const bool valid = k < ke;
+            const int j = valid ? col[k] : i;
+            double xj, yj, zj;
+            load_q4_256(q4, j, xj, yj, zj);
+            double dx = xj - xi, dy = yj - yi, dz = zj - zi;
+            min_image3(dx, dy, dz, P.L, P.half_bits, gm);
+            double s = fma(dz, dz, fma(dy, dy, dx * dx));
+            const long long sb = __double_as_longlong(s);
+            bool in = valid && sb < P.rc2_bits;
+            const bool near = valid && static_cast<unsigned long long>(sb - P.rc2_bits + 64) < 128ull;
+            if (__any_sync(gm, near)) {
+                if (near) in = exact_in_cutoff(dx, dy, dz, P.rc2);
+            }
+            if (!valid) s = 1.0;
+            if (__any_sync(gm, in)) {
+                double Rxj, Ryj, Rzj;
+                load_r3(R4, j, Rxj, Ryj, Rzj);
+                const double u = rcp_fp64(s, gm);
+                const double u2 = u * u, u3 = u2 * u, u4 = u2 * u2, u5 = u4 * u;
+                const double g = u4 * fma(C.G1, u3, -C.G2);
+                const double gp = u5 * fma(-C.H1, u3, C.H2);
+                const double dgs = u4 * fma(C.S1, u3, -C.S2);
+                const double wx = Rxj - Rxi, wy = Ryj - Ryi, wz = Rzj - Rzi;
+                const double rw = fma(dz, wz, fma(dy, wy, dx * wx));
+                const double t = 2.0 * gp * rw;
+                const double cx = fma(g, wx, t * dx), cy = fma(g, wy, t * dy),
+                             cz = fma(g, wz, t * dz);
+                if (in) {
+                    ax -= cx;
+                    ay -= cy;
+                    az -= cz;
+                    ge = fma(g, rw, ge);
+                    gs = fma(dgs, rw, gs);
+                    if (HALF) {
+                        atomicAdd(gq4 + 4 * static_cast<int64_t>(j) + 0, cx);
+                        atomicAdd(gq4 + 4 * static_cast<int64_t>(j) + 1, cy);
+                        atomicAdd(gq4 + 4 * static_cast<int64_t>(j) + 2, cz);
+                    }
+                }
+            }
+        }
+        ax = group_sum<TPI>(ax);
+        ay = group_sum<TPI>(ay);
+        az = group_sum<TPI>(az);
+        if (sub == 0) {
+            double *g = gq4 + 4 * static_cast<int64_t>(i);
+            if (HALF) {
+                atomicAdd(g + 0, ax);
+                atomicAdd(g + 1, ay);
+                atomicAdd(g + 2, az);
+            } else {
+                g[0] = ax;
+                g[1] = ay;
+                g[2] = az;
+                g[3] = 0.0;
+            }
+        }
+    }
+    block_pair_sum(ge, gs, partial);
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(kVjpThreads)
+vjp_mixed_kernel(const double *__restrict__ q4, const float4 *__restrict__ rel,
+                 const double *__restrict__ R4, int n, const int *__restrict__ row_ptr,
+                 const int *__restrict__ col, MixedParams P, float G1, float G2, float H1,
+                 float H2, float S1, float S2, double *__restrict__ gq4,
+                 double *__restrict__ partial)
+{
+    constexpr int TPI = kVjpTpi;
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
+    const int sub = threadIdx.x & (TPI - 1);
+    const unsigned gm = group_mask<TPI>();
+    float es = 0.f, ec = 0.f, ss = 0.f, sc = 0.f;  // Kahan sums of g (d.w), dg/dsigma (d.w)
+    if (gid < n) {
+        const int i = gid;
+        const float4 pi = rel[i];
+        const int ci = __float_as_int(pi.w);
+        const int cix = ci & 1023, ciy = (ci >> 10) & 1023, ciz = ci >> 20;
+        double Rxd, Ryd, Rzd;
+        load_r3(R4, i, Rxd, Ryd, Rzd);
+        const float Rxi = static_cast<float>(Rxd), Ryi = static_cast<float>(Ryd),
+                    Rzi = static_cast<float>(Rzd);
+        float sx = 0.f, sy = 0.f, sz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
+        const int kb = row_ptr[i], ke = row_ptr[i + 1];
+        for (int base = kb; base < ke; base += TPI) {
+            const int k = base + sub;
+            const bool valid = k < ke;
+            const int j = valid ? col[k] : i;
+            const float4 pj = rel[j];
+            const int cj = __float_as_int(pj.w);
+            const float dx = mixed_disp(pj.x, pi.x, cj & 1023, cix, P.h[0], P.hLf[0], P.nc[0], P.nhalf[0], P.wrap_fix);
+            const float dy = mixed_disp(pj.y, pi.y, (cj >> 10) & 1023, ciy, P.h[1], P.hLf[1], P.nc[1], P.nhalf[1], P.wrap_fix);
+            const float dz = mixed_disp(pj.z, pi.z, cj >> 20, ciz, P.h[2], P.hLf[2], P.nc[2], P.nhalf[2], P.wrap_fix);
+            float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            bool in = valid && s < P.rc2f;
+            const bool near = valid && fabsf(s - P.rc2f) <= P.band;
+            if (__any_sync(gm, near)) {
+                if (near) {
+                    double xi, yi, zi, xj, yj, zj;
+                    load_xyz(q4, i, xi, yi, zi);
+                    load_xyz(q4, j, xj, yj, zj);
+                    const double ex = min_image(xj - xi, P.L[0], P.half_bits[0]);
+                    const double ey = min_image(yj - yi, P.L[1], P.half_bits[1]);
+                    const double ez = min_image(zj - zi, P.L[2], P.half_bits[2]);
+                    in = exact_in_cutoff(ex, ey, ez, P.rc2);
+                }
+            }
+            if (!valid) s = 1.0f;
+            if (in) {
+                double Rxj, Ryj, Rzj;
+                load_r3(R4, j, Rxj, Ryj, Rzj);
+                const float u = rcp_fp32(s);
+                const float u2 = u * u, u3 = u2 * u, u4 = u2 * u2, u5 = u4 * u;
+                const float g = u4 * fmaf(G1, u3, -G2);
+                const float gp = u5 * fmaf(-H1, u3, H2);
+                const float dgs = u4 * fmaf(S1, u3, -S2);
+                const float wx = static_cast<float>(Rxj) - Rxi, wy = static_cast<float>(Ryj) - Ryi,
+                            wz = static_cast<float>(Rzj) - Rzi;
+                const float rw = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
+                const float t = 2.0f * gp * rw;
+                const float cx = fmaf(g, wx, t * dx), cy = fmaf(g, wy, t * dy), cz = fmaf(g, wz, t * dz);
+                kahan_add(sx, kx, -cx);
+                kahan_add(sy, ky, -cy);
+                kahan_add(sz, kz, -cz);
+                kahan_add(es, ec, g * rw);
+                kahan_add(ss, sc, dgs * rw);
+                if (HALF) {
+                    atomicAdd(gq4 + 4 * static_cast<int64_t>(j) + 0, static_cast<double>(cx));
+                    atomicAdd(gq4 + 4 * static_cast<int64_t>(j) + 1, static_cast<double>(cy));
+                    atomicAdd(gq4 + 4 * static_cast<int64_t>(j) + 2, static_cast<double>(cz));
+                }
+            }
+        }
+        group_kahan<TPI>(sx, kx);
+        group_kahan<TPI>(sy, ky);
+        group_kahan<TPI>(sz, kz);
+        if (sub == 0) {
+            const double ax = static_cast<double>(sx) - static_cast<double>(kx);
+            const double ay = static_cast<double>(sy) - static_cast<double>(ky);
+            const double az = static_cast<double>(sz) - static_cast<double>(kz);
+            double *g = gq4 + 4 * static_cast<int64_t>(i);
+            if (HALF) {
+                atomicAdd(g + 0, ax);
+                atomicAdd(g + 1, ay);
+                atomicAdd(g + 2, az);
+            } else {
+                g[0] = ax;
+                g[1] = ay;
+                g[2] = az;
+                g[3] = 0.0;
+            }
+        }
+    }
+    block_pair_sum(static_cast<double>(es) - static_cast<double>(ec),
+                   static_cast<double>(ss) - static_cast<double>(sc), partial);
+}
+
+// grads[0] = scale * inv_eps * sum(partial[2b]), grads[1] = scale * sum(partial[2b+1]),
+// summed in a fixed order.
+__global__ void vjp_final_kernel(const double *__restrict__ partial, int blocks, double scale,
+                                 double inv_eps, double *__restrict__ grads)
+{
+    __shared__ double red[2][32];
+    double a = 0.0, b = 0.0;
+    for (int t = threadIdx.x; t < blocks; t += blockDim.x) {
+        a += partial[2 * t];
+        b += partial[2 * t + 1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = a;
+        red[1][threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int w = 0; w < int(blockDim.x / 32); ++w) {
+            sa += red[0][w];
+            sb += red[1][w];
+        }
+        grads[0] = scale * inv_eps * sa;
+        grads[1] = scale * sb;
+    }
+}
+
+int vjp_blocks(int64_t n) { return int((n * kVjpTpi + kVjpThreads - 1) / kVjpThreads); }
+
+}  // namespace
+
+int check_force_args(const double *q4, const double *p4, int64_t n, const int32_t *row_ptr,
+                     const int32_t *col, int64_t nnz, double r_cut, const double box[3], double eps,
+                     double sigma, double dt);
+
+}  // namespace lj
+
+extern "C" size_t lj_force_vjp_workspace_bytes(int64_t n, int precision)
+{
+    const size_t blocks = size_t(lj::vjp_blocks(n > 0 ? n : 1));
+    size_t bytes = 2 * blocks * sizeof(double) + 256;
+    if (precision == LJ_MIXED) bytes += size_t(n > 0 ? n : 1) * sizeof(float4) + 256;
+    return bytes;
+}
+
+extern "C" int lj_force_vjp(const double *q4_dev, const double *gradF4_dev, int64_t n,
+                            const int32_t *row_ptr_dev, const int32_t *col_dev, int64_t nnz,
+                            int half, double r_cut, const double box[3], double eps, double sigma,
+                            int precision, double *gradq4_dev, double *grad_eps_sigma_dev,
+                            void *workspace_dev, size_t workspace_bytes, void *stream)
+{
+    using namespace lj;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_force_args(q4_dev, gradq4_dev, n, row_ptr_dev, col_dev, nnz, r_cut, box, eps,
+                              sigma, 1.0);
+    if (rc != LJ_OK) return rc;
+    if (!grad_eps_sigma_dev || (n > 0 && !gradF4_dev)) return LJ_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(gradF4_dev) & 31u) return LJ_ERR_ARG;
+    if (precision != LJ_FP64 && precision != LJ_MIXED) return LJ_ERR_ARG;
+    if (n == 0) {
+        LJ_TRY_CUDA(cudaMemsetAsync(grad_eps_sigma_dev, 0, 2 * sizeof(double), st));
+        return LJ_OK;
+    }
+    if (!workspace_dev || workspace_bytes < lj_force_vjp_workspace_bytes(n, precision))
+        return LJ_ERR_CAPACITY;
+    const int ni = static_cast<int>(n);
+    const int blocks = vjp_blocks(n);
+    Carver c(workspace_dev);
+    double *partial = c.take<double>(2 * size_t(blocks));
+    if (half || nnz == 0)
+        LJ_TRY_CUDA(cudaMemsetAsync(gradq4_dev, 0, size_t(n) * 4 * sizeof(double), st));
+    if (precision == LJ_FP64) {
+        const Fp64Params P = make_fp64_params(box, 1.0, r_cut, eps, sigma);
+        const VjpCoef C = make_coef(eps, sigma);
+        if (half)
+            vjp_fp64_kernel<true><<<blocks, kVjpThreads, 0, st>>>(q4_dev, gradF4_dev, ni, row_ptr_dev,
+                                                                   col_dev, P, C, gradq4_dev, partial);
+        else
+            vjp_fp64_kernel<false><<<blocks, kVjpThreads, 0, st>>>(q4_dev, gradF4_dev, ni, row_ptr_dev,
+                                                                    col_dev, P, C, gradq4_dev, partial);
+        LJ_TRY_LAUNCH("vjp_fp64_kernel");
+    } else {
+        const MixedParams P = make_mixed_params(box, 1.0, r_cut, eps, sigma);
+        const VjpCoef C = make_coef(eps, sigma);
+        float4 *rel = c.take<float4>(size_t(n));
+        mixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, ni, P, rel);
+        LJ_TRY_LAUNCH("mixed_prepass_kernel");
+        const float G1 = float(C.G1), G2 = float(C.G2), H1 = float(C.H1), H2 = float(C.H2),
+                    S1 = float(C.S1), S2 = float(C.S2);
+        if (half)
+            vjp_mixed_kernel<true><<<blocks, kVjpThreads, 0, st>>>(q4_dev, rel, gradF4_dev, ni, row_ptr_dev,
+                                                                    col_dev, P, G1, G2, H1, H2, S1, S2,
+                                                                    gradq4_dev, partial);
+        else
+            vjp_mixed_kernel<false><<<blocks, kVjpThreads, 0, st>>>(q4_dev, rel, gradF4_dev, ni, row_ptr_dev,
+                                                                     col_dev, P, G1, G2, H1, H2, S1, S2,
+                                                                     gradq4_dev, partial);
+        LJ_TRY_LAUNCH("vjp_mixed_kernel");
+    }
+    const double scale = half ? 1.0 : 0.5;
+    vjp_final_kernel<<<1, 1024, 0, st>>>(partial, blocks, scale, 1.0 / eps, grad_eps_sigma_dev);
+    LJ_TRY_LAUNCH("vjp_final_kernel");
+    return LJ_OK;
+}

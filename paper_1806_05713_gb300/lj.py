@@ -27,7 +27,8 @@ LJ_ERR_DEVICE = 6
 LJ_FP64 = 0
 LJ_MIXED = 1
 LJ_TPI_AUTO = 0
-LJ_SCHED_STREAM = 64
+LJ_SCHED_REFILL = 64
+LJ_SCHED_SWP2 = 128
 LJ_STATIC_MAX_ATOMS = 131072
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liblj_gb300.so")
@@ -36,6 +37,29 @@ _lib = None
 _i64, _dbl, _int, _vp, _sz = ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
 _dbl3 = ctypes.c_double * 3
 _i64p = ctypes.POINTER(ctypes.c_int64)
+
+class LjSystem(ctypes.Structure):
+    """Mirror of the C struct lj_system."""
+    _fields_ = [("atom_offset", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("row_offset", ctypes.c_int64), ("entry_offset", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("box", ctypes.c_double * 3), ("r_cut", ctypes.c_double),
+                ("eps", ctypes.c_double), ("sigma", ctypes.c_double), ("half", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class LjBatch(ctypes.Structure):
+    """Mirror of the C struct lj_batch."""
+    _fields_ = [("plan_dev", ctypes.c_void_p), ("plan_bytes", ctypes.c_size_t),
+                ("nitems", ctypes.c_int64), ("total_atoms", ctypes.c_int64),
+                ("dt", ctypes.c_double), ("nsys", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("tpi", ctypes.c_int32), ("rows_per_item", ctypes.c_int32),
+                ("blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_sysp = ctypes.POINTER(LjSystem)
+_batchp = ctypes.POINTER(LjBatch)
+_intp = ctypes.POINTER(ctypes.c_int)
+_fltp = ctypes.POINTER(ctypes.c_float)
 
 # (name, restype, argtypes) of every exported entry point.
 SIGNATURES = {
@@ -51,6 +75,17 @@ SIGNATURES = {
     "lj_force_workspace_bytes": (_sz, [_i64, _dbl3, _int]),
     "lj_force": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl, _dbl3, _dbl, _dbl, _int,
                         _int, _vp, _sz, _vp]),
+    "lj_batch_plan_bytes": (_sz, [_sysp, _int, _int]),
+    "lj_batch_init": (_int, [_batchp, _sysp, _int, _dbl, _int, _int, _int, _vp, _sz, _vp]),
+    "lj_force_batched_workspace_bytes": (_sz, [_batchp]),
+    "lj_force_batched": (_int, [_batchp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "lj_autotune_force": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl, _dbl3, _dbl, _dbl,
+                                 _int, _intp, _int, _int, _vp, _sz, _intp, _fltp, _fltp, _vp]),
+    "lj_autotune_batched": (_int, [_sysp, _int, _dbl, _int, _intp, _int, _intp, _int, _vp, _vp, _vp,
+                                   _vp, _vp, _sz, _vp, _sz, _int, _intp, _intp, _fltp, _vp]),
+    "lj_force_vjp_workspace_bytes": (_sz, [_i64, _int]),
+    "lj_force_vjp": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl3, _dbl, _dbl, _int,
+                            _vp, _vp, _vp, _sz, _vp]),
     "lj_energy_workspace_bytes": (_sz, [_i64]),
     "lj_energy": (_int, [_vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl3, _dbl, _dbl, _int, _vp, _vp,
                          _sz, _vp]),
@@ -275,3 +310,58 @@ def lj_energy(q4: torch.Tensor, plist: PairList, r_cut: float, box, eps: float =
                        workspace.numel(), _stream(stream))
     _check(st, "lj_energy")
     return out
+
+
+def lj_force_vjp_workspace_bytes(n: int, precision: int = LJ_FP64) -> int:
+    return int(load().lj_force_vjp_workspace_bytes(int(n), int(precision)))
+
+
+def lj_force_vjp(q4: torch.Tensor, gradF4: torch.Tensor, plist: PairList, r_cut: float, box,
+                 eps: float = 1.0, sigma: float = 1.0, precision: int = LJ_FP64,
+                 gradq4: torch.Tensor | None = None, grad_eps_sigma: torch.Tensor | None = None,
+                 workspace: torch.Tensor | None = None, stream=None):
+    """(dLoss/dq (n, 4), dLoss/d(eps, sigma) (2,)) for dLoss/dF = gradF4."""
+    lib = load()
+    n = plist.n
+    if gradq4 is None:
+        gradq4 = torch.empty((n, 4), dtype=torch.float64, device=q4.device)
+    if grad_eps_sigma is None:
+        grad_eps_sigma = torch.empty(2, dtype=torch.float64, device=q4.device)
+    if workspace is None:
+        workspace = _workspace(lib.lj_force_vjp_workspace_bytes(n, int(precision)), q4.device)
+    st = lib.lj_force_vjp(_dev(q4, torch.float64, "q4", (n, 4)),
+                          _dev(gradF4, torch.float64, "gradF4", (n, 4)), n,
+                          plist.row_ptr.data_ptr(), plist.col.data_ptr(), plist.nnz,
+                          int(plist.half), float(r_cut), _box3(box), float(eps), float(sigma),
+                          int(precision), _dev(gradq4, torch.float64, "gradq4", (n, 4)),
+                          _dev(grad_eps_sigma, torch.float64, "grad_eps_sigma", (2,)),
+                          workspace.data_ptr(), workspace.numel(), _stream(stream))
+    _check(st, "lj_force_vjp")
+    return gradq4, grad_eps_sigma
+
+
+def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float, box,
+                      eps: float = 1.0, sigma: float = 1.0, precision: int = LJ_FP64,
+                      candidates=None, reps: int = 5, stream=None):
+    """Fastest schedule among `candidates` for this system and list (times
+    each with CUDA events on a scratch momentum array).  Returns
+    (best_tpi, best_ms, {tpi: ms})."""
+    lib = load()
+    if candidates is None:
+        candidates = ([8, 4, 16, 32, LJ_SCHED_SWP2 | 4, LJ_SCHED_SWP2 | 8, LJ_SCHED_SWP2 | 16,
+                       LJ_SCHED_REFILL] if precision == LJ_FP64 else [1, 2, 4, 8, 16, 32])
+    n = plist.n
+    scratch = torch.zeros((n, 4), dtype=torch.float64, device=q4.device)
+    ws = _workspace(lib.lj_force_workspace_bytes(n, _box3(box), int(precision)), q4.device)
+    arr = (ctypes.c_int * len(candidates))(*candidates)
+    ms = (ctypes.c_float * len(candidates))()
+    best = ctypes.c_int(0)
+    best_ms = ctypes.c_float(0)
+    st = lib.lj_autotune_force(_dev(q4, torch.float64, "q4", (n, 4)), scratch.data_ptr(), n,
+                               plist.row_ptr.data_ptr(), plist.col.data_ptr(), plist.nnz,
+                               int(plist.half), float(dt), float(r_cut), _box3(box), float(eps),
+                               float(sigma), int(precision), arr, len(candidates), int(reps),
+                               ws.data_ptr(), ws.numel(), ctypes.byref(best), ctypes.byref(best_ms),
+                               ms, _stream(stream))
+    _check(st, "lj_autotune_force")
+    return int(best.value), float(best_ms.value), {c: float(m) for c, m in zip(candidates, ms)}

@@ -1,0 +1,106 @@
+"""Batched persistent launch (lj_force_batched) vs the oracle per system,
+vs per-system launches, under CUDA-graph replay, and after autotuning."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1806_05713_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-5
+
+
+def _oracle_dp(oracle_lib, s, dt, half):
+    rp, col = oracle_lib.pairlist(s.q, s.box, s.rs, half)
+    return oracle_lib.force(s.q, np.zeros((s.n, 3)), rp, col, half, dt, s.rc, s.box)
+
+
+def _per_system(b, p):
+    out = p.cpu().numpy()
+    return [out[int(o):int(o) + s.n, :3] for o, s in zip(b.atom_offset, b.systems)]
+
+
+@pytest.fixture(scope="module")
+def systems():
+    return inputs.batched_systems(nsys=24, seed=5, n_min=500, n_max=6000)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+@pytest.mark.parametrize("half", [True, False])
+def test_batched_matches_oracle_per_system(cuda_lib, oracle_lib, systems, precision, tol, half):
+    from paper_1806_05713_gb300.batch import Batch
+    b = Batch(systems, 0.01, precision, half, tpi=8, rows_per_item=32)
+    b.force()
+    torch.cuda.synchronize()
+    for s, got in zip(systems, _per_system(b, b.p4)):
+        want = _oracle_dp(oracle_lib, s, 0.01, half)
+        assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
+def test_batched_equals_per_system_launches_full_list(cuda_lib, systems):
+    """Full lists are deterministic: the persistent launch gives the same bits
+    as one lj_force call per system with the same lanes per row."""
+    from paper_1806_05713_gb300.batch import Batch
+    b = Batch(systems, 0.01, 0, False, tpi=8, rows_per_item=16)
+    p_a = torch.zeros_like(b.p4)
+    p_b = torch.zeros_like(b.p4)
+    b.force(p_a)
+    b.force_per_system(p_b, tpi=8)
+    torch.cuda.synchronize()
+    assert torch.equal(p_a, p_b)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay(cuda_lib, systems, precision):
+    from paper_1806_05713_gb300.batch import Batch
+    b = Batch(systems, 0.01, precision, False, tpi=4, rows_per_item=64)
+    once = torch.zeros_like(b.p4)
+    b.force(once)
+    p = torch.zeros_like(b.p4)
+    g = b.capture_graph(p)   # capture runs no kernels; the warm-up call adds one update
+    torch.cuda.synchronize()
+    p.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.allclose(p, 2 * once, rtol=0, atol=1e-14 * float(once.abs().max()))
+
+
+def test_autotune_picks_a_valid_schedule(cuda_lib, oracle_lib, systems):
+    from paper_1806_05713_gb300.batch import Batch
+    b = Batch(systems, 0.01, 0, True, tpi=8, rows_per_item=64, plan_rows_min=16)
+    tpi, rows, ms = b.autotune(tpis=(4, 8, 16), rows=(16, 64), reps=3)
+    assert tpi in (4, 8, 16) and rows in (16, 64) and 0 < ms < 1e3
+    b.p4.zero_()
+    b.force()
+    torch.cuda.synchronize()
+    s = systems[3]
+    got = _per_system(b, b.p4)[3]
+    want = _oracle_dp(oracle_lib, s, 0.01, True)
+    assert np.max(np.abs(got - want)) <= FP64_TOL * np.max(np.abs(want))
+
+
+def test_autotune_force_single_system(cuda_lib):
+    lj = cuda_lib
+    s = inputs.workload_small()
+    q = torch.from_numpy(s.q).cuda()
+    pl = lj.lj_build_pairlist(q, s.box, s.rs, True)
+    best, ms, table = lj.lj_autotune_force(q, pl, 0.01, s.rc, s.box, reps=3)
+    assert best in table and ms == min(table.values()) and np.isfinite(ms)
+
+
+@pytest.mark.slow
+def test_full_batch_sampled_systems(cuda_lib, oracle_lib):
+    """512 systems (N log-uniform 500..32000): the bench's batch, checked on
+    sampled systems against the oracle."""
+    from paper_1806_05713_gb300.batch import Batch
+    systems = inputs.batched_systems(nsys=512, seed=0)
+    b = Batch(systems, 0.01, 0, True, tpi=8, rows_per_item=64)
+    b.force()
+    torch.cuda.synchronize()
+    got = _per_system(b, b.p4)
+    for k in (0, 1, 97, 255, 300, 511):
+        want = _oracle_dp(oracle_lib, systems[k], 0.01, True)
+        assert np.max(np.abs(got[k] - want)) <= FP64_TOL * np.max(np.abs(want))
