@@ -148,6 +148,22 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest x over all ranks (all-reduce MAX); x itself when world = 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def workload(rank: int, order: str):
     from paper_1806_05713_gb300 import inputs
     return inputs.fcc_system(31, 1.0, 0.05, seed=rank, order=order, rc=RC, margin=MARGIN)
@@ -325,13 +341,9 @@ def main():
     launches = lib.lj_kernel_launch_count() - launches0
     if world > 1:
         dist.barrier()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    pairs = FORCE_CALLS * nnz * args.steps * world
-    value = pairs / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    pairs_rank = FORCE_CALLS * nnz * args.steps
+    value = whole_job_rate(pairs_rank, world, total_ms)
 
     # ---- end to end through the public API, host buffers --------------------
     q_host = torch.from_numpy(s.q).pin_memory()
@@ -352,12 +364,8 @@ def main():
         e1.synchronize()
         if it >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = pairs / (e2e_total / 1e3)
+    e2e_total = max_over_ranks(sum(e2e_ms), world, dev)
+    e2e_value = whole_job_rate(pairs_rank, world, e2e_total)
 
     if rank != 0:
         if world > 1:
@@ -423,11 +431,17 @@ def main():
 
 
 def schedule_name(tpi: int) -> str:
-    if tpi == 64:
-        return "lane-refill"
+    t = tpi & 63
+    name = f"{max(t, 1)} lanes/row"
+    if tpi & 256:
+        name = f"lane-queue, {name}"
+    if tpi & 64:
+        name = f"group-refill, {name}"
     if tpi & 128:
-        return f"{tpi & 127} lanes/row, 2 entries/lane (software-pipelined)"
-    return f"{tpi} lanes/row"
+        name += ", 2 entries/lane (software-pipelined)"
+    if tpi & 512:
+        name += ", rows by length"
+    return name
 
 
 def extra_million(lj, dev, stream, flush):
@@ -443,7 +457,7 @@ def extra_million(lj, dev, stream, flush):
     res = {"n_atoms": s.n, "pairs_per_call": pl.nnz, "list_build_ms": t_list}
     best, _, _ = lj.lj_autotune_force(q, pl, DT, s.rc, box, reps=3)
     out = {}
-    for name, prec, tpis in (("fp64", lj.LJ_FP64, (best,)), ("mixed", lj.LJ_MIXED, (4, 8, 16))):
+    for name, prec, tpis in (("fp64", lj.LJ_FP64, (best,)), ("mixed", lj.LJ_MIXED, (4, 8, 516, 520))):
         for t in tpis:
             pp = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
             fn = lj.lj_force_prepared(q, pp, pl, DT, s.rc, box, precision=prec, tpi=t)
@@ -567,7 +581,7 @@ def variants(lj, s, q, pl_half, box, dev, stream, flush):
             res[f"list_build_ms/{order}/{kind}"] = t_list
             p64 = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
             ref = None
-            for prec, tpis in ((lj.LJ_FP64, (136, 8, 144, 64)), (lj.LJ_MIXED, (4, 8, 16))):
+            for prec, tpis in ((lj.LJ_FP64, (136, 648, 644, 200)), (lj.LJ_MIXED, (4, 8, 516, 520))):
                 for tpi in tpis:
                     pp = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
                     fn = lj.lj_force_prepared(qq, pp, pl, DT, sys_.rc, box, precision=prec, tpi=tpi)

@@ -57,8 +57,9 @@ extern "C" {
 
 /* ---- arithmetic forms of the force kernels ----------------------------- */
 #define LJ_FP64 0  /* every step in IEEE double precision */
-#define LJ_MIXED 1 /* FP32 pair arithmetic; cell-relative displacement derived
-                      from the FP64 positions; compensated FP32 per-i sums and
+#define LJ_MIXED 1 /* FP32 pair arithmetic; the displacement formed exactly in
+                      32-bit fixed point derived from the FP64 positions and
+                      rounded once to FP32; compensated FP32 per-i sums and
                       FP64 momentum updates */
 
 /* ---- schedules ---------------------------------------------------------- */
@@ -66,16 +67,31 @@ extern "C" {
  * row and reduce their partial sums with warp shuffles; 0 = library default
  * (8 lanes per row). */
 #define LJ_TPI_AUTO 0
-/* LJ_SCHED_REFILL: the FP64 lane-refill schedule (the FP64 default).  Each
- * lane owns one row, keeps its q_i and p_i sum in registers, and takes the
- * next row as soon as its own ends (rows are handed out to warps in chunks
- * of 32 from a counter in the workspace), so no lane waits for a longer row
- * of its warp; a persistent grid of one launch. */
+/* LJ_SCHED_REFILL | t (t = 1, 4 or 8; FP64 only): the group-refill schedule.
+ * Each group of t lanes owns one row at a time and takes the next row as
+ * soon as its own ends (rows are handed to warps in chunks from a counter in
+ * the workspace), so no group waits for a longer row of its warp; a
+ * persistent grid of one launch.  Half lists add each lane's partial sums to
+ * p_i with FP64 atomics. */
 #define LJ_SCHED_REFILL 64
-/* LJ_SCHED_SWP2 | tpi (tpi = 4, 8 or 16; FP64 only): software pipelining,
- * the paper's section "Software Pipelining" -- each lane carries two
- * independent entries per iteration so that their FP64 chains overlap. */
+/* LJ_SCHED_SWP2 | tpi (tpi = 4, 8 or 16, or with LJ_SCHED_REFILL | 1, 4, 8;
+ * FP64 only): software pipelining, the paper's section "Software
+ * Pipelining" -- each lane carries two independent entries per iteration so
+ * that their FP64 chains overlap. */
 #define LJ_SCHED_SWP2 128
+/* LJ_SCHED_QUEUE | t (t = 1, 2, 4 or 8; FP64 only): the lane-queue schedule.
+ * Groups of t lanes take rows as in LJ_SCHED_REFILL; each lane screens the
+ * entries of its share of the row (d, r^2, cutoff) into its own FIFO of
+ * in-cutoff pairs in shared memory, and the force arithmetic runs only when
+ * every lane with work holds a queued pair, so no FP64 instruction is spent
+ * on margin pairs, row tails or idle groups.  Half lists add p_i by FP64
+ * atomics per lane and row. */
+#define LJ_SCHED_QUEUE 256
+/* LJ_SCHED_SORTED | (a row-group schedule, FP64 or mixed): rows are walked
+ * in order of decreasing length (a counting sort of the row lengths in the
+ * workspace, three small kernels per call), so the groups of a warp walk
+ * rows of equal length and none waits for a longer one. */
+#define LJ_SCHED_SORTED 512
 
 const char *lj_status_string(int status);
 /* Text of the last CUDA error seen by this library in this thread. */
@@ -162,9 +178,9 @@ int lj_build_pairlist_static(const double *q4_dev, int64_t n, const double box[3
 /* Force (Algorithm 1 inside Algorithm 3)                                    */
 /* ======================================================================== */
 
-/* Bytes of device workspace lj_force needs: 256 for LJ_FP64 (a row counter
- * of the lane-refill schedule), 16 n + 256 for LJ_MIXED (cell-relative FP32
- * positions). */
+/* Bytes of device workspace lj_force needs (about 8 n + 2.5 KB for LJ_FP64:
+ * a row counter and the length-sorted row order; 16 n more for LJ_MIXED:
+ * fixed-point positions). */
 size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
 
 /*
@@ -182,12 +198,15 @@ size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
  *  box              host, 3 box sides.
  *  eps, sigma       Eq. (1) parameters (> 0).
  *  precision        LJ_FP64 or LJ_MIXED.
- *  tpi              LJ_TPI_AUTO, 1..32 (power of two), LJ_SCHED_REFILL or
- *                   LJ_SCHED_SWP2 | 4, 8, 16 (the last two FP64 only).
+ *  tpi              LJ_TPI_AUTO, 1..32 (power of two), LJ_SCHED_SWP2 | 4, 8,
+ *                   16, LJ_SCHED_REFILL | 1, 4, 8 (optionally | SWP2), or
+ *                   LJ_SCHED_QUEUE | 1, 2, 4, 8; the last three families
+ *                   FP64 only.  LJ_SCHED_SORTED may be or-ed into the plain
+ *                   and SWP2 schedules.
  *  workspace_dev    scratch of lj_force_workspace_bytes() (NULL if 0).
  * Half lists add p_j with FP64 atomics, so their rounding order (not their
  * value beyond the last bits) varies between calls; full lists are
- * deterministic.  Asynchronous.  Errors: LJ_ERR_ARG, LJ_ERR_BOX,
+ * deterministic except under LJ_SCHED_REFILL | 1 and LJ_SCHED_QUEUE.  Asynchronous.  Errors: LJ_ERR_ARG, LJ_ERR_BOX,
  * LJ_ERR_CAPACITY (workspace too small), LJ_ERR_CUDA.
  */
 int lj_force(const double *q4_dev, double *p4_dev, int64_t n, const int32_t *row_ptr_dev,

@@ -67,10 +67,10 @@ long long count_items(const lj_system *systems, int nsys, int rpi)
     return items;
 }
 
-// Per-atom cell-relative FP32 positions of every system (MIXED form):
-// one block per work item, one thread per row of the item.
+// Per-atom fixed-point positions of every system (MIXED form): one block
+// per work item, one thread per row of the item.
 __global__ void batched_prepass_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ items,
-                                       const double *__restrict__ q4, float4 *__restrict__ rel)
+                                       const double *__restrict__ q4, uint4 *__restrict__ rel)
 {
     const Item it = items[blockIdx.x];
     const SysDev &S = sys[it.sys];
@@ -78,23 +78,16 @@ __global__ void batched_prepass_kernel(const SysDev *__restrict__ sys, const Ite
         const long long a = S.atom_off + r;
         double x[3];
         load_xyz(q4, a, x[0], x[1], x[2]);
-        int c[3];
-        float rr[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            int ca = static_cast<int>(x[d] * S.mp.inv_h[d]);
-            ca = ca < 0 ? 0 : (ca >= S.mp.nc[d] ? S.mp.nc[d] - 1 : ca);
-            c[d] = ca;
-            rr[d] = __double2float_rn(x[d] - ca * S.mp.hd[d]);
-        }
-        rel[a] = make_float4(rr[0], rr[1], rr[2], __int_as_float(c[0] | (c[1] << 10) | (c[2] << 20)));
+        rel[a] = make_uint4(__double2uint_rz(x[0] * S.mp.to_fixed[0]),
+                            __double2uint_rz(x[1] * S.mp.to_fixed[1]),
+                            __double2uint_rz(x[2] * S.mp.to_fixed[2]), 0u);
     }
 }
 
 template <int TPI, bool MIXED>
 __global__ void __launch_bounds__(kBatchThreads)
 batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ items,
-                     long long nitems, const double *__restrict__ q4, const float4 *__restrict__ rel,
+                     long long nitems, const double *__restrict__ q4, const uint4 *__restrict__ rel,
                      double *__restrict__ p4, const int *__restrict__ row_ptr,
                      const int *__restrict__ col, unsigned long long *__restrict__ counter)
 {
@@ -117,7 +110,7 @@ batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ it
             const int r = r0 + lane / TPI;
             if (r < I.row_end) {  // uniform within a group
                 if (MIXED) {
-                    const float4 *srel = rel + S.atom_off;
+                    const uint4 *srel = rel + S.atom_off;
                     const MixedParams P = S.mp;
                     if (half)
                         mixed_row<TPI, true>(sq, srel, sp, srp, scol, r, P);
@@ -136,7 +129,7 @@ batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ it
 }
 
 template <bool MIXED>
-int launch_batched(const lj_batch *b, const PlanView &v, const double *q4, const float4 *rel,
+int launch_batched(const lj_batch *b, const PlanView &v, const double *q4, const uint4 *rel,
                    double *p4, const int *rp, const int *col, unsigned long long *counter,
                    cudaStream_t st)
 {
@@ -275,7 +268,7 @@ extern "C" size_t lj_force_batched_workspace_bytes(const lj_batch *batch)
 {
     if (!batch) return 0;
     size_t bytes = 256;
-    if (batch->precision == LJ_MIXED) bytes += size_t(batch->total_atoms) * sizeof(float4) + 256;
+    if (batch->precision == LJ_MIXED) bytes += size_t(batch->total_atoms) * sizeof(uint4) + 256;
     return bytes;
 }
 
@@ -296,7 +289,7 @@ extern "C" int lj_force_batched(const lj_batch *batch, const double *q4_dev, dou
     unsigned long long *counter = c.take<unsigned long long>(1);
     LJ_TRY_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
     if (batch->precision == LJ_MIXED) {
-        float4 *rel = c.take<float4>(size_t(batch->total_atoms));
+        uint4 *rel = c.take<uint4>(size_t(batch->total_atoms));
         batched_prepass_kernel<<<unsigned(batch->nitems), 128, 0, st>>>(v.sys, v.items, q4_dev, rel);
         LJ_TRY_LAUNCH("batched_prepass_kernel");
         return launch_batched<true>(batch, v, q4_dev, rel, p4_dev, row_ptr_dev, col_dev, counter, st);

@@ -17,13 +17,16 @@
 //    test are integer compares of IEEE bit patterns, the division is an FP32
 //    seed plus one third-order FP64 correction, and
 //    df = u^4 (A - B u^3) with u = 1/r^2 takes five FP64 operations.
-//  * MIXED: a pre-pass turns each FP64 position into a cell index and an
-//    FP32 offset inside a cell of side ~2-4 sigma (computed in FP64), so the
-//    pair displacement m h + (rel_j - rel_i) is accurate to ~1e-7 absolute
-//    (absolute FP32 coordinates would lose ~1e-5 at L ~ 100).  The pair
-//    arithmetic is FP32, per-lane i-sums are Kahan-compensated FP32,
-//    combined across lanes with error-free transformations and added to the
-//    FP64 momentum once per row; half-list p_j updates are FP64 atomics.
+//  * MIXED: a pre-pass turns each FP64 position into a 32-bit fixed-point
+//    fraction of the box side (X = floor(x 2^32 / L), computed in FP64), so
+//    X_j - X_i in wrapping integer arithmetic is the minimum-image
+//    displacement exactly, and one conversion and one multiply give it in
+//    FP32 to its last bit (absolute FP32 coordinates would lose ~1e-5 at
+//    L ~ 100).  The pair arithmetic is FP32, per-lane i-sums are
+//    Kahan-compensated FP32, combined across lanes with error-free
+//    transformations and added to the FP64 momentum once per row (head and
+//    compensation as two FP64 additions in L2); half-list p_j updates are
+//    FP64 atomics of exactly converted FP32 values.
 // In both forms a pair whose r^2 lies within a proven error band of r_c^2
 // is re-decided with the exact FP64 definition, so the set of interacting
 // pairs is the same as in double precision.
@@ -38,27 +41,84 @@ namespace {
 // ---------------------------------------------------------------------------
 // FP64 form
 // ---------------------------------------------------------------------------
+// order: NULL (rows in index order) or a permutation of the rows (the
+// length-sorted order of LJ_SCHED_SORTED).
 template <int TPI, bool HALF, int U>
 __global__ void __launch_bounds__(256)
 force_fp64_kernel(const double *__restrict__ q4, double *__restrict__ p4, int n,
-                  const int *__restrict__ row_ptr, const int *__restrict__ col, Fp64Params P)
+                  const int *__restrict__ row_ptr, const int *__restrict__ col, Fp64Params P,
+                  const int *__restrict__ order)
 {
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
     // A group past the last row exits as a whole; the votes and shuffles in
     // the row walk name only the group's own lanes, which iterate together.
     if (gid >= n) return;
-    fp64_row<TPI, HALF, U>(q4, p4, row_ptr, col, gid, P, group_mask<TPI>());
+    const int i = order ? order[gid] : gid;
+    fp64_row<TPI, HALF, U>(q4, p4, row_ptr, col, i, P, group_mask<TPI>());
 }
 
 template <int TPI, bool HALF>
 __global__ void __launch_bounds__(256)
-force_mixed_kernel(const double *__restrict__ q4, const float4 *__restrict__ rel,
+force_mixed_kernel(const double *__restrict__ q4, const uint4 *__restrict__ rel,
                    double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
-                   const int *__restrict__ col, MixedParams P)
+                   const int *__restrict__ col, MixedParams P, const int *__restrict__ order)
 {
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
     if (gid >= n) return;
-    mixed_row<TPI, HALF>(q4, rel, p4, row_ptr, col, gid, P);
+    const int i = order ? order[gid] : gid;
+    mixed_row<TPI, HALF>(q4, rel, p4, row_ptr, col, i, P);
+}
+
+// Rows in order of decreasing length (LJ_SCHED_SORTED): a counting sort on
+// min(length, kLenBuckets - 1), so that the groups of one warp walk rows of
+// equal length and none idles while another finishes.
+constexpr int kLenBuckets = 512;
+
+__global__ void row_len_hist_kernel(const int *__restrict__ row_ptr, int n, int *__restrict__ hist,
+                                    int *__restrict__ slot)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int len = min(row_ptr[i + 1] - row_ptr[i], kLenBuckets - 1);
+    slot[i] = atomicAdd(&hist[kLenBuckets - 1 - len], 1);
+}
+
+__global__ void row_len_scan_kernel(int *__restrict__ hist)
+{
+    __shared__ int s[kLenBuckets];
+    const int t = threadIdx.x;
+    s[t] = hist[t];
+    __syncthreads();
+    for (int o = 1; o < kLenBuckets; o <<= 1) {
+        const int v = t >= o ? s[t - o] : 0;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    hist[t] = s[t] - hist[t];  // exclusive
+}
+
+__global__ void row_len_scatter_kernel(const int *__restrict__ row_ptr, int n,
+                                       const int *__restrict__ start, const int *__restrict__ slot,
+                                       int *__restrict__ order)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int len = min(row_ptr[i + 1] - row_ptr[i], kLenBuckets - 1);
+    order[start[kLenBuckets - 1 - len] + slot[i]] = i;
+}
+
+int sort_rows_by_length(const int *row_ptr, int n, int *hist, int *slot, int *order, cudaStream_t st)
+{
+    LJ_TRY_CUDA(cudaMemsetAsync(hist, 0, sizeof(int) * kLenBuckets, st));
+    const unsigned g = unsigned((n + 255) / 256);
+    row_len_hist_kernel<<<g, 256, 0, st>>>(row_ptr, n, hist, slot);
+    LJ_TRY_LAUNCH("row_len_hist_kernel");
+    row_len_scan_kernel<<<1, kLenBuckets, 0, st>>>(hist);
+    LJ_TRY_LAUNCH("row_len_scan_kernel");
+    row_len_scatter_kernel<<<g, 256, 0, st>>>(row_ptr, n, hist, slot, order);
+    LJ_TRY_LAUNCH("row_len_scatter_kernel");
+    return LJ_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -67,28 +127,28 @@ force_mixed_kernel(const double *__restrict__ q4, const float4 *__restrict__ rel
 
 template <int TPI, int U>
 int launch_fp64(const double *q4, double *p4, int n, const int *rp, const int *col, int half,
-                const Fp64Params &P, cudaStream_t st)
+                const Fp64Params &P, const int *order, cudaStream_t st)
 {
     const int64_t threads = int64_t(n) * TPI;
     const unsigned grid = unsigned((threads + 255) / 256);
     if (half)
-        force_fp64_kernel<TPI, true, U><<<grid, 256, 0, st>>>(q4, p4, n, rp, col, P);
+        force_fp64_kernel<TPI, true, U><<<grid, 256, 0, st>>>(q4, p4, n, rp, col, P, order);
     else
-        force_fp64_kernel<TPI, false, U><<<grid, 256, 0, st>>>(q4, p4, n, rp, col, P);
+        force_fp64_kernel<TPI, false, U><<<grid, 256, 0, st>>>(q4, p4, n, rp, col, P, order);
     LJ_TRY_LAUNCH("force_fp64_kernel");
     return LJ_OK;
 }
 
 template <int TPI>
-int launch_mixed(const double *q4, const float4 *rel, double *p4, int n, const int *rp,
-                 const int *col, int half, const MixedParams &P, cudaStream_t st)
+int launch_mixed(const double *q4, const uint4 *rel, double *p4, int n, const int *rp,
+                 const int *col, int half, const MixedParams &P, const int *order, cudaStream_t st)
 {
     const int64_t threads = int64_t(n) * TPI;
     const unsigned grid = unsigned((threads + 255) / 256);
     if (half)
-        force_mixed_kernel<TPI, true><<<grid, 256, 0, st>>>(q4, rel, p4, n, rp, col, P);
+        force_mixed_kernel<TPI, true><<<grid, 256, 0, st>>>(q4, rel, p4, n, rp, col, P, order);
     else
-        force_mixed_kernel<TPI, false><<<grid, 256, 0, st>>>(q4, rel, p4, n, rp, col, P);
+        force_mixed_kernel<TPI, false><<<grid, 256, 0, st>>>(q4, rel, p4, n, rp, col, P, order);
     LJ_TRY_LAUNCH("force_mixed_kernel");
     return LJ_OK;
 }
@@ -98,7 +158,11 @@ int launch_mixed(const double *q4, const float4 *rel, double *p4, int n, const i
 size_t force_refill_workspace_bytes();
 int force_refill_fp64(const double *q4, double *p4, int n, const int *row_ptr, const int *col,
                       int half, const double box[3], double dt, double rc, double eps,
-                      double sigma, void *ws, size_t ws_bytes, cudaStream_t st);
+                      double sigma, int sched, void *ws, size_t ws_bytes, cudaStream_t st);
+
+int force_queue_fp64(const double *q4, double *p4, int n, const int *row_ptr, const int *col,
+                     int half, const double box[3], double dt, double rc, double eps, double sigma,
+                     int sched, void *ws, size_t ws_bytes, cudaStream_t st);
 
 int check_force_args(const double *q4, const double *p4, int64_t n, const int32_t *row_ptr,
                      const int32_t *col, int64_t nnz, double r_cut, const double box[3], double eps,
@@ -117,11 +181,51 @@ int check_force_args(const double *q4, const double *p4, int64_t n, const int32_
     return check_box(box, r_cut);
 }
 
+// Workspace: [256 B: refill/queue counter][order: n int][slot: n int]
+// [length histogram] and, for LJ_MIXED, the fixed-point positions.
+struct ForceWs {
+    unsigned *counter;
+    int *order, *slot, *hist;
+    uint4 *rel;
+};
+
+ForceWs carve_force_ws(void *base, int64_t n, int precision)
+{
+    Carver c(base);
+    ForceWs w;
+    const size_t nn = size_t(n > 0 ? n : 1);
+    w.counter = c.take<unsigned>(64);
+    w.order = c.take<int>(nn);
+    w.slot = c.take<int>(nn);
+    w.hist = c.take<int>(kLenBuckets);
+    w.rel = precision == LJ_MIXED ? c.take<uint4>(nn) : nullptr;
+    return w;
+}
+
+bool valid_schedule(int s, int precision)
+{
+    const int t = s & 63;
+    const bool pow2 = t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32;
+    if (s & LJ_SCHED_QUEUE)
+        return precision == LJ_FP64 && (s & ~(LJ_SCHED_QUEUE | 63)) == 0 && (t <= 8) && (t == 0 || pow2);
+    if (s & LJ_SCHED_REFILL)
+        return precision == LJ_FP64 && (s & ~(LJ_SCHED_REFILL | LJ_SCHED_SWP2 | 63)) == 0 &&
+               (t == 0 || t == 1 || t == 4 || t == 8);
+    if (s & ~(LJ_SCHED_SORTED | LJ_SCHED_SWP2 | 63)) return false;
+    if (s & LJ_SCHED_SWP2) return precision == LJ_FP64 && (t == 4 || t == 8 || t == 16);
+    return pow2;
+}
+
 size_t force_workspace_bytes_impl(int64_t n, int precision)
 {
-    if (precision == LJ_FP64) return force_refill_workspace_bytes();
-    if (n <= 0) return 256;
-    return size_t(n) * sizeof(float4) + 256;
+    Carver c(nullptr);
+    const size_t nn = size_t(n > 0 ? n : 1);
+    c.take<unsigned>(64);
+    c.take<int>(nn);
+    c.take<int>(nn);
+    c.take<int>(kLenBuckets);
+    if (precision == LJ_MIXED) c.take<uint4>(nn);
+    return c.used + 256;
 }
 
 int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, const int32_t *col,
@@ -133,40 +237,53 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
     if (precision != LJ_FP64 && precision != LJ_MIXED) return LJ_ERR_ARG;
     if (n == 0 || nnz == 0) return LJ_OK;
     const int ni = static_cast<int>(n);
-    if (tpi == LJ_TPI_AUTO) tpi = 8;
-    if (tpi == LJ_SCHED_REFILL) {
+    if (tpi == LJ_TPI_AUTO) tpi = precision == LJ_FP64 ? (LJ_SCHED_SWP2 | 8) : 8;
+    if (!valid_schedule(tpi, precision)) return LJ_ERR_ARG;
+    if (!ws || ws_bytes < force_workspace_bytes_impl(n, precision)) return LJ_ERR_CAPACITY;
+    const ForceWs W = carve_force_ws(ws, n, precision);
+    if (tpi & LJ_SCHED_QUEUE) {
         if (precision != LJ_FP64) return LJ_ERR_ARG;
-        return force_refill_fp64(q4, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma, ws,
-                                 ws_bytes, st);
+        return force_queue_fp64(q4, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma, tpi,
+                                W.counter, 256, st);
+    }
+    if (tpi & LJ_SCHED_REFILL) {
+        if (precision != LJ_FP64) return LJ_ERR_ARG;
+        return force_refill_fp64(q4, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma, tpi,
+                                 W.counter, 256, st);
+    }
+    const int *order = nullptr;
+    if (tpi & LJ_SCHED_SORTED) {
+        const int rc2 = sort_rows_by_length(row_ptr, ni, W.hist, W.slot, W.order, st);
+        if (rc2 != LJ_OK) return rc2;
+        order = W.order;
+        tpi &= ~LJ_SCHED_SORTED;
     }
     if (precision == LJ_FP64) {
         const Fp64Params P = make_fp64_params(box, dt, rc, eps, sigma);
         switch (tpi) {
-            case 1: return launch_fp64<1, 1>(q4, p4, ni, row_ptr, col, half, P, st);
-            case 2: return launch_fp64<2, 1>(q4, p4, ni, row_ptr, col, half, P, st);
-            case 4: return launch_fp64<4, 1>(q4, p4, ni, row_ptr, col, half, P, st);
-            case 8: return launch_fp64<8, 1>(q4, p4, ni, row_ptr, col, half, P, st);
-            case 16: return launch_fp64<16, 1>(q4, p4, ni, row_ptr, col, half, P, st);
-            case 32: return launch_fp64<32, 1>(q4, p4, ni, row_ptr, col, half, P, st);
-            case 4 | LJ_SCHED_SWP2: return launch_fp64<4, 2>(q4, p4, ni, row_ptr, col, half, P, st);
-            case 8 | LJ_SCHED_SWP2: return launch_fp64<8, 2>(q4, p4, ni, row_ptr, col, half, P, st);
-            case 16 | LJ_SCHED_SWP2: return launch_fp64<16, 2>(q4, p4, ni, row_ptr, col, half, P, st);
+            case 1: return launch_fp64<1, 1>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 2: return launch_fp64<2, 1>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 4: return launch_fp64<4, 1>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 8: return launch_fp64<8, 1>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 16: return launch_fp64<16, 1>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 32: return launch_fp64<32, 1>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 4 | LJ_SCHED_SWP2: return launch_fp64<4, 2>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 8 | LJ_SCHED_SWP2: return launch_fp64<8, 2>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 16 | LJ_SCHED_SWP2: return launch_fp64<16, 2>(q4, p4, ni, row_ptr, col, half, P, order, st);
             default: return LJ_ERR_ARG;
         }
     }
-    if (!ws || ws_bytes < force_workspace_bytes_impl(n, precision)) return LJ_ERR_CAPACITY;
     const MixedParams P = make_mixed_params(box, dt, rc, eps, sigma);
-    Carver c(ws);
-    float4 *rel = c.take<float4>(size_t(n));
+    uint4 *rel = W.rel;
     mixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4, ni, P, rel);
     LJ_TRY_LAUNCH("mixed_prepass_kernel");
     switch (tpi) {
-        case 1: return launch_mixed<1>(q4, rel, p4, ni, row_ptr, col, half, P, st);
-        case 2: return launch_mixed<2>(q4, rel, p4, ni, row_ptr, col, half, P, st);
-        case 4: return launch_mixed<4>(q4, rel, p4, ni, row_ptr, col, half, P, st);
-        case 8: return launch_mixed<8>(q4, rel, p4, ni, row_ptr, col, half, P, st);
-        case 16: return launch_mixed<16>(q4, rel, p4, ni, row_ptr, col, half, P, st);
-        case 32: return launch_mixed<32>(q4, rel, p4, ni, row_ptr, col, half, P, st);
+        case 1: return launch_mixed<1>(q4, rel, p4, ni, row_ptr, col, half, P, order, st);
+        case 2: return launch_mixed<2>(q4, rel, p4, ni, row_ptr, col, half, P, order, st);
+        case 4: return launch_mixed<4>(q4, rel, p4, ni, row_ptr, col, half, P, order, st);
+        case 8: return launch_mixed<8>(q4, rel, p4, ni, row_ptr, col, half, P, order, st);
+        case 16: return launch_mixed<16>(q4, rel, p4, ni, row_ptr, col, half, P, order, st);
+        case 32: return launch_mixed<32>(q4, rel, p4, ni, row_ptr, col, half, P, order, st);
         default: return LJ_ERR_ARG;
     }
 }

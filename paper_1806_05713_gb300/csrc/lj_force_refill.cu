@@ -1,68 +1,69 @@
-// lj_force_refill.cu -- FP64 "lane-refill" schedule of the LJ momentum update.
+// lj_force_refill.cu -- FP64 "group-refill" schedule of the LJ momentum
+// update.
 //
-// Same arithmetic as the FP64 form in lj_force.cu (Algorithm 1 inside the
-// sorted-list loop of Algorithm 3), scheduled for a GPU on which FP64
-// instructions are the bottleneck.  Each lane owns one row i at a time --
-// q_i and the p_i sum stay in registers, as Algorithm 3 keeps the i data in
-// registers -- and walks its row one entry per iteration.  A lane whose row
-// ends adds its sum to p_i (one FP64 atomic per component, done in L2 and
-// not on the FP64 pipe) and immediately takes the next row from its warp's
-// chunk of 32 rows; a warp whose chunk is used up takes the next chunk from
-// a global counter.  So every lane does useful work on every iteration until
-// the rows run out: no lane waits for a longer row of its warp (the
-// imbalance the paper's remainder-loop elimination attacks for SIMD), and no
-// cross-lane reduction is needed.  The grid is persistent: one launch of
-// as many blocks as fit on the GPU at once.
+// Same arithmetic as fp64_row (Algorithm 1 inside the sorted-list loop of
+// Algorithm 3).  On GB300 an FP64 instruction occupies the FP64 pipe for its
+// full issue slot whatever the number of active lanes, so a warp whose
+// groups walk rows of different length (a half list in random order has rows
+// of 0 to ~140 entries) keeps paying for the groups that have finished.
+// Here each group of TPI lanes takes the next row as soon as its own ends:
+// the warp takes chunks of rows from a global counter and hands them to its
+// groups, so every group is busy on every iteration until the rows run out
+// (the lane-counter / remainder-loop idea of the paper's Algorithm 4,
+// applied across rows).  A finished row adds its partial sums to p_i with
+// FP64 atomics in L2 (one per lane and component), so no FP64 reduction
+// runs on the pipe.  U = 2 carries two entries per lane and iteration (the
+// paper's software pipelining).  The grid is persistent and sized so that
+// each group sees several rows.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
-#include "lj_internal.cuh"
+#include "lj_rows.cuh"
 
 namespace lj {
 namespace {
 
 constexpr int kRefillThreads = 256;
-constexpr int kChunk = 32;
+constexpr int kRowsPerGroupTarget = 8;
 
-struct RefillParams {
-    double L[3];
-    long long half_bits[3];
-    long long rc2_bits;
-    double rc2;
-    double A, B;  // df = u^4 (A - B u^3)
-};
-
-__device__ __forceinline__ void gather_q(const double *__restrict__ q4, int j, double &x,
-                                         double &y, double &z)
-{
-    double w;
-    asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
-        : "=d"(x), "=d"(y), "=d"(z), "=d"(w)
-        : "l"(q4 + 4 * static_cast<int64_t>(j)));
-}
-
-template <bool HALF>
+template <int TPI, bool HALF, int U>
 __global__ void __launch_bounds__(kRefillThreads)
 force_refill_kernel(const double *__restrict__ q4, double *__restrict__ p4, int n,
-                    const int *__restrict__ row_ptr, const int *__restrict__ col, RefillParams P,
+                    const int *__restrict__ row_ptr, const int *__restrict__ col, Fp64Params P,
                     unsigned *__restrict__ counter)
 {
+    constexpr int G = 32 / TPI;          // groups per warp
+    constexpr int kChunk = 4 * G;        // rows per counter fetch
     const int lane = threadIdx.x & 31;
-    int chunk_next = 0, chunk_end = 0;  // warp-uniform
-    bool exhausted = false;             // warp-uniform: no rows left anywhere
-    int row = -1, k = 0, ke = 0;
+    const int sub = lane & (TPI - 1);
+    const int leader = lane & ~(TPI - 1);
+    const unsigned below_leader = (1u << leader) - 1u;
+    int chunk_next = 0, chunk_end = 0;   // warp-uniform
+    bool exhausted = false;              // warp-uniform
+    int row = -1, k = 0, ke = 0;         // group-uniform
     double xi = 0.0, yi = 0.0, zi = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
     while (true) {
-        // Lanes whose row is done hand in their sum and take a new row.
         bool need = k >= ke;
         if (need && row >= 0) {
             double *pi = p4 + 4 * static_cast<int64_t>(row);
-            atomicAdd(pi + 0, ax);
-            atomicAdd(pi + 1, ay);
-            atomicAdd(pi + 2, az);
+            if (HALF || TPI == 1) {
+                atomicAdd(pi + 0, ax);
+                atomicAdd(pi + 1, ay);
+                atomicAdd(pi + 2, az);
+            } else {
+                ax = group_sum<TPI>(ax);
+                ay = group_sum<TPI>(ay);
+                az = group_sum<TPI>(az);
+                if (sub == 0) {
+                    atomicAdd(pi + 0, ax);
+                    atomicAdd(pi + 1, ay);
+                    atomicAdd(pi + 2, az);
+                }
+            }
             row = -1;
         }
-        unsigned want = __ballot_sync(0xffffffffu, need);
+        unsigned want = __ballot_sync(0xffffffffu, need && sub == 0);
         while (want && !exhausted) {
             if (chunk_next >= chunk_end) {
                 unsigned c = 0;
@@ -76,113 +77,151 @@ force_refill_kernel(const double *__restrict__ q4, double *__restrict__ p4, int 
                 chunk_end = min(n, chunk_next + kChunk);
             }
             const int avail = chunk_end - chunk_next;
-            const int rank = __popc(want & lanemask_lt());
+            const int rank = __popc(want & below_leader);
             if (need && rank < avail) {
                 row = chunk_next + rank;
                 k = row_ptr[row];
                 ke = row_ptr[row + 1];
-                gather_q(q4, row, xi, yi, zi);
+                load_q4_256(q4, row, xi, yi, zi);
                 ax = ay = az = 0.0;
                 need = false;
             }
             chunk_next += min(avail, __popc(want));
-            want = __ballot_sync(0xffffffffu, need);
+            want = __ballot_sync(0xffffffffu, need && sub == 0);
         }
-        const bool valid = k < ke;
-        if (!__any_sync(0xffffffffu, valid)) {
-            if (exhausted || !__any_sync(0xffffffffu, need)) break;
-            continue;  // every lane got an empty row: hand them in, refill
+        if (!__any_sync(0xffffffffu, k < ke)) {
+            if (exhausted) break;
+            continue;  // only empty rows were handed out: hand them in, refill
         }
-        const int j = valid ? col[k] : (row >= 0 ? row : 0);
-        double xj, yj, zj;
-        gather_q(q4, j, xj, yj, zj);
-        double dx = xj - xi, dy = yj - yi, dz = zj - zi;
-        min_image3(dx, dy, dz, P.L, P.half_bits);
-        double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-        const long long rb = __double_as_longlong(r2);
-        bool in = valid && rb < P.rc2_bits;
-        const bool near = valid && static_cast<unsigned long long>(rb - P.rc2_bits + 64) < 128ull;
-        if (__any_sync(0xffffffffu, near)) {
-            if (near) {
-                const double e2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                                            __dmul_rn(dz, dz));
-                in = e2 < P.rc2;
+        // One iteration of the row walk for every group (fp64_row's body).
+        int j[U];
+        bool valid[U], in[U], near[U];
+        double dx[U], dy[U], dz[U], r2[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int kk = k + sub + u * TPI;
+            valid[u] = kk < ke;
+            j[u] = valid[u] ? col[kk] : (row >= 0 ? row : 0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            double xj, yj, zj;
+            load_q4_256(q4, j[u], xj, yj, zj);
+            dx[u] = xj - xi;
+            dy[u] = yj - yi;
+            dz[u] = zj - zi;
+        }
+        bool anynear = false, anyin = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            min_image3(dx[u], dy[u], dz[u], P.L, P.half_bits);
+            r2[u] = fma(dz[u], dz[u], fma(dy[u], dy[u], dx[u] * dx[u]));
+            const long long rb = __double_as_longlong(r2[u]);
+            in[u] = valid[u] && rb < P.rc2_bits;
+            near[u] = valid[u] && static_cast<unsigned long long>(rb - P.rc2_bits + 64) < 128ull;
+            anynear |= near[u];
+        }
+        if (__any_sync(0xffffffffu, anynear)) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (near[u]) in[u] = exact_in_cutoff(dx[u], dy[u], dz[u], P.rc2);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!valid[u]) r2[u] = 1.0;
+            anyin |= in[u];
+        }
+        if (__any_sync(0xffffffffu, anyin)) {
+            double fn[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const double w = rcp_fp64(r2[u]);
+                const double w2 = w * w;
+                const double w4 = w2 * w2;
+                const double w3 = w2 * w;
+                fn[u] = w4 * fma(P.B, w3, -P.A);  // -df: p_i -= fn d, p_j += fn d
             }
-        }
-        if (!valid) r2 = 1.0;
-        if (__any_sync(0xffffffffu, in)) {
-            const double u = rcp_fp64(r2);
-            const double u2 = u * u;
-            const double u4 = u2 * u2;
-            const double u3 = u2 * u;
-            const double fn = u4 * fma(P.B, u3, -P.A);  // -df: p_i -= fn d, p_j += fn d
-            if (in) {
-                if (HALF) {
-                    const double fx = fn * dx, fy = fn * dy, fz = fn * dz;
-                    atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 0, fx);
-                    atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 1, fy);
-                    atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 2, fz);
-                    ax -= fx;
-                    ay -= fy;
-                    az -= fz;
-                } else {
-                    ax = fma(-fn, dx, ax);
-                    ay = fma(-fn, dy, ay);
-                    az = fma(-fn, dz, az);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (in[u]) {
+                    if (HALF) {
+                        const double fx = fn[u] * dx[u], fy = fn[u] * dy[u], fz = fn[u] * dz[u];
+                        atomicAdd(p4 + 4 * static_cast<int64_t>(j[u]) + 0, fx);
+                        atomicAdd(p4 + 4 * static_cast<int64_t>(j[u]) + 1, fy);
+                        atomicAdd(p4 + 4 * static_cast<int64_t>(j[u]) + 2, fz);
+                        ax -= fx;
+                        ay -= fy;
+                        az -= fz;
+                    } else {
+                        ax = fma(-fn[u], dx[u], ax);
+                        ay = fma(-fn[u], dy[u], ay);
+                        az = fma(-fn[u], dz[u], az);
+                    }
                 }
             }
         }
-        if (valid) ++k;
+        if (k < ke) k += TPI * U;
     }
 }
 
-template <bool HALF>
-int grid_for()
+template <int TPI, bool HALF, int U>
+int launch_refill(const double *q4, double *p4, int n, const int *rp, const int *col,
+                  const Fp64Params &P, unsigned *counter, cudaStream_t st)
 {
-    static int blocks = 0;
-    if (blocks == 0) {
+    static int max_blocks = 0;
+    if (max_blocks == 0) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, force_refill_kernel<HALF>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, force_refill_kernel<TPI, HALF, U>,
                                                           kRefillThreads, 0) != cudaSuccess ||
             per_sm < 1)
-            per_sm = 4;
-        blocks = per_sm * num_sms();
+            per_sm = 2;
+        max_blocks = per_sm * num_sms();
     }
-    return blocks;
+    constexpr int G = 32 / TPI;
+    constexpr int warps_per_block = kRefillThreads / 32;
+    // Enough warps to fill the GPU, few enough that each group sees several rows.
+    const long long want_warps = std::max<long long>(1, n / (G * kRowsPerGroupTarget));
+    int blocks = static_cast<int>((want_warps + warps_per_block - 1) / warps_per_block);
+    blocks = std::max(std::min(blocks, max_blocks), std::min(max_blocks, 2 * num_sms()));
+    force_refill_kernel<TPI, HALF, U><<<blocks, kRefillThreads, 0, st>>>(q4, p4, n, rp, col, P, counter);
+    LJ_TRY_LAUNCH("force_refill_kernel");
+    return LJ_OK;
 }
 
 }  // namespace
 
 size_t force_refill_workspace_bytes() { return 256; }
 
+// sched: LJ_SCHED_REFILL | tpi (tpi 0 or 1: one lane per row), optionally
+// | LJ_SCHED_SWP2 for two entries per lane and iteration.
 int force_refill_fp64(const double *q4, double *p4, int n, const int *row_ptr, const int *col,
                       int half, const double box[3], double dt, double rc, double eps,
-                      double sigma, void *ws, size_t ws_bytes, cudaStream_t st)
+                      double sigma, int sched, void *ws, size_t ws_bytes, cudaStream_t st)
 {
     if (!ws || ws_bytes < force_refill_workspace_bytes()) return LJ_ERR_CAPACITY;
-    RefillParams P{};
-    for (int a = 0; a < 3; ++a) {
-        P.L[a] = box[a];
-        const double h = 0.5 * box[a];
-        std::memcpy(&P.half_bits[a], &h, sizeof(double));
-    }
-    P.rc2 = rc * rc;
-    std::memcpy(&P.rc2_bits, &P.rc2, sizeof(double));
-    const double s2 = sigma * sigma, s6 = s2 * s2 * s2, s12 = s6 * s6;
-    P.A = 24.0 * eps * s6 * dt;
-    P.B = 48.0 * eps * s12 * dt;
+    const Fp64Params P = make_fp64_params(box, dt, rc, eps, sigma);
     unsigned *counter = static_cast<unsigned *>(ws);
     LJ_TRY_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
-    const int needed = (n + kChunk - 1) / kChunk;
-    if (half) {
-        const int grid = std::min(grid_for<true>(), needed);
-        force_refill_kernel<true><<<grid, kRefillThreads, 0, st>>>(q4, p4, n, row_ptr, col, P, counter);
-    } else {
-        const int grid = std::min(grid_for<false>(), needed);
-        force_refill_kernel<false><<<grid, kRefillThreads, 0, st>>>(q4, p4, n, row_ptr, col, P, counter);
+    const bool swp = (sched & LJ_SCHED_SWP2) != 0;
+    const int tpi = sched & 63;
+#define LJ_REFILL(T, U)                                                                          \
+    return half ? launch_refill<T, true, U>(q4, p4, n, row_ptr, col, P, counter, st)            \
+                : launch_refill<T, false, U>(q4, p4, n, row_ptr, col, P, counter, st)
+    switch (tpi) {
+        case 0:
+        case 1:
+            if (swp) LJ_REFILL(1, 2);
+            LJ_REFILL(1, 1);
+        case 4:
+            if (swp) LJ_REFILL(4, 2);
+            LJ_REFILL(4, 1);
+        case 8:
+            if (swp) LJ_REFILL(8, 2);
+            LJ_REFILL(8, 1);
+        default:
+            return LJ_ERR_ARG;
     }
-    LJ_TRY_LAUNCH("force_refill_kernel");
-    return LJ_OK;
+#undef LJ_REFILL
 }
 
 }  // namespace lj

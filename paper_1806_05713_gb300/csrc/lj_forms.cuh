@@ -19,21 +19,18 @@ struct Fp64Params {
 };
 
 struct MixedParams {
-    // FP32 cell-relative geometry
-    float h[3];      // cell side per axis (FP32 copy of L/nc)
-    float hLf[3];    // L/2 in FP32
-    int nc[3];       // cells per axis (< 1024)
-    int nhalf[3];    // nc / 2
-    float rc2f;      // r_c^2 in FP32
-    float band;      // |r2f - r_c^2| <= band  => decide in FP64
-    float Af, Bf;    // FP32 copies of A, B
-    int wrap_fix;    // nonzero when a pair within r_c can need the second image choice
+    // Fixed-point positions: X = floor(x 2^32 / L) as a 32-bit unsigned
+    // integer per axis, so X_j - X_i in wrapping 32-bit arithmetic is the
+    // minimum-image displacement in units of L / 2^32, exactly.
+    double to_fixed[3];  // 2^32 / L (FP64, pre-pass)
+    float scale[3];      // L / 2^32 (FP32, pair loop)
+    float rc2f;          // r_c^2 in FP32
+    float band;          // |r2f - r_c^2| <= band  => decide in FP64
+    float Af, Bf;        // FP32 copies of A, B
     // FP64 geometry for the exact decisions
     double L[3];
     long long half_bits[3];
-    double rc2;      // r_c^2 in FP64 (exact definition, no FMA)
-    double inv_h[3]; // nc / L
-    double hd[3];    // L / nc in FP64
+    double rc2;          // r_c^2 in FP64 (exact definition, no FMA)
 };
 
 // 32-byte read-only gather of one AoS4 record (a single 256-bit load).
@@ -77,50 +74,42 @@ __device__ __forceinline__ double group_sum(double v)
 // MIXED form helpers
 // ---------------------------------------------------------------------------
 
-// Pre-pass: q (FP64) -> {rel_x, rel_y, rel_z, packed cell} with
-// rel = q - c h computed in FP64 and rounded once to FP32.
+// Pre-pass: q (FP64) -> {X, Y, Z, 0}, X = floor(x 2^32 / L) computed in
+// FP64 (x in [0, L) maps to [0, 2^32); a product that rounds up to 2^32
+// saturates to 2^32 - 1).
 __global__ void mixed_prepass_kernel(const double *__restrict__ q4, int n, MixedParams P,
-                                     float4 *__restrict__ rel)
+                                     uint4 *__restrict__ fx)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double x[3];
     load_xyz(q4, i, x[0], x[1], x[2]);
-    int c[3];
-    float r[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        int ca = static_cast<int>(x[a] * P.inv_h[a]);
-        ca = ca < 0 ? 0 : (ca >= P.nc[a] ? P.nc[a] - 1 : ca);
-        c[a] = ca;
-        r[a] = __double2float_rn(x[a] - ca * P.hd[a]);
-    }
-    rel[i] = make_float4(r[0], r[1], r[2], __int_as_float(c[0] | (c[1] << 10) | (c[2] << 20)));
+    fx[i] = make_uint4(__double2uint_rz(x[0] * P.to_fixed[0]), __double2uint_rz(x[1] * P.to_fixed[1]),
+                       __double2uint_rz(x[2] * P.to_fixed[2]), 0u);
 }
 
-// Small integer (|m| < 2^22) to float without a conversion instruction:
-// 1.5 * 2^23 + m has m in its low mantissa bits.
-__device__ __forceinline__ float small_int_to_float(int m)
+// One displacement component: the wrapping 32-bit difference is the
+// minimum image (exact, in units of L / 2^32); one conversion and one
+// multiply round it to FP32.
+__device__ __forceinline__ float fixed_disp(unsigned xj, unsigned xi, float scale)
 {
-    return __int_as_float(0x4B400000 + m) - 12582912.0f;
+    return static_cast<float>(static_cast<int>(xj - xi)) * scale;
 }
 
-// One displacement component from cell-relative coordinates: the cell
-// difference m is wrapped to its nearest representative, d = m h + (rel_j -
-// rel_i).  In small boxes (fix != 0, a warp-uniform flag) a pair within r_c
-// can still sit across the half-box from that representative; then the other
-// image is taken.
-__device__ __forceinline__ float mixed_disp(float rj, float ri, int cj, int ci, float h, float hL,
-                                            int nc, int nhalf, int fix)
+// Exact float -> double conversion with integer instructions only (GB300
+// runs float<->double conversions on its slow FP64 pipe): rebias the
+// exponent and shift the mantissa.  Zero and subnormal inputs give +-0
+// (their magnitude, below 1.2e-38, is far under any momentum's last digit),
+// infinities and NaNs stay non-finite.
+__device__ __forceinline__ double f32_to_f64(float x)
 {
-    int m = cj - ci;
-    m = m > nhalf ? m - nc : (m < -nhalf ? m + nc : m);
-    const float dr = rj - ri;
-    float d = fmaf(small_int_to_float(m), h, dr);
-    if (fix) {
-        if (fabsf(d) > hL) d = fmaf(small_int_to_float(d > 0.0f ? m - nc : m + nc), h, dr);
-    }
-    return d;
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned ed = e == 255u ? 2047u : e + 896u;
+    const unsigned hi = (u & 0x80000000u) | (ed << 20) | ((u >> 3) & 0xfffffu);
+    const unsigned lo = u << 29;
+    return e == 0u ? __hiloint2double(static_cast<int>(u & 0x80000000u), 0)
+                   : __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
 }
 
 // Kahan step: (s, c) with true sum ~ s - c.
@@ -178,33 +167,22 @@ Fp64Params make_fp64_params(const double box[3], double dt, double rc, double ep
 MixedParams make_mixed_params(const double box[3], double dt, double rc, double eps, double sigma)
 {
     MixedParams P{};
-    double hmax = 0.0;
+    double Lmax = 0.0;
     for (int a = 0; a < 3; ++a) {
-        int nc = static_cast<int>(std::floor(box[a] / 2.0));
-        nc = nc < 1 ? 1 : (nc > 1023 ? 1023 : nc);
-        P.nc[a] = nc;
-        P.nhalf[a] = nc / 2;
-        P.hd[a] = box[a] / nc;
-        P.inv_h[a] = nc / box[a];
-        P.h[a] = static_cast<float>(P.hd[a]);
-        P.hLf[a] = static_cast<float>(0.5 * box[a]);
+        P.to_fixed[a] = std::ldexp(1.0, 32) / box[a];
+        P.scale[a] = static_cast<float>(std::ldexp(box[a], -32));
         P.L[a] = box[a];
         const double hh = 0.5 * box[a];
         std::memcpy(&P.half_bits[a], &hh, sizeof(double));
-        hmax = P.hd[a] > hmax ? P.hd[a] : hmax;
+        Lmax = box[a] > Lmax ? box[a] : Lmax;
     }
-    // With |m| <= nc/2 and |rel_j - rel_i| < h, |d| <= L/2 + h; the other
-    // image is then at least L/2 - h away, so it can matter only if
-    // L/2 - h < r_c (plus a rounding allowance).
-    P.wrap_fix = 0;
-    for (int a = 0; a < 3; ++a)
-        if (0.5 * box[a] - P.hd[a] < rc * (1.0 + 1e-6) + 1e-6) P.wrap_fix = 1;
     P.rc2 = rc * rc;
     P.rc2f = static_cast<float>(P.rc2);
-    // Per-axis displacement error <= 4 h 2^-23 (offset roundings, FP32 h,
-    // the fused add); r^2 error <= 2 sqrt(3) r_c e + 3 e^2 + 4 2^-24 r_c^2
-    // plus the rounding of r_c^2 itself; the band is four times that.
-    const double e = 4.0 * hmax * std::ldexp(1.0, -23);
+    // Per-axis displacement error: two position quantisations (< L 2^-32
+    // each), the conversion and the scaling (2^-24 |d| each) and the FP32
+    // scale (2^-24 |d|); r^2 error <= 2 sqrt(3) r_c e + 3 e^2 + 4 2^-24 r_c^2
+    // plus the rounding of r_c^2; the band is four times that.
+    const double e = 2.0 * Lmax * std::ldexp(1.0, -32) + 3.0 * std::ldexp(1.0, -24) * rc;
     const double err = 2.0 * std::sqrt(3.0) * rc * e + 3.0 * e * e + 4.0 * std::ldexp(1.0, -24) * P.rc2 +
                        std::fabs(static_cast<double>(P.rc2f) - P.rc2);
     P.band = static_cast<float>(4.0 * err);

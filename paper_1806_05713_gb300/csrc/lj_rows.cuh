@@ -94,39 +94,47 @@ __device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *
             }
         }
     }
-    if (TPI > 1) {
-        ax = group_sum<TPI>(ax);
-        ay = group_sum<TPI>(ay);
-        az = group_sum<TPI>(az);
-    }
-    if (sub == 0) {
+    if (HALF) {
+        // p_i already receives other rows' atomics: each lane adds its own
+        // partial sum in L2 (no FP64 shuffle reduction on the FP64 pipe).
         double *pi = p4 + 4 * static_cast<int64_t>(i);
         atomicAdd(pi + 0, ax);
         atomicAdd(pi + 1, ay);
         atomicAdd(pi + 2, az);
+    } else {
+        // Full list: a fixed-order group reduction keeps p_i deterministic.
+        if (TPI > 1) {
+            ax = group_sum<TPI>(ax);
+            ay = group_sum<TPI>(ay);
+            az = group_sum<TPI>(az);
+        }
+        if (sub == 0) {
+            double *pi = p4 + 4 * static_cast<int64_t>(i);
+            atomicAdd(pi + 0, ax);
+            atomicAdd(pi + 1, ay);
+            atomicAdd(pi + 2, az);
+        }
     }
 }
 
-// One row i of the MIXED form (see lj_force.cu), walked by a TPI group.
+// One row i of the MIXED form (see lj_force.cu), walked by a TPI group;
+// rel holds the fixed-point positions of the system.
 template <int TPI, bool HALF>
 __device__ __forceinline__ void mixed_row(const double *__restrict__ q4,
-                                          const float4 *__restrict__ rel, double *__restrict__ p4,
+                                          const uint4 *__restrict__ rel, double *__restrict__ p4,
                                           const int *__restrict__ row_ptr,
                                           const int *__restrict__ col, int i, const MixedParams &P)
 {
     const int sub = threadIdx.x & (TPI - 1);
-    const float4 pi = rel[i];
-    const int ci = __float_as_int(pi.w);
-    const int cix = ci & 1023, ciy = (ci >> 10) & 1023, ciz = ci >> 20;
+    const uint4 pi = rel[i];
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     const int kb = row_ptr[i], ke = row_ptr[i + 1];
     for (int k = kb + sub; k < ke; k += TPI) {
         const int j = col[k];
-        const float4 pj = rel[j];
-        const int cj = __float_as_int(pj.w);
-        const float dx = mixed_disp(pj.x, pi.x, cj & 1023, cix, P.h[0], P.hLf[0], P.nc[0], P.nhalf[0], P.wrap_fix);
-        const float dy = mixed_disp(pj.y, pi.y, (cj >> 10) & 1023, ciy, P.h[1], P.hLf[1], P.nc[1], P.nhalf[1], P.wrap_fix);
-        const float dz = mixed_disp(pj.z, pi.z, cj >> 20, ciz, P.h[2], P.hLf[2], P.nc[2], P.nhalf[2], P.wrap_fix);
+        const uint4 pj = rel[j];
+        const float dx = fixed_disp(pj.x, pi.x, P.scale[0]);
+        const float dy = fixed_disp(pj.y, pi.y, P.scale[1]);
+        const float dz = fixed_disp(pj.z, pi.z, P.scale[2]);
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         bool in = r2 < P.rc2f;
         if (fabsf(r2 - P.rc2f) <= P.band) {
@@ -149,9 +157,9 @@ __device__ __forceinline__ void mixed_row(const double *__restrict__ q4,
             kahan_add(sy, cy, fy);
             kahan_add(sz, cz, fz);
             if (HALF) {
-                atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 0, -static_cast<double>(fx));
-                atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 1, -static_cast<double>(fy));
-                atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 2, -static_cast<double>(fz));
+                atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 0, f32_to_f64(-fx));
+                atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 1, f32_to_f64(-fy));
+                atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 2, f32_to_f64(-fz));
             }
         }
     }
@@ -161,13 +169,15 @@ __device__ __forceinline__ void mixed_row(const double *__restrict__ q4,
         group_kahan<TPI>(sz, cz);
     }
     if (sub == 0) {
-        const double ax = static_cast<double>(sx) - static_cast<double>(cx);
-        const double ay = static_cast<double>(sy) - static_cast<double>(cy);
-        const double az = static_cast<double>(sz) - static_cast<double>(cz);
+        // p_i += s - c: the head and the compensation go to p as two FP64
+        // additions done in L2 (no FP64-pipe instruction in this kernel).
         double *pp = p4 + 4 * static_cast<int64_t>(i);
-        atomicAdd(pp + 0, ax);
-        atomicAdd(pp + 1, ay);
-        atomicAdd(pp + 2, az);
+        atomicAdd(pp + 0, f32_to_f64(sx));
+        atomicAdd(pp + 1, f32_to_f64(sy));
+        atomicAdd(pp + 2, f32_to_f64(sz));
+        atomicAdd(pp + 0, f32_to_f64(-cx));
+        atomicAdd(pp + 1, f32_to_f64(-cy));
+        atomicAdd(pp + 2, f32_to_f64(-cz));
     }
 }
 

@@ -18,7 +18,8 @@
 // two scalar gradients take half of the sum over entries.  A half list
 // scatters c to q_j with FP64 atomics.
 //
-// Forms: FP64 (every step double), MIXED (cell-relative FP32 displacement
+// Forms: FP64 (every step double), MIXED (fixed-point displacement rounded
+// once to FP32,
 // and FP32 pair arithmetic as in lj_force, Kahan-compensated FP32 row and
 // scalar sums, FP64 outputs).  Pairs within the error band of r_c^2 are
 // decided by the exact FP64 definition in both forms.
@@ -172,7 +173,7 @@ vjp_fp64_kernel(const double *__restrict__ q4, const double *__restrict__ R4, in
 
 template <bool HALF>
 __global__ void __launch_bounds__(kVjpThreads)
-vjp_mixed_kernel(const double *__restrict__ q4, const float4 *__restrict__ rel,
+vjp_mixed_kernel(const double *__restrict__ q4, const uint4 *__restrict__ rel,
                  const double *__restrict__ R4, int n, const int *__restrict__ row_ptr,
                  const int *__restrict__ col, MixedParams P, float G1, float G2, float H1,
                  float H2, float S1, float S2, double *__restrict__ gq4,
@@ -185,9 +186,7 @@ vjp_mixed_kernel(const double *__restrict__ q4, const float4 *__restrict__ rel,
     float es = 0.f, ec = 0.f, ss = 0.f, sc = 0.f;  // Kahan sums of g (d.w), dg/dsigma (d.w)
     if (gid < n) {
         const int i = gid;
-        const float4 pi = rel[i];
-        const int ci = __float_as_int(pi.w);
-        const int cix = ci & 1023, ciy = (ci >> 10) & 1023, ciz = ci >> 20;
+        const uint4 pi = rel[i];
         double Rxd, Ryd, Rzd;
         load_r3(R4, i, Rxd, Ryd, Rzd);
         const float Rxi = static_cast<float>(Rxd), Ryi = static_cast<float>(Ryd),
@@ -198,11 +197,10 @@ vjp_mixed_kernel(const double *__restrict__ q4, const float4 *__restrict__ rel,
             const int k = base + sub;
             const bool valid = k < ke;
             const int j = valid ? col[k] : i;
-            const float4 pj = rel[j];
-            const int cj = __float_as_int(pj.w);
-            const float dx = mixed_disp(pj.x, pi.x, cj & 1023, cix, P.h[0], P.hLf[0], P.nc[0], P.nhalf[0], P.wrap_fix);
-            const float dy = mixed_disp(pj.y, pi.y, (cj >> 10) & 1023, ciy, P.h[1], P.hLf[1], P.nc[1], P.nhalf[1], P.wrap_fix);
-            const float dz = mixed_disp(pj.z, pi.z, cj >> 20, ciz, P.h[2], P.hLf[2], P.nc[2], P.nhalf[2], P.wrap_fix);
+            const uint4 pj = rel[j];
+            const float dx = fixed_disp(pj.x, pi.x, P.scale[0]);
+            const float dy = fixed_disp(pj.y, pi.y, P.scale[1]);
+            const float dz = fixed_disp(pj.z, pi.z, P.scale[2]);
             float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             bool in = valid && s < P.rc2f;
             const bool near = valid && fabsf(s - P.rc2f) <= P.band;
@@ -313,7 +311,7 @@ extern "C" size_t lj_force_vjp_workspace_bytes(int64_t n, int precision)
 {
     const size_t blocks = size_t(lj::vjp_blocks(n > 0 ? n : 1));
     size_t bytes = 2 * blocks * sizeof(double) + 256;
-    if (precision == LJ_MIXED) bytes += size_t(n > 0 ? n : 1) * sizeof(float4) + 256;
+    if (precision == LJ_MIXED) bytes += size_t(n > 0 ? n : 1) * sizeof(uint4) + 256;
     return bytes;
 }
 
@@ -356,7 +354,7 @@ extern "C" int lj_force_vjp(const double *q4_dev, const double *gradF4_dev, int6
     } else {
         const MixedParams P = make_mixed_params(box, 1.0, r_cut, eps, sigma);
         const VjpCoef C = make_coef(eps, sigma);
-        float4 *rel = c.take<float4>(size_t(n));
+        uint4 *rel = c.take<uint4>(size_t(n));
         mixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, ni, P, rel);
         LJ_TRY_LAUNCH("mixed_prepass_kernel");
         const float G1 = float(C.G1), G2 = float(C.G2), H1 = float(C.H1), H2 = float(C.H2),

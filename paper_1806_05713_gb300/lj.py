@@ -29,6 +29,8 @@ LJ_MIXED = 1
 LJ_TPI_AUTO = 0
 LJ_SCHED_REFILL = 64
 LJ_SCHED_SWP2 = 128
+LJ_SCHED_QUEUE = 256
+LJ_SCHED_SORTED = 512
 LJ_STATIC_MAX_ATOMS = 131072
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liblj_gb300.so")
@@ -348,8 +350,10 @@ def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float
     (best_tpi, best_ms, {tpi: ms})."""
     lib = load()
     if candidates is None:
-        candidates = ([8, 4, 16, 32, LJ_SCHED_SWP2 | 4, LJ_SCHED_SWP2 | 8, LJ_SCHED_SWP2 | 16,
-                       LJ_SCHED_REFILL] if precision == LJ_FP64 else [1, 2, 4, 8, 16, 32])
+        S, W = LJ_SCHED_SORTED, LJ_SCHED_SWP2
+        candidates = ([8, W | 4, W | 8, W | 16, S | 8, S | W | 4, S | W | 8, S | W | 16,
+                       LJ_SCHED_REFILL | W | 4, LJ_SCHED_REFILL | W | 8, LJ_SCHED_QUEUE | 8]
+                      if precision == LJ_FP64 else [2, 4, 8, 16, S | 4, S | 8, S | 16])
     n = plist.n
     scratch = torch.zeros((n, 4), dtype=torch.float64, device=q4.device)
     ws = _workspace(lib.lj_force_workspace_bytes(n, _box3(box), int(precision)), q4.device)
