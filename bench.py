@@ -50,9 +50,11 @@ L2_FLUSH_BYTES = 256 << 20
 # (4 flop) x 2070 MHz (the nominal 1.25 TFLOP/s FP64 of GB300).
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
-# DRAM bytes per launch from an ncu capture of the kernel as it stands
-# (profiles/); None until captured for the current kernel source.
-TRAFFIC_PER_LAUNCH = {"force_refill_kernel": None}
+# DRAM bytes (read + write) per launch of the FP64 force kernel, by
+# schedule, from one ncu capture of the kernel as it stands on this workload
+# (profiles/force_fp64_swp2_tpi8_half_N119164.md); a schedule without an
+# entry reports null.
+TRAFFIC_PER_LAUNCH = {136: 41906944.0 + 0.0}
 
 
 def parse():
@@ -66,7 +68,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (1M atoms, 512-system batch, 64-replica adjoint)")
-    ap.add_argument("--profile", choices=["fp64", "fp64-full", "mixed", "mixed-full", "list"],
+    ap.add_argument("--profile", choices=["fp64", "fp64-full", "mixed", "mixed-full", "list", "vjp",
+                                          "batched"],
                     help="no timing: build the list and run a few calls of one kernel (for ncu)")
     ap.add_argument("--profile-atoms", choices=["paper", "million"], default="paper")
     ap.add_argument("--profile-tpi", type=int, default=0, help="schedule for --profile (0 = auto)")
@@ -243,9 +246,24 @@ def run_profile(args):
     q = torch.from_numpy(s.q).cuda()
     p = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
     half = not args.profile.endswith("full")
+    if args.profile == "batched":
+        from paper_1806_05713_gb300.batch import Batch
+        systems = inputs.batched_systems(nsys=64, seed=0)
+        b = Batch(systems, DT, lj.LJ_FP64, True, tpi=8, rows_per_item=16)
+        for _ in range(5):
+            b.force()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "batched", "systems": len(systems), "atoms": b.total_atoms}))
+        return
+    if args.profile == "vjp":
+        half = False
     pl = lj.lj_build_pairlist(q, box, s.rs, half)
     pl = lj.lj_build_pairlist(q, box, s.rs, half, reuse=pl)
-    if args.profile == "list":
+    if args.profile == "vjp":
+        R = torch.ones((s.n, 4), dtype=torch.float64, device="cuda")
+        for _ in range(5):
+            lj.lj_force_vjp(q, R, pl, s.rc, box, 1.1, 0.97, lj.LJ_FP64)
+    elif args.profile == "list":
         for _ in range(3):
             lj.lj_build_pairlist(q, box, s.rs, half, reuse=pl)
     else:
@@ -380,7 +398,8 @@ def main():
     alg_bytes = 4.0 * nnz + 4.0 * (s.n + 1) + 32.0 * s.n + 64.0 * s.n
     roof = {"bound": "alu", "achieved": flops / t_force / 1e12, "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": flops / t_force / 1e12 / FP64_PEAK_TFLOPS,
-            "traffic": TRAFFIC_PER_LAUNCH["force_refill_kernel"],
+            "traffic": TRAFFIC_PER_LAUNCH.get(best_tpi),
+            "traffic_source": "profiles/force_fp64_swp2_tpi8_half_N119164.md (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold cache)",
             "kernel": f"FP64 force kernel, {schedule_name(best_tpi)}, half list",
             "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
             "flops_per_launch": flops, "launch_ms": t_force * 1e3}
