@@ -436,6 +436,7 @@ def main():
             "million_fp64_vs_mixed": extra_million(lj, dev, stream, flush),
             "batched_512_systems": extra_batched(lj, dev, stream, flush),
             "adjoint_64_replicas": extra_adjoint(lj, dev, stream, flush),
+            "md_velocity_verlet": extra_md(lj, dev, stream),
         }
     if world == 1 and not args.no_cpu:
         t, m = oracle_sample(s, CPU_FORCE_CALLS)
@@ -561,6 +562,37 @@ def extra_adjoint(lj, dev, stream, flush):
         ms = time_calls(step, stream, flush, 5, 1)
         res[name] = {"forward_backward_ms": ms, "grad_eps": float(eps.grad), "grad_sigma": float(sig.grad)}
     return res
+
+
+def extra_md(lj, dev, stream):
+    """Velocity Verlet on the N = 119,164 workload with random initial momenta
+    (T ~ 1): one drift and one force call per step, the list rebuilt by the
+    fastest-atom bookkeeping rule; reports steps/s and pairs/s including the
+    rebuilds."""
+    import torch
+    from paper_1806_05713_gb300 import inputs
+    from paper_1806_05713_gb300.md import VelocityVerlet
+    s = inputs.workload_paper()
+    q = torch.from_numpy(s.q).to(dev)
+    g = np.random.default_rng(0).normal(size=(s.n, 4))
+    g[:, 3] = 0.0
+    g[:, :3] -= g[:, :3].mean(axis=0)
+    p = torch.from_numpy(g).to(dev)
+    vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, 0.005)
+    vv.run(20)
+    e0 = vv.kinetic_energy() + vv.potential_energy()
+    r0 = vv.rebuilds
+    steps = 200
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    vv.run(steps)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    e1 = vv.kinetic_energy() + vv.potential_energy()
+    return {"n_atoms": s.n, "dt": 0.005, "steps": steps, "ms_per_step": ms / steps,
+            "list_rebuilds": vv.rebuilds - r0, "pairs_per_s": vv.plist.nnz * steps / (ms / 1e3),
+            "energy_drift_rel": abs(e1 - e0) / abs(e0)}
 
 
 def time_calls(fn, stream, flush, calls=20, warm=3):

@@ -233,6 +233,25 @@ int lj_energy(const double *q4_dev, int64_t n, const int32_t *row_ptr_dev,
               size_t workspace_bytes, void *stream);
 
 /* ======================================================================== */
+/* Drift (the position update around the force; bookkeeping criterion)      */
+/* ======================================================================== */
+
+/*
+ * Velocity-Verlet drift with unit mass: q += dt p per atom and axis (round-
+ * to-nearest double operations, no fused multiply-add), then one periodic
+ * wrap back into [0, L) (a result equal to L becomes 0).  Writes
+ * max_disp2_dev[0] (one device double, overwritten) = max over atoms of
+ * |dt p|^2, the squared largest displacement of this step: with the
+ * fastest-atom criterion of section "Verlet List and Bookkeeping Method", a
+ * list built with margin r_s - r_c stays valid while 2 * (sum over steps of
+ * sqrt(max_disp2)) < r_s - r_c.  Requires |dt p| < L per axis.  The pad
+ * element of q is untouched.  Asynchronous.  Errors: LJ_ERR_ARG, LJ_ERR_BOX,
+ * LJ_ERR_CUDA.
+ */
+int lj_drift(double *q4_dev, const double *p4_dev, int64_t n, double dt, const double box[3],
+             double *max_disp2_dev, void *stream);
+
+/* ======================================================================== */
 /* Batched systems: many independent LJ systems in one persistent launch    */
 /* (the Algorithm 3 loop of each system, work-shared across the GPU)        */
 /* ======================================================================== */

@@ -85,7 +85,7 @@ __global__ void batched_prepass_kernel(const SysDev *__restrict__ sys, const Ite
 }
 
 template <int TPI, bool MIXED>
-__global__ void __launch_bounds__(kBatchThreads)
+__global__ void __launch_bounds__(kBatchThreads, 4)
 batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ items,
                      long long nitems, const double *__restrict__ q4, const uint4 *__restrict__ rel,
                      double *__restrict__ p4, const int *__restrict__ row_ptr,

@@ -85,6 +85,7 @@ SIGNATURES = {
                                  _int, _intp, _int, _int, _vp, _sz, _intp, _fltp, _fltp, _vp]),
     "lj_autotune_batched": (_int, [_sysp, _int, _dbl, _int, _intp, _int, _intp, _int, _vp, _vp, _vp,
                                    _vp, _vp, _sz, _vp, _sz, _int, _intp, _intp, _fltp, _vp]),
+    "lj_drift": (_int, [_vp, _vp, _i64, _dbl, _dbl3, _vp, _vp]),
     "lj_force_vjp_workspace_bytes": (_sz, [_i64, _int]),
     "lj_force_vjp": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl3, _dbl, _dbl, _int,
                             _vp, _vp, _vp, _sz, _vp]),
@@ -369,3 +370,17 @@ def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float
                                ms, _stream(stream))
     _check(st, "lj_autotune_force")
     return int(best.value), float(best_ms.value), {c: float(m) for c, m in zip(candidates, ms)}
+
+
+def lj_drift(q4: torch.Tensor, p4: torch.Tensor, dt: float, box,
+             max_disp2: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """q += dt p (wrapped); returns the 1-element device tensor max |dt p|^2."""
+    lib = load()
+    n = int(q4.shape[0])
+    if max_disp2 is None:
+        max_disp2 = torch.empty(1, dtype=torch.float64, device=q4.device)
+    st = lib.lj_drift(_dev(q4, torch.float64, "q4", (n, 4)), _dev(p4, torch.float64, "p4", (n, 4)),
+                      n, float(dt), _box3(box), _dev(max_disp2, torch.float64, "max_disp2"),
+                      _stream(stream))
+    _check(st, "lj_drift")
+    return max_disp2

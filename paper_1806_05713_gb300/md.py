@@ -1,0 +1,73 @@
+"""Molecular dynamics around the force kernel: velocity Verlet (unit mass)
+with the bookkeeping method of the paper's section "Verlet List and
+Bookkeeping Method".
+
+The list is built with search length r_s = r_c + margin and reused while
+twice the accumulated fastest-atom displacement (the sum over steps of the
+largest |dt p|, reported by ``lj_drift``) stays below the margin; then it is
+rebuilt.  The kick and drift of consecutive steps are merged (leapfrog form
+of velocity Verlet), so each step is one ``lj_drift`` and one ``lj_force``
+call -- the force kernel applies the kick directly (Algorithm 1 updates the
+momenta with dt).  Host-side orchestration only: every step of the
+computation runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import lj
+
+
+class VelocityVerlet:
+    """Integrates q4, p4 (device, AoS4, updated in place)."""
+
+    def __init__(self, q4: torch.Tensor, p4: torch.Tensor, box, r_cut: float, margin: float,
+                 dt: float, eps: float = 1.0, sigma: float = 1.0, precision: int = lj.LJ_FP64,
+                 tpi: int = lj.LJ_TPI_AUTO, half: bool = True):
+        self.q4, self.p4 = q4, p4
+        self.box = [float(x) for x in box]
+        self.r_cut, self.margin, self.dt = float(r_cut), float(margin), float(dt)
+        self.eps, self.sigma = float(eps), float(sigma)
+        self.precision, self.tpi, self.half = int(precision), int(tpi), bool(half)
+        self.plist = None
+        self.rebuilds = 0
+        self.moved = 0.0          # fastest-atom displacement bound since the last build
+        self.max_disp2 = torch.zeros(1, dtype=torch.float64, device=q4.device)
+        self.ws = lj._workspace(lj.lj_force_workspace_bytes(q4.shape[0], self.box, self.precision),
+                                q4.device)
+        self._half_kicked = False
+        self._rebuild()
+
+    def _rebuild(self):
+        self.plist = lj.lj_build_pairlist(self.q4, self.box, self.r_cut + self.margin, self.half,
+                                          reuse=self.plist)
+        self.rebuilds += 1
+        self.moved = 0.0
+
+    def _kick(self, h: float):
+        lj.lj_force(self.q4, self.p4, self.plist, h, self.r_cut, self.box, self.eps, self.sigma,
+                    self.precision, self.tpi, workspace=self.ws)
+
+    def run(self, steps: int):
+        """Advance `steps` steps; p4 ends at the same time as q4."""
+        if steps <= 0:
+            return
+        if not self._half_kicked:
+            self._kick(0.5 * self.dt)              # p(t + dt/2)
+        for s in range(steps):
+            lj.lj_drift(self.q4, self.p4, self.dt, self.box, self.max_disp2)
+            self.moved += math.sqrt(float(self.max_disp2.item()))
+            if 2.0 * self.moved >= self.margin:
+                self._rebuild()
+            last = s == steps - 1
+            self._kick(0.5 * self.dt if last else self.dt)
+        self._half_kicked = False
+
+    def kinetic_energy(self) -> float:
+        return 0.5 * float((self.p4[:, :3] ** 2).sum())
+
+    def potential_energy(self, shifted: bool = True) -> float:
+        return float(lj.lj_energy(self.q4, self.plist, self.r_cut, self.box, self.eps, self.sigma,
+                                  shifted).item())

@@ -1,0 +1,94 @@
+"""Drift kernel and velocity-Verlet driver with the bookkeeping rebuild rule."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1806_05713_gb300 import inputs
+from conftest import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _np_drift(q, p, dt, L):
+    """The definition: x = q + dt p (separately rounded), one periodic wrap."""
+    out = q.copy()
+    d2 = np.zeros(q.shape[0])
+    for a in range(3):
+        dq = dt * p[:, a]
+        x = q[:, a] + dq
+        x = np.where(x >= L[a], x - L[a], np.where(x < 0.0, x + L[a], x))
+        x = np.where(x < L[a], x, 0.0)
+        out[:, a] = x
+        d2 = d2 + dq * dq
+    return out, float(d2.max())
+
+
+def test_drift_bit_exact(cuda_lib):
+    lj = cuda_lib
+    rng = np.random.default_rng(0)
+    L = np.array([10.0, 12.5, 7.25])
+    q = np.zeros((5000, 4))
+    q[:, :3] = rng.random((5000, 3)) * L
+    q[:3, 0] = [0.0, np.nextafter(L[0], 0), 5.0]
+    p = rng.normal(size=(5000, 4)) * 3.0
+    want, want_d2 = _np_drift(q, p, 0.013, L)
+    qd = to_dev(q)
+    m = lj.lj_drift(qd, to_dev(p), 0.013, L)
+    got = qd.cpu().numpy()
+    assert np.array_equal(got[:, :3], want[:, :3])
+    assert np.array_equal(got[:, 3], q[:, 3])
+    assert m.item() == want_d2
+    assert np.all((got[:, :3] >= 0) & (got[:, :3] < L))
+
+
+def test_verlet_matches_oracle_integrator(cuda_lib, oracle_lib):
+    from paper_1806_05713_gb300.md import VelocityVerlet
+    lj = cuda_lib
+    s = inputs.fcc_system(10, 1.0, 0.05, seed=3)
+    dt, steps = 0.005, 20
+    p0 = np.random.default_rng(1).normal(size=(s.n, 4)) * 0.5
+    p0[:, 3] = 0.0
+    q, p = to_dev(s.q), to_dev(p0)
+    vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, dt)
+    vv.run(steps)
+    torch.cuda.synchronize()
+    # reference: the same leapfrog with the oracle's list and force, fresh list every step
+    qr, pr = s.q.copy(), p0[:, :3].copy()
+
+    def kick(h):
+        rp, col = oracle_lib.pairlist(qr, s.box, s.rs, True)
+        return oracle_lib.force(qr, pr, rp, col, True, h, s.rc, s.box)
+    pr = kick(0.5 * dt)
+    for k in range(steps):
+        qn, _ = _np_drift(qr, np.concatenate([pr, np.zeros((s.n, 1))], 1), dt, s.box)
+        qr = qn
+        pr = kick(0.5 * dt if k == steps - 1 else dt)
+    dq = q.cpu().numpy()[:, :3] - qr[:, :3]
+    dq -= s.box * np.round(dq / s.box)
+    assert np.max(np.abs(dq)) < 1e-11
+    assert np.max(np.abs(p.cpu().numpy()[:, :3] - pr)) < 1e-9 * np.max(np.abs(pr))
+
+
+def test_energy_conservation_and_bookkeeping(cuda_lib):
+    from paper_1806_05713_gb300.md import VelocityVerlet
+    lj = cuda_lib
+    s = inputs.fcc_system(10, 0.8, 0.05, seed=2)
+    p0 = np.random.default_rng(5).normal(size=(s.n, 4)) * 1.2   # hot: atoms move, lists rebuild
+    p0[:, 3] = 0.0
+    p0[:, :3] -= p0[:, :3].mean(axis=0)
+    q, p = to_dev(s.q), to_dev(p0)
+    vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, 0.002)
+    e0 = vv.kinetic_energy() + vv.potential_energy(shifted=True)
+    vv.run(400)
+    e1 = vv.kinetic_energy() + vv.potential_energy(shifted=True)
+    assert vv.rebuilds >= 3
+    assert abs(e1 - e0) < 2e-3 * abs(e0), (e0, e1)
+    # the list in use still holds every pair within r_c: same forces as a fresh list
+    F_old = torch.zeros_like(q)
+    lj.lj_force(q, F_old, vv.plist, 1.0, s.rc, s.box)
+    fresh = lj.lj_build_pairlist(q, s.box, s.rs, True)
+    F_new = torch.zeros_like(q)
+    lj.lj_force(q, F_new, fresh, 1.0, s.rc, s.box)
+    assert float((F_old - F_new).abs().max()) <= 1e-12 * float(F_new.abs().max())
+    # total momentum stays zero (Newton's third law, half-list atomics)
+    assert float(p[:, :3].sum(0).abs().max()) < 1e-9
