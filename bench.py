@@ -52,9 +52,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of the FP64 force kernel, by
 # schedule, from one ncu capture of the kernel as it stands on this workload
-# (profiles/force_fp64_swp2_tpi8_half_N119164.md); a schedule without an
+# (profiles/force_fp64_images_tpi8_half_N119164.md); a schedule without an
 # entry reports null.
-TRAFFIC_PER_LAUNCH = {136: 41906944.0 + 0.0}
+TRAFFIC_PER_LAUNCH = {1032: 41903872.0 + 1280.0}
 
 
 def parse():
@@ -399,7 +399,7 @@ def main():
     roof = {"bound": "alu", "achieved": flops / t_force / 1e12, "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": flops / t_force / 1e12 / FP64_PEAK_TFLOPS,
             "traffic": TRAFFIC_PER_LAUNCH.get(best_tpi),
-            "traffic_source": "profiles/force_fp64_swp2_tpi8_half_N119164.md (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold cache)",
+            "traffic_source": "profiles/force_fp64_images_tpi8_half_N119164.md (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold cache)",
             "kernel": f"FP64 force kernel, {schedule_name(best_tpi)}, half list",
             "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
             "flops_per_launch": flops, "launch_ms": t_force * 1e3}
@@ -461,6 +461,8 @@ def schedule_name(tpi: int) -> str:
         name += ", 2 entries/lane (software-pipelined)"
     if tpi & 512:
         name += ", rows by length"
+    if tpi & 1024:
+        name += ", image-selected displacement"
     return name
 
 
@@ -477,7 +479,7 @@ def extra_million(lj, dev, stream, flush):
     res = {"n_atoms": s.n, "pairs_per_call": pl.nnz, "list_build_ms": t_list}
     best, _, _ = lj.lj_autotune_force(q, pl, DT, s.rc, box, reps=3)
     out = {}
-    for name, prec, tpis in (("fp64", lj.LJ_FP64, (best,)), ("mixed", lj.LJ_MIXED, (4, 8, 516, 520))):
+    for name, prec, tpis in (("fp64", lj.LJ_FP64, (best,)), ("mixed", lj.LJ_MIXED, (4, 8, 16))):
         for t in tpis:
             pp = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
             fn = lj.lj_force_prepared(q, pp, pl, DT, s.rc, box, precision=prec, tpi=t)
@@ -511,7 +513,7 @@ def extra_batched(lj, dev, stream, flush):
         tpi, rows, _ = b.autotune(tpis=(4, 8, 16), rows=(16, 32, 64, 128), reps=3)
         g = b.capture_graph()
         t_graph = time_calls(g.replay, stream, flush, 10, 2)
-        t_sep = time_calls(lambda: b.force_per_system(tpi=8 if prec == lj.LJ_MIXED else 136),
+        t_sep = time_calls(lambda: b.force_per_system(tpi=lj.LJ_TPI_AUTO),
                            stream, flush, 5, 1)
         res[name] = {"tpi": tpi, "rows_per_item": rows, "pairs_per_call": b.pairs,
                      "graph_persistent_ms": t_graph,
@@ -632,7 +634,7 @@ def variants(lj, s, q, pl_half, box, dev, stream, flush):
             res[f"list_build_ms/{order}/{kind}"] = t_list
             p64 = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
             ref = None
-            for prec, tpis in ((lj.LJ_FP64, (136, 648, 644, 200)), (lj.LJ_MIXED, (4, 8, 516, 520))):
+            for prec, tpis in ((lj.LJ_FP64, (136, 1160, 1672, 200)), (lj.LJ_MIXED, (4, 8, 16))):
                 for tpi in tpis:
                     pp = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
                     fn = lj.lj_force_prepared(qq, pp, pl, DT, sys_.rc, box, precision=prec, tpi=tpi)

@@ -65,7 +65,7 @@ extern "C" {
 /* ---- schedules ---------------------------------------------------------- */
 /* `tpi` = threads per i-row: 1, 2, 4, 8, 16 or 32 lanes of one warp walk one
  * row and reduce their partial sums with warp shuffles; 0 = library default
- * (8 lanes per row). */
+ * (FP64: LJ_SCHED_IMAGES | 8; mixed: 8 lanes per row). */
 #define LJ_TPI_AUTO 0
 /* LJ_SCHED_REFILL | t (t = 1, 4 or 8; FP64 only): the group-refill schedule.
  * Each group of t lanes owns one row at a time and takes the next row as
@@ -92,6 +92,11 @@ extern "C" {
  * workspace, three small kernels per call), so the groups of a warp walk
  * rows of equal length and none waits for a longer one. */
 #define LJ_SCHED_SORTED 512
+/* LJ_SCHED_IMAGES | 8 or | LJ_SCHED_SWP2 | 4, 8, 16 (FP64 only): each row
+ * precomputes the periodic images q_i +- L and each entry picks the minimum
+ * image of q_i with integer compares of IEEE high words, so the
+ * displacement costs one FP64 subtraction and no wrap addition. */
+#define LJ_SCHED_IMAGES 1024
 
 const char *lj_status_string(int status);
 /* Text of the last CUDA error seen by this library in this thread. */
@@ -202,7 +207,8 @@ size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
  *                   16, LJ_SCHED_REFILL | 1, 4, 8 (optionally | SWP2), or
  *                   LJ_SCHED_QUEUE | 1, 2, 4, 8; the last three families
  *                   FP64 only.  LJ_SCHED_SORTED may be or-ed into the plain
- *                   and SWP2 schedules.
+ *                   and SWP2 schedules, LJ_SCHED_IMAGES into FP64 | 8 and
+ *                   the SWP2 schedules.
  *  workspace_dev    scratch of lj_force_workspace_bytes() (NULL if 0).
  * Half lists add p_j with FP64 atomics, so their rounding order (not their
  * value beyond the last bits) varies between calls; full lists are

@@ -106,7 +106,8 @@ class Batch:
                   "lj_force_batched")
         return p4
 
-    def force_per_system(self, p4: torch.Tensor | None = None, tpi: int = 8, stream=None):
+    def force_per_system(self, p4: torch.Tensor | None = None, tpi: int = lj.LJ_TPI_AUTO,
+                         stream=None):
         """The same update as separate lj_force calls, one per system."""
         p4 = self.p4 if p4 is None else p4
         ws = getattr(self, "_ws1", None)

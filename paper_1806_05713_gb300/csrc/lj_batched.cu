@@ -85,7 +85,7 @@ __global__ void batched_prepass_kernel(const SysDev *__restrict__ sys, const Ite
 }
 
 template <int TPI, bool MIXED>
-__global__ void __launch_bounds__(kBatchThreads, 4)
+__global__ void __launch_bounds__(kBatchThreads)
 batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ items,
                      long long nitems, const double *__restrict__ q4, const uint4 *__restrict__ rel,
                      double *__restrict__ p4, const int *__restrict__ row_ptr,
@@ -119,9 +119,9 @@ batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ it
                 } else {
                     const Fp64Params P = S.fp;
                     if (half)
-                        fp64_row<TPI, true, 1>(sq, sp, srp, scol, r, P, gm);
+                        fp64_row<TPI, true, 1, true>(sq, sp, srp, scol, r, P, gm);
                     else
-                        fp64_row<TPI, false, 1>(sq, sp, srp, scol, r, P, gm);
+                        fp64_row<TPI, false, 1, true>(sq, sp, srp, scol, r, P, gm);
                 }
             }
         }

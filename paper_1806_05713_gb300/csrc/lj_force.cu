@@ -43,7 +43,7 @@ namespace {
 // ---------------------------------------------------------------------------
 // order: NULL (rows in index order) or a permutation of the rows (the
 // length-sorted order of LJ_SCHED_SORTED).
-template <int TPI, bool HALF, int U>
+template <int TPI, bool HALF, int U, bool IMG>
 __global__ void __launch_bounds__(256)
 force_fp64_kernel(const double *__restrict__ q4, double *__restrict__ p4, int n,
                   const int *__restrict__ row_ptr, const int *__restrict__ col, Fp64Params P,
@@ -54,7 +54,7 @@ force_fp64_kernel(const double *__restrict__ q4, double *__restrict__ p4, int n,
     // the row walk name only the group's own lanes, which iterate together.
     if (gid >= n) return;
     const int i = order ? order[gid] : gid;
-    fp64_row<TPI, HALF, U>(q4, p4, row_ptr, col, i, P, group_mask<TPI>());
+    fp64_row<TPI, HALF, U, IMG>(q4, p4, row_ptr, col, i, P, group_mask<TPI>());
 }
 
 template <int TPI, bool HALF>
@@ -125,16 +125,16 @@ int sort_rows_by_length(const int *row_ptr, int n, int *hist, int *slot, int *or
 // Host side
 // ---------------------------------------------------------------------------
 
-template <int TPI, int U>
+template <int TPI, int U, bool IMG = false>
 int launch_fp64(const double *q4, double *p4, int n, const int *rp, const int *col, int half,
                 const Fp64Params &P, const int *order, cudaStream_t st)
 {
     const int64_t threads = int64_t(n) * TPI;
     const unsigned grid = unsigned((threads + 255) / 256);
     if (half)
-        force_fp64_kernel<TPI, true, U><<<grid, 256, 0, st>>>(q4, p4, n, rp, col, P, order);
+        force_fp64_kernel<TPI, true, U, IMG><<<grid, 256, 0, st>>>(q4, p4, n, rp, col, P, order);
     else
-        force_fp64_kernel<TPI, false, U><<<grid, 256, 0, st>>>(q4, p4, n, rp, col, P, order);
+        force_fp64_kernel<TPI, false, U, IMG><<<grid, 256, 0, st>>>(q4, p4, n, rp, col, P, order);
     LJ_TRY_LAUNCH("force_fp64_kernel");
     return LJ_OK;
 }
@@ -211,7 +211,10 @@ bool valid_schedule(int s, int precision)
     if (s & LJ_SCHED_REFILL)
         return precision == LJ_FP64 && (s & ~(LJ_SCHED_REFILL | LJ_SCHED_SWP2 | 63)) == 0 &&
                (t == 0 || t == 1 || t == 4 || t == 8);
-    if (s & ~(LJ_SCHED_SORTED | LJ_SCHED_SWP2 | 63)) return false;
+    if (s & ~(LJ_SCHED_SORTED | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES | 63)) return false;
+    if (s & LJ_SCHED_IMAGES)
+        return precision == LJ_FP64 &&
+               ((s & LJ_SCHED_SWP2) ? (t == 4 || t == 8 || t == 16) : t == 8);
     if (s & LJ_SCHED_SWP2) return precision == LJ_FP64 && (t == 4 || t == 8 || t == 16);
     return pow2;
 }
@@ -237,7 +240,7 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
     if (precision != LJ_FP64 && precision != LJ_MIXED) return LJ_ERR_ARG;
     if (n == 0 || nnz == 0) return LJ_OK;
     const int ni = static_cast<int>(n);
-    if (tpi == LJ_TPI_AUTO) tpi = precision == LJ_FP64 ? (LJ_SCHED_SWP2 | 8) : 8;
+    if (tpi == LJ_TPI_AUTO) tpi = precision == LJ_FP64 ? (LJ_SCHED_IMAGES | 8) : 8;
     if (!valid_schedule(tpi, precision)) return LJ_ERR_ARG;
     if (!ws || ws_bytes < force_workspace_bytes_impl(n, precision)) return LJ_ERR_CAPACITY;
     const ForceWs W = carve_force_ws(ws, n, precision);
@@ -270,6 +273,10 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
             case 4 | LJ_SCHED_SWP2: return launch_fp64<4, 2>(q4, p4, ni, row_ptr, col, half, P, order, st);
             case 8 | LJ_SCHED_SWP2: return launch_fp64<8, 2>(q4, p4, ni, row_ptr, col, half, P, order, st);
             case 16 | LJ_SCHED_SWP2: return launch_fp64<16, 2>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 8 | LJ_SCHED_IMAGES: return launch_fp64<8, 1, true>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 4 | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES: return launch_fp64<4, 2, true>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 8 | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES: return launch_fp64<8, 2, true>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 16 | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES: return launch_fp64<16, 2, true>(q4, p4, ni, row_ptr, col, half, P, order, st);
             default: return LJ_ERR_ARG;
         }
     }

@@ -15,7 +15,7 @@ namespace {
 // and distance work of one entry overlap the force arithmetic of the other,
 // so the long dependent FP64 chains of two pairs are in flight together).
 // Pointers are the system's own arrays (local indices).
-template <int TPI, bool HALF, int U>
+template <int TPI, bool HALF, int U, bool IMG = false>
 __device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *__restrict__ p4,
                                          const int *__restrict__ row_ptr,
                                          const int *__restrict__ col, int i, const Fp64Params &P,
@@ -24,6 +24,25 @@ __device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *
     const int sub = threadIdx.x & (TPI - 1);
     double xi, yi, zi;
     load_q4_256(q4, i, xi, yi, zi);
+    // IMG: the two periodic images of q_i per axis and the high words of
+    // q_i +- L/2, so that each entry picks the minimum image of q_i with
+    // integer compares and needs one FP64 subtraction, never a wrap add.
+    // (An entry whose high word ties the threshold lies within 2^-20 of half
+    // a box from i, beyond r_c in either image.)
+    double im[3][2];
+    int th[3][2];
+    if (IMG) {
+        const double c[3] = {xi, yi, zi};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            im[a][0] = c[a] - P.L[a];
+            im[a][1] = c[a] + P.L[a];
+            double hl;
+            memcpy(&hl, &P.half_bits[a], sizeof(double));
+            th[a][0] = __double2hiint(c[a] - hl);
+            th[a][1] = __double2hiint(c[a] + hl);
+        }
+    }
     double ax = 0.0, ay = 0.0, az = 0.0;
     const int kb = row_ptr[i], ke = row_ptr[i + 1];
     for (int base = kb; base < ke; base += TPI * U) {
@@ -36,18 +55,33 @@ __device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *
             valid[u] = k < ke;
             j[u] = valid[u] ? col[k] : i;
         }
+        double xj[U], yj[U], zj[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            double xj, yj, zj;
-            load_q4_256(q4, j[u], xj, yj, zj);
-            dx[u] = xj - xi;
-            dy[u] = yj - yi;
-            dz[u] = zj - zi;
+            load_q4_256(q4, j[u], xj[u], yj[u], zj[u]);
+            if (IMG) {
+                const double cj[3] = {xj[u], yj[u], zj[u]};
+                const double ci[3] = {xi, yi, zi};
+                double d[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int hj = __double2hiint(cj[a]);
+                    const double img = hj > th[a][1] ? im[a][1] : (hj < th[a][0] ? im[a][0] : ci[a]);
+                    d[a] = cj[a] - img;
+                }
+                dx[u] = d[0];
+                dy[u] = d[1];
+                dz[u] = d[2];
+            } else {
+                dx[u] = xj[u] - xi;
+                dy[u] = yj[u] - yi;
+                dz[u] = zj[u] - zi;
+            }
         }
         bool anynear = false, anyin = false;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            min_image3(dx[u], dy[u], dz[u], P.L, P.half_bits, gm);
+            if (!IMG) min_image3(dx[u], dy[u], dz[u], P.L, P.half_bits, gm);
             r2[u] = fma(dz[u], dz[u], fma(dy[u], dy[u], dx[u] * dx[u]));
             const long long rb = __double_as_longlong(r2[u]);
             in[u] = valid[u] && rb < P.rc2_bits;
@@ -56,8 +90,20 @@ __device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *
         }
         if (__any_sync(gm, anynear)) {
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (near[u]) in[u] = exact_in_cutoff(dx[u], dy[u], dz[u], P.rc2);
+            for (int u = 0; u < U; ++u) {
+                if (near[u]) {
+                    if (IMG) {
+                        // the definition's operations: d = q_j - q_i, then the wrap
+                        const double ex = min_image(xj[u] - xi, P.L[0], P.half_bits[0]);
+                        const double ey = min_image(yj[u] - yi, P.L[1], P.half_bits[1]);
+                        const double ez = min_image(zj[u] - zi, P.L[2], P.half_bits[2]);
+                        in[u] = exact_in_cutoff(ex, ey, ez, P.rc2);
+                    } else {
+                        // dx, dy, dz were formed with exactly those operations
+                        in[u] = exact_in_cutoff(dx[u], dy[u], dz[u], P.rc2);
+                    }
+                }
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {

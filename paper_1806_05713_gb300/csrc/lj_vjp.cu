@@ -106,6 +106,21 @@ vjp_fp64_kernel(const double *__restrict__ q4, const double *__restrict__ R4, in
         double xi, yi, zi, Rxi, Ryi, Rzi;
         load_q4_256(q4, i, xi, yi, zi);
         load_r3(R4, i, Rxi, Ryi, Rzi);
+        // Periodic images of q_i and the high words of q_i +- L/2: each entry
+        // picks the minimum image with integer compares (one FP64
+        // subtraction per axis, no wrap addition).
+        const double ci[3] = {xi, yi, zi};
+        double im[3][2];
+        int th[3][2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            im[a][0] = ci[a] - P.L[a];
+            im[a][1] = ci[a] + P.L[a];
+            double hl;
+            memcpy(&hl, &P.half_bits[a], sizeof(double));
+            th[a][0] = __double2hiint(ci[a] - hl);
+            th[a][1] = __double2hiint(ci[a] + hl);
+        }
         double ax = 0.0, ay = 0.0, az = 0.0;
         const int kb = row_ptr[i], ke = row_ptr[i + 1];
         for (int base = kb; base < ke; base += TPI) {
@@ -114,14 +129,26 @@ vjp_fp64_kernel(const double *__restrict__ q4, const double *__restrict__ R4, in
             const int j = valid ? col[k] : i;
             double xj, yj, zj;
             load_q4_256(q4, j, xj, yj, zj);
-            double dx = xj - xi, dy = yj - yi, dz = zj - zi;
-            min_image3(dx, dy, dz, P.L, P.half_bits, gm);
+            const double cj[3] = {xj, yj, zj};
+            double dd[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int hj = __double2hiint(cj[a]);
+                const double img = hj > th[a][1] ? im[a][1] : (hj < th[a][0] ? im[a][0] : ci[a]);
+                dd[a] = cj[a] - img;
+            }
+            const double dx = dd[0], dy = dd[1], dz = dd[2];
             double s = fma(dz, dz, fma(dy, dy, dx * dx));
             const long long sb = __double_as_longlong(s);
             bool in = valid && sb < P.rc2_bits;
             const bool near = valid && static_cast<unsigned long long>(sb - P.rc2_bits + 64) < 128ull;
             if (__any_sync(gm, near)) {
-                if (near) in = exact_in_cutoff(dx, dy, dz, P.rc2);
+                if (near) {
+                    const double ex = min_image(xj - xi, P.L[0], P.half_bits[0]);
+                    const double ey = min_image(yj - yi, P.L[1], P.half_bits[1]);
+                    const double ez = min_image(zj - zi, P.L[2], P.half_bits[2]);
+                    in = exact_in_cutoff(ex, ey, ez, P.rc2);
+                }
             }
             if (!valid) s = 1.0;
             if (__any_sync(gm, in)) {

@@ -31,6 +31,7 @@ LJ_SCHED_REFILL = 64
 LJ_SCHED_SWP2 = 128
 LJ_SCHED_QUEUE = 256
 LJ_SCHED_SORTED = 512
+LJ_SCHED_IMAGES = 1024
 LJ_STATIC_MAX_ATOMS = 131072
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liblj_gb300.so")
@@ -351,9 +352,10 @@ def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float
     (best_tpi, best_ms, {tpi: ms})."""
     lib = load()
     if candidates is None:
-        S, W = LJ_SCHED_SORTED, LJ_SCHED_SWP2
-        candidates = ([8, W | 4, W | 8, W | 16, S | 8, S | W | 4, S | W | 8, S | W | 16,
-                       LJ_SCHED_REFILL | W | 4, LJ_SCHED_REFILL | W | 8, LJ_SCHED_QUEUE | 8]
+        S, W, I = LJ_SCHED_SORTED, LJ_SCHED_SWP2, LJ_SCHED_IMAGES
+        candidates = ([8, W | 4, W | 8, W | 16, I | 8, I | W | 4, I | W | 8, I | W | 16,
+                       S | W | 8, S | I | W | 8, LJ_SCHED_REFILL | W | 4,
+                       LJ_SCHED_REFILL | W | 8, LJ_SCHED_QUEUE | 8]
                       if precision == LJ_FP64 else [2, 4, 8, 16, S | 4, S | 8, S | 16])
     n = plist.n
     scratch = torch.zeros((n, 4), dtype=torch.float64, device=q4.device)

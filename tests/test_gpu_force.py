@@ -14,8 +14,9 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-12
 MIXED_TOL = 1e-5
 SCHEDULES = [1, 2, 4, 8, 16, 32, 132, 136, 144, 64, 68, 72, 196, 200, 257, 258, 260, 264, 520,
-             644, 648, 656]
-# 128|t software-pipelined, 64|t group-refill, 256|t lane-queue, 512|... length-sorted rows
+             644, 648, 656, 1032, 1156, 1160, 1168, 1672]
+# 128|t software-pipelined, 64|t group-refill, 256|t lane-queue, 512|... length-sorted rows,
+# 1024|... image-selected displacement
 
 
 def _run(lj, s, half, precision, tpi, dt=0.01, eps=1.0, sigma=1.0, p0=None, rc=None, pl=None):
@@ -67,7 +68,7 @@ def test_eps_sigma_dt_and_existing_momenta(cuda_lib, oracle_lib, precision, tol)
     p0 = np.random.default_rng(2).normal(size=(s.n, 4))
     kw = dict(dt=0.005, eps=1.3, sigma=1.1, rc=3.0)
     for half in (True, False):
-        for tpi in ((64, 8, 136, 200, 260) if precision == 0 else (8,)):
+        for tpi in ((64, 8, 136, 200, 260, 1160) if precision == 0 else (8,)):
             got, _ = _run(cuda_lib, s, half, precision, tpi, p0=p0, **kw)
             want = _oracle(oracle_lib, s, half, p0=p0, **kw)
             assert _relerr(got - p0[:, :3], want - p0[:, :3]) <= tol
@@ -137,7 +138,7 @@ def test_fp64_paper_size(cuda_lib, oracle_lib, order, half):
     s = inputs.workload_paper(order=order)
     want = _oracle(oracle_lib, s, half)
     pl = None
-    for tpi in (64, 8, 32, 136, 72, 200, 258, 260, 264, 648):
+    for tpi in (64, 8, 32, 136, 72, 200, 258, 260, 264, 648, 1160, 1672):
         got, pl = _run(cuda_lib, s, half, 0, tpi, pl=pl)
         assert _relerr(got, want) <= FP64_TOL, tpi
 
