@@ -634,7 +634,7 @@ def variants(lj, s, q, pl_half, box, dev, stream, flush):
             res[f"list_build_ms/{order}/{kind}"] = t_list
             p64 = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
             ref = None
-            for prec, tpis in ((lj.LJ_FP64, (136, 1160, 1672, 200)), (lj.LJ_MIXED, (4, 8, 16))):
+            for prec, tpis in ((lj.LJ_FP64, (1032, 1028, 1544, 1160)), (lj.LJ_MIXED, (4, 8, 16))):
                 for tpi in tpis:
                     pp = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
                     fn = lj.lj_force_prepared(qq, pp, pl, DT, sys_.rc, box, precision=prec, tpi=tpi)

@@ -92,7 +92,7 @@ extern "C" {
  * workspace, three small kernels per call), so the groups of a warp walk
  * rows of equal length and none waits for a longer one. */
 #define LJ_SCHED_SORTED 512
-/* LJ_SCHED_IMAGES | 8 or | LJ_SCHED_SWP2 | 4, 8, 16 (FP64 only): each row
+/* LJ_SCHED_IMAGES | 4, 8, 16, optionally | LJ_SCHED_SWP2 (FP64 only): each row
  * precomputes the periodic images q_i +- L and each entry picks the minimum
  * image of q_i with integer compares of IEEE high words, so the
  * displacement costs one FP64 subtraction and no wrap addition. */
@@ -207,8 +207,8 @@ size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
  *                   16, LJ_SCHED_REFILL | 1, 4, 8 (optionally | SWP2), or
  *                   LJ_SCHED_QUEUE | 1, 2, 4, 8; the last three families
  *                   FP64 only.  LJ_SCHED_SORTED may be or-ed into the plain
- *                   and SWP2 schedules, LJ_SCHED_IMAGES into FP64 | 8 and
- *                   the SWP2 schedules.
+ *                   and SWP2 schedules, LJ_SCHED_IMAGES into the FP64
+ *                   4, 8, 16 and SWP2 schedules.
  *  workspace_dev    scratch of lj_force_workspace_bytes() (NULL if 0).
  * Half lists add p_j with FP64 atomics, so their rounding order (not their
  * value beyond the last bits) varies between calls; full lists are

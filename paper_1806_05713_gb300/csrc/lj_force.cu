@@ -212,9 +212,7 @@ bool valid_schedule(int s, int precision)
         return precision == LJ_FP64 && (s & ~(LJ_SCHED_REFILL | LJ_SCHED_SWP2 | 63)) == 0 &&
                (t == 0 || t == 1 || t == 4 || t == 8);
     if (s & ~(LJ_SCHED_SORTED | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES | 63)) return false;
-    if (s & LJ_SCHED_IMAGES)
-        return precision == LJ_FP64 &&
-               ((s & LJ_SCHED_SWP2) ? (t == 4 || t == 8 || t == 16) : t == 8);
+    if (s & LJ_SCHED_IMAGES) return precision == LJ_FP64 && (t == 4 || t == 8 || t == 16);
     if (s & LJ_SCHED_SWP2) return precision == LJ_FP64 && (t == 4 || t == 8 || t == 16);
     return pow2;
 }
@@ -273,7 +271,9 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
             case 4 | LJ_SCHED_SWP2: return launch_fp64<4, 2>(q4, p4, ni, row_ptr, col, half, P, order, st);
             case 8 | LJ_SCHED_SWP2: return launch_fp64<8, 2>(q4, p4, ni, row_ptr, col, half, P, order, st);
             case 16 | LJ_SCHED_SWP2: return launch_fp64<16, 2>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 4 | LJ_SCHED_IMAGES: return launch_fp64<4, 1, true>(q4, p4, ni, row_ptr, col, half, P, order, st);
             case 8 | LJ_SCHED_IMAGES: return launch_fp64<8, 1, true>(q4, p4, ni, row_ptr, col, half, P, order, st);
+            case 16 | LJ_SCHED_IMAGES: return launch_fp64<16, 1, true>(q4, p4, ni, row_ptr, col, half, P, order, st);
             case 4 | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES: return launch_fp64<4, 2, true>(q4, p4, ni, row_ptr, col, half, P, order, st);
             case 8 | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES: return launch_fp64<8, 2, true>(q4, p4, ni, row_ptr, col, half, P, order, st);
             case 16 | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES: return launch_fp64<16, 2, true>(q4, p4, ni, row_ptr, col, half, P, order, st);

@@ -353,9 +353,8 @@ def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float
     lib = load()
     if candidates is None:
         S, W, I = LJ_SCHED_SORTED, LJ_SCHED_SWP2, LJ_SCHED_IMAGES
-        candidates = ([8, W | 4, W | 8, W | 16, I | 8, I | W | 4, I | W | 8, I | W | 16,
-                       S | W | 8, S | I | W | 8, LJ_SCHED_REFILL | W | 4,
-                       LJ_SCHED_REFILL | W | 8, LJ_SCHED_QUEUE | 8]
+        candidates = ([8, W | 8, I | 4, I | 8, I | 16, I | W | 4, I | W | 8, S | I | 4,
+                       S | I | 8, S | I | 16, LJ_SCHED_REFILL | W | 8, LJ_SCHED_QUEUE | 8]
                       if precision == LJ_FP64 else [2, 4, 8, 16, S | 4, S | 8, S | 16])
     n = plist.n
     scratch = torch.zeros((n, 4), dtype=torch.float64, device=q4.device)

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-12
 MIXED_TOL = 1e-5
 SCHEDULES = [1, 2, 4, 8, 16, 32, 132, 136, 144, 64, 68, 72, 196, 200, 257, 258, 260, 264, 520,
-             644, 648, 656, 1032, 1156, 1160, 1168, 1672]
+             644, 648, 656, 1028, 1032, 1040, 1156, 1160, 1168, 1672, 1544]
 # 128|t software-pipelined, 64|t group-refill, 256|t lane-queue, 512|... length-sorted rows,
 # 1024|... image-selected displacement
 
