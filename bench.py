@@ -632,7 +632,6 @@ def variants(lj, s, q, pl_half, box, dev, stream, flush):
             pl = lj.lj_build_pairlist(qq, box, sys_.rs, half)
             m_half = pl.nnz if half else pl.nnz // 2
             res[f"list_build_ms/{order}/{kind}"] = t_list
-            p64 = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
             ref = None
             for prec, tpis in ((lj.LJ_FP64, (1032, 1028, 1544, 1160)), (lj.LJ_MIXED, (4, 8, 16))):
                 for tpi in tpis:
@@ -650,7 +649,23 @@ def variants(lj, s, q, pl_half, box, dev, stream, flush):
                         err = pp[:, :3] - ref
                         res[name]["max_err_rel"] = float(err.abs().max() / ref.abs().max())
                         res[name]["rms_err_rel"] = float(err.pow(2).mean().sqrt() / ref.pow(2).mean().sqrt())
-            del p64
+    # the paper's layout question on GB300: AoS4 vs AoS8 vs SoA, FP64, 8 lanes/row
+    for half in (True, False):
+        kind = "half" if half else "full"
+        pl = lj.lj_build_pairlist(q, box, s.rs, half)
+        m_half = pl.nnz if half else pl.nnz // 2
+        n = s.n
+        rec = torch.zeros((n, 8), dtype=torch.float64, device=dev)
+        rec[:, :3] = q[:, :3]
+        qs = q[:, :3].t().contiguous()
+        ps = torch.zeros_like(qs)
+        p4 = torch.zeros_like(q)
+        for name, fn in (("aos4", lambda: lj.lj_force_strided(q, p4, n, 4, 1, pl, DT, s.rc, box)),
+                         ("aos8", lambda: lj.lj_force_strided(rec, rec, n, 8, 1, pl, DT, s.rc, box,
+                                                              p_offset=4)),
+                         ("soa", lambda: lj.lj_force_strided(qs, ps, n, 1, n, pl, DT, s.rc, box))):
+            ms = time_calls(fn, stream, flush)
+            res[f"layout/fp64/random/{kind}/{name}"] = {"ms": ms, "pairs_per_s": m_half / (ms / 1e3)}
     return res
 
 

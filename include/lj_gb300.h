@@ -220,6 +220,44 @@ int lj_force(const double *q4_dev, double *p4_dev, int64_t n, const int32_t *row
              const double box[3], double eps, double sigma, int precision, int tpi,
              void *workspace_dev, size_t workspace_bytes, void *stream);
 
+/*
+ * lj_force in the FP64 form for positions and momenta in any strided layout
+ * -- the data-layout question of the paper (Fig. "Data layout"; sections
+ * "AoS with Padding" and "AoS with Eight Elements"): element (i, a) of q and
+ * of p is at q_dev[i * row_stride + a * comp_stride] (same strides for p).
+ *   AoS4: row_stride 4, comp_stride 1 (lj_force's layout);
+ *   AoS8: row_stride 8, comp_stride 1, p_dev = q_dev + 4 (q and p of an atom
+ *         in one 64-byte record);
+ *   SoA:  row_stride 1, comp_stride n (x[], y[], z[] back to back).
+ * Rows are read with one 256-bit load when comp_stride = 1, row_stride is a
+ * multiple of 4 and q_dev is 32-byte aligned, else with three 8-byte loads.
+ * lanes_per_row: 4, 8 or 16 (the image-selected FP64 schedule).  Pointers
+ * 8-byte aligned.  Same semantics and errors as lj_force; no workspace.
+ */
+int lj_force_strided(const double *q_dev, double *p_dev, int64_t n, int64_t row_stride,
+                     int64_t comp_stride, const int32_t *row_ptr_dev, const int32_t *col_dev,
+                     int64_t nnz, int half, double dt, double r_cut, const double box[3],
+                     double eps, double sigma, int lanes_per_row, void *stream);
+
+/* Bytes of device workspace lj_force_energy needs. */
+size_t lj_force_energy_workspace_bytes(int64_t n);
+
+/*
+ * lj_force (FP64 form, 8 lanes per row, image-selected displacement) that
+ * also returns the potential energy of the same configuration, Eq. (1)
+ * truncated at r_cut and, if shifted != 0, shifted so that V(r_cut) = 0 --
+ * the energy a velocity-Verlet loop monitors, as a by-product of the force
+ * pass (the pair energy reuses the pass's 1/r^2: three extra FP64
+ * instructions per pair).  e_out_dev: one device double, overwritten; a
+ * full list counts each pair once (half of its entries' sum).  The energy
+ * sum is deterministic (fixed-order reduction).  Asynchronous.  Errors as
+ * lj_force and lj_energy.
+ */
+int lj_force_energy(const double *q4_dev, double *p4_dev, int64_t n, const int32_t *row_ptr_dev,
+                    const int32_t *col_dev, int64_t nnz, int half, double dt, double r_cut,
+                    const double box[3], double eps, double sigma, int shifted, double *e_out_dev,
+                    void *workspace_dev, size_t workspace_bytes, void *stream);
+
 /* ======================================================================== */
 /* Energy (Eq. 1, truncated at r_c, optionally shifted)                     */
 /* ======================================================================== */

@@ -30,6 +30,7 @@
 // In both forms a pair whose r^2 lies within a proven error band of r_c^2
 // is re-decided with the exact FP64 definition, so the set of interacting
 // pairs is the same as in double precision.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -67,6 +68,82 @@ force_mixed_kernel(const double *__restrict__ q4, const uint4 *__restrict__ rel,
     if (gid >= n) return;
     const int i = order ? order[gid] : gid;
     mixed_row<TPI, HALF>(q4, rel, p4, row_ptr, col, i, P);
+}
+
+// Force and potential energy in one pass (FP64, 8 lanes per row, image-
+// selected displacement): each thread keeps its row's pair-energy sum and
+// in-cutoff count; a fixed-order block reduction writes one partial per
+// block (the final sum is taken by energy_partials_kernel).
+__global__ void __launch_bounds__(256)
+force_energy_fp64_kernel(const double *__restrict__ q4, double *__restrict__ p4, int n,
+                         const int *__restrict__ row_ptr, const int *__restrict__ col,
+                         Fp64Params P, int half, double *__restrict__ partial)
+{
+    constexpr int TPI = 8;
+    __shared__ double red_e[8];
+    __shared__ long long red_c[8];
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
+    double ev = 0.0;
+    int cnt = 0;
+    if (gid < n) {
+        if (half)
+            fp64_row<TPI, true, 1, true, 0, true>(q4, p4, row_ptr, col, gid, P, group_mask<TPI>(),
+                                                  Layout{4, 1}, &ev, &cnt);
+        else
+            fp64_row<TPI, false, 1, true, 0, true>(q4, p4, row_ptr, col, gid, P, group_mask<TPI>(),
+                                                   Layout{4, 1}, &ev, &cnt);
+    }
+    long long c = cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ev += __shfl_xor_sync(0xffffffffu, ev, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red_e[threadIdx.x >> 5] = ev;
+        red_c[threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double se = 0.0;
+        long long sc = 0;
+        for (int w = 0; w < 8; ++w) {
+            se += red_e[w];
+            sc += red_c[w];
+        }
+        partial[2 * blockIdx.x] = se;
+        partial[2 * blockIdx.x + 1] = static_cast<double>(sc);
+    }
+}
+
+// E = scale * (sum of pair energies - vshift * number of in-cutoff entries).
+__global__ void energy_partials_kernel(const double *__restrict__ partial, int blocks, double scale,
+                                       double vshift, double *__restrict__ out)
+{
+    __shared__ double se[32], sc[32];
+    double e = 0.0, c = 0.0;
+    for (int t = threadIdx.x; t < blocks; t += blockDim.x) {
+        e += partial[2 * t];
+        c += partial[2 * t + 1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        se[threadIdx.x >> 5] = e;
+        sc[threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double te = 0.0, tc = 0.0;
+        for (int w = 0; w < int(blockDim.x / 32); ++w) {
+            te += se[w];
+            tc += sc[w];
+        }
+        *out = scale * (te - vshift * tc);
+    }
 }
 
 // Rows in order of decreasing length (LJ_SCHED_SORTED): a counting sort on
@@ -296,6 +373,46 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
 }
 
 }  // namespace lj
+
+extern "C" size_t lj_force_energy_workspace_bytes(int64_t n)
+{
+    const int64_t blocks = (std::max<int64_t>(n, 1) * 8 + 255) / 256;
+    return size_t(2 * blocks) * sizeof(double) + 256;
+}
+
+extern "C" int lj_force_energy(const double *q4_dev, double *p4_dev, int64_t n,
+                               const int32_t *row_ptr_dev, const int32_t *col_dev, int64_t nnz,
+                               int half, double dt, double r_cut, const double box[3], double eps,
+                               double sigma, int shifted, double *e_out_dev, void *workspace_dev,
+                               size_t workspace_bytes, void *stream)
+{
+    using namespace lj;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_force_args(q4_dev, p4_dev, n, row_ptr_dev, col_dev, nnz, r_cut, box, eps, sigma,
+                              dt);
+    if (rc != LJ_OK) return rc;
+    if (!e_out_dev || (reinterpret_cast<uintptr_t>(e_out_dev) & 7u)) return LJ_ERR_ARG;
+    if (n == 0 || nnz == 0) {
+        LJ_TRY_CUDA(cudaMemsetAsync(e_out_dev, 0, sizeof(double), st));
+        return LJ_OK;
+    }
+    if (!workspace_dev || workspace_bytes < lj_force_energy_workspace_bytes(n)) return LJ_ERR_CAPACITY;
+    const Fp64Params P = make_fp64_params(box, dt, r_cut, eps, sigma);
+    const int blocks = static_cast<int>((n * 8 + 255) / 256);
+    Carver c(workspace_dev);
+    double *partial = c.take<double>(2 * size_t(blocks));
+    force_energy_fp64_kernel<<<blocks, 256, 0, st>>>(q4_dev, p4_dev, static_cast<int>(n), row_ptr_dev,
+                                                     col_dev, P, half, partial);
+    LJ_TRY_LAUNCH("force_energy_fp64_kernel");
+    double vshift = 0.0;
+    if (shifted) {
+        const double sr2 = sigma * sigma / (r_cut * r_cut), sr6 = sr2 * sr2 * sr2;
+        vshift = 4.0 * eps * (sr6 * sr6 - sr6);
+    }
+    energy_partials_kernel<<<1, 1024, 0, st>>>(partial, blocks, half ? 1.0 : 0.5, vshift, e_out_dev);
+    LJ_TRY_LAUNCH("energy_partials_kernel");
+    return LJ_OK;
+}
 
 extern "C" size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision)
 {

@@ -16,6 +16,7 @@ struct Fp64Params {
     long long rc2_bits;
     double rc2;
     double A, B;  // df = u^4 (A - B u^3): A = 24 eps sigma^6 dt, B = 48 eps sigma^12 dt
+    double C12, C6;  // V = u^3 (C12 u^3 - C6): C12 = 4 eps sigma^12, C6 = 4 eps sigma^6
 };
 
 struct MixedParams {
@@ -161,6 +162,8 @@ Fp64Params make_fp64_params(const double box[3], double dt, double rc, double ep
     const double s2 = sigma * sigma, s6 = s2 * s2 * s2, s12 = s6 * s6;
     P.A = 24.0 * eps * s6 * dt;
     P.B = 48.0 * eps * s12 * dt;
+    P.C12 = 4.0 * eps * s12;
+    P.C6 = 4.0 * eps * s6;
     return P;
 }
 

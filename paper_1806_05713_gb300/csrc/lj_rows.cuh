@@ -9,21 +9,61 @@
 namespace lj {
 namespace {
 
+// Memory layout of positions and momenta for the FP64 row walk: element
+// (i, a) of q or p is at base[i * rs + a * cs].  LAY 0: AoS4 (rs = 4,
+// cs = 1, one 256-bit load per atom); LAY 1: any AoS with rs a multiple of 4
+// and cs = 1 (e.g. the paper's AoS8, q and p of an atom in one 64-byte
+// record); LAY 2: anything else, e.g. SoA (rs = 1, cs = n), three scalar
+// loads per atom.
+struct Layout {
+    long long rs, cs;
+};
+
+template <int LAY>
+__device__ __forceinline__ void load_pos(const double *__restrict__ q, int i, const Layout &L,
+                                         double &x, double &y, double &z)
+{
+    if (LAY == 0) {
+        load_q4_256(q, i, x, y, z);
+    } else if (LAY == 1) {
+        double w;
+        asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+            : "=d"(x), "=d"(y), "=d"(z), "=d"(w)
+            : "l"(q + static_cast<long long>(i) * L.rs));
+    } else {
+        const double *b = q + static_cast<long long>(i) * L.rs;
+        x = __ldg(b);
+        y = __ldg(b + L.cs);
+        z = __ldg(b + 2 * L.cs);
+    }
+}
+
+template <int LAY>
+__device__ __forceinline__ double *mom_at(double *__restrict__ p, int i, int a, const Layout &L)
+{
+    if (LAY == 0) return p + 4 * static_cast<long long>(i) + a;
+    return p + static_cast<long long>(i) * L.rs + static_cast<long long>(a) * L.cs;
+}
+
 // One row i of the FP64 form, walked by the TPI lanes of the calling group
 // (gm = their mask).  U independent entries per lane and iteration (U = 2 is
 // the paper's software pipelining, section "Software Pipelining": the loads
 // and distance work of one entry overlap the force arithmetic of the other,
 // so the long dependent FP64 chains of two pairs are in flight together).
 // Pointers are the system's own arrays (local indices).
-template <int TPI, bool HALF, int U, bool IMG = false>
+// EN: also accumulate the pair energy 4 eps [(sigma/r)^12 - (sigma/r)^6] of
+// every in-cutoff entry into *ev and count the entries into *ecount (the
+// caller applies the shift and, for a full list, the factor 1/2).
+template <int TPI, bool HALF, int U, bool IMG = false, int LAY = 0, bool EN = false>
 __device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *__restrict__ p4,
                                          const int *__restrict__ row_ptr,
                                          const int *__restrict__ col, int i, const Fp64Params &P,
-                                         unsigned gm)
+                                         unsigned gm, const Layout &Lay = Layout{4, 1},
+                                         double *ev = nullptr, int *ecount = nullptr)
 {
     const int sub = threadIdx.x & (TPI - 1);
     double xi, yi, zi;
-    load_q4_256(q4, i, xi, yi, zi);
+    load_pos<LAY>(q4, i, Lay, xi, yi, zi);
     // IMG: the two periodic images of q_i per axis and the high words of
     // q_i +- L/2, so that each entry picks the minimum image of q_i with
     // integer compares and needs one FP64 subtraction, never a wrap add.
@@ -58,7 +98,7 @@ __device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *
         double xj[U], yj[U], zj[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            load_q4_256(q4, j[u], xj[u], yj[u], zj[u]);
+            load_pos<LAY>(q4, j[u], Lay, xj[u], yj[u], zj[u]);
             if (IMG) {
                 const double cj[3] = {xj[u], yj[u], zj[u]};
                 const double ci[3] = {xi, yi, zi};
@@ -119,15 +159,19 @@ __device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *
                 const double w4 = w2 * w2;
                 const double w3 = w2 * w;
                 fn[u] = w4 * fma(P.B, w3, -P.A);  // -df: p_i -= fn d, p_j += fn d
+                if (EN && in[u]) {
+                    *ev += w3 * fma(P.C12, w3, -P.C6);  // 4 eps [(s/r)^12 - (s/r)^6]
+                    ++*ecount;
+                }
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (in[u]) {
                     if (HALF) {
                         const double fx = fn[u] * dx[u], fy = fn[u] * dy[u], fz = fn[u] * dz[u];
-                        atomicAdd(p4 + 4 * static_cast<int64_t>(j[u]) + 0, fx);
-                        atomicAdd(p4 + 4 * static_cast<int64_t>(j[u]) + 1, fy);
-                        atomicAdd(p4 + 4 * static_cast<int64_t>(j[u]) + 2, fz);
+                        atomicAdd(mom_at<LAY>(p4, j[u], 0, Lay), fx);
+                        atomicAdd(mom_at<LAY>(p4, j[u], 1, Lay), fy);
+                        atomicAdd(mom_at<LAY>(p4, j[u], 2, Lay), fz);
                         ax -= fx;
                         ay -= fy;
                         az -= fz;
@@ -143,10 +187,9 @@ __device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *
     if (HALF) {
         // p_i already receives other rows' atomics: each lane adds its own
         // partial sum in L2 (no FP64 shuffle reduction on the FP64 pipe).
-        double *pi = p4 + 4 * static_cast<int64_t>(i);
-        atomicAdd(pi + 0, ax);
-        atomicAdd(pi + 1, ay);
-        atomicAdd(pi + 2, az);
+        atomicAdd(mom_at<LAY>(p4, i, 0, Lay), ax);
+        atomicAdd(mom_at<LAY>(p4, i, 1, Lay), ay);
+        atomicAdd(mom_at<LAY>(p4, i, 2, Lay), az);
     } else {
         // Full list: a fixed-order group reduction keeps p_i deterministic.
         if (TPI > 1) {
@@ -155,10 +198,9 @@ __device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *
             az = group_sum<TPI>(az);
         }
         if (sub == 0) {
-            double *pi = p4 + 4 * static_cast<int64_t>(i);
-            atomicAdd(pi + 0, ax);
-            atomicAdd(pi + 1, ay);
-            atomicAdd(pi + 2, az);
+            atomicAdd(mom_at<LAY>(p4, i, 0, Lay), ax);
+            atomicAdd(mom_at<LAY>(p4, i, 1, Lay), ay);
+            atomicAdd(mom_at<LAY>(p4, i, 2, Lay), az);
         }
     }
 }

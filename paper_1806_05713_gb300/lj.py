@@ -90,6 +90,11 @@ SIGNATURES = {
     "lj_force_vjp_workspace_bytes": (_sz, [_i64, _int]),
     "lj_force_vjp": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl3, _dbl, _dbl, _int,
                             _vp, _vp, _vp, _sz, _vp]),
+    "lj_force_strided": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _i64, _int, _dbl, _dbl, _dbl3,
+                                _dbl, _dbl, _int, _vp]),
+    "lj_force_energy_workspace_bytes": (_sz, [_i64]),
+    "lj_force_energy": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl, _dbl3, _dbl, _dbl,
+                               _int, _vp, _vp, _sz, _vp]),
     "lj_energy_workspace_bytes": (_sz, [_i64]),
     "lj_energy": (_int, [_vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl3, _dbl, _dbl, _int, _vp, _vp,
                          _sz, _vp]),
@@ -385,3 +390,42 @@ def lj_drift(q4: torch.Tensor, p4: torch.Tensor, dt: float, box,
                       _stream(stream))
     _check(st, "lj_drift")
     return max_disp2
+
+
+def lj_force_strided(q: torch.Tensor, p: torch.Tensor, n: int, row_stride: int, comp_stride: int,
+                     plist: PairList, dt: float, r_cut: float, box, eps: float = 1.0,
+                     sigma: float = 1.0, lanes_per_row: int = 8, p_offset: int = 0, stream=None):
+    """FP64 force with q and p in a strided layout (AoS4, AoS8, SoA, ...);
+    p is read at p.data_ptr() + 8 * p_offset (p_offset = 4 for AoS8 records)."""
+    lib = load()
+    for t, name in ((q, "q"), (p, "p")):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+            raise TypeError(f"{name} must be a CUDA float64 tensor")
+    st = lib.lj_force_strided(q.data_ptr(), p.data_ptr() + 8 * int(p_offset), int(n),
+                              int(row_stride), int(comp_stride), plist.row_ptr.data_ptr(),
+                              plist.col.data_ptr(), plist.nnz, int(plist.half), float(dt),
+                              float(r_cut), _box3(box), float(eps), float(sigma),
+                              int(lanes_per_row), _stream(stream))
+    _check(st, "lj_force_strided")
+    return p
+
+
+def lj_force_energy(q4: torch.Tensor, p4: torch.Tensor, plist: PairList, dt: float, r_cut: float,
+                    box, eps: float = 1.0, sigma: float = 1.0, shifted: bool = False,
+                    out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """p4 += impulses (FP64) and the potential energy into a 1-element tensor."""
+    lib = load()
+    n = plist.n
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=q4.device)
+    if workspace is None:
+        workspace = _workspace(lib.lj_force_energy_workspace_bytes(n), q4.device)
+    st = lib.lj_force_energy(_dev(q4, torch.float64, "q4", (n, 4)),
+                             _dev(p4, torch.float64, "p4", (n, 4)), n, plist.row_ptr.data_ptr(),
+                             plist.col.data_ptr(), plist.nnz, int(plist.half), float(dt),
+                             float(r_cut), _box3(box), float(eps), float(sigma), int(bool(shifted)),
+                             _dev(out, torch.float64, "out"), workspace.data_ptr(),
+                             workspace.numel(), _stream(stream))
+    _check(st, "lj_force_energy")
+    return out

@@ -46,14 +46,25 @@ class VelocityVerlet:
         self.rebuilds += 1
         self.moved = 0.0
 
-    def _kick(self, h: float):
-        lj.lj_force(self.q4, self.p4, self.plist, h, self.r_cut, self.box, self.eps, self.sigma,
-                    self.precision, self.tpi, workspace=self.ws)
+    def _kick(self, h: float, energy_out: torch.Tensor | None = None):
+        if energy_out is not None:
+            # the FP64 force pass that also returns U(q) (shifted potential)
+            lj.lj_force_energy(self.q4, self.p4, self.plist, h, self.r_cut, self.box, self.eps,
+                               self.sigma, True, out=energy_out, workspace=self._ews)
+        else:
+            lj.lj_force(self.q4, self.p4, self.plist, h, self.r_cut, self.box, self.eps,
+                        self.sigma, self.precision, self.tpi, workspace=self.ws)
 
-    def run(self, steps: int):
-        """Advance `steps` steps; p4 ends at the same time as q4."""
+    def run(self, steps: int, energies: torch.Tensor | None = None):
+        """Advance `steps` steps; p4 ends at the same time as q4.  If
+        `energies` (a device tensor of `steps` doubles) is given, the force
+        passes also write the shifted potential energy U(q(t_k)) of each new
+        position into it (FP64 form)."""
         if steps <= 0:
             return
+        if energies is not None:
+            self._ews = lj._workspace(lj.lj_force_energy_workspace_bytes(self.q4.shape[0]),
+                                      self.q4.device)
         if not self._half_kicked:
             self._kick(0.5 * self.dt)              # p(t + dt/2)
         for s in range(steps):
@@ -62,7 +73,8 @@ class VelocityVerlet:
             if 2.0 * self.moved >= self.margin:
                 self._rebuild()
             last = s == steps - 1
-            self._kick(0.5 * self.dt if last else self.dt)
+            self._kick(0.5 * self.dt if last else self.dt,
+                       None if energies is None else energies[s:s + 1])
         self._half_kicked = False
 
     def kinetic_energy(self) -> float:

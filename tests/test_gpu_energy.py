@@ -35,3 +35,27 @@ def test_energy_closed_form_and_determinism(cuda_lib):
     a = lj.lj_energy(qd, pl, 3.0, s.box).item()
     b = lj.lj_energy(qd, pl, 3.0, s.box).item()
     assert a == b
+
+
+@pytest.mark.parametrize("half", [True, False])
+@pytest.mark.parametrize("shifted", [False, True])
+def test_force_energy_one_pass(cuda_lib, oracle_lib, half, shifted):
+    """lj_force_energy: the same momenta as lj_force and the oracle's energy."""
+    lj = cuda_lib
+    s = inputs.fcc_system(12, 0.95, 0.05, seed=6)
+    q = to_dev(s.q)
+    pl = lj.lj_build_pairlist(q, s.box, s.rs, half)
+    p1 = torch.zeros_like(q)
+    e = lj.lj_force_energy(q, p1, pl, 0.01, 3.0, s.box, 1.1, 0.97, shifted).item()
+    p2 = torch.zeros_like(q)
+    lj.lj_force(q, p2, pl, 0.01, 3.0, s.box, 1.1, 0.97, tpi=lj.LJ_SCHED_IMAGES | 8)
+    torch.cuda.synchronize()
+    if half:
+        assert float((p1 - p2).abs().max()) <= 1e-13 * float(p2.abs().max())
+    else:
+        assert torch.equal(p1, p2)
+    rp, col = oracle_lib.pairlist(s.q, s.box, s.rs, half)
+    want = oracle_lib.energy(s.q, rp, col, half, 3.0, s.box, 1.1, 0.97, shifted)
+    assert abs(e - want) <= 1e-12 * abs(want)
+    again = lj.lj_force_energy(q, torch.zeros_like(q), pl, 0.01, 3.0, s.box, 1.1, 0.97, shifted).item()
+    assert again == e

@@ -92,3 +92,19 @@ def test_energy_conservation_and_bookkeeping(cuda_lib):
     assert float((F_old - F_new).abs().max()) <= 1e-12 * float(F_new.abs().max())
     # total momentum stays zero (Newton's third law, half-list atomics)
     assert float(p[:, :3].sum(0).abs().max()) < 1e-9
+
+
+def test_energies_from_the_force_pass(cuda_lib):
+    """run(energies=...) records U(q(t_k)) from lj_force_energy; the last one
+    equals a separate lj_energy pass on the final positions."""
+    from paper_1806_05713_gb300.md import VelocityVerlet
+    lj = cuda_lib
+    s = inputs.fcc_system(8, 1.0, 0.05, seed=4)
+    q = to_dev(s.q)
+    p = torch.zeros_like(q)
+    vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, 0.005)
+    U = torch.zeros(30, dtype=torch.float64, device="cuda")
+    vv.run(30, energies=U)
+    u_last = float(U[-1])
+    assert abs(u_last - vv.potential_energy(shifted=True)) <= 1e-12 * abs(u_last)
+    assert torch.all(U < 0)
