@@ -410,6 +410,10 @@ def lj_force_strided(q: torch.Tensor, p: torch.Tensor, n: int, row_stride: int, 
     return p
 
 
+def lj_force_energy_workspace_bytes(n: int) -> int:
+    return int(load().lj_force_energy_workspace_bytes(int(n)))
+
+
 def lj_force_energy(q4: torch.Tensor, p4: torch.Tensor, plist: PairList, dt: float, r_cut: float,
                     box, eps: float = 1.0, sigma: float = 1.0, shifted: bool = False,
                     out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
@@ -429,3 +433,64 @@ def lj_force_energy(q4: torch.Tensor, p4: torch.Tensor, plist: PairList, dt: flo
                              workspace.numel(), _stream(stream))
     _check(st, "lj_force_energy")
     return out
+
+
+# ---- remaining entry points, same names, argument marshalling only --------
+
+def lj_status_string(status: int) -> str:
+    return load().lj_status_string(int(status)).decode()
+
+
+def lj_last_cuda_error() -> str:
+    return load().lj_last_cuda_error().decode()
+
+
+def lj_version() -> int:
+    return int(load().lj_version())
+
+
+def lj_kernel_launch_count() -> int:
+    return int(load().lj_kernel_launch_count())
+
+
+def lj_batch_plan_bytes(systems, rows_per_item: int) -> int:
+    """systems: a ctypes array of LjSystem."""
+    return int(load().lj_batch_plan_bytes(systems, len(systems), int(rows_per_item)))
+
+
+def lj_batch_init(batch: LjBatch, systems, dt: float, precision: int, tpi: int,
+                  rows_per_item: int, plan: torch.Tensor, stream=None) -> LjBatch:
+    _check(load().lj_batch_init(ctypes.byref(batch), systems, len(systems), float(dt),
+                                int(precision), int(tpi), int(rows_per_item), plan.data_ptr(),
+                                plan.numel(), _stream(stream)), "lj_batch_init")
+    return batch
+
+
+def lj_force_batched_workspace_bytes(batch: LjBatch) -> int:
+    return int(load().lj_force_batched_workspace_bytes(ctypes.byref(batch)))
+
+
+def lj_force_batched(batch: LjBatch, q4: torch.Tensor, p4: torch.Tensor, row_ptr: torch.Tensor,
+                     col: torch.Tensor, workspace: torch.Tensor, stream=None) -> torch.Tensor:
+    _check(load().lj_force_batched(ctypes.byref(batch), q4.data_ptr(), p4.data_ptr(),
+                                   row_ptr.data_ptr(), col.data_ptr(), workspace.data_ptr(),
+                                   workspace.numel(), _stream(stream)), "lj_force_batched")
+    return p4
+
+
+def lj_autotune_batched(systems, dt: float, precision: int, tpis, rows_per_item,
+                        q4: torch.Tensor, p4_scratch: torch.Tensor, row_ptr: torch.Tensor,
+                        col: torch.Tensor, plan: torch.Tensor, workspace: torch.Tensor,
+                        reps: int = 5, stream=None):
+    """Returns (best_tpi, best_rows_per_item, best_ms)."""
+    ta = (ctypes.c_int * len(tpis))(*tpis)
+    ra = (ctypes.c_int * len(rows_per_item))(*rows_per_item)
+    bt, br, bm = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_float(0)
+    _check(load().lj_autotune_batched(systems, len(systems), float(dt), int(precision), ta,
+                                      len(tpis), ra, len(rows_per_item), q4.data_ptr(),
+                                      p4_scratch.data_ptr(), row_ptr.data_ptr(), col.data_ptr(),
+                                      plan.data_ptr(), plan.numel(), workspace.data_ptr(),
+                                      workspace.numel(), int(reps), ctypes.byref(bt),
+                                      ctypes.byref(br), ctypes.byref(bm), _stream(stream)),
+           "lj_autotune_batched")
+    return bt.value, br.value, bm.value

@@ -45,6 +45,12 @@ def test_binding_covers_every_declared_symbol():
     assert _declared() == set(lj.SIGNATURES)
 
 
+def test_binding_has_a_same_named_function_for_every_entry_point():
+    from paper_1806_05713_gb300 import lj
+    for name in _declared():
+        assert callable(getattr(lj, name, None)), f"lj.{name} missing"
+
+
 def test_status_strings_and_version():
     from paper_1806_05713_gb300 import lj
     L = lj.load()
