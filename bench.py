@@ -68,8 +68,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (1M atoms, 512-system batch, 64-replica adjoint)")
-    ap.add_argument("--profile", choices=["fp64", "fp64-full", "mixed", "mixed-full", "list", "vjp",
-                                          "batched"],
+    ap.add_argument("--profile", choices=["fp64", "fp64-full", "mixed", "mixed-full", "dfloat",
+                                          "dfloat-full", "list", "vjp", "batched"],
                     help="no timing: build the list and run a few calls of one kernel (for ncu)")
     ap.add_argument("--profile-atoms", choices=["paper", "million"], default="paper")
     ap.add_argument("--profile-tpi", type=int, default=0, help="schedule for --profile (0 = auto)")
@@ -267,7 +267,8 @@ def run_profile(args):
         for _ in range(3):
             lj.lj_build_pairlist(q, box, s.rs, half, reuse=pl)
     else:
-        prec = lj.LJ_MIXED if args.profile.startswith("mixed") else lj.LJ_FP64
+        prec = (lj.LJ_MIXED if args.profile.startswith("mixed") else
+                lj.LJ_DFLOAT if args.profile.startswith("dfloat") else lj.LJ_FP64)
         tpi = args.profile_tpi
         fn = lj.lj_force_prepared(q, p, pl, DT, s.rc, box, precision=prec, tpi=tpi)
         for _ in range(5):
@@ -479,7 +480,8 @@ def extra_million(lj, dev, stream, flush):
     res = {"n_atoms": s.n, "pairs_per_call": pl.nnz, "list_build_ms": t_list}
     best, _, _ = lj.lj_autotune_force(q, pl, DT, s.rc, box, reps=3)
     out = {}
-    for name, prec, tpis in (("fp64", lj.LJ_FP64, (best,)), ("mixed", lj.LJ_MIXED, (4, 8, 16))):
+    for name, prec, tpis in (("fp64", lj.LJ_FP64, (best,)), ("mixed", lj.LJ_MIXED, (4, 8, 16)),
+                             ("dfloat", lj.LJ_DFLOAT, (8, 16))):
         for t in tpis:
             pp = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
             fn = lj.lj_force_prepared(q, pp, pl, DT, s.rc, box, precision=prec, tpi=t)
@@ -496,6 +498,13 @@ def extra_million(lj, dev, stream, flush):
                     "max_err_rel_vs_fp64": float(err.abs().max() / ref.abs().max()),
                     "rms_err_rel_vs_fp64": float(err.pow(2).mean().sqrt() / ref.pow(2).mean().sqrt())}
     res["speedup_mixed_vs_fp64"] = ms64 / msm
+    dk = min((k for k in out if k[0] == "dfloat"), key=lambda k: out[k][0])
+    msd, pd = out[dk]
+    err = pd - ref
+    res["dfloat"] = {"schedule": schedule_name(dk[1]), "ms": msd, "pairs_per_s": pl.nnz / (msd / 1e3),
+                     "max_err_rel_vs_fp64": float(err.abs().max() / ref.abs().max()),
+                     "rms_err_rel_vs_fp64": float(err.pow(2).mean().sqrt() / ref.pow(2).mean().sqrt())}
+    res["speedup_dfloat_vs_fp64"] = ms64 / msd
     return res
 
 
@@ -597,6 +606,9 @@ def extra_md(lj, dev, stream):
             "energy_drift_rel": abs(e1 - e0) / abs(e0)}
 
 
+FORM_NAMES = {0: "fp64", 1: "mixed", 2: "dfloat"}
+
+
 def time_calls(fn, stream, flush, calls=20, warm=3):
     import torch
     for _ in range(warm):
@@ -633,19 +645,20 @@ def variants(lj, s, q, pl_half, box, dev, stream, flush):
             m_half = pl.nnz if half else pl.nnz // 2
             res[f"list_build_ms/{order}/{kind}"] = t_list
             ref = None
-            for prec, tpis in ((lj.LJ_FP64, (1032, 1028, 1544, 1160)), (lj.LJ_MIXED, (4, 8, 16))):
+            for prec, tpis in ((lj.LJ_FP64, (1032, 1028, 1544, 1160)), (lj.LJ_MIXED, (4, 8, 16)),
+                               (lj.LJ_DFLOAT, (4, 8, 16, 520))):
                 for tpi in tpis:
                     pp = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
                     fn = lj.lj_force_prepared(qq, pp, pl, DT, sys_.rc, box, precision=prec, tpi=tpi)
                     ms = time_calls(fn, stream, flush)
-                    name = f"{'fp64' if prec == 0 else 'mixed'}/{order}/{kind}/tpi{tpi}"
+                    name = f"{FORM_NAMES[prec]}/{order}/{kind}/tpi{tpi}"
                     res[name] = {"ms": ms, "pairs_per_s": m_half / (ms / 1e3)}
                     # error of one call vs the FP64 result (itself within 1e-12 of the oracle)
                     pp.zero_()
                     fn()
                     if prec == lj.LJ_FP64 and ref is None:
                         ref = pp[:, :3].clone()
-                    elif prec == lj.LJ_MIXED and ref is not None:
+                    elif prec != lj.LJ_FP64 and ref is not None:
                         err = pp[:, :3] - ref
                         res[name]["max_err_rel"] = float(err.abs().max() / ref.abs().max())
                         res[name]["rms_err_rel"] = float(err.pow(2).mean().sqrt() / ref.pow(2).mean().sqrt())

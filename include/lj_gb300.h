@@ -61,6 +61,15 @@ extern "C" {
                       32-bit fixed point derived from the FP64 positions and
                       rounded once to FP32; compensated FP32 per-i sums and
                       FP64 momentum updates */
+#define LJ_DFLOAT 2 /* FP64-class accuracy from FP32 instructions: the
+                       displacement exact from 58-bit fixed-point positions,
+                       the pair arithmetic in double-float (unevaluated sums
+                       of two FP32 numbers: Dekker 1971, Knuth's TwoSum),
+                       compensated per-i sums, FP64 momentum updates; pairs
+                       at the cutoff or closer than the FP32 range of r^-14
+                       take the FP64 formula.  Not in the paper (which is
+                       FP64 throughout): GB300 issues FP32 ~70 times faster
+                       than FP64.  lj_force only; tpi = 4, 8, 16. */
 
 /* ---- schedules ---------------------------------------------------------- */
 /* `tpi` = threads per i-row: 1, 2, 4, 8, 16 or 32 lanes of one warp walk one
@@ -184,8 +193,8 @@ int lj_build_pairlist_static(const double *q4_dev, int64_t n, const double box[3
 /* ======================================================================== */
 
 /* Bytes of device workspace lj_force needs (about 8 n + 2.5 KB for LJ_FP64:
- * a row counter and the length-sorted row order; 16 n more for LJ_MIXED:
- * fixed-point positions). */
+ * a row counter and the length-sorted row order; 16 n more for LJ_MIXED,
+ * 32 n more for LJ_DFLOAT: fixed-point positions). */
 size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
 
 /*
@@ -202,8 +211,9 @@ size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
  *  dt, r_cut        time step and cutoff (0 < r_cut <= L/2).
  *  box              host, 3 box sides.
  *  eps, sigma       Eq. (1) parameters (> 0).
- *  precision        LJ_FP64 or LJ_MIXED.
- *  tpi              LJ_TPI_AUTO, 1..32 (power of two), LJ_SCHED_SWP2 | 4, 8,
+ *  precision        LJ_FP64, LJ_MIXED or LJ_DFLOAT.
+ *  tpi              LJ_TPI_AUTO, 1..32 (power of two; LJ_DFLOAT: 4, 8, 16,
+ *                   optionally | LJ_SCHED_SORTED), LJ_SCHED_SWP2 | 4, 8,
  *                   16, LJ_SCHED_REFILL | 1, 4, 8 (optionally | SWP2), or
  *                   LJ_SCHED_QUEUE | 1, 2, 4, 8; the last three families
  *                   FP64 only.  LJ_SCHED_SORTED may be or-ed into the plain
@@ -212,8 +222,12 @@ size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
  *  workspace_dev    scratch of lj_force_workspace_bytes() (NULL if 0).
  * Half lists add p_j with FP64 atomics, so their rounding order (not their
  * value beyond the last bits) varies between calls; full lists are
- * deterministic except under LJ_SCHED_REFILL | 1 and LJ_SCHED_QUEUE.  Asynchronous.  Errors: LJ_ERR_ARG, LJ_ERR_BOX,
- * LJ_ERR_CAPACITY (workspace too small), LJ_ERR_CUDA.
+ * deterministic except under LJ_SCHED_REFILL | 1 and LJ_SCHED_QUEUE (and,
+ * for LJ_DFLOAT, rows with two or more pairs that take the FP64 formula).
+ * LJ_DFLOAT agrees with LJ_FP64 to ~1e-14 of max |dp|; it returns
+ * LJ_ERR_ARG if 24 eps sigma^6 dt / r_c^7 is outside 2^-690 .. 2^690.
+ * Asynchronous.  Errors: LJ_ERR_ARG, LJ_ERR_BOX, LJ_ERR_CAPACITY (workspace
+ * too small), LJ_ERR_CUDA.
  */
 int lj_force(const double *q4_dev, double *p4_dev, int64_t n, const int32_t *row_ptr_dev,
              const int32_t *col_dev, int64_t nnz, int half, double dt, double r_cut,

@@ -241,6 +241,11 @@ int force_queue_fp64(const double *q4, double *p4, int n, const int *row_ptr, co
                      int half, const double box[3], double dt, double rc, double eps, double sigma,
                      int sched, void *ws, size_t ws_bytes, cudaStream_t st);
 
+size_t dfloat_record_bytes(int64_t n);
+int force_dfloat(const double *q4, double *p4, int n, const int *row_ptr, const int *col, int half,
+                 const double box[3], double dt, double rc, double eps, double sigma, int tpi,
+                 const int *order, void *rec_ws, cudaStream_t st);
+
 int check_force_args(const double *q4, const double *p4, int64_t n, const int32_t *row_ptr,
                      const int32_t *col, int64_t nnz, double r_cut, const double box[3], double eps,
                      double sigma, double dt)
@@ -259,11 +264,13 @@ int check_force_args(const double *q4, const double *p4, int64_t n, const int32_
 }
 
 // Workspace: [256 B: refill/queue counter][order: n int][slot: n int]
-// [length histogram] and, for LJ_MIXED, the fixed-point positions.
+// [length histogram] and, for LJ_MIXED and LJ_DFLOAT, the fixed-point
+// positions.
 struct ForceWs {
     unsigned *counter;
     int *order, *slot, *hist;
     uint4 *rel;
+    void *rec;
 };
 
 ForceWs carve_force_ws(void *base, int64_t n, int precision)
@@ -276,6 +283,7 @@ ForceWs carve_force_ws(void *base, int64_t n, int precision)
     w.slot = c.take<int>(nn);
     w.hist = c.take<int>(kLenBuckets);
     w.rel = precision == LJ_MIXED ? c.take<uint4>(nn) : nullptr;
+    w.rec = precision == LJ_DFLOAT ? static_cast<void *>(c.take<char>(dfloat_record_bytes(n))) : nullptr;
     return w;
 }
 
@@ -289,6 +297,8 @@ bool valid_schedule(int s, int precision)
         return precision == LJ_FP64 && (s & ~(LJ_SCHED_REFILL | LJ_SCHED_SWP2 | 63)) == 0 &&
                (t == 0 || t == 1 || t == 4 || t == 8);
     if (s & ~(LJ_SCHED_SORTED | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES | 63)) return false;
+    if (precision == LJ_DFLOAT)
+        return (s & (LJ_SCHED_SWP2 | LJ_SCHED_IMAGES)) == 0 && (t == 4 || t == 8 || t == 16);
     if (s & LJ_SCHED_IMAGES) return precision == LJ_FP64 && (t == 4 || t == 8 || t == 16);
     if (s & LJ_SCHED_SWP2) return precision == LJ_FP64 && (t == 4 || t == 8 || t == 16);
     return pow2;
@@ -303,6 +313,7 @@ size_t force_workspace_bytes_impl(int64_t n, int precision)
     c.take<int>(nn);
     c.take<int>(kLenBuckets);
     if (precision == LJ_MIXED) c.take<uint4>(nn);
+    if (precision == LJ_DFLOAT) c.take<char>(dfloat_record_bytes(n));
     return c.used + 256;
 }
 
@@ -312,7 +323,7 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
 {
     int rcode = check_force_args(q4, p4, n, row_ptr, col, nnz, rc, box, eps, sigma, dt);
     if (rcode != LJ_OK) return rcode;
-    if (precision != LJ_FP64 && precision != LJ_MIXED) return LJ_ERR_ARG;
+    if (precision != LJ_FP64 && precision != LJ_MIXED && precision != LJ_DFLOAT) return LJ_ERR_ARG;
     if (n == 0 || nnz == 0) return LJ_OK;
     const int ni = static_cast<int>(n);
     if (tpi == LJ_TPI_AUTO) tpi = precision == LJ_FP64 ? (LJ_SCHED_IMAGES | 8) : 8;
@@ -336,6 +347,9 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
         order = W.order;
         tpi &= ~LJ_SCHED_SORTED;
     }
+    if (precision == LJ_DFLOAT)
+        return force_dfloat(q4, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma, tpi, order,
+                            W.rec, st);
     if (precision == LJ_FP64) {
         const Fp64Params P = make_fp64_params(box, dt, rc, eps, sigma);
         switch (tpi) {

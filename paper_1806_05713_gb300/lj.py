@@ -26,6 +26,7 @@ LJ_ERR_DEVICE = 6
 
 LJ_FP64 = 0
 LJ_MIXED = 1
+LJ_DFLOAT = 2
 LJ_TPI_AUTO = 0
 LJ_SCHED_REFILL = 64
 LJ_SCHED_SWP2 = 128
@@ -360,7 +361,9 @@ def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float
         S, W, I = LJ_SCHED_SORTED, LJ_SCHED_SWP2, LJ_SCHED_IMAGES
         candidates = ([8, W | 8, I | 4, I | 8, I | 16, I | W | 4, I | W | 8, S | I | 4,
                        S | I | 8, S | I | 16, LJ_SCHED_REFILL | W | 8, LJ_SCHED_QUEUE | 8]
-                      if precision == LJ_FP64 else [2, 4, 8, 16, S | 4, S | 8, S | 16])
+                      if precision == LJ_FP64 else
+                      [4, 8, 16, S | 4, S | 8, S | 16] if precision == LJ_DFLOAT else
+                      [2, 4, 8, 16, S | 4, S | 8, S | 16])
     n = plist.n
     scratch = torch.zeros((n, 4), dtype=torch.float64, device=q4.device)
     ws = _workspace(lib.lj_force_workspace_bytes(n, _box3(box), int(precision)), q4.device)

@@ -80,10 +80,10 @@ def test_host_argument_checks_without_gpu():
     args = lambda **k: dict(dict(q=fake, p=fake, n=10, rp=fake, col=fake, nnz=10, half=1, dt=0.01,
                                  rc=3.0, box=box, eps=1.0, sig=1.0, prec=0, tpi=0), **k)
 
-    def force(**k):
+    def force(ws=None, wsb=0, **k):
         a = args(**k)
         return L.lj_force(a["q"], a["p"], a["n"], a["rp"], a["col"], a["nnz"], a["half"], a["dt"],
-                          a["rc"], a["box"], a["eps"], a["sig"], a["prec"], a["tpi"], None, 0, None)
+                          a["rc"], a["box"], a["eps"], a["sig"], a["prec"], a["tpi"], ws, wsb, None)
     assert force(prec=7) == lj.LJ_ERR_ARG
     assert force(rc=-1.0) == lj.LJ_ERR_ARG
     assert force(rc=6.0) == lj.LJ_ERR_BOX
@@ -95,6 +95,14 @@ def test_host_argument_checks_without_gpu():
     assert force(prec=1, tpi=8) == lj.LJ_ERR_CAPACITY
     assert force(prec=0, tpi=64) == lj.LJ_ERR_CAPACITY
     assert force(prec=0, tpi=8) == lj.LJ_ERR_CAPACITY
+    # double-float form: 4, 8 or 16 lanes (optionally length-sorted), a
+    # workspace with the fixed-point records, K = 24 eps sigma^6 dt / lambda^7
+    # within its exponent range (checked before any launch)
+    assert force(prec=2, tpi=2) == lj.LJ_ERR_ARG
+    assert force(prec=2, tpi=lj.LJ_SCHED_SWP2 | 8) == lj.LJ_ERR_ARG
+    assert force(prec=2, tpi=lj.LJ_SCHED_IMAGES | 8) == lj.LJ_ERR_ARG
+    assert force(prec=2, tpi=8) == lj.LJ_ERR_CAPACITY
+    assert force(prec=2, tpi=8, dt=1e-250, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG
     # empty work is a no-op that succeeds
     assert force(n=0, nnz=0) == lj.LJ_OK
 
@@ -107,6 +115,7 @@ def test_workspace_sizes_are_sane():
     assert 119164 * 32 <= w1 < 119164 * 200
     assert L.lj_force_workspace_bytes(1000, b, 0) >= 256 + 8 * 1000
     assert L.lj_force_workspace_bytes(1000, b, 1) >= 24000
+    assert L.lj_force_workspace_bytes(1000, b, 2) >= 40000
     assert L.lj_energy_workspace_bytes(1000) >= 8
 
 
