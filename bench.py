@@ -481,7 +481,7 @@ def extra_million(lj, dev, stream, flush):
     best, _, _ = lj.lj_autotune_force(q, pl, DT, s.rc, box, reps=3)
     out = {}
     for name, prec, tpis in (("fp64", lj.LJ_FP64, (best,)), ("mixed", lj.LJ_MIXED, (4, 8, 16)),
-                             ("dfloat", lj.LJ_DFLOAT, (8, 16))):
+                             ("dfloat", lj.LJ_DFLOAT, (136, 132))):
         for t in tpis:
             pp = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
             fn = lj.lj_force_prepared(q, pp, pl, DT, s.rc, box, precision=prec, tpi=t)
@@ -646,7 +646,7 @@ def variants(lj, s, q, pl_half, box, dev, stream, flush):
             res[f"list_build_ms/{order}/{kind}"] = t_list
             ref = None
             for prec, tpis in ((lj.LJ_FP64, (1032, 1028, 1544, 1160)), (lj.LJ_MIXED, (4, 8, 16)),
-                               (lj.LJ_DFLOAT, (4, 8, 16, 520))):
+                               (lj.LJ_DFLOAT, (136, 132, 144, 648, 8))):
                 for tpi in tpis:
                     pp = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
                     fn = lj.lj_force_prepared(qq, pp, pl, DT, sys_.rc, box, precision=prec, tpi=tpi)

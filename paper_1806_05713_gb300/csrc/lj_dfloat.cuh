@@ -299,6 +299,178 @@ __device__ __forceinline__ void group_df_acc(float &s, float &c)
     }
 }
 
+// ---- packed form: two entries per lane in f32x2 registers ------------------
+// sm_100 and later execute add/sub/mul/fma on a pair of FP32 values held in
+// one 64-bit register with one instruction; two list entries of a lane go
+// through the double-float sequence side by side, half the instructions.
+
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk2(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ void up2(f2 v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Exact negation (sign bits).
+__device__ __forceinline__ f2 neg2(f2 a)
+{
+    return a ^ 0x8000000080000000ull;
+}
+
+struct df2 {
+    f2 h, l;
+};
+
+__device__ __forceinline__ void two_sum2(f2 a, f2 b, f2 &s, f2 &e)
+{
+    s = add2(a, b);
+    const f2 bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum2(f2 a, f2 b, f2 &s, f2 &e)
+{
+    s = add2(a, b);
+    e = sub2(b, sub2(s, a));
+}
+
+__device__ __forceinline__ df2 df2_mul(df2 a, df2 b)
+{
+    const f2 p = mul2(a.h, b.h);
+    f2 e = fma2(a.h, b.h, neg2(p));
+    e = fma2(a.h, b.l, e);
+    e = fma2(a.l, b.h, e);
+    df2 r;
+    fast_two_sum2(p, e, r.h, r.l);
+    return r;
+}
+
+__device__ __forceinline__ df2 df2_sq(df2 a)
+{
+    const f2 p = mul2(a.h, a.h);
+    f2 e = fma2(a.h, a.h, neg2(p));
+    e = fma2(add2(a.h, a.h), a.l, e);
+    df2 r;
+    fast_two_sum2(p, e, r.h, r.l);
+    return r;
+}
+
+__device__ __forceinline__ df2 df2_add(df2 a, df2 b)
+{
+    f2 s, e;
+    two_sum2(a.h, b.h, s, e);
+    e = add2(e, add2(a.l, b.l));
+    df2 r;
+    fast_two_sum2(s, e, r.h, r.l);
+    return r;
+}
+
+// 1/a as df_rcp, written with t = a y - 1 = -e so that no negation is
+// needed: 1/a ~ y + y t (t - 1).
+__device__ __forceinline__ df2 df2_rcp(df2 a)
+{
+    float a0, a1, y0, y1;
+    up2(a.h, a0, a1);
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(a0));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(a1));
+    const f2 y = pk2(y0, y1);
+    const f2 one = pk2(1.0f, 1.0f), mone = pk2(-1.0f, -1.0f);
+    f2 t = fma2(a.h, y, mone);
+    t = fma2(a.l, y, t);
+    const f2 q = mul2(y, t);
+    const f2 l = mul2(q, sub2(t, one));
+    df2 r;
+    fast_two_sum2(y, l, r.h, r.l);
+    return r;
+}
+
+__device__ __forceinline__ df2 pair_g2(df2 R, const DfParams &P)
+{
+    const df2 u = df2_rcp(R);
+    const df2 u2 = df2_sq(u);
+    const df2 u3 = df2_mul(u2, u);
+    const df2 u4 = df2_sq(u2);
+    const df2 bu3 = df2_mul(df2{pk2(P.kb_h, P.kb_h), pk2(P.kb_l, P.kb_l)}, u3);
+    const df2 v = df2_add(bu3, df2{pk2(-P.ka_h, -P.ka_h), pk2(-P.ka_l, -P.ka_l)});
+    return df2_mul(u4, v);
+}
+
+// chunk_disp for the two entries of the pair (hj, mj, lj packed; hi, mi,
+// li the row's values in both halves).
+__device__ __forceinline__ df2 chunk_disp2(f2 hj, f2 hi, f2 mj, f2 mi, f2 lj, f2 li, f2 inv_period,
+                                          f2 magic, f2 neg_period)
+{
+    f2 dh = sub2(hj, hi);
+    const f2 k = sub2(fma2(dh, inv_period, magic), magic);
+    dh = fma2(k, neg_period, dh);
+    df2 d;
+    f2 t;
+    fast_two_sum2(dh, sub2(mj, mi), d.h, t);
+    d.l = add2(t, sub2(lj, li));
+    return d;
+}
+
+__device__ __forceinline__ df2 df2_norm2(df2 x, df2 y, df2 z)
+{
+    const f2 px = mul2(x.h, x.h), py = mul2(y.h, y.h), pz = mul2(z.h, z.h);
+    f2 e = fma2(x.h, x.h, neg2(px));
+    e = add2(e, fma2(y.h, y.h, neg2(py)));
+    e = add2(e, fma2(z.h, z.h, neg2(pz)));
+    f2 c = mul2(x.h, x.l);
+    c = fma2(y.h, y.l, c);
+    c = fma2(z.h, z.l, c);
+    e = fma2(pk2(2.0f, 2.0f), c, e);
+    f2 s, t1, t2;
+    two_sum2(px, py, s, t1);
+    two_sum2(s, pz, s, t2);
+    e = add2(e, add2(t1, t2));
+    df2 r;
+    fast_two_sum2(s, e, r.h, r.l);
+    return r;
+}
+
+__device__ __forceinline__ void df2_acc(f2 &s, f2 &c, df2 x)
+{
+    f2 e;
+    two_sum2(s, x.h, s, e);
+    c = add2(c, add2(e, x.l));
+}
+
 // ---- host --------------------------------------------------------------
 
 inline void split_df(double v, float &h, float &l)

@@ -297,8 +297,7 @@ bool valid_schedule(int s, int precision)
         return precision == LJ_FP64 && (s & ~(LJ_SCHED_REFILL | LJ_SCHED_SWP2 | 63)) == 0 &&
                (t == 0 || t == 1 || t == 4 || t == 8);
     if (s & ~(LJ_SCHED_SORTED | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES | 63)) return false;
-    if (precision == LJ_DFLOAT)
-        return (s & (LJ_SCHED_SWP2 | LJ_SCHED_IMAGES)) == 0 && (t == 4 || t == 8 || t == 16);
+    if (precision == LJ_DFLOAT) return (s & LJ_SCHED_IMAGES) == 0 && (t == 4 || t == 8 || t == 16);
     if (s & LJ_SCHED_IMAGES) return precision == LJ_FP64 && (t == 4 || t == 8 || t == 16);
     if (s & LJ_SCHED_SWP2) return precision == LJ_FP64 && (t == 4 || t == 8 || t == 16);
     return pow2;
@@ -326,7 +325,8 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
     if (precision != LJ_FP64 && precision != LJ_MIXED && precision != LJ_DFLOAT) return LJ_ERR_ARG;
     if (n == 0 || nnz == 0) return LJ_OK;
     const int ni = static_cast<int>(n);
-    if (tpi == LJ_TPI_AUTO) tpi = precision == LJ_FP64 ? (LJ_SCHED_IMAGES | 8) : 8;
+    if (tpi == LJ_TPI_AUTO)
+        tpi = precision == LJ_FP64 ? (LJ_SCHED_IMAGES | 8) : precision == LJ_DFLOAT ? (LJ_SCHED_SWP2 | 8) : 8;
     if (!valid_schedule(tpi, precision)) return LJ_ERR_ARG;
     if (!ws || ws_bytes < force_workspace_bytes_impl(n, precision)) return LJ_ERR_CAPACITY;
     const ForceWs W = carve_force_ws(ws, n, precision);

@@ -99,7 +99,7 @@ def test_host_argument_checks_without_gpu():
     # workspace with the fixed-point records, K = 24 eps sigma^6 dt / lambda^7
     # within its exponent range (checked before any launch)
     assert force(prec=2, tpi=2) == lj.LJ_ERR_ARG
-    assert force(prec=2, tpi=lj.LJ_SCHED_SWP2 | 8) == lj.LJ_ERR_ARG
+    assert force(prec=2, tpi=lj.LJ_SCHED_SWP2 | 2) == lj.LJ_ERR_ARG
     assert force(prec=2, tpi=lj.LJ_SCHED_IMAGES | 8) == lj.LJ_ERR_ARG
     assert force(prec=2, tpi=8) == lj.LJ_ERR_CAPACITY
     assert force(prec=2, tpi=8, dt=1e-250, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG

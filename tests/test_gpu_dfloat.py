@@ -14,7 +14,9 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 DF = 2
-TPIS = [4, 8, 16, 516, 520, 528]   # 512|t: rows in order of decreasing length
+TPIS = [4, 8, 16, 132, 136, 144, 516, 520, 528, 648]
+# 128|t: two entries per lane in packed f32x2 registers; 512|t: rows in order of
+# decreasing length
 
 
 def _run(lj, s, half, tpi=8, dt=0.01, eps=1.0, sigma=1.0, p0=None, rc=None, pl=None):
@@ -61,8 +63,8 @@ def test_eps_sigma_dt_existing_momenta_noncubic(cuda_lib, oracle_lib):
     s.box = s.box * stretch
     p0 = np.random.default_rng(2).normal(size=(s.n, 4))
     kw = dict(dt=0.005, eps=1.3, sigma=1.1, rc=3.0)
-    for half in (True, False):
-        got, _ = _run(cuda_lib, s, half, 8, p0=p0, **kw)
+    for half, tpi in ((True, 8), (False, 8), (True, 136), (False, 136)):
+        got, _ = _run(cuda_lib, s, half, tpi, p0=p0, **kw)
         want = _oracle(oracle_lib, s, half, p0=p0, **kw)
         assert _relerr(got[:, :3] - p0[:, :3], want - p0[:, :3]) <= FP64_TOL
         assert np.array_equal(got[:, 3], p0[:, 3])
@@ -76,8 +78,8 @@ def test_two_body_closed_form(cuda_lib):
         q[:, :3] = 5.0
         q[1, 0] += r
         s = inputs.LJSystem(q=q, box=np.array([20.0] * 3), rho=0.0)
-        for half in (True, False):
-            got, _ = _run(cuda_lib, s, half, 4, dt=dt)
+        for half, tpi in ((True, 4), (False, 4), (True, 132), (False, 132)):
+            got, _ = _run(cuda_lib, s, half, tpi, dt=dt)
             assert abs(got[1, 0] - want) <= 1e-13 * 24 * dt
             assert abs(got[0, 0] + want) <= 1e-13 * 24 * dt
             assert np.all(got[:, 1:3] == 0.0)
@@ -90,8 +92,8 @@ def test_wrap_across_boundary(cuda_lib, oracle_lib):
     q[2, :3] = [5.0, 0.05, 9.9]
     q[3, :3] = [5.5, 9.6, 0.4]
     s = inputs.LJSystem(q=q, box=np.array([10.0] * 3), rho=0.0)
-    for half in (True, False):
-        got, _ = _run(cuda_lib, s, half, 8)
+    for half, tpi in ((True, 8), (False, 8), (True, 136), (False, 136)):
+        got, _ = _run(cuda_lib, s, half, tpi)
         want = _oracle(oracle_lib, s, half)
         assert _relerr(got[:, :3], want) <= FP64_TOL
         assert abs(got[0, 0] - 0.24) < 1e-13
@@ -112,8 +114,8 @@ def test_pairs_on_the_cutoff(cuda_lib, oracle_lib):
     q = np.zeros((len(xs), 4))
     q[:, :3] = xs
     s = inputs.LJSystem(q=q, box=np.array([L] * 3), rho=0.0)
-    for half in (True, False):
-        got, _ = _run(cuda_lib, s, half, 8)
+    for half, tpi in ((True, 8), (False, 8), (True, 136), (False, 136)):
+        got, _ = _run(cuda_lib, s, half, tpi)
         want = _oracle(oracle_lib, s, half)
         nz_want = np.any(want != 0.0, axis=1)
         nz_got = np.any(got[:, :3] != 0.0, axis=1)
@@ -131,8 +133,8 @@ def test_close_pair_takes_fp64(cuda_lib, oracle_lib):
     q[2, :3] = [6.1, 5.3, 5.0]
     q[3, :3] = [5.0, 6.2, 5.9]
     s = inputs.LJSystem(q=q, box=np.array([20.0] * 3), rho=0.0)
-    for half in (True, False):
-        got, _ = _run(cuda_lib, s, half, 4)
+    for half, tpi in ((True, 4), (False, 4), (True, 132), (False, 132)):
+        got, _ = _run(cuda_lib, s, half, tpi)
         want = _oracle(oracle_lib, s, half)
         assert np.all(np.isfinite(got))
         assert _relerr(got[:, :3], want) <= FP64_TOL
@@ -144,13 +146,14 @@ def test_full_list_is_deterministic(cuda_lib, small):
     lj = cuda_lib
     q = to_dev(small.q)
     pl = lj.lj_build_pairlist(q, small.box, small.rs, False)
-    out = []
-    for _ in range(3):
-        p = torch.zeros((small.n, 4), dtype=torch.float64, device="cuda")
-        lj.lj_force(q, p, pl, 0.01, 3.0, small.box, precision=DF, tpi=8)
-        out.append(p)
-    torch.cuda.synchronize()
-    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
+    for tpi in (8, 136):
+        out = []
+        for _ in range(3):
+            p = torch.zeros((small.n, 4), dtype=torch.float64, device="cuda")
+            lj.lj_force(q, p, pl, 0.01, 3.0, small.box, precision=DF, tpi=tpi)
+            out.append(p)
+        torch.cuda.synchronize()
+        assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
 
 
 def test_agrees_with_the_fp64_kernel(cuda_lib, small):
@@ -174,7 +177,7 @@ def test_paper_size(cuda_lib, oracle_lib, order, half):
     s = inputs.workload_paper(order=order)
     want = _oracle(oracle_lib, s, half)
     pl = None
-    for tpi in (8, 16, 520):
+    for tpi in (8, 136, 144, 520, 648):
         got, pl = _run(cuda_lib, s, half, tpi, pl=pl)
         assert _relerr(got[:, :3], want) <= FP64_TOL, tpi
 
@@ -183,5 +186,5 @@ def test_paper_size(cuda_lib, oracle_lib, order, half):
 def test_million_atoms(cuda_lib, oracle_lib):
     s = inputs.workload_million()
     want = _oracle(oracle_lib, s, True)
-    got, _ = _run(cuda_lib, s, True, 8)
+    got, _ = _run(cuda_lib, s, True, 0)
     assert _relerr(got[:, :3], want) <= FP64_TOL
