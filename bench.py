@@ -1,5 +1,5 @@
 #!/usr/bin/env python3
-"""LJ pair interactions/s on one GB300: FP64 and mixed precision.
+"""LJ pair interactions/s on one GB300: FP64, mixed precision and double-float.
 
 Workload: the paper's benchmark (section "Benchmark Conditions"): an FCC
 crystal of N = 119,164 = 4*31^3 atoms at density 1.0, cutoff 3.0 sigma,
@@ -428,6 +428,7 @@ def main():
     }
 
     out["autotune_ms"] = {schedule_name(k): v for k, v in tune_table.items()}
+    out["forms"] = forms(lj, q, pl, box, s, best_tpi, flops, dev, stream, flush)
     if not args.no_variants:
         out["variants"] = variants(lj, s, q, pl, box, dev, stream, flush)
     if not args.no_extra:
@@ -511,13 +512,13 @@ def extra_million(lj, dev, stream, flush):
 def extra_batched(lj, dev, stream, flush):
     """512 systems, N log-uniform in 500..32000, rho in 0.8..1.2, rc 2.5 or
     3.0: one persistent launch replayed from a CUDA graph vs one launch per
-    system, FP64 and mixed, half lists."""
+    system, FP64, mixed and double-float, half lists."""
     import torch
     from paper_1806_05713_gb300 import inputs
     from paper_1806_05713_gb300.batch import Batch
     systems = inputs.batched_systems(nsys=512, seed=0)
     res = {"n_systems": len(systems), "total_atoms": int(sum(s.n for s in systems))}
-    for name, prec in (("fp64", lj.LJ_FP64), ("mixed", lj.LJ_MIXED)):
+    for name, prec in (("fp64", lj.LJ_FP64), ("mixed", lj.LJ_MIXED), ("dfloat", lj.LJ_DFLOAT)):
         b = Batch(systems, DT, prec, True, tpi=8, rows_per_item=64, plan_rows_min=16)
         tpi, rows, _ = b.autotune(tpis=(4, 8, 16), rows=(16, 32, 64, 128), reps=3)
         g = b.capture_graph()
@@ -607,6 +608,41 @@ def extra_md(lj, dev, stream):
 
 
 FORM_NAMES = {0: "fp64", 1: "mixed", 2: "dfloat"}
+
+
+def forms(lj, q, pl, box, s, best_tpi, flops, dev, stream, flush):
+    """The three arithmetic forms on the headline workload (half list, one
+    force call, L2 flushed): time, pair interactions/s, FP64-equivalent
+    TFLOP/s (the paper's 28 flops per in-cutoff pair), error vs the FP64
+    kernel (itself within 1e-12 of the oracle in the tests)."""
+    import torch
+    res, ref = {}, None
+    for name, prec, tpis in (("fp64", lj.LJ_FP64, (best_tpi,)), ("mixed", lj.LJ_MIXED, (8, 16)),
+                             ("dfloat", lj.LJ_DFLOAT, (136, 132))):
+        best = None
+        for t in tpis:
+            pp = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
+            fn = lj.lj_force_prepared(q, pp, pl, DT, s.rc, box, precision=prec, tpi=t)
+            ms = time_calls(fn, stream, flush)
+            if best is None or ms < best[0]:
+                best = (ms, t, fn, pp)
+        ms, t, fn, pp = best
+        pp.zero_()
+        fn()
+        torch.cuda.synchronize()
+        r = {"schedule": schedule_name(t), "ms_per_call": ms, "pairs_per_s": pl.nnz / (ms / 1e3),
+             "fp64_equivalent_tflops": flops / (ms / 1e3) / 1e12}
+        if ref is None:
+            ref = pp[:, :3].clone()
+        else:
+            err = pp[:, :3] - ref
+            r["max_err_rel_vs_fp64"] = float(err.abs().max() / ref.abs().max())
+            r["rms_err_rel_vs_fp64"] = float(err.pow(2).mean().sqrt() / ref.pow(2).mean().sqrt())
+            r["speedup_vs_fp64"] = res["fp64"]["ms_per_call"] / ms
+        res[name] = r
+    res["note"] = ("dfloat: pair arithmetic in double-float on the FP32 pipe, exact fixed-point "
+                   "displacement; mixed: FP32 pair arithmetic; both add into FP64 momenta")
+    return res
 
 
 def time_calls(fn, stream, flush, calls=20, warm=3):

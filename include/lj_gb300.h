@@ -348,7 +348,7 @@ typedef struct lj_batch {
     int32_t tpi;           /* lanes per row: 1, 2, 4, 8, 16, 32 */
     int32_t rows_per_item; /* rows per work item (>= 1) */
     int32_t blocks;        /* persistent grid size */
-    int32_t reserved;
+    int32_t flags;         /* bit 0: every system has a cubic box */
 } lj_batch;
 
 /* Bytes of the device plan for these systems and rows_per_item. */
@@ -359,21 +359,23 @@ size_t lj_batch_plan_bytes(const lj_system *systems, int nsys, int rows_per_item
  * (items of at most rows_per_item rows of one system, ordered by decreasing
  * estimated cost nnz/n * rows, the longest-first rule), and copy it and the
  * per-system constants of Algorithm 1 (dt, eps, sigma, cutoff, box) to
- * plan_dev.  Blocks until the copy is done.  Errors: LJ_ERR_ARG, LJ_ERR_BOX,
- * LJ_ERR_CAPACITY (plan_bytes too small), LJ_ERR_CUDA.
+ * plan_dev.  precision: LJ_FP64, LJ_MIXED or LJ_DFLOAT (tpi 4, 8 or 16; two
+ * entries per lane in packed f32x2 registers).  Blocks until the copy is
+ * done.  Errors: LJ_ERR_ARG, LJ_ERR_BOX, LJ_ERR_CAPACITY (plan_bytes too
+ * small), LJ_ERR_CUDA.
  */
 int lj_batch_init(lj_batch *batch, const lj_system *systems, int nsys, double dt, int precision,
                   int tpi, int rows_per_item, void *plan_dev, size_t plan_bytes, void *stream);
 
 /* Bytes of device workspace lj_force_batched needs (a work counter; for
- * LJ_MIXED also 16 bytes per atom). */
+ * LJ_MIXED also 16 bytes per atom, for LJ_DFLOAT 32). */
 size_t lj_force_batched_workspace_bytes(const lj_batch *batch);
 
 /*
  * p += impulses for every system of the batch (lj_force semantics per
  * system) in one persistent launch: warps take work items from a counter in
  * the workspace until none is left.  Enqueues a memset of the counter, (for
- * LJ_MIXED) one pre-pass kernel and the force kernel; no host
+ * LJ_MIXED and LJ_DFLOAT) one pre-pass kernel and the force kernel; no host
  * synchronisation and no allocation, so the call can be captured in a CUDA
  * graph and replayed.  Errors: LJ_ERR_ARG, LJ_ERR_CAPACITY, LJ_ERR_CUDA.
  */

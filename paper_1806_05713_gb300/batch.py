@@ -140,8 +140,10 @@ class Batch:
             self.force(p4)
         return g
 
-    def autotune(self, tpis=(2, 4, 8, 16), rows=(16, 32, 64, 128), reps: int = 5):
+    def autotune(self, tpis=None, rows=(16, 32, 64, 128), reps: int = 5):
         """Pick lanes-per-row and rows-per-item by timing; applies and returns them."""
+        if tpis is None:
+            tpis = (4, 8, 16) if self.precision == lj.LJ_DFLOAT else (2, 4, 8, 16)
         scratch = torch.zeros_like(self.p4)
         ta = (ctypes.c_int * len(tpis))(*tpis)
         ra = (ctypes.c_int * len(rows))(*rows)

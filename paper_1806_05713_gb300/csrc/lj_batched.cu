@@ -17,6 +17,7 @@
 #include <cstring>
 #include <vector>
 
+#include "lj_dfloat.cuh"
 #include "lj_rows.cuh"
 
 namespace lj {
@@ -26,10 +27,14 @@ constexpr int kBatchThreads = 256;
 
 struct SysDev {
     long long atom_off, row_off, entry_off;
-    int n, half;
+    int n, half, cubic;
     Fp64Params fp;
     MixedParams mp;
+    DfParams dp;
 };
+
+// Arithmetic form of a batched launch (lj_batch.precision).
+enum Form { kFp64 = LJ_FP64, kMixed = LJ_MIXED, kDfloat = LJ_DFLOAT };
 
 struct Item {
     int sys;
@@ -84,12 +89,31 @@ __global__ void batched_prepass_kernel(const SysDev *__restrict__ sys, const Ite
     }
 }
 
-template <int TPI, bool MIXED>
+// Double-float records of every system (DFLOAT form), as dfloat_prepass_kernel.
+__global__ void batched_df_prepass_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ items,
+                                          const double *__restrict__ q4, DfRec *__restrict__ rec)
+{
+    const Item it = items[blockIdx.x];
+    const SysDev &S = sys[it.sys];
+    for (int r = it.row_begin + threadIdx.x; r < it.row_end; r += blockDim.x) {
+        const long long a = S.atom_off + r;
+        double x[3];
+        load_xyz(q4, a, x[0], x[1], x[2]);
+        rec[a] = make_rec(x, S.dp);
+    }
+}
+
+// rel: MIXED fixed-point positions; rec: DFLOAT records (each indexed by
+// the batch-wide atom number).
+// CUBIC (DFLOAT only): every system of the batch has a cubic box; otherwise
+// the displacement is scaled per axis (by 1 on the cubic systems).
+template <int TPI, int FORM, bool CUBIC>
 __global__ void __launch_bounds__(kBatchThreads)
 batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ items,
                      long long nitems, const double *__restrict__ q4, const uint4 *__restrict__ rel,
-                     double *__restrict__ p4, const int *__restrict__ row_ptr,
-                     const int *__restrict__ col, unsigned long long *__restrict__ counter)
+                     const DfRec *__restrict__ rec, double *__restrict__ p4,
+                     const int *__restrict__ row_ptr, const int *__restrict__ col,
+                     unsigned long long *__restrict__ counter)
 {
     const int lane = threadIdx.x & 31;
     const unsigned gm = group_mask<TPI>();
@@ -109,7 +133,14 @@ batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ it
         for (int r0 = I.row_begin; r0 < I.row_end; r0 += kGroups) {
             const int r = r0 + lane / TPI;
             if (r < I.row_end) {  // uniform within a group
-                if (MIXED) {
+                if (FORM == kDfloat) {
+                    const DfRec *srec = rec + S.atom_off;
+                    const DfParams P = S.dp;
+                    if (half)
+                        dfloat_row2<TPI, true, CUBIC>(sq, srec, sp, srp, scol, r, P, gm);
+                    else
+                        dfloat_row2<TPI, false, CUBIC>(sq, srec, sp, srp, scol, r, P, gm);
+                } else if (FORM == kMixed) {
                     const uint4 *srel = rel + S.atom_off;
                     const MixedParams P = S.mp;
                     if (half)
@@ -128,17 +159,17 @@ batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ it
     }
 }
 
-template <bool MIXED>
+template <int FORM, bool CUBIC>
 int launch_batched(const lj_batch *b, const PlanView &v, const double *q4, const uint4 *rel,
-                   double *p4, const int *rp, const int *col, unsigned long long *counter,
-                   cudaStream_t st)
+                   const DfRec *rec, double *p4, const int *rp, const int *col,
+                   unsigned long long *counter, cudaStream_t st)
 {
     const long long ni = b->nitems;
     const int grid = b->blocks;
-#define LJ_BATCH_CASE(T)                                                                          \
-    case T:                                                                                       \
-        batched_force_kernel<T, MIXED><<<grid, kBatchThreads, 0, st>>>(v.sys, v.items, ni, q4, rel, \
-                                                                        p4, rp, col, counter);    \
+#define LJ_BATCH_CASE(T)                                                                        \
+    case T:                                                                                     \
+        batched_force_kernel<T, FORM, CUBIC><<<grid, kBatchThreads, 0, st>>>(v.sys, v.items, ni, q4, \
+                                                                  rel, rec, p4, rp, col, counter); \
         break;
     switch (b->tpi) {
         LJ_BATCH_CASE(1)
@@ -154,15 +185,15 @@ int launch_batched(const lj_batch *b, const PlanView &v, const double *q4, const
     return LJ_OK;
 }
 
-template <bool MIXED>
+template <int FORM, bool CUBIC>
 int persistent_blocks(int tpi)
 {
     int per_sm = 0;
     cudaError_t e = cudaErrorInvalidValue;
-#define LJ_OCC(T)                                                                          \
-    case T:                                                                                \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_force_kernel<T, MIXED>, \
-                                                          kBatchThreads, 0);               \
+#define LJ_OCC(T)                                                                                 \
+    case T:                                                                                       \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_force_kernel<T, FORM, CUBIC>, \
+                                                          kBatchThreads, 0);                      \
         break;
     switch (tpi) {
         LJ_OCC(1)
@@ -178,7 +209,11 @@ int persistent_blocks(int tpi)
     return per_sm * num_sms();
 }
 
-bool valid_tpi(int t) { return t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32; }
+bool valid_tpi(int t, int precision)
+{
+    if (precision == LJ_DFLOAT) return t == 4 || t == 8 || t == 16;
+    return t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32;
+}
 
 }  // namespace
 
@@ -201,8 +236,8 @@ extern "C" int lj_batch_init(lj_batch *batch, const lj_system *systems, int nsys
     using namespace lj;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (!batch || !systems || nsys <= 0 || rows_per_item < 1 || !plan_dev) return LJ_ERR_ARG;
-    if (precision != LJ_FP64 && precision != LJ_MIXED) return LJ_ERR_ARG;
-    if (!valid_tpi(tpi)) return LJ_ERR_ARG;
+    if (precision != LJ_FP64 && precision != LJ_MIXED && precision != LJ_DFLOAT) return LJ_ERR_ARG;
+    if (!valid_tpi(tpi, precision)) return LJ_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(plan_dev) & 255u) return LJ_ERR_ARG;
     long long total_atoms = 0;
     std::vector<SysDev> host_sys(static_cast<size_t>(nsys));
@@ -224,6 +259,9 @@ extern "C" int lj_batch_init(lj_batch *batch, const lj_system *systems, int nsys
         d.half = y.half ? 1 : 0;
         d.fp = make_fp64_params(y.box, dt, y.r_cut, y.eps, y.sigma);
         d.mp = make_mixed_params(y.box, dt, y.r_cut, y.eps, y.sigma);
+        d.dp = make_dfloat_params(y.box, dt, y.r_cut, y.eps, y.sigma);
+        d.cubic = y.box[1] == y.box[0] && y.box[2] == y.box[0];
+        if (precision == LJ_DFLOAT && (d.dp.k_exp < -700 || d.dp.k_exp > 700)) return LJ_ERR_ARG;
         total_atoms = std::max<long long>(total_atoms, y.atom_offset + y.n);
     }
     // Work items, longest (estimated entries) first.
@@ -259,8 +297,13 @@ extern "C" int lj_batch_init(lj_batch *batch, const lj_system *systems, int nsys
     batch->precision = precision;
     batch->tpi = tpi;
     batch->rows_per_item = rows_per_item;
-    batch->blocks = precision == LJ_MIXED ? persistent_blocks<true>(tpi) : persistent_blocks<false>(tpi);
-    batch->reserved = 0;
+    bool all_cubic = true;
+    for (int s = 0; s < nsys; ++s) all_cubic = all_cubic && host_sys[size_t(s)].cubic;
+    batch->flags = all_cubic ? 1 : 0;
+    batch->blocks = precision == LJ_MIXED    ? persistent_blocks<kMixed, true>(tpi)
+                    : precision == LJ_DFLOAT ? (all_cubic ? persistent_blocks<kDfloat, true>(tpi)
+                                                          : persistent_blocks<kDfloat, false>(tpi))
+                                             : persistent_blocks<kFp64, true>(tpi);
     return LJ_OK;
 }
 
@@ -269,6 +312,7 @@ extern "C" size_t lj_force_batched_workspace_bytes(const lj_batch *batch)
     if (!batch) return 0;
     size_t bytes = 256;
     if (batch->precision == LJ_MIXED) bytes += size_t(batch->total_atoms) * sizeof(uint4) + 256;
+    if (batch->precision == LJ_DFLOAT) bytes += size_t(batch->total_atoms) * sizeof(lj::DfRec) + 256;
     return bytes;
 }
 
@@ -292,10 +336,21 @@ extern "C" int lj_force_batched(const lj_batch *batch, const double *q4_dev, dou
         uint4 *rel = c.take<uint4>(size_t(batch->total_atoms));
         batched_prepass_kernel<<<unsigned(batch->nitems), 128, 0, st>>>(v.sys, v.items, q4_dev, rel);
         LJ_TRY_LAUNCH("batched_prepass_kernel");
-        return launch_batched<true>(batch, v, q4_dev, rel, p4_dev, row_ptr_dev, col_dev, counter, st);
+        return launch_batched<kMixed, true>(batch, v, q4_dev, rel, nullptr, p4_dev, row_ptr_dev,
+                                            col_dev, counter, st);
     }
-    return launch_batched<false>(batch, v, q4_dev, nullptr, p4_dev, row_ptr_dev, col_dev, counter,
-                                 st);
+    if (batch->precision == LJ_DFLOAT) {
+        DfRec *rec = c.take<DfRec>(size_t(batch->total_atoms));
+        batched_df_prepass_kernel<<<unsigned(batch->nitems), 128, 0, st>>>(v.sys, v.items, q4_dev, rec);
+        LJ_TRY_LAUNCH("batched_df_prepass_kernel");
+        if (batch->flags & 1)
+            return launch_batched<kDfloat, true>(batch, v, q4_dev, nullptr, rec, p4_dev, row_ptr_dev,
+                                                 col_dev, counter, st);
+        return launch_batched<kDfloat, false>(batch, v, q4_dev, nullptr, rec, p4_dev, row_ptr_dev,
+                                              col_dev, counter, st);
+    }
+    return launch_batched<kFp64, true>(batch, v, q4_dev, nullptr, nullptr, p4_dev, row_ptr_dev,
+                                       col_dev, counter, st);
 }
 
 // ---------------------------------------------------------------------------

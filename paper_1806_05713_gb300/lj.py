@@ -57,7 +57,7 @@ class LjBatch(ctypes.Structure):
                 ("nitems", ctypes.c_int64), ("total_atoms", ctypes.c_int64),
                 ("dt", ctypes.c_double), ("nsys", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tpi", ctypes.c_int32), ("rows_per_item", ctypes.c_int32),
-                ("blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("blocks", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 _sysp = ctypes.POINTER(LjSystem)

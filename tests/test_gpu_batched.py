@@ -27,7 +27,7 @@ def systems():
     return inputs.batched_systems(nsys=24, seed=5, n_min=500, n_max=6000)
 
 
-@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL), (2, FP64_TOL)])
 @pytest.mark.parametrize("half", [True, False])
 def test_batched_matches_oracle_per_system(cuda_lib, oracle_lib, systems, precision, tol, half):
     from paper_1806_05713_gb300.batch import Batch
@@ -53,7 +53,7 @@ def test_batched_equals_per_system_launches_full_list(cuda_lib, systems):
     assert torch.equal(p_a, p_b)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_graph_replay(cuda_lib, systems, precision):
     from paper_1806_05713_gb300.batch import Batch
     b = Batch(systems, 0.01, precision, False, tpi=4, rows_per_item=64)
@@ -67,6 +67,38 @@ def test_graph_replay(cuda_lib, systems, precision):
     g.replay()
     torch.cuda.synchronize()
     assert torch.allclose(p, 2 * once, rtol=0, atol=1e-14 * float(once.abs().max()))
+
+
+def test_batched_dfloat_equals_per_system_launches_full_list(cuda_lib, systems):
+    """The double-float row walk is the same in the persistent launch and in
+    lj_force (two entries per lane, 8 lanes per row): same bits."""
+    from paper_1806_05713_gb300.batch import Batch
+    b = Batch(systems, 0.01, 2, False, tpi=8, rows_per_item=16)
+    p_a = torch.zeros_like(b.p4)
+    p_b = torch.zeros_like(b.p4)
+    b.force(p_a)
+    b.force_per_system(p_b, tpi=cuda_lib.LJ_SCHED_SWP2 | 8)
+    torch.cuda.synchronize()
+    assert torch.equal(p_a, p_b)
+
+
+def test_batched_dfloat_noncubic_boxes(cuda_lib, oracle_lib):
+    """Systems in stretched boxes take the per-axis scaled displacement."""
+    from paper_1806_05713_gb300.batch import Batch
+    systems = inputs.batched_systems(nsys=6, seed=8, n_min=500, n_max=3000)
+    for k, s in enumerate(systems):
+        if k % 2:
+            st = np.array([1.0, 1.15, 1.3])
+            s.q[:, :3] *= st
+            s.box = s.box * st
+    for half in (True, False):
+        b = Batch(systems, 0.01, 2, half, tpi=8, rows_per_item=32)
+        assert b.c_batch.flags == 0
+        b.force()
+        torch.cuda.synchronize()
+        for s, got in zip(systems, _per_system(b, b.p4)):
+            want = _oracle_dp(oracle_lib, s, 0.01, half)
+            assert np.max(np.abs(got - want)) <= FP64_TOL * np.max(np.abs(want))
 
 
 def test_autotune_picks_a_valid_schedule(cuda_lib, oracle_lib, systems):
