@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (1M atoms, 512-system batch, 64-replica adjoint)")
     ap.add_argument("--profile", choices=["fp64", "fp64-full", "mixed", "mixed-full", "dfloat",
-                                          "dfloat-full", "list", "vjp", "batched"],
+                                          "dfloat-full", "list", "vjp", "batched", "batched-dfloat"],
                     help="no timing: build the list and run a few calls of one kernel (for ncu)")
     ap.add_argument("--profile-atoms", choices=["paper", "million"], default="paper")
     ap.add_argument("--profile-tpi", type=int, default=0, help="schedule for --profile (0 = auto)")
@@ -246,14 +246,15 @@ def run_profile(args):
     q = torch.from_numpy(s.q).cuda()
     p = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
     half = not args.profile.endswith("full")
-    if args.profile == "batched":
+    if args.profile.startswith("batched"):
         from paper_1806_05713_gb300.batch import Batch
         systems = inputs.batched_systems(nsys=64, seed=0)
-        b = Batch(systems, DT, lj.LJ_FP64, True, tpi=8, rows_per_item=16)
+        prec = lj.LJ_DFLOAT if args.profile == "batched-dfloat" else lj.LJ_FP64
+        b = Batch(systems, DT, prec, True, tpi=8 if prec == lj.LJ_FP64 else 4, rows_per_item=16)
         for _ in range(5):
             b.force()
         torch.cuda.synchronize()
-        print(json.dumps({"profile": "batched", "systems": len(systems), "atoms": b.total_atoms}))
+        print(json.dumps({"profile": args.profile, "systems": len(systems), "atoms": b.total_atoms}))
         return
     if args.profile == "vjp":
         half = False
