@@ -581,31 +581,34 @@ def extra_md(lj, dev, stream):
     """Velocity Verlet on the N = 119,164 workload with random initial momenta
     (T ~ 1): one drift and one force call per step, the list rebuilt by the
     fastest-atom bookkeeping rule; reports steps/s and pairs/s including the
-    rebuilds."""
+    rebuilds, with the FP64 and the double-float force."""
     import torch
     from paper_1806_05713_gb300 import inputs
     from paper_1806_05713_gb300.md import VelocityVerlet
     s = inputs.workload_paper()
-    q = torch.from_numpy(s.q).to(dev)
     g = np.random.default_rng(0).normal(size=(s.n, 4))
     g[:, 3] = 0.0
     g[:, :3] -= g[:, :3].mean(axis=0)
-    p = torch.from_numpy(g).to(dev)
-    vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, 0.005)
-    vv.run(20)
-    e0 = vv.kinetic_energy() + vv.potential_energy()
-    r0 = vv.rebuilds
-    steps = 200
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    vv.run(steps)
-    b.record(stream)
-    b.synchronize()
-    ms = a.elapsed_time(b)
-    e1 = vv.kinetic_energy() + vv.potential_energy()
-    return {"n_atoms": s.n, "dt": 0.005, "steps": steps, "ms_per_step": ms / steps,
-            "list_rebuilds": vv.rebuilds - r0, "pairs_per_s": vv.plist.nnz * steps / (ms / 1e3),
-            "energy_drift_rel": abs(e1 - e0) / abs(e0)}
+    res = {"n_atoms": s.n, "dt": 0.005}
+    for name, prec in (("fp64", lj.LJ_FP64), ("dfloat", lj.LJ_DFLOAT)):
+        q = torch.from_numpy(s.q).to(dev)
+        p = torch.from_numpy(g).to(dev)
+        vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, 0.005, precision=prec)
+        vv.run(20)
+        e0 = vv.kinetic_energy() + vv.potential_energy()
+        r0 = vv.rebuilds
+        steps = 200
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        vv.run(steps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        e1 = vv.kinetic_energy() + vv.potential_energy()
+        res[name] = {"steps": steps, "ms_per_step": ms / steps, "list_rebuilds": vv.rebuilds - r0,
+                     "pairs_per_s": vv.plist.nnz * steps / (ms / 1e3),
+                     "energy_drift_rel": abs(e1 - e0) / abs(e0)}
+    return res
 
 
 FORM_NAMES = {0: "fp64", 1: "mixed", 2: "dfloat"}

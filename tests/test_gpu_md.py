@@ -41,7 +41,9 @@ def test_drift_bit_exact(cuda_lib):
     assert np.all((got[:, :3] >= 0) & (got[:, :3] < L))
 
 
-def test_verlet_matches_oracle_integrator(cuda_lib, oracle_lib):
+@pytest.mark.parametrize("precision", [0, 2])
+def test_verlet_matches_oracle_integrator(cuda_lib, oracle_lib, precision):
+    """FP64 and double-float forces: the same trajectory as the oracle's."""
     from paper_1806_05713_gb300.md import VelocityVerlet
     lj = cuda_lib
     s = inputs.fcc_system(10, 1.0, 0.05, seed=3)
@@ -49,7 +51,7 @@ def test_verlet_matches_oracle_integrator(cuda_lib, oracle_lib):
     p0 = np.random.default_rng(1).normal(size=(s.n, 4)) * 0.5
     p0[:, 3] = 0.0
     q, p = to_dev(s.q), to_dev(p0)
-    vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, dt)
+    vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, dt, precision=precision)
     vv.run(steps)
     torch.cuda.synchronize()
     # reference: the same leapfrog with the oracle's list and force, fresh list every step
