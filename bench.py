@@ -466,6 +466,8 @@ def schedule_name(tpi: int) -> str:
         name += ", rows by length"
     if tpi & 1024:
         name += ", image-selected displacement"
+    if tpi & 2048:
+        name += ", exact fixed-point displacement"
     return name
 
 
@@ -685,7 +687,8 @@ def variants(lj, s, q, pl_half, box, dev, stream, flush):
             m_half = pl.nnz if half else pl.nnz // 2
             res[f"list_build_ms/{order}/{kind}"] = t_list
             ref = None
-            for prec, tpis in ((lj.LJ_FP64, (1032, 1028, 1544, 1160)), (lj.LJ_MIXED, (4, 8, 16)),
+            for prec, tpis in ((lj.LJ_FP64, (1032, 1028, 1544, 1160, 2056, 2052, 2568)),
+                               (lj.LJ_MIXED, (4, 8, 16)),
                                (lj.LJ_DFLOAT, (136, 132, 144, 648, 8))):
                 for tpi in tpis:
                     pp = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)

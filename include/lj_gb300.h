@@ -74,7 +74,8 @@ extern "C" {
 /* ---- schedules ---------------------------------------------------------- */
 /* `tpi` = threads per i-row: 1, 2, 4, 8, 16 or 32 lanes of one warp walk one
  * row and reduce their partial sums with warp shuffles; 0 = library default
- * (FP64: LJ_SCHED_IMAGES | 8; mixed: 8 lanes per row). */
+ * (FP64: LJ_SCHED_FIXED | 8; mixed: 8 lanes per row; double-float:
+ * LJ_SCHED_SWP2 | 8). */
 #define LJ_TPI_AUTO 0
 /* LJ_SCHED_REFILL | t (t = 1, 4 or 8; FP64 only): the group-refill schedule.
  * Each group of t lanes owns one row at a time and takes the next row as
@@ -106,6 +107,12 @@ extern "C" {
  * image of q_i with integer compares of IEEE high words, so the
  * displacement costs one FP64 subtraction and no wrap addition. */
 #define LJ_SCHED_IMAGES 1024
+/* LJ_SCHED_FIXED | 4, 8, 16, optionally | LJ_SCHED_SORTED (FP64 only): the
+ * displacement and r^2 computed exactly in 64/128-bit integer fixed point
+ * (positions x 2^k, the minimum image by one integer compare) and rounded
+ * once to double; the rest of Algorithm 1 in IEEE double as in the other
+ * FP64 schedules.  Six fewer FP64 instructions per entry. */
+#define LJ_SCHED_FIXED 2048
 
 const char *lj_status_string(int status);
 /* Text of the last CUDA error seen by this library in this thread. */
@@ -192,9 +199,9 @@ int lj_build_pairlist_static(const double *q4_dev, int64_t n, const double box[3
 /* Force (Algorithm 1 inside Algorithm 3)                                    */
 /* ======================================================================== */
 
-/* Bytes of device workspace lj_force needs (about 8 n + 2.5 KB for LJ_FP64:
- * a row counter and the length-sorted row order; 16 n more for LJ_MIXED,
- * 32 n more for LJ_DFLOAT: fixed-point positions). */
+/* Bytes of device workspace lj_force needs (about 8 n + 2.5 KB: a row
+ * counter and the length-sorted row order; plus fixed-point positions,
+ * 32 n for LJ_FP64 (LJ_SCHED_FIXED) and LJ_DFLOAT, 16 n for LJ_MIXED). */
 size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
 
 /*
@@ -218,7 +225,8 @@ size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
  *                   LJ_SCHED_QUEUE | 1, 2, 4, 8; the last three families
  *                   FP64 only.  LJ_SCHED_SORTED may be or-ed into the plain
  *                   and SWP2 schedules, LJ_SCHED_IMAGES into the FP64
- *                   4, 8, 16 and SWP2 schedules.
+ *                   4, 8, 16 and SWP2 schedules; LJ_SCHED_FIXED | 4, 8, 16
+ *                   (FP64, optionally | LJ_SCHED_SORTED).
  *  workspace_dev    scratch of lj_force_workspace_bytes() (NULL if 0).
  * Half lists add p_j with FP64 atomics, so their rounding order (not their
  * value beyond the last bits) varies between calls; full lists are

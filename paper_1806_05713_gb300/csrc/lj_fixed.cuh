@@ -1,0 +1,251 @@
+// lj_fixed.cuh -- the FP64 form with the displacement and r^2 exact in
+// integer fixed point (schedule LJ_SCHED_FIXED).
+//
+// GB300 issues one FP64 warp instruction per 16 cycles of an SM, its
+// integer units four per cycle, so the FP64 kernel is bound by its count of
+// FP64 instructions per list entry (20 with image-selected displacement:
+// 3 for d, 3 for r^2, 14 for Algorithm 1's impulse and the sums).  Here a
+// pre-pass writes each coordinate as the 64-bit integer X = x 2^k (exact for
+// x >= L/512, since 2^k L < 2^61 leaves every mantissa bit of x above the
+// binary point; a rounding of 2^-(k+1) below that), and per entry
+//   D = X_j - X_i, wrapped by one compare against M/2 = L 2^k / 2 (the
+//       paper's minimum image, decided exactly),
+//   r^2 = (D_x^2 + D_y^2 + D_z^2) 2^-2k exact in 128-bit integers,
+// each rounded once to double with integer instructions.  The FP64
+// definition rounds d = x_j - x_i (and the wrap) and the three products and
+// sums of r^2; these values are at least as accurate.  Everything after --
+// 1/r^2, the powers, df, df d and the momentum sums -- is the FP64 form's
+// IEEE double arithmetic, unchanged: 14 FP64 instructions per entry (half
+// list).  Entries whose r^2 lies within 64 ulp of r_c^2 take the FP64
+// definition for the decision and the displacement, so the interacting set
+// and every pair near the cutoff are the oracle's.
+#pragma once
+
+#include <cmath>
+
+#include "lj_rows.cuh"
+
+namespace lj {
+namespace {
+
+struct FixParams {
+    int k;                   // X = x 2^k
+    double scale;            // 2^k
+    long long M[3], Mh[3];   // L_a 2^k and floor(M / 2)
+};
+
+FixParams make_fix_params(const double box[3])
+{
+    FixParams F{};
+    double Lmax = 0.0;
+    for (int a = 0; a < 3; ++a) Lmax = box[a] > Lmax ? box[a] : Lmax;
+    int e = 0;
+    std::frexp(Lmax, &e);  // Lmax < 2^e
+    F.k = 61 - e;          // L 2^k < 2^61: |D| <= 2^60 after the wrap
+    F.scale = std::ldexp(1.0, F.k);
+    for (int a = 0; a < 3; ++a) {
+        F.M[a] = std::llround(std::ldexp(box[a], F.k));
+        F.Mh[a] = F.M[a] >> 1;
+    }
+    return F;
+}
+
+__global__ void fixed_prepass_kernel(const double *__restrict__ q4, int n, FixParams F,
+                                     longlong4 *__restrict__ X)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x, y, z;
+    load_xyz(q4, i, x, y, z);
+    X[i] = make_longlong4(__double2ll_rn(x * F.scale), __double2ll_rn(y * F.scale),
+                          __double2ll_rn(z * F.scale), 0);
+}
+
+__device__ __forceinline__ void load_fixed(const longlong4 *__restrict__ X, int j, long long &x,
+                                           long long &y, long long &z)
+{
+    long long w;
+    asm("ld.global.nc.v4.s64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(x), "=l"(y), "=l"(z), "=l"(w)
+        : "l"(X + j));
+}
+
+// The minimum image of D = X_j - X_i (|D| < M): if D > M/2, D - M; if
+// D < -M/2, D + M (strict, as the paper's definition; M/2 compared exactly).
+__device__ __forceinline__ long long wrap_fixed(long long D, long long M, long long Mh)
+{
+    return D > Mh ? D - M : (D < -Mh ? D + M : D);
+}
+
+// m 2^(n-53-k), m in [2^52, 2^53], as double bits: the exponent field
+// absorbs the carry of a mantissa rounded up to 2^53.
+__device__ __forceinline__ double assemble_f64(unsigned long long m, int n, int k,
+                                               unsigned long long sign)
+{
+    const unsigned long long ebias = static_cast<unsigned long long>(n - 1 - k + 1023);
+    return __longlong_as_double(static_cast<long long>(sign | (((ebias - 1ull) << 52) + m)));
+}
+
+// Round-to-nearest-even of the top 53 bits of a (bit length n > 53).
+__device__ __forceinline__ unsigned long long round53(unsigned long long top, unsigned long long rem,
+                                                      unsigned long long half)
+{
+    return top + ((rem > half || (rem == half && (top & 1ull))) ? 1ull : 0ull);
+}
+
+// v 2^-k rounded to the nearest double (|v| < 2^63), integer instructions.
+__device__ __forceinline__ double fixed_to_f64(long long v, int k)
+{
+    if (v == 0) return 0.0;
+    const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned long long a = static_cast<unsigned long long>(v < 0 ? -v : v);
+    const int n = 64 - __clzll(static_cast<long long>(a));
+    if (n <= 53) return assemble_f64(a << (53 - n), n, k, sign);
+    const int sh = n - 53;
+    return assemble_f64(round53(a >> sh, a & ((1ull << sh) - 1ull), 1ull << (sh - 1)), n, k, sign);
+}
+
+// (hi 2^64 + lo) 2^-k2 rounded to the nearest double, integer instructions.
+__device__ __forceinline__ double fixed128_to_f64(unsigned long long hi, unsigned long long lo, int k2)
+{
+    if ((hi | lo) == 0ull) return 0.0;
+    int n;
+    unsigned long long top, rem, half;
+    if (hi == 0ull) {
+        n = 64 - __clzll(static_cast<long long>(lo));
+        if (n <= 53) return assemble_f64(lo << (53 - n), n, k2, 0ull);
+        const int sh = n - 53;
+        top = lo >> sh;
+        rem = lo & ((1ull << sh) - 1ull);
+        half = 1ull << (sh - 1);
+    } else {
+        n = 128 - __clzll(static_cast<long long>(hi));
+        const int sh = n - 53;  // 12 .. 75
+        if (sh < 64) {
+            top = (hi << (64 - sh)) | (lo >> sh);
+            rem = lo & ((1ull << sh) - 1ull);
+            half = 1ull << (sh - 1);
+        } else {
+            // sh >= 64: the dropped part spans all of lo and the low bits of hi
+            const int s2 = sh - 64;
+            top = hi >> s2;
+            const unsigned long long rhi = hi & ((1ull << s2) - 1ull);
+            // compare (rhi, lo) with the half-way point 2^(sh-1)
+            const unsigned long long hh = s2 > 0 ? (1ull << (s2 - 1)) : 0ull;
+            const bool gt = s2 > 0 ? (rhi > hh || (rhi == hh && lo > 0ull)) : (lo > (1ull << 63));
+            const bool eq = s2 > 0 ? (rhi == hh && lo == 0ull) : (lo == (1ull << 63));
+            return assemble_f64(top + ((gt || (eq && (top & 1ull))) ? 1ull : 0ull), n, k2, 0ull);
+        }
+    }
+    return assemble_f64(round53(top, rem, half), n, k2, 0ull);
+}
+
+// |D|^2 summed over three axes as a 128-bit integer (|D| <= 2^60 each).
+__device__ __forceinline__ void norm2_fixed(long long dx, long long dy, long long dz,
+                                            unsigned long long &hi, unsigned long long &lo)
+{
+    const unsigned long long ax = static_cast<unsigned long long>(dx < 0 ? -dx : dx);
+    const unsigned long long ay = static_cast<unsigned long long>(dy < 0 ? -dy : dy);
+    const unsigned long long az = static_cast<unsigned long long>(dz < 0 ? -dz : dz);
+    unsigned long long l0 = ax * ax, h0 = __umul64hi(ax, ax);
+    const unsigned long long l1 = ay * ay, h1 = __umul64hi(ay, ay);
+    const unsigned long long l2 = az * az, h2 = __umul64hi(az, az);
+    unsigned long long s = l0 + l1;
+    h0 += h1 + (s < l0 ? 1ull : 0ull);
+    l0 = s;
+    s = l0 + l2;
+    h0 += h2 + (s < l0 ? 1ull : 0ull);
+    hi = h0;
+    lo = s;
+}
+
+// One row of the FP64 form with the exact fixed-point displacement (see the
+// header comment); the arithmetic after r^2 is fp64_row's.
+template <int TPI, bool HALF>
+__device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
+                                               const longlong4 *__restrict__ X,
+                                               double *__restrict__ p4,
+                                               const int *__restrict__ row_ptr,
+                                               const int *__restrict__ col, int i,
+                                               const Fp64Params &P, const FixParams &F, unsigned gm)
+{
+    const int sub = threadIdx.x & (TPI - 1);
+    long long xi, yi, zi;
+    load_fixed(X, i, xi, yi, zi);
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    const int kb = row_ptr[i], ke = row_ptr[i + 1];
+    for (int k0 = kb; k0 < ke; k0 += TPI) {
+        const int k = k0 + sub;
+        const bool valid = k < ke;
+        const int j = valid ? col[k] : i;
+        long long xj, yj, zj;
+        load_fixed(X, j, xj, yj, zj);
+        const long long Dx = wrap_fixed(xj - xi, F.M[0], F.Mh[0]);
+        const long long Dy = wrap_fixed(yj - yi, F.M[1], F.Mh[1]);
+        const long long Dz = wrap_fixed(zj - zi, F.M[2], F.Mh[2]);
+        unsigned long long hi, lo;
+        norm2_fixed(Dx, Dy, Dz, hi, lo);
+        double r2 = valid ? fixed128_to_f64(hi, lo, 2 * F.k) : 1.0;
+        double dx = fixed_to_f64(Dx, F.k), dy = fixed_to_f64(Dy, F.k), dz = fixed_to_f64(Dz, F.k);
+        const long long rb = __double_as_longlong(r2);
+        bool in = valid && rb < P.rc2_bits;
+        const bool near = valid && static_cast<unsigned long long>(rb - P.rc2_bits + 64) < 128ull;
+        if (__any_sync(gm, near)) {
+            if (near) {
+                // the FP64 definition: its displacement, its decision
+                double qxi, qyi, qzi, qxj, qyj, qzj;
+                load_xyz(q4, i, qxi, qyi, qzi);
+                load_xyz(q4, j, qxj, qyj, qzj);
+                dx = min_image(__dsub_rn(qxj, qxi), P.L[0], P.half_bits[0]);
+                dy = min_image(__dsub_rn(qyj, qyi), P.L[1], P.half_bits[1]);
+                dz = min_image(__dsub_rn(qzj, qzi), P.L[2], P.half_bits[2]);
+                in = exact_in_cutoff(dx, dy, dz, P.rc2);
+                r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+            }
+        }
+        if (__any_sync(gm, in)) {
+            if (!in) r2 = 1.0;
+            const double w = rcp_fp64(r2, gm);
+            const double w2 = w * w;
+            const double w4 = w2 * w2;
+            const double w3 = w2 * w;
+            const double fn = w4 * fma(P.B, w3, -P.A);  // -df: p_i -= fn d, p_j += fn d
+            if (in) {
+                if (HALF) {
+                    const double fx = fn * dx, fy = fn * dy, fz = fn * dz;
+                    double *pj = p4 + 4 * static_cast<int64_t>(j);
+                    atomicAdd(pj + 0, fx);
+                    atomicAdd(pj + 1, fy);
+                    atomicAdd(pj + 2, fz);
+                    ax -= fx;
+                    ay -= fy;
+                    az -= fz;
+                } else {
+                    ax = fma(-fn, dx, ax);
+                    ay = fma(-fn, dy, ay);
+                    az = fma(-fn, dz, az);
+                }
+            }
+        }
+    }
+    double *pi = p4 + 4 * static_cast<int64_t>(i);
+    if (HALF) {
+        atomicAdd(pi + 0, ax);
+        atomicAdd(pi + 1, ay);
+        atomicAdd(pi + 2, az);
+    } else {
+        if (TPI > 1) {
+            ax = group_sum<TPI>(ax);
+            ay = group_sum<TPI>(ay);
+            az = group_sum<TPI>(az);
+        }
+        if (sub == 0) {
+            atomicAdd(pi + 0, ax);
+            atomicAdd(pi + 1, ay);
+            atomicAdd(pi + 2, az);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace lj

@@ -34,6 +34,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "lj_fixed.cuh"
 #include "lj_rows.cuh"
 
 namespace lj {
@@ -56,6 +57,20 @@ force_fp64_kernel(const double *__restrict__ q4, double *__restrict__ p4, int n,
     if (gid >= n) return;
     const int i = order ? order[gid] : gid;
     fp64_row<TPI, HALF, U, IMG>(q4, p4, row_ptr, col, i, P, group_mask<TPI>());
+}
+
+// FP64 form with the exact fixed-point displacement (LJ_SCHED_FIXED).
+template <int TPI, bool HALF>
+__global__ void __launch_bounds__(256)
+force_fixed_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
+                   double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
+                   const int *__restrict__ col, Fp64Params P, FixParams F,
+                   const int *__restrict__ order)
+{
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
+    if (gid >= n) return;
+    const int i = order ? order[gid] : gid;
+    fp64_fixed_row<TPI, HALF>(q4, X, p4, row_ptr, col, i, P, F, group_mask<TPI>());
 }
 
 template <int TPI, bool HALF>
@@ -217,6 +232,21 @@ int launch_fp64(const double *q4, double *p4, int n, const int *rp, const int *c
 }
 
 template <int TPI>
+int launch_fixed(const double *q4, const longlong4 *X, double *p4, int n, const int *rp,
+                 const int *col, int half, const Fp64Params &P, const FixParams &F, const int *order,
+                 cudaStream_t st)
+{
+    const int64_t threads = int64_t(n) * TPI;
+    const unsigned grid = unsigned((threads + 255) / 256);
+    if (half)
+        force_fixed_kernel<TPI, true><<<grid, 256, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
+    else
+        force_fixed_kernel<TPI, false><<<grid, 256, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
+    LJ_TRY_LAUNCH("force_fixed_kernel");
+    return LJ_OK;
+}
+
+template <int TPI>
 int launch_mixed(const double *q4, const uint4 *rel, double *p4, int n, const int *rp,
                  const int *col, int half, const MixedParams &P, const int *order, cudaStream_t st)
 {
@@ -264,8 +294,8 @@ int check_force_args(const double *q4, const double *p4, int64_t n, const int32_
 }
 
 // Workspace: [256 B: refill/queue counter][order: n int][slot: n int]
-// [length histogram] and, for LJ_MIXED and LJ_DFLOAT, the fixed-point
-// positions.
+// [length histogram] and the fixed-point positions of the form (LJ_FP64:
+// 64-bit integers for LJ_SCHED_FIXED; LJ_MIXED: 32-bit; LJ_DFLOAT: chunks).
 struct ForceWs {
     unsigned *counter;
     int *order, *slot, *hist;
@@ -283,7 +313,9 @@ ForceWs carve_force_ws(void *base, int64_t n, int precision)
     w.slot = c.take<int>(nn);
     w.hist = c.take<int>(kLenBuckets);
     w.rel = precision == LJ_MIXED ? c.take<uint4>(nn) : nullptr;
-    w.rec = precision == LJ_DFLOAT ? static_cast<void *>(c.take<char>(dfloat_record_bytes(n))) : nullptr;
+    w.rec = precision == LJ_DFLOAT ? static_cast<void *>(c.take<char>(dfloat_record_bytes(n)))
+            : precision == LJ_FP64 ? static_cast<void *>(c.take<longlong4>(nn))
+                                   : nullptr;
     return w;
 }
 
@@ -296,6 +328,9 @@ bool valid_schedule(int s, int precision)
     if (s & LJ_SCHED_REFILL)
         return precision == LJ_FP64 && (s & ~(LJ_SCHED_REFILL | LJ_SCHED_SWP2 | 63)) == 0 &&
                (t == 0 || t == 1 || t == 4 || t == 8);
+    if (s & LJ_SCHED_FIXED)
+        return precision == LJ_FP64 && (s & ~(LJ_SCHED_FIXED | LJ_SCHED_SORTED | 63)) == 0 &&
+               (t == 4 || t == 8 || t == 16);
     if (s & ~(LJ_SCHED_SORTED | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES | 63)) return false;
     if (precision == LJ_DFLOAT) return (s & LJ_SCHED_IMAGES) == 0 && (t == 4 || t == 8 || t == 16);
     if (s & LJ_SCHED_IMAGES) return precision == LJ_FP64 && (t == 4 || t == 8 || t == 16);
@@ -313,6 +348,7 @@ size_t force_workspace_bytes_impl(int64_t n, int precision)
     c.take<int>(kLenBuckets);
     if (precision == LJ_MIXED) c.take<uint4>(nn);
     if (precision == LJ_DFLOAT) c.take<char>(dfloat_record_bytes(n));
+    if (precision == LJ_FP64) c.take<longlong4>(nn);
     return c.used + 256;
 }
 
@@ -326,7 +362,7 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
     if (n == 0 || nnz == 0) return LJ_OK;
     const int ni = static_cast<int>(n);
     if (tpi == LJ_TPI_AUTO)
-        tpi = precision == LJ_FP64 ? (LJ_SCHED_IMAGES | 8) : precision == LJ_DFLOAT ? (LJ_SCHED_SWP2 | 8) : 8;
+        tpi = precision == LJ_FP64 ? (LJ_SCHED_FIXED | 8) : precision == LJ_DFLOAT ? (LJ_SCHED_SWP2 | 8) : 8;
     if (!valid_schedule(tpi, precision)) return LJ_ERR_ARG;
     if (!ws || ws_bytes < force_workspace_bytes_impl(n, precision)) return LJ_ERR_CAPACITY;
     const ForceWs W = carve_force_ws(ws, n, precision);
@@ -350,6 +386,19 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
     if (precision == LJ_DFLOAT)
         return force_dfloat(q4, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma, tpi, order,
                             W.rec, st);
+    if (precision == LJ_FP64 && (tpi & LJ_SCHED_FIXED)) {
+        const Fp64Params P = make_fp64_params(box, dt, rc, eps, sigma);
+        const FixParams F = make_fix_params(box);
+        longlong4 *X = static_cast<longlong4 *>(W.rec);
+        fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4, ni, F, X);
+        LJ_TRY_LAUNCH("fixed_prepass_kernel");
+        switch (tpi & 63) {
+            case 4: return launch_fixed<4>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
+            case 8: return launch_fixed<8>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
+            case 16: return launch_fixed<16>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
+            default: return LJ_ERR_ARG;
+        }
+    }
     if (precision == LJ_FP64) {
         const Fp64Params P = make_fp64_params(box, dt, rc, eps, sigma);
         switch (tpi) {

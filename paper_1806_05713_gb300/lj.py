@@ -33,6 +33,7 @@ LJ_SCHED_SWP2 = 128
 LJ_SCHED_QUEUE = 256
 LJ_SCHED_SORTED = 512
 LJ_SCHED_IMAGES = 1024
+LJ_SCHED_FIXED = 2048
 LJ_STATIC_MAX_ATOMS = 131072
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liblj_gb300.so")
@@ -358,9 +359,10 @@ def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float
     (best_tpi, best_ms, {tpi: ms})."""
     lib = load()
     if candidates is None:
-        S, W, I = LJ_SCHED_SORTED, LJ_SCHED_SWP2, LJ_SCHED_IMAGES
+        S, W, I, F = LJ_SCHED_SORTED, LJ_SCHED_SWP2, LJ_SCHED_IMAGES, LJ_SCHED_FIXED
         candidates = ([8, W | 8, I | 4, I | 8, I | 16, I | W | 4, I | W | 8, S | I | 4,
-                       S | I | 8, S | I | 16, LJ_SCHED_REFILL | W | 8, LJ_SCHED_QUEUE | 8]
+                       S | I | 8, S | I | 16, F | 4, F | 8, F | 16, S | F | 8,
+                       LJ_SCHED_REFILL | W | 8, LJ_SCHED_QUEUE | 8]
                       if precision == LJ_FP64 else
                       [4, 8, 16, S | 4, S | 8, S | 16] if precision == LJ_DFLOAT else
                       [2, 4, 8, 16, S | 4, S | 8, S | 16])

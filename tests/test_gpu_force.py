@@ -14,9 +14,9 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-12
 MIXED_TOL = 1e-5
 SCHEDULES = [1, 2, 4, 8, 16, 32, 132, 136, 144, 64, 68, 72, 196, 200, 257, 258, 260, 264, 520,
-             644, 648, 656, 1028, 1032, 1040, 1156, 1160, 1168, 1672, 1544]
+             644, 648, 656, 1028, 1032, 1040, 1156, 1160, 1168, 1672, 1544, 2052, 2056, 2064, 2568]
 # 128|t software-pipelined, 64|t group-refill, 256|t lane-queue, 512|... length-sorted rows,
-# 1024|... image-selected displacement
+# 1024|... image-selected displacement, 2048|... exact fixed-point displacement
 
 
 def _run(lj, s, half, precision, tpi, dt=0.01, eps=1.0, sigma=1.0, p0=None, rc=None, pl=None):
@@ -68,7 +68,7 @@ def test_eps_sigma_dt_and_existing_momenta(cuda_lib, oracle_lib, precision, tol)
     p0 = np.random.default_rng(2).normal(size=(s.n, 4))
     kw = dict(dt=0.005, eps=1.3, sigma=1.1, rc=3.0)
     for half in (True, False):
-        for tpi in ((64, 8, 136, 200, 260, 1160) if precision == 0 else (8,)):
+        for tpi in ((64, 8, 136, 200, 260, 1160, 2056) if precision == 0 else (8,)):
             got, _ = _run(cuda_lib, s, half, precision, tpi, p0=p0, **kw)
             want = _oracle(oracle_lib, s, half, p0=p0, **kw)
             assert _relerr(got - p0[:, :3], want - p0[:, :3]) <= tol
@@ -115,6 +115,47 @@ def test_small_box_mixed_image_choice(cuda_lib, oracle_lib):
         assert _relerr(got, want) <= MIXED_TOL
 
 
+@pytest.mark.parametrize("tpi", [1032, 2056])
+def test_fp64_pairs_on_the_cutoff(cuda_lib, oracle_lib, tpi):
+    """Pairs at r_c and one ulp either side, along an axis and a diagonal:
+    the FP64 schedules interact exactly the oracle's pairs."""
+    xs = []
+    for k, d in enumerate([3.0, np.nextafter(3.0, 0.0), np.nextafter(3.0, 4.0),
+                           3.0 - 1e-15, 3.0 + 2e-15, 3.0 - 1e-12]):
+        y = 2.0 + 4.0 * k
+        xs += [[10.0, y, 5.0], [10.0 + d, y, 5.0]]
+    h = 3.0 / np.sqrt(3.0)
+    xs += [[20.0, 30.0, 20.0], [20.0 + h, 30.0 + h, 20.0 + h]]
+    xs += [[39.0, 35.0, 35.0], [np.nextafter(2.0, 0.0), 35.0, 35.0]]   # across the boundary
+    q = np.zeros((len(xs), 4))
+    q[:, :3] = xs
+    s = inputs.LJSystem(q=q, box=np.array([40.0] * 3), rho=0.0)
+    for half in (True, False):
+        got, _ = _run(cuda_lib, s, half, 0, tpi)
+        want = _oracle(oracle_lib, s, half)
+        assert np.array_equal(np.any(want != 0.0, axis=1), np.any(got != 0.0, axis=1))
+        assert _relerr(got, want) <= FP64_TOL
+
+
+@pytest.mark.parametrize("scale", [0.3, 1.0, 25.0])
+def test_fp64_fixed_point_box_sizes(cuda_lib, oracle_lib, scale):
+    """The fixed-point shift k follows the box: tiny, unit and large boxes
+    (sigma, r_c scaled with them), non-cubic, with momenta already set."""
+    s = inputs.fcc_system(7, 0.9, 0.05, seed=4)
+    st = np.array([1.0, 1.07, 1.15]) * scale
+    s.q[:, :3] *= st
+    s.box = s.box * st
+    # momenta already set, at the scale of one impulse (a larger p0 would
+    # hide the impulse's last digits in the rounding of p0 + dp)
+    p0 = np.random.default_rng(6).normal(size=(s.n, 4)) * 1e-3 / scale
+    kw = dict(dt=0.004, eps=0.8, sigma=1.05 * scale, rc=3.0 * scale)
+    s.rc, s.margin = 3.0 * scale, 0.3 * scale
+    for half in (True, False):
+        got, _ = _run(cuda_lib, s, half, 0, 2056, p0=p0, **kw)
+        want = _oracle(oracle_lib, s, half, p0=p0, **kw)
+        assert _relerr(got - p0[:, :3], want - p0[:, :3]) <= FP64_TOL
+
+
 def test_newton_third_law_half_list(cuda_lib, small):
     got, _ = _run(cuda_lib, small, True, 0, 64)
     assert np.max(np.abs(got.sum(axis=0))) < 1e-12 * np.abs(got).sum()
@@ -138,7 +179,7 @@ def test_fp64_paper_size(cuda_lib, oracle_lib, order, half):
     s = inputs.workload_paper(order=order)
     want = _oracle(oracle_lib, s, half)
     pl = None
-    for tpi in (64, 8, 32, 136, 72, 200, 258, 260, 264, 648, 1160, 1672):
+    for tpi in (64, 8, 32, 136, 72, 200, 258, 260, 264, 648, 1160, 1672, 2052, 2056, 2568):
         got, pl = _run(cuda_lib, s, half, 0, tpi, pl=pl)
         assert _relerr(got, want) <= FP64_TOL, tpi
 
