@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "lj_dfloat.cuh"
+#include "lj_fixed.cuh"
 #include "lj_rows.cuh"
 
 namespace lj {
@@ -29,6 +30,7 @@ struct SysDev {
     long long atom_off, row_off, entry_off;
     int n, half, cubic;
     Fp64Params fp;
+    FixParams fx;
     MixedParams mp;
     DfParams dp;
 };
@@ -103,15 +105,32 @@ __global__ void batched_df_prepass_kernel(const SysDev *__restrict__ sys, const 
     }
 }
 
-// rel: MIXED fixed-point positions; rec: DFLOAT records (each indexed by
-// the batch-wide atom number).
+// 64-bit fixed-point positions of every system (FP64 form).
+__global__ void batched_fixed_prepass_kernel(const SysDev *__restrict__ sys,
+                                             const Item *__restrict__ items,
+                                             const double *__restrict__ q4, longlong4 *__restrict__ X)
+{
+    const Item it = items[blockIdx.x];
+    const SysDev &S = sys[it.sys];
+    for (int r = it.row_begin + threadIdx.x; r < it.row_end; r += blockDim.x) {
+        const long long a = S.atom_off + r;
+        double x, y, z;
+        load_xyz(q4, a, x, y, z);
+        X[a] = make_longlong4(__double2ll_rn(x * S.fx.scale), __double2ll_rn(y * S.fx.scale),
+                              __double2ll_rn(z * S.fx.scale), 0);
+    }
+}
+
+// rel: MIXED fixed-point positions; rec: DFLOAT records; X: FP64 fixed-point
+// positions (each indexed by the batch-wide atom number).
 // CUBIC (DFLOAT only): every system of the batch has a cubic box; otherwise
 // the displacement is scaled per axis (by 1 on the cubic systems).
 template <int TPI, int FORM, bool CUBIC>
 __global__ void __launch_bounds__(kBatchThreads)
 batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ items,
                      long long nitems, const double *__restrict__ q4, const uint4 *__restrict__ rel,
-                     const DfRec *__restrict__ rec, double *__restrict__ p4,
+                     const DfRec *__restrict__ rec, const longlong4 *__restrict__ X,
+                     double *__restrict__ p4,
                      const int *__restrict__ row_ptr, const int *__restrict__ col,
                      unsigned long long *__restrict__ counter)
 {
@@ -135,24 +154,26 @@ batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ it
             if (r < I.row_end) {  // uniform within a group
                 if (FORM == kDfloat) {
                     const DfRec *srec = rec + S.atom_off;
-                    const DfParams P = S.dp;
+                    const DfParams &P = S.dp;  // fields read where used
                     if (half)
                         dfloat_row2<TPI, true, CUBIC>(sq, srec, sp, srp, scol, r, P, gm);
                     else
                         dfloat_row2<TPI, false, CUBIC>(sq, srec, sp, srp, scol, r, P, gm);
                 } else if (FORM == kMixed) {
                     const uint4 *srel = rel + S.atom_off;
-                    const MixedParams P = S.mp;
+                    const MixedParams &P = S.mp;
                     if (half)
                         mixed_row<TPI, true>(sq, srel, sp, srp, scol, r, P);
                     else
                         mixed_row<TPI, false>(sq, srel, sp, srp, scol, r, P);
                 } else {
-                    const Fp64Params P = S.fp;
+                    const longlong4 *sX = X + S.atom_off;
+                    const Fp64Params &P = S.fp;
+                    const FixParams &F = S.fx;
                     if (half)
-                        fp64_row<TPI, true, 1, true>(sq, sp, srp, scol, r, P, gm);
+                        fp64_fixed_row<TPI, true>(sq, sX, sp, srp, scol, r, P, F, gm);
                     else
-                        fp64_row<TPI, false, 1, true>(sq, sp, srp, scol, r, P, gm);
+                        fp64_fixed_row<TPI, false>(sq, sX, sp, srp, scol, r, P, F, gm);
                 }
             }
         }
@@ -161,7 +182,7 @@ batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ it
 
 template <int FORM, bool CUBIC>
 int launch_batched(const lj_batch *b, const PlanView &v, const double *q4, const uint4 *rel,
-                   const DfRec *rec, double *p4, const int *rp, const int *col,
+                   const DfRec *rec, const longlong4 *X, double *p4, const int *rp, const int *col,
                    unsigned long long *counter, cudaStream_t st)
 {
     const long long ni = b->nitems;
@@ -169,7 +190,7 @@ int launch_batched(const lj_batch *b, const PlanView &v, const double *q4, const
 #define LJ_BATCH_CASE(T)                                                                        \
     case T:                                                                                     \
         batched_force_kernel<T, FORM, CUBIC><<<grid, kBatchThreads, 0, st>>>(v.sys, v.items, ni, q4, \
-                                                                  rel, rec, p4, rp, col, counter); \
+                                                               rel, rec, X, p4, rp, col, counter); \
         break;
     switch (b->tpi) {
         LJ_BATCH_CASE(1)
@@ -258,6 +279,7 @@ extern "C" int lj_batch_init(lj_batch *batch, const lj_system *systems, int nsys
         d.n = static_cast<int>(y.n);
         d.half = y.half ? 1 : 0;
         d.fp = make_fp64_params(y.box, dt, y.r_cut, y.eps, y.sigma);
+        d.fx = make_fix_params(y.box);
         d.mp = make_mixed_params(y.box, dt, y.r_cut, y.eps, y.sigma);
         d.dp = make_dfloat_params(y.box, dt, y.r_cut, y.eps, y.sigma);
         d.cubic = y.box[1] == y.box[0] && y.box[2] == y.box[0];
@@ -313,6 +335,7 @@ extern "C" size_t lj_force_batched_workspace_bytes(const lj_batch *batch)
     size_t bytes = 256;
     if (batch->precision == LJ_MIXED) bytes += size_t(batch->total_atoms) * sizeof(uint4) + 256;
     if (batch->precision == LJ_DFLOAT) bytes += size_t(batch->total_atoms) * sizeof(lj::DfRec) + 256;
+    if (batch->precision == LJ_FP64) bytes += size_t(batch->total_atoms) * sizeof(longlong4) + 256;
     return bytes;
 }
 
@@ -336,20 +359,23 @@ extern "C" int lj_force_batched(const lj_batch *batch, const double *q4_dev, dou
         uint4 *rel = c.take<uint4>(size_t(batch->total_atoms));
         batched_prepass_kernel<<<unsigned(batch->nitems), 128, 0, st>>>(v.sys, v.items, q4_dev, rel);
         LJ_TRY_LAUNCH("batched_prepass_kernel");
-        return launch_batched<kMixed, true>(batch, v, q4_dev, rel, nullptr, p4_dev, row_ptr_dev,
-                                            col_dev, counter, st);
+        return launch_batched<kMixed, true>(batch, v, q4_dev, rel, nullptr, nullptr, p4_dev,
+                                            row_ptr_dev, col_dev, counter, st);
     }
     if (batch->precision == LJ_DFLOAT) {
         DfRec *rec = c.take<DfRec>(size_t(batch->total_atoms));
         batched_df_prepass_kernel<<<unsigned(batch->nitems), 128, 0, st>>>(v.sys, v.items, q4_dev, rec);
         LJ_TRY_LAUNCH("batched_df_prepass_kernel");
         if (batch->flags & 1)
-            return launch_batched<kDfloat, true>(batch, v, q4_dev, nullptr, rec, p4_dev, row_ptr_dev,
-                                                 col_dev, counter, st);
-        return launch_batched<kDfloat, false>(batch, v, q4_dev, nullptr, rec, p4_dev, row_ptr_dev,
-                                              col_dev, counter, st);
+            return launch_batched<kDfloat, true>(batch, v, q4_dev, nullptr, rec, nullptr, p4_dev,
+                                                 row_ptr_dev, col_dev, counter, st);
+        return launch_batched<kDfloat, false>(batch, v, q4_dev, nullptr, rec, nullptr, p4_dev,
+                                              row_ptr_dev, col_dev, counter, st);
     }
-    return launch_batched<kFp64, true>(batch, v, q4_dev, nullptr, nullptr, p4_dev, row_ptr_dev,
+    longlong4 *X = c.take<longlong4>(size_t(batch->total_atoms));
+    batched_fixed_prepass_kernel<<<unsigned(batch->nitems), 128, 0, st>>>(v.sys, v.items, q4_dev, X);
+    LJ_TRY_LAUNCH("batched_fixed_prepass_kernel");
+    return launch_batched<kFp64, true>(batch, v, q4_dev, nullptr, nullptr, X, p4_dev, row_ptr_dev,
                                        col_dev, counter, st);
 }
 

@@ -159,15 +159,56 @@ __device__ __forceinline__ void norm2_fixed(long long dx, long long dy, long lon
     lo = s;
 }
 
+// The exact fixed-point displacement of entry j of row i (see the header
+// comment): d in double, r^2 in double (1.0 for an invalid lane), and the
+// FP64 definition's d, r^2 and decision for entries within 64 ulp of r_c^2.
+// Returns whether the pair interacts.  Every lane of gm calls it.
+__device__ __forceinline__ bool fixed_entry(const double *__restrict__ q4, long long xi, long long yi,
+                                            long long zi, long long xj, long long yj, long long zj,
+                                            bool valid, int i, int j, const Fp64Params &P,
+                                            const FixParams &F, unsigned gm, double &dx, double &dy,
+                                            double &dz, double &r2)
+{
+    const long long Dx = wrap_fixed(xj - xi, F.M[0], F.Mh[0]);
+    const long long Dy = wrap_fixed(yj - yi, F.M[1], F.Mh[1]);
+    const long long Dz = wrap_fixed(zj - zi, F.M[2], F.Mh[2]);
+    unsigned long long hi, lo;
+    norm2_fixed(Dx, Dy, Dz, hi, lo);
+    r2 = valid ? fixed128_to_f64(hi, lo, 2 * F.k) : 1.0;
+    dx = fixed_to_f64(Dx, F.k);
+    dy = fixed_to_f64(Dy, F.k);
+    dz = fixed_to_f64(Dz, F.k);
+    const long long rb = __double_as_longlong(r2);
+    bool in = valid && rb < P.rc2_bits;
+    const bool near = valid && static_cast<unsigned long long>(rb - P.rc2_bits + 64) < 128ull;
+    if (__any_sync(gm, near)) {
+        if (near) {
+            // the FP64 definition: its displacement, its decision
+            double qxi, qyi, qzi, qxj, qyj, qzj;
+            load_xyz(q4, i, qxi, qyi, qzi);
+            load_xyz(q4, j, qxj, qyj, qzj);
+            dx = min_image(__dsub_rn(qxj, qxi), P.L[0], P.half_bits[0]);
+            dy = min_image(__dsub_rn(qyj, qyi), P.L[1], P.half_bits[1]);
+            dz = min_image(__dsub_rn(qzj, qzi), P.L[2], P.half_bits[2]);
+            in = exact_in_cutoff(dx, dy, dz, P.rc2);
+            r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        }
+    }
+    return in;
+}
+
 // One row of the FP64 form with the exact fixed-point displacement (see the
-// header comment); the arithmetic after r^2 is fp64_row's.
-template <int TPI, bool HALF>
+// header comment); the arithmetic after r^2 is fp64_row's.  EN: also sum the
+// pair energy 4 eps [(sigma/r)^12 - (sigma/r)^6] of every interacting entry
+// into *ev and count them in *ecount.
+template <int TPI, bool HALF, bool EN = false>
 __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
                                                const longlong4 *__restrict__ X,
                                                double *__restrict__ p4,
                                                const int *__restrict__ row_ptr,
                                                const int *__restrict__ col, int i,
-                                               const Fp64Params &P, const FixParams &F, unsigned gm)
+                                               const Fp64Params &P, const FixParams &F, unsigned gm,
+                                               double *ev = nullptr, int *ecount = nullptr)
 {
     const int sub = threadIdx.x & (TPI - 1);
     long long xi, yi, zi;
@@ -180,29 +221,8 @@ __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
         const int j = valid ? col[k] : i;
         long long xj, yj, zj;
         load_fixed(X, j, xj, yj, zj);
-        const long long Dx = wrap_fixed(xj - xi, F.M[0], F.Mh[0]);
-        const long long Dy = wrap_fixed(yj - yi, F.M[1], F.Mh[1]);
-        const long long Dz = wrap_fixed(zj - zi, F.M[2], F.Mh[2]);
-        unsigned long long hi, lo;
-        norm2_fixed(Dx, Dy, Dz, hi, lo);
-        double r2 = valid ? fixed128_to_f64(hi, lo, 2 * F.k) : 1.0;
-        double dx = fixed_to_f64(Dx, F.k), dy = fixed_to_f64(Dy, F.k), dz = fixed_to_f64(Dz, F.k);
-        const long long rb = __double_as_longlong(r2);
-        bool in = valid && rb < P.rc2_bits;
-        const bool near = valid && static_cast<unsigned long long>(rb - P.rc2_bits + 64) < 128ull;
-        if (__any_sync(gm, near)) {
-            if (near) {
-                // the FP64 definition: its displacement, its decision
-                double qxi, qyi, qzi, qxj, qyj, qzj;
-                load_xyz(q4, i, qxi, qyi, qzi);
-                load_xyz(q4, j, qxj, qyj, qzj);
-                dx = min_image(__dsub_rn(qxj, qxi), P.L[0], P.half_bits[0]);
-                dy = min_image(__dsub_rn(qyj, qyi), P.L[1], P.half_bits[1]);
-                dz = min_image(__dsub_rn(qzj, qzi), P.L[2], P.half_bits[2]);
-                in = exact_in_cutoff(dx, dy, dz, P.rc2);
-                r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-            }
-        }
+        double dx, dy, dz, r2;
+        const bool in = fixed_entry(q4, xi, yi, zi, xj, yj, zj, valid, i, j, P, F, gm, dx, dy, dz, r2);
         if (__any_sync(gm, in)) {
             if (!in) r2 = 1.0;
             const double w = rcp_fp64(r2, gm);
@@ -211,6 +231,10 @@ __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
             const double w3 = w2 * w;
             const double fn = w4 * fma(P.B, w3, -P.A);  // -df: p_i -= fn d, p_j += fn d
             if (in) {
+                if (EN) {
+                    *ev += w3 * fma(P.C12, w3, -P.C6);
+                    ++*ecount;
+                }
                 if (HALF) {
                     const double fx = fn * dx, fy = fn * dy, fz = fn * dz;
                     double *pj = p4 + 4 * static_cast<int64_t>(j);

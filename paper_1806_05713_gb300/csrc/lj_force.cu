@@ -85,14 +85,15 @@ force_mixed_kernel(const double *__restrict__ q4, const uint4 *__restrict__ rel,
     mixed_row<TPI, HALF>(q4, rel, p4, row_ptr, col, i, P);
 }
 
-// Force and potential energy in one pass (FP64, 8 lanes per row, image-
-// selected displacement): each thread keeps its row's pair-energy sum and
+// Force and potential energy in one pass (FP64, 8 lanes per row, exact
+// fixed-point displacement): each thread keeps its row's pair-energy sum and
 // in-cutoff count; a fixed-order block reduction writes one partial per
 // block (the final sum is taken by energy_partials_kernel).
 __global__ void __launch_bounds__(256)
-force_energy_fp64_kernel(const double *__restrict__ q4, double *__restrict__ p4, int n,
-                         const int *__restrict__ row_ptr, const int *__restrict__ col,
-                         Fp64Params P, int half, double *__restrict__ partial)
+force_energy_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
+                         double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
+                         const int *__restrict__ col, Fp64Params P, FixParams F, int half,
+                         double *__restrict__ partial)
 {
     constexpr int TPI = 8;
     __shared__ double red_e[8];
@@ -102,11 +103,11 @@ force_energy_fp64_kernel(const double *__restrict__ q4, double *__restrict__ p4,
     int cnt = 0;
     if (gid < n) {
         if (half)
-            fp64_row<TPI, true, 1, true, 0, true>(q4, p4, row_ptr, col, gid, P, group_mask<TPI>(),
-                                                  Layout{4, 1}, &ev, &cnt);
+            fp64_fixed_row<TPI, true, true>(q4, X, p4, row_ptr, col, gid, P, F, group_mask<TPI>(),
+                                            &ev, &cnt);
         else
-            fp64_row<TPI, false, 1, true, 0, true>(q4, p4, row_ptr, col, gid, P, group_mask<TPI>(),
-                                                   Layout{4, 1}, &ev, &cnt);
+            fp64_fixed_row<TPI, false, true>(q4, X, p4, row_ptr, col, gid, P, F, group_mask<TPI>(),
+                                             &ev, &cnt);
     }
     long long c = cnt;
 #pragma unroll
@@ -440,7 +441,10 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
 extern "C" size_t lj_force_energy_workspace_bytes(int64_t n)
 {
     const int64_t blocks = (std::max<int64_t>(n, 1) * 8 + 255) / 256;
-    return size_t(2 * blocks) * sizeof(double) + 256;
+    lj::Carver c(nullptr);
+    c.take<double>(2 * size_t(blocks));
+    c.take<longlong4>(size_t(std::max<int64_t>(n, 1)));
+    return c.used + 256;
 }
 
 extern "C" int lj_force_energy(const double *q4_dev, double *p4_dev, int64_t n,
@@ -461,11 +465,15 @@ extern "C" int lj_force_energy(const double *q4_dev, double *p4_dev, int64_t n,
     }
     if (!workspace_dev || workspace_bytes < lj_force_energy_workspace_bytes(n)) return LJ_ERR_CAPACITY;
     const Fp64Params P = make_fp64_params(box, dt, r_cut, eps, sigma);
+    const FixParams F = make_fix_params(box);
     const int blocks = static_cast<int>((n * 8 + 255) / 256);
     Carver c(workspace_dev);
     double *partial = c.take<double>(2 * size_t(blocks));
-    force_energy_fp64_kernel<<<blocks, 256, 0, st>>>(q4_dev, p4_dev, static_cast<int>(n), row_ptr_dev,
-                                                     col_dev, P, half, partial);
+    longlong4 *X = c.take<longlong4>(size_t(n));
+    fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, static_cast<int>(n), F, X);
+    LJ_TRY_LAUNCH("fixed_prepass_kernel");
+    force_energy_fp64_kernel<<<blocks, 256, 0, st>>>(q4_dev, X, p4_dev, static_cast<int>(n), row_ptr_dev,
+                                                     col_dev, P, F, half, partial);
     LJ_TRY_LAUNCH("force_energy_fp64_kernel");
     double vshift = 0.0;
     if (shifted) {

@@ -18,14 +18,16 @@
 // two scalar gradients take half of the sum over entries.  A half list
 // scatters c to q_j with FP64 atomics.
 //
-// Forms: FP64 (every step double), MIXED (fixed-point displacement rounded
-// once to FP32,
-// and FP32 pair arithmetic as in lj_force, Kahan-compensated FP32 row and
-// scalar sums, FP64 outputs).  Pairs within the error band of r_c^2 are
+// Forms: FP64 (the displacement and s exact in integer fixed point and
+// rounded once to double, as lj_force's LJ_SCHED_FIXED; every later step
+// double), MIXED (fixed-point displacement rounded once to FP32, FP32 pair
+// arithmetic as in lj_force, Kahan-compensated FP32 row and scalar sums,
+// FP64 outputs).  Pairs within the error band of r_c^2 are
 // decided by the exact FP64 definition in both forms.
 #include <cmath>
 #include <cstring>
 
+#include "lj_fixed.cuh"
 #include "lj_forms.cuh"
 
 namespace lj {
@@ -92,9 +94,10 @@ __device__ __forceinline__ void block_pair_sum(double a, double b, double *__res
 
 template <bool HALF>
 __global__ void __launch_bounds__(kVjpThreads)
-vjp_fp64_kernel(const double *__restrict__ q4, const double *__restrict__ R4, int n,
-                const int *__restrict__ row_ptr, const int *__restrict__ col, Fp64Params P,
-                VjpCoef C, double *__restrict__ gq4, double *__restrict__ partial)
+vjp_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
+                const double *__restrict__ R4, int n, const int *__restrict__ row_ptr,
+                const int *__restrict__ col, Fp64Params P, FixParams F, VjpCoef C,
+                double *__restrict__ gq4, double *__restrict__ partial)
 {
     constexpr int TPI = kVjpTpi;
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
@@ -103,54 +106,23 @@ vjp_fp64_kernel(const double *__restrict__ q4, const double *__restrict__ R4, in
     double ge = 0.0, gs = 0.0;
     if (gid < n) {
         const int i = gid;
-        double xi, yi, zi, Rxi, Ryi, Rzi;
-        load_q4_256(q4, i, xi, yi, zi);
+        double Rxi, Ryi, Rzi;
+        long long fxi, fyi, fzi;
+        load_fixed(X, i, fxi, fyi, fzi);
         load_r3(R4, i, Rxi, Ryi, Rzi);
-        // Periodic images of q_i and the high words of q_i +- L/2: each entry
-        // picks the minimum image with integer compares (one FP64
-        // subtraction per axis, no wrap addition).
-        const double ci[3] = {xi, yi, zi};
-        double im[3][2];
-        int th[3][2];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            im[a][0] = ci[a] - P.L[a];
-            im[a][1] = ci[a] + P.L[a];
-            double hl;
-            memcpy(&hl, &P.half_bits[a], sizeof(double));
-            th[a][0] = __double2hiint(ci[a] - hl);
-            th[a][1] = __double2hiint(ci[a] + hl);
-        }
         double ax = 0.0, ay = 0.0, az = 0.0;
         const int kb = row_ptr[i], ke = row_ptr[i + 1];
         for (int base = kb; base < ke; base += TPI) {
             const int k = base + sub;
             const bool valid = k < ke;
             const int j = valid ? col[k] : i;
-            double xj, yj, zj;
-            load_q4_256(q4, j, xj, yj, zj);
-            const double cj[3] = {xj, yj, zj};
-            double dd[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const int hj = __double2hiint(cj[a]);
-                const double img = hj > th[a][1] ? im[a][1] : (hj < th[a][0] ? im[a][0] : ci[a]);
-                dd[a] = cj[a] - img;
-            }
-            const double dx = dd[0], dy = dd[1], dz = dd[2];
-            double s = fma(dz, dz, fma(dy, dy, dx * dx));
-            const long long sb = __double_as_longlong(s);
-            bool in = valid && sb < P.rc2_bits;
-            const bool near = valid && static_cast<unsigned long long>(sb - P.rc2_bits + 64) < 128ull;
-            if (__any_sync(gm, near)) {
-                if (near) {
-                    const double ex = min_image(xj - xi, P.L[0], P.half_bits[0]);
-                    const double ey = min_image(yj - yi, P.L[1], P.half_bits[1]);
-                    const double ez = min_image(zj - zi, P.L[2], P.half_bits[2]);
-                    in = exact_in_cutoff(ex, ey, ez, P.rc2);
-                }
-            }
-            if (!valid) s = 1.0;
+            long long fxj, fyj, fzj;
+            load_fixed(X, j, fxj, fyj, fzj);
+            // the exact fixed-point displacement and r^2 (the FP64 definition
+            // within 64 ulp of r_c^2); s = 1 on an invalid lane
+            double dx, dy, dz, s;
+            const bool in = fixed_entry(q4, fxi, fyi, fzi, fxj, fyj, fzj, valid, i, j, P, F, gm, dx,
+                                        dy, dz, s);
             if (__any_sync(gm, in)) {
                 double Rxj, Ryj, Rzj;
                 load_r3(R4, j, Rxj, Ryj, Rzj);
@@ -339,6 +311,7 @@ extern "C" size_t lj_force_vjp_workspace_bytes(int64_t n, int precision)
     const size_t blocks = size_t(lj::vjp_blocks(n > 0 ? n : 1));
     size_t bytes = 2 * blocks * sizeof(double) + 256;
     if (precision == LJ_MIXED) bytes += size_t(n > 0 ? n : 1) * sizeof(uint4) + 256;
+    if (precision == LJ_FP64) bytes += size_t(n > 0 ? n : 1) * sizeof(longlong4) + 256;
     return bytes;
 }
 
@@ -370,13 +343,17 @@ extern "C" int lj_force_vjp(const double *q4_dev, const double *gradF4_dev, int6
         LJ_TRY_CUDA(cudaMemsetAsync(gradq4_dev, 0, size_t(n) * 4 * sizeof(double), st));
     if (precision == LJ_FP64) {
         const Fp64Params P = make_fp64_params(box, 1.0, r_cut, eps, sigma);
+        const FixParams F = make_fix_params(box);
         const VjpCoef C = make_coef(eps, sigma);
+        longlong4 *X = c.take<longlong4>(size_t(n));
+        fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, ni, F, X);
+        LJ_TRY_LAUNCH("fixed_prepass_kernel");
         if (half)
-            vjp_fp64_kernel<true><<<blocks, kVjpThreads, 0, st>>>(q4_dev, gradF4_dev, ni, row_ptr_dev,
-                                                                   col_dev, P, C, gradq4_dev, partial);
+            vjp_fp64_kernel<true><<<blocks, kVjpThreads, 0, st>>>(q4_dev, X, gradF4_dev, ni, row_ptr_dev,
+                                                                   col_dev, P, F, C, gradq4_dev, partial);
         else
-            vjp_fp64_kernel<false><<<blocks, kVjpThreads, 0, st>>>(q4_dev, gradF4_dev, ni, row_ptr_dev,
-                                                                    col_dev, P, C, gradq4_dev, partial);
+            vjp_fp64_kernel<false><<<blocks, kVjpThreads, 0, st>>>(q4_dev, X, gradF4_dev, ni, row_ptr_dev,
+                                                                    col_dev, P, F, C, gradq4_dev, partial);
         LJ_TRY_LAUNCH("vjp_fp64_kernel");
     } else {
         const MixedParams P = make_mixed_params(box, 1.0, r_cut, eps, sigma);

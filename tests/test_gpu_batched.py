@@ -42,13 +42,13 @@ def test_batched_matches_oracle_per_system(cuda_lib, oracle_lib, systems, precis
 def test_batched_equals_per_system_launches_full_list(cuda_lib, systems):
     """Full lists are deterministic: the persistent launch gives the same bits
     as one lj_force call per system with the same row arithmetic (8 lanes
-    per row, image-selected displacement)."""
+    per row, exact fixed-point displacement)."""
     from paper_1806_05713_gb300.batch import Batch
     b = Batch(systems, 0.01, 0, False, tpi=8, rows_per_item=16)
     p_a = torch.zeros_like(b.p4)
     p_b = torch.zeros_like(b.p4)
     b.force(p_a)
-    b.force_per_system(p_b, tpi=cuda_lib.LJ_SCHED_IMAGES | 8)
+    b.force_per_system(p_b, tpi=cuda_lib.LJ_SCHED_FIXED | 8)
     torch.cuda.synchronize()
     assert torch.equal(p_a, p_b)
 
