@@ -48,7 +48,7 @@ def test_force_energy_one_pass(cuda_lib, oracle_lib, half, shifted):
     p1 = torch.zeros_like(q)
     e = lj.lj_force_energy(q, p1, pl, 0.01, 3.0, s.box, 1.1, 0.97, shifted).item()
     p2 = torch.zeros_like(q)
-    lj.lj_force(q, p2, pl, 0.01, 3.0, s.box, 1.1, 0.97, tpi=lj.LJ_SCHED_IMAGES | 8)
+    lj.lj_force(q, p2, pl, 0.01, 3.0, s.box, 1.1, 0.97, tpi=lj.LJ_SCHED_FIXED | 8)
     torch.cuda.synchronize()
     if half:
         assert float((p1 - p2).abs().max()) <= 1e-13 * float(p2.abs().max())
