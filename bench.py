@@ -468,6 +468,8 @@ def schedule_name(tpi: int) -> str:
         name += ", image-selected displacement"
     if tpi & 2048:
         name += ", exact fixed-point displacement"
+    if tpi & 4096:
+        name += ", exact fixed-point displacement, margin entries compacted away"
     return name
 
 
@@ -687,7 +689,7 @@ def variants(lj, s, q, pl_half, box, dev, stream, flush):
             m_half = pl.nnz if half else pl.nnz // 2
             res[f"list_build_ms/{order}/{kind}"] = t_list
             ref = None
-            for prec, tpis in ((lj.LJ_FP64, (1032, 1028, 1544, 1160, 2056, 2052, 2568)),
+            for prec, tpis in ((lj.LJ_FP64, (1032, 1028, 1544, 1160, 2056, 2052, 2568, 4104, 4100, 4112)),
                                (lj.LJ_MIXED, (4, 8, 16)),
                                (lj.LJ_DFLOAT, (136, 132, 144, 648, 8))):
                 for tpi in tpis:

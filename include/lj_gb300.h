@@ -113,6 +113,12 @@ extern "C" {
  * once to double; the rest of Algorithm 1 in IEEE double as in the other
  * FP64 schedules.  Six fewer FP64 instructions per entry. */
 #define LJ_SCHED_FIXED 2048
+/* LJ_SCHED_COMPACT | 4, 8, 16 (FP64 only; implies LJ_SCHED_FIXED, optionally
+ * | LJ_SCHED_SORTED): each row is first screened on the integer pipe with
+ * the exact fixed-point r^2 and its interacting entries compacted in
+ * shared memory; the FP64 arithmetic then runs over those entries only
+ * (no FP64 instruction for margin entries or ragged row tails). */
+#define LJ_SCHED_COMPACT 4096
 
 const char *lj_status_string(int status);
 /* Text of the last CUDA error seen by this library in this thread. */
@@ -226,7 +232,8 @@ size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
  *                   FP64 only.  LJ_SCHED_SORTED may be or-ed into the plain
  *                   and SWP2 schedules, LJ_SCHED_IMAGES into the FP64
  *                   4, 8, 16 and SWP2 schedules; LJ_SCHED_FIXED | 4, 8, 16
- *                   (FP64, optionally | LJ_SCHED_SORTED).
+ *                   and LJ_SCHED_COMPACT | 4, 8, 16 (FP64, optionally |
+ *                   LJ_SCHED_SORTED).
  *  workspace_dev    scratch of lj_force_workspace_bytes() (NULL if 0).
  * Half lists add p_j with FP64 atomics, so their rounding order (not their
  * value beyond the last bits) varies between calls; full lists are

@@ -73,6 +73,26 @@ force_fixed_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ 
     fp64_fixed_row<TPI, HALF>(q4, X, p4, row_ptr, col, i, P, F, group_mask<TPI>());
 }
 
+// FP64 form, exact fixed-point displacement, margin entries compacted away
+// (LJ_SCHED_COMPACT): one shared-memory buffer of kCompactChunk column
+// indices per group.
+constexpr int kCompactChunk = 128;
+
+template <int TPI, bool HALF>
+__global__ void __launch_bounds__(256)
+force_compact_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
+                     double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
+                     const int *__restrict__ col, Fp64Params P, FixParams F,
+                     const int *__restrict__ order)
+{
+    __shared__ int buf[256 / TPI][kCompactChunk];
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
+    if (gid >= n) return;
+    const int i = order ? order[gid] : gid;
+    fp64_compact_row<TPI, HALF, kCompactChunk>(q4, X, p4, row_ptr, col, i, P, F, group_mask<TPI>(),
+                                               buf[threadIdx.x / TPI]);
+}
+
 template <int TPI, bool HALF>
 __global__ void __launch_bounds__(256)
 force_mixed_kernel(const double *__restrict__ q4, const uint4 *__restrict__ rel,
@@ -248,6 +268,21 @@ int launch_fixed(const double *q4, const longlong4 *X, double *p4, int n, const 
 }
 
 template <int TPI>
+int launch_compact(const double *q4, const longlong4 *X, double *p4, int n, const int *rp,
+                   const int *col, int half, const Fp64Params &P, const FixParams &F,
+                   const int *order, cudaStream_t st)
+{
+    const int64_t threads = int64_t(n) * TPI;
+    const unsigned grid = unsigned((threads + 255) / 256);
+    if (half)
+        force_compact_kernel<TPI, true><<<grid, 256, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
+    else
+        force_compact_kernel<TPI, false><<<grid, 256, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
+    LJ_TRY_LAUNCH("force_compact_kernel");
+    return LJ_OK;
+}
+
+template <int TPI>
 int launch_mixed(const double *q4, const uint4 *rel, double *p4, int n, const int *rp,
                  const int *col, int half, const MixedParams &P, const int *order, cudaStream_t st)
 {
@@ -329,8 +364,9 @@ bool valid_schedule(int s, int precision)
     if (s & LJ_SCHED_REFILL)
         return precision == LJ_FP64 && (s & ~(LJ_SCHED_REFILL | LJ_SCHED_SWP2 | 63)) == 0 &&
                (t == 0 || t == 1 || t == 4 || t == 8);
-    if (s & LJ_SCHED_FIXED)
-        return precision == LJ_FP64 && (s & ~(LJ_SCHED_FIXED | LJ_SCHED_SORTED | 63)) == 0 &&
+    if (s & (LJ_SCHED_FIXED | LJ_SCHED_COMPACT))
+        return precision == LJ_FP64 &&
+               (s & ~(LJ_SCHED_FIXED | LJ_SCHED_COMPACT | LJ_SCHED_SORTED | 63)) == 0 &&
                (t == 4 || t == 8 || t == 16);
     if (s & ~(LJ_SCHED_SORTED | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES | 63)) return false;
     if (precision == LJ_DFLOAT) return (s & LJ_SCHED_IMAGES) == 0 && (t == 4 || t == 8 || t == 16);
@@ -387,12 +423,20 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
     if (precision == LJ_DFLOAT)
         return force_dfloat(q4, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma, tpi, order,
                             W.rec, st);
-    if (precision == LJ_FP64 && (tpi & LJ_SCHED_FIXED)) {
+    if (precision == LJ_FP64 && (tpi & (LJ_SCHED_FIXED | LJ_SCHED_COMPACT))) {
         const Fp64Params P = make_fp64_params(box, dt, rc, eps, sigma);
         const FixParams F = make_fix_params(box);
         longlong4 *X = static_cast<longlong4 *>(W.rec);
         fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4, ni, F, X);
         LJ_TRY_LAUNCH("fixed_prepass_kernel");
+        if (tpi & LJ_SCHED_COMPACT) {
+            switch (tpi & 63) {
+                case 4: return launch_compact<4>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
+                case 8: return launch_compact<8>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
+                case 16: return launch_compact<16>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
+                default: return LJ_ERR_ARG;
+            }
+        }
         switch (tpi & 63) {
             case 4: return launch_fixed<4>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
             case 8: return launch_fixed<8>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);

@@ -34,6 +34,7 @@ LJ_SCHED_QUEUE = 256
 LJ_SCHED_SORTED = 512
 LJ_SCHED_IMAGES = 1024
 LJ_SCHED_FIXED = 2048
+LJ_SCHED_COMPACT = 4096
 LJ_STATIC_MAX_ATOMS = 131072
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liblj_gb300.so")
@@ -359,9 +360,10 @@ def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float
     (best_tpi, best_ms, {tpi: ms})."""
     lib = load()
     if candidates is None:
-        S, W, I, F = LJ_SCHED_SORTED, LJ_SCHED_SWP2, LJ_SCHED_IMAGES, LJ_SCHED_FIXED
+        S, W, I, F, C = (LJ_SCHED_SORTED, LJ_SCHED_SWP2, LJ_SCHED_IMAGES, LJ_SCHED_FIXED,
+                         LJ_SCHED_COMPACT)
         candidates = ([8, W | 8, I | 4, I | 8, I | 16, I | W | 4, I | W | 8, S | I | 4,
-                       S | I | 8, S | I | 16, F | 4, F | 8, F | 16, S | F | 8,
+                       S | I | 8, S | I | 16, F | 4, F | 8, F | 16, S | F | 8, C | 4, C | 8, C | 16,
                        LJ_SCHED_REFILL | W | 8, LJ_SCHED_QUEUE | 8]
                       if precision == LJ_FP64 else
                       [4, 8, 16, S | 4, S | 8, S | 16] if precision == LJ_DFLOAT else

@@ -14,9 +14,11 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-12
 MIXED_TOL = 1e-5
 SCHEDULES = [1, 2, 4, 8, 16, 32, 132, 136, 144, 64, 68, 72, 196, 200, 257, 258, 260, 264, 520,
-             644, 648, 656, 1028, 1032, 1040, 1156, 1160, 1168, 1672, 1544, 2052, 2056, 2064, 2568]
+             644, 648, 656, 1028, 1032, 1040, 1156, 1160, 1168, 1672, 1544, 2052, 2056, 2064, 2568,
+             4100, 4104, 4112, 4616]
 # 128|t software-pipelined, 64|t group-refill, 256|t lane-queue, 512|... length-sorted rows,
-# 1024|... image-selected displacement, 2048|... exact fixed-point displacement
+# 1024|... image-selected displacement, 2048|... exact fixed-point displacement,
+# 4096|... fixed point with the margin entries compacted away
 
 
 def _run(lj, s, half, precision, tpi, dt=0.01, eps=1.0, sigma=1.0, p0=None, rc=None, pl=None):
@@ -115,7 +117,7 @@ def test_small_box_mixed_image_choice(cuda_lib, oracle_lib):
         assert _relerr(got, want) <= MIXED_TOL
 
 
-@pytest.mark.parametrize("tpi", [1032, 2056])
+@pytest.mark.parametrize("tpi", [1032, 2056, 4104])
 def test_fp64_pairs_on_the_cutoff(cuda_lib, oracle_lib, tpi):
     """Pairs at r_c and one ulp either side, along an axis and a diagonal:
     the FP64 schedules interact exactly the oracle's pairs."""
@@ -151,9 +153,22 @@ def test_fp64_fixed_point_box_sizes(cuda_lib, oracle_lib, scale):
     kw = dict(dt=0.004, eps=0.8, sigma=1.05 * scale, rc=3.0 * scale)
     s.rc, s.margin = 3.0 * scale, 0.3 * scale
     for half in (True, False):
-        got, _ = _run(cuda_lib, s, half, 0, 2056, p0=p0, **kw)
         want = _oracle(oracle_lib, s, half, p0=p0, **kw)
-        assert _relerr(got - p0[:, :3], want - p0[:, :3]) <= FP64_TOL
+        for tpi in (2056, 4104):
+            got, _ = _run(cuda_lib, s, half, 0, tpi, p0=p0, **kw)
+            assert _relerr(got - p0[:, :3], want - p0[:, :3]) <= FP64_TOL
+
+
+@pytest.mark.parametrize("tpi", [4100, 4104, 4112])
+def test_fp64_compact_long_rows(cuda_lib, oracle_lib, tpi):
+    """r_c = 4, full list: ~330 entries a row, so a row spans three chunks of
+    the compacted schedule's shared-memory buffer."""
+    s = inputs.fcc_system(10, 1.0, 0.05, seed=8)
+    s.rc, s.margin = 4.0, 0.3
+    for half in (True, False):
+        got, _ = _run(cuda_lib, s, half, 0, tpi, rc=4.0)
+        want = _oracle(oracle_lib, s, half, rc=4.0)
+        assert _relerr(got, want) <= FP64_TOL
 
 
 def test_newton_third_law_half_list(cuda_lib, small):
@@ -179,7 +194,8 @@ def test_fp64_paper_size(cuda_lib, oracle_lib, order, half):
     s = inputs.workload_paper(order=order)
     want = _oracle(oracle_lib, s, half)
     pl = None
-    for tpi in (64, 8, 32, 136, 72, 200, 258, 260, 264, 648, 1160, 1672, 2052, 2056, 2568):
+    for tpi in (64, 8, 32, 136, 72, 200, 258, 260, 264, 648, 1160, 1672, 2052, 2056, 2568, 4104,
+                4100):
         got, pl = _run(cuda_lib, s, half, 0, tpi, pl=pl)
         assert _relerr(got, want) <= FP64_TOL, tpi
 
