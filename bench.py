@@ -54,7 +54,13 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
 # schedule, from one ncu capture of the kernel as it stands on this workload
 # (profiles/force_fp64_images_tpi8_half_N119164.md); a schedule without an
 # entry reports null.
-TRAFFIC_PER_LAUNCH = {1032: 41903872.0 + 1280.0}
+# DRAM bytes (read + write) of one launch of the FP64 force kernel per
+# schedule, from ncu (cold cache), with the profile that records them.
+TRAFFIC_PER_LAUNCH = {
+    1032: (41903872.0 + 1280.0, "profiles/force_fp64_images_tpi8_half_N119164.md"),
+    2056: (41909760.0, "profiles/force_fp64_fixed_tpi8_half_N119164.md"),
+    4104: (41915904.0, "profiles/force_fp64_compact_tpi8_half_N119164.md"),
+}
 
 
 def parse():
@@ -400,8 +406,9 @@ def main():
     alg_bytes = 4.0 * nnz + 4.0 * (s.n + 1) + 32.0 * s.n + 64.0 * s.n
     roof = {"bound": "alu", "achieved": flops / t_force / 1e12, "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": flops / t_force / 1e12 / FP64_PEAK_TFLOPS,
-            "traffic": TRAFFIC_PER_LAUNCH.get(best_tpi),
-            "traffic_source": "profiles/force_fp64_images_tpi8_half_N119164.md (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold cache)",
+            "traffic": TRAFFIC_PER_LAUNCH.get(best_tpi, (None, None))[0],
+            "traffic_source": (TRAFFIC_PER_LAUNCH.get(best_tpi, (None, "not profiled"))[1] +
+                               " (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold cache)"),
             "kernel": f"FP64 force kernel, {schedule_name(best_tpi)}, half list",
             "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
             "flops_per_launch": flops, "launch_ms": t_force * 1e3}
