@@ -111,7 +111,10 @@ extern "C" {
  * displacement and r^2 computed exactly in 64/128-bit integer fixed point
  * (positions x 2^k, the minimum image by one integer compare) and rounded
  * once to double; the rest of Algorithm 1 in IEEE double as in the other
- * FP64 schedules.  Six fewer FP64 instructions per entry. */
+ * FP64 schedules.  Six fewer FP64 instructions per entry.  Offered for boxes
+ * up to 1024 r_c wide (the fixed point then resolves 2^-50 r_c); wider
+ * boxes return LJ_ERR_ARG, and the default schedule, lj_force_energy,
+ * lj_force_vjp and lj_force_batched use image selection there. */
 #define LJ_SCHED_FIXED 2048
 /* LJ_SCHED_COMPACT | 4, 8, 16 (FP64 only; implies LJ_SCHED_FIXED, optionally
  * | LJ_SCHED_SORTED): each row is first screened on the integer pipe with

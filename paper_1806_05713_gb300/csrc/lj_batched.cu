@@ -28,7 +28,7 @@ constexpr int kBatchThreads = 256;
 
 struct SysDev {
     long long atom_off, row_off, entry_off;
-    int n, half, cubic;
+    int n, half, cubic, fixed;
     Fp64Params fp;
     FixParams fx;
     MixedParams mp;
@@ -170,10 +170,17 @@ batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ it
                     const longlong4 *sX = X + S.atom_off;
                     const Fp64Params &P = S.fp;
                     const FixParams &F = S.fx;
-                    if (half)
-                        fp64_fixed_row<TPI, true>(sq, sX, sp, srp, scol, r, P, F, gm);
-                    else
-                        fp64_fixed_row<TPI, false>(sq, sX, sp, srp, scol, r, P, F, gm);
+                    if (S.fixed) {
+                        if (half)
+                            fp64_fixed_row<TPI, true>(sq, sX, sp, srp, scol, r, P, F, gm);
+                        else
+                            fp64_fixed_row<TPI, false>(sq, sX, sp, srp, scol, r, P, F, gm);
+                    } else {  // a box wider than 1024 r_c
+                        if (half)
+                            fp64_row<TPI, true, 1, true>(sq, sp, srp, scol, r, P, gm);
+                        else
+                            fp64_row<TPI, false, 1, true>(sq, sp, srp, scol, r, P, gm);
+                    }
                 }
             }
         }
@@ -280,6 +287,7 @@ extern "C" int lj_batch_init(lj_batch *batch, const lj_system *systems, int nsys
         d.half = y.half ? 1 : 0;
         d.fp = make_fp64_params(y.box, dt, y.r_cut, y.eps, y.sigma);
         d.fx = make_fix_params(y.box);
+        d.fixed = fixed_point_ok(y.box, y.r_cut) ? 1 : 0;
         d.mp = make_mixed_params(y.box, dt, y.r_cut, y.eps, y.sigma);
         d.dp = make_dfloat_params(y.box, dt, y.r_cut, y.eps, y.sigma);
         d.cubic = y.box[1] == y.box[0] && y.box[2] == y.box[0];

@@ -34,6 +34,17 @@ struct FixParams {
     long long M[3], Mh[3];   // L_a 2^k and floor(M / 2)
 };
 
+// The fixed point resolves 2^-k, with 2^k L_max < 2^61; positions below
+// 2^(52-k) are rounded to it.  For L_max <= 1024 r_c that is below 2^-50 r_c
+// (an FP64 rounding of d), so the fixed-point schedules are offered only
+// there; larger boxes take the image-selected FP64 rows.
+inline bool fixed_point_ok(const double box[3], double rc)
+{
+    double Lmax = 0.0;
+    for (int a = 0; a < 3; ++a) Lmax = box[a] > Lmax ? box[a] : Lmax;
+    return Lmax <= 1024.0 * rc;
+}
+
 FixParams make_fix_params(const double box[3])
 {
     FixParams F{};
@@ -248,6 +259,86 @@ __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
                     ax = fma(-fn, dx, ax);
                     ay = fma(-fn, dy, ay);
                     az = fma(-fn, dz, az);
+                }
+            }
+        }
+    }
+    double *pi = p4 + 4 * static_cast<int64_t>(i);
+    if (HALF) {
+        atomicAdd(pi + 0, ax);
+        atomicAdd(pi + 1, ay);
+        atomicAdd(pi + 2, az);
+    } else {
+        if (TPI > 1) {
+            ax = group_sum<TPI>(ax);
+            ay = group_sum<TPI>(ay);
+            az = group_sum<TPI>(az);
+        }
+        if (sub == 0) {
+            atomicAdd(pi + 0, ax);
+            atomicAdd(pi + 1, ay);
+            atomicAdd(pi + 2, az);
+        }
+    }
+}
+
+// Two entries per lane and iteration (k and k + TPI; LJ_SCHED_FIXED |
+// LJ_SCHED_SWP2): the two FP64 dependency chains of Algorithm 1 in flight
+// together, the paper's software pipelining.
+template <int TPI, bool HALF>
+__device__ __forceinline__ void fp64_fixed_row2(const double *__restrict__ q4,
+                                                const longlong4 *__restrict__ X,
+                                                double *__restrict__ p4,
+                                                const int *__restrict__ row_ptr,
+                                                const int *__restrict__ col, int i,
+                                                const Fp64Params &P, const FixParams &F, unsigned gm)
+{
+    const int sub = threadIdx.x & (TPI - 1);
+    long long xi, yi, zi;
+    load_fixed(X, i, xi, yi, zi);
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    const int kb = row_ptr[i], ke = row_ptr[i + 1];
+    for (int k0 = kb; k0 < ke; k0 += 2 * TPI) {
+        const int k[2] = {k0 + sub, k0 + sub + TPI};
+        bool in[2];
+        int j[2];
+        double dx[2], dy[2], dz[2], r2[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const bool valid = k[u] < ke;
+            j[u] = valid ? col[k[u]] : i;
+            long long xj, yj, zj;
+            load_fixed(X, j[u], xj, yj, zj);
+            in[u] = fixed_entry(q4, xi, yi, zi, xj, yj, zj, valid, i, j[u], P, F, gm, dx[u], dy[u],
+                                dz[u], r2[u]);
+        }
+        if (__any_sync(gm, in[0] || in[1])) {
+            double fn[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const double w = rcp_fp64(in[u] ? r2[u] : 1.0, gm);
+                const double w2 = w * w;
+                const double w4 = w2 * w2;
+                const double w3 = w2 * w;
+                fn[u] = w4 * fma(P.B, w3, -P.A);  // -df: p_i -= fn d, p_j += fn d
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (in[u]) {
+                    if (HALF) {
+                        const double fx = fn[u] * dx[u], fy = fn[u] * dy[u], fz = fn[u] * dz[u];
+                        double *pj = p4 + 4 * static_cast<int64_t>(j[u]);
+                        atomicAdd(pj + 0, fx);
+                        atomicAdd(pj + 1, fy);
+                        atomicAdd(pj + 2, fz);
+                        ax -= fx;
+                        ay -= fy;
+                        az -= fz;
+                    } else {
+                        ax = fma(-fn[u], dx[u], ax);
+                        ay = fma(-fn[u], dy[u], ay);
+                        az = fma(-fn[u], dz[u], az);
+                    }
                 }
             }
         }

@@ -59,8 +59,9 @@ force_fp64_kernel(const double *__restrict__ q4, double *__restrict__ p4, int n,
     fp64_row<TPI, HALF, U, IMG>(q4, p4, row_ptr, col, i, P, group_mask<TPI>());
 }
 
-// FP64 form with the exact fixed-point displacement (LJ_SCHED_FIXED).
-template <int TPI, bool HALF>
+// FP64 form with the exact fixed-point displacement (LJ_SCHED_FIXED; U = 2:
+// | LJ_SCHED_SWP2).
+template <int TPI, bool HALF, int U>
 __global__ void __launch_bounds__(256)
 force_fixed_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
                    double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
@@ -70,7 +71,10 @@ force_fixed_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ 
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
     if (gid >= n) return;
     const int i = order ? order[gid] : gid;
-    fp64_fixed_row<TPI, HALF>(q4, X, p4, row_ptr, col, i, P, F, group_mask<TPI>());
+    if (U == 2)
+        fp64_fixed_row2<TPI, HALF>(q4, X, p4, row_ptr, col, i, P, F, group_mask<TPI>());
+    else
+        fp64_fixed_row<TPI, HALF>(q4, X, p4, row_ptr, col, i, P, F, group_mask<TPI>());
 }
 
 // FP64 form, exact fixed-point displacement, margin entries compacted away
@@ -122,12 +126,21 @@ force_energy_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restr
     double ev = 0.0;
     int cnt = 0;
     if (gid < n) {
-        if (half)
-            fp64_fixed_row<TPI, true, true>(q4, X, p4, row_ptr, col, gid, P, F, group_mask<TPI>(),
-                                            &ev, &cnt);
-        else
-            fp64_fixed_row<TPI, false, true>(q4, X, p4, row_ptr, col, gid, P, F, group_mask<TPI>(),
-                                             &ev, &cnt);
+        if (X) {
+            if (half)
+                fp64_fixed_row<TPI, true, true>(q4, X, p4, row_ptr, col, gid, P, F, group_mask<TPI>(),
+                                                &ev, &cnt);
+            else
+                fp64_fixed_row<TPI, false, true>(q4, X, p4, row_ptr, col, gid, P, F, group_mask<TPI>(),
+                                                 &ev, &cnt);
+        } else {  // a box wider than 1024 r_c: image-selected rows
+            if (half)
+                fp64_row<TPI, true, 1, true, 0, true>(q4, p4, row_ptr, col, gid, P, group_mask<TPI>(),
+                                                      Layout{4, 1}, &ev, &cnt);
+            else
+                fp64_row<TPI, false, 1, true, 0, true>(q4, p4, row_ptr, col, gid, P, group_mask<TPI>(),
+                                                       Layout{4, 1}, &ev, &cnt);
+        }
     }
     long long c = cnt;
 #pragma unroll
@@ -252,7 +265,7 @@ int launch_fp64(const double *q4, double *p4, int n, const int *rp, const int *c
     return LJ_OK;
 }
 
-template <int TPI>
+template <int TPI, int U = 1>
 int launch_fixed(const double *q4, const longlong4 *X, double *p4, int n, const int *rp,
                  const int *col, int half, const Fp64Params &P, const FixParams &F, const int *order,
                  cudaStream_t st)
@@ -260,9 +273,9 @@ int launch_fixed(const double *q4, const longlong4 *X, double *p4, int n, const 
     const int64_t threads = int64_t(n) * TPI;
     const unsigned grid = unsigned((threads + 255) / 256);
     if (half)
-        force_fixed_kernel<TPI, true><<<grid, 256, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
+        force_fixed_kernel<TPI, true, U><<<grid, 256, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
     else
-        force_fixed_kernel<TPI, false><<<grid, 256, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
+        force_fixed_kernel<TPI, false, U><<<grid, 256, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
     LJ_TRY_LAUNCH("force_fixed_kernel");
     return LJ_OK;
 }
@@ -364,9 +377,13 @@ bool valid_schedule(int s, int precision)
     if (s & LJ_SCHED_REFILL)
         return precision == LJ_FP64 && (s & ~(LJ_SCHED_REFILL | LJ_SCHED_SWP2 | 63)) == 0 &&
                (t == 0 || t == 1 || t == 4 || t == 8);
-    if (s & (LJ_SCHED_FIXED | LJ_SCHED_COMPACT))
+    if (s & LJ_SCHED_COMPACT)
         return precision == LJ_FP64 &&
                (s & ~(LJ_SCHED_FIXED | LJ_SCHED_COMPACT | LJ_SCHED_SORTED | 63)) == 0 &&
+               (t == 4 || t == 8 || t == 16);
+    if (s & LJ_SCHED_FIXED)
+        return precision == LJ_FP64 &&
+               (s & ~(LJ_SCHED_FIXED | LJ_SCHED_SWP2 | LJ_SCHED_SORTED | 63)) == 0 &&
                (t == 4 || t == 8 || t == 16);
     if (s & ~(LJ_SCHED_SORTED | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES | 63)) return false;
     if (precision == LJ_DFLOAT) return (s & LJ_SCHED_IMAGES) == 0 && (t == 4 || t == 8 || t == 16);
@@ -399,7 +416,9 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
     if (n == 0 || nnz == 0) return LJ_OK;
     const int ni = static_cast<int>(n);
     if (tpi == LJ_TPI_AUTO)
-        tpi = precision == LJ_FP64 ? (LJ_SCHED_FIXED | 8) : precision == LJ_DFLOAT ? (LJ_SCHED_SWP2 | 8) : 8;
+        tpi = precision == LJ_FP64 ? (fixed_point_ok(box, rc) ? (LJ_SCHED_FIXED | 8) : (LJ_SCHED_IMAGES | 8))
+              : precision == LJ_DFLOAT ? (LJ_SCHED_SWP2 | 8) : 8;
+    if ((tpi & (LJ_SCHED_FIXED | LJ_SCHED_COMPACT)) && !fixed_point_ok(box, rc)) return LJ_ERR_ARG;
     if (!valid_schedule(tpi, precision)) return LJ_ERR_ARG;
     if (!ws || ws_bytes < force_workspace_bytes_impl(n, precision)) return LJ_ERR_CAPACITY;
     const ForceWs W = carve_force_ws(ws, n, precision);
@@ -437,10 +456,13 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
                 default: return LJ_ERR_ARG;
             }
         }
-        switch (tpi & 63) {
+        switch (tpi & (63 | LJ_SCHED_SWP2)) {
             case 4: return launch_fixed<4>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
             case 8: return launch_fixed<8>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
             case 16: return launch_fixed<16>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
+            case LJ_SCHED_SWP2 | 4: return launch_fixed<4, 2>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
+            case LJ_SCHED_SWP2 | 8: return launch_fixed<8, 2>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
+            case LJ_SCHED_SWP2 | 16: return launch_fixed<16, 2>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
             default: return LJ_ERR_ARG;
         }
     }
@@ -514,8 +536,12 @@ extern "C" int lj_force_energy(const double *q4_dev, double *p4_dev, int64_t n,
     Carver c(workspace_dev);
     double *partial = c.take<double>(2 * size_t(blocks));
     longlong4 *X = c.take<longlong4>(size_t(n));
-    fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, static_cast<int>(n), F, X);
-    LJ_TRY_LAUNCH("fixed_prepass_kernel");
+    if (fixed_point_ok(box, r_cut)) {
+        fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, static_cast<int>(n), F, X);
+        LJ_TRY_LAUNCH("fixed_prepass_kernel");
+    } else {
+        X = nullptr;
+    }
     force_energy_fp64_kernel<<<blocks, 256, 0, st>>>(q4_dev, X, p4_dev, static_cast<int>(n), row_ptr_dev,
                                                      col_dev, P, F, half, partial);
     LJ_TRY_LAUNCH("force_energy_fp64_kernel");

@@ -92,7 +92,9 @@ __device__ __forceinline__ void block_pair_sum(double a, double b, double *__res
     }
 }
 
-template <bool HALF>
+// FIX: the exact fixed-point displacement (boxes up to 1024 r_c wide);
+// otherwise image selection by integer compares of the FP64 coordinates.
+template <bool HALF, bool FIX>
 __global__ void __launch_bounds__(kVjpThreads)
 vjp_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
                 const double *__restrict__ R4, int n, const int *__restrict__ row_ptr,
@@ -107,8 +109,23 @@ vjp_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
     if (gid < n) {
         const int i = gid;
         double Rxi, Ryi, Rzi;
-        long long fxi, fyi, fzi;
-        load_fixed(X, i, fxi, fyi, fzi);
+        long long fxi = 0, fyi = 0, fzi = 0;
+        double ci[3], im[3][2];
+        int th[3][2];
+        if (FIX) {
+            load_fixed(X, i, fxi, fyi, fzi);
+        } else {
+            load_q4_256(q4, i, ci[0], ci[1], ci[2]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                im[a][0] = ci[a] - P.L[a];
+                im[a][1] = ci[a] + P.L[a];
+                double hl;
+                memcpy(&hl, &P.half_bits[a], sizeof(double));
+                th[a][0] = __double2hiint(ci[a] - hl);
+                th[a][1] = __double2hiint(ci[a] + hl);
+            }
+        }
         load_r3(R4, i, Rxi, Ryi, Rzi);
         double ax = 0.0, ay = 0.0, az = 0.0;
         const int kb = row_ptr[i], ke = row_ptr[i + 1];
@@ -116,13 +133,41 @@ vjp_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
             const int k = base + sub;
             const bool valid = k < ke;
             const int j = valid ? col[k] : i;
-            long long fxj, fyj, fzj;
-            load_fixed(X, j, fxj, fyj, fzj);
-            // the exact fixed-point displacement and r^2 (the FP64 definition
-            // within 64 ulp of r_c^2); s = 1 on an invalid lane
             double dx, dy, dz, s;
-            const bool in = fixed_entry(q4, fxi, fyi, fzi, fxj, fyj, fzj, valid, i, j, P, F, gm, dx,
-                                        dy, dz, s);
+            bool in;
+            if (FIX) {
+                // the exact fixed-point displacement and r^2 (the FP64
+                // definition within 64 ulp of r_c^2); s = 1 on an invalid lane
+                long long fxj, fyj, fzj;
+                load_fixed(X, j, fxj, fyj, fzj);
+                in = fixed_entry(q4, fxi, fyi, fzi, fxj, fyj, fzj, valid, i, j, P, F, gm, dx, dy, dz, s);
+            } else {
+                double cj[3];
+                load_q4_256(q4, j, cj[0], cj[1], cj[2]);
+                double dd[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int hj = __double2hiint(cj[a]);
+                    const double img = hj > th[a][1] ? im[a][1] : (hj < th[a][0] ? im[a][0] : ci[a]);
+                    dd[a] = cj[a] - img;
+                }
+                dx = dd[0];
+                dy = dd[1];
+                dz = dd[2];
+                s = fma(dz, dz, fma(dy, dy, dx * dx));
+                const long long sb = __double_as_longlong(s);
+                in = valid && sb < P.rc2_bits;
+                const bool near = valid && static_cast<unsigned long long>(sb - P.rc2_bits + 64) < 128ull;
+                if (__any_sync(gm, near)) {
+                    if (near) {
+                        const double ex = min_image(cj[0] - ci[0], P.L[0], P.half_bits[0]);
+                        const double ey = min_image(cj[1] - ci[1], P.L[1], P.half_bits[1]);
+                        const double ez = min_image(cj[2] - ci[2], P.L[2], P.half_bits[2]);
+                        in = exact_in_cutoff(ex, ey, ez, P.rc2);
+                    }
+                }
+                if (!valid) s = 1.0;
+            }
             if (__any_sync(gm, in)) {
                 double Rxj, Ryj, Rzj;
                 load_r3(R4, j, Rxj, Ryj, Rzj);
@@ -346,14 +391,23 @@ extern "C" int lj_force_vjp(const double *q4_dev, const double *gradF4_dev, int6
         const FixParams F = make_fix_params(box);
         const VjpCoef C = make_coef(eps, sigma);
         longlong4 *X = c.take<longlong4>(size_t(n));
-        fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, ni, F, X);
-        LJ_TRY_LAUNCH("fixed_prepass_kernel");
-        if (half)
-            vjp_fp64_kernel<true><<<blocks, kVjpThreads, 0, st>>>(q4_dev, X, gradF4_dev, ni, row_ptr_dev,
-                                                                   col_dev, P, F, C, gradq4_dev, partial);
-        else
-            vjp_fp64_kernel<false><<<blocks, kVjpThreads, 0, st>>>(q4_dev, X, gradF4_dev, ni, row_ptr_dev,
-                                                                    col_dev, P, F, C, gradq4_dev, partial);
+        if (fixed_point_ok(box, r_cut)) {
+            fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, ni, F, X);
+            LJ_TRY_LAUNCH("fixed_prepass_kernel");
+            if (half)
+                vjp_fp64_kernel<true, true><<<blocks, kVjpThreads, 0, st>>>(
+                    q4_dev, X, gradF4_dev, ni, row_ptr_dev, col_dev, P, F, C, gradq4_dev, partial);
+            else
+                vjp_fp64_kernel<false, true><<<blocks, kVjpThreads, 0, st>>>(
+                    q4_dev, X, gradF4_dev, ni, row_ptr_dev, col_dev, P, F, C, gradq4_dev, partial);
+        } else {
+            if (half)
+                vjp_fp64_kernel<true, false><<<blocks, kVjpThreads, 0, st>>>(
+                    q4_dev, X, gradF4_dev, ni, row_ptr_dev, col_dev, P, F, C, gradq4_dev, partial);
+            else
+                vjp_fp64_kernel<false, false><<<blocks, kVjpThreads, 0, st>>>(
+                    q4_dev, X, gradF4_dev, ni, row_ptr_dev, col_dev, P, F, C, gradq4_dev, partial);
+        }
         LJ_TRY_LAUNCH("vjp_fp64_kernel");
     } else {
         const MixedParams P = make_mixed_params(box, 1.0, r_cut, eps, sigma);

@@ -103,6 +103,11 @@ def test_host_argument_checks_without_gpu():
     assert force(prec=2, tpi=lj.LJ_SCHED_IMAGES | 8) == lj.LJ_ERR_ARG
     assert force(prec=2, tpi=8) == lj.LJ_ERR_CAPACITY
     assert force(prec=2, tpi=8, dt=1e-250, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG
+    # the fixed-point FP64 schedules need a box at most 1024 r_c wide
+    wide = lj._box3([4000.0, 4000.0, 4000.0])
+    assert force(tpi=lj.LJ_SCHED_FIXED | 8, box=wide, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG
+    assert force(tpi=lj.LJ_SCHED_COMPACT | 8, box=wide, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG
+    assert force(tpi=lj.LJ_SCHED_FIXED | 2, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG
     # empty work is a no-op that succeeds
     assert force(n=0, nnz=0) == lj.LJ_OK
 

@@ -15,10 +15,11 @@ FP64_TOL = 1e-12
 MIXED_TOL = 1e-5
 SCHEDULES = [1, 2, 4, 8, 16, 32, 132, 136, 144, 64, 68, 72, 196, 200, 257, 258, 260, 264, 520,
              644, 648, 656, 1028, 1032, 1040, 1156, 1160, 1168, 1672, 1544, 2052, 2056, 2064, 2568,
-             4100, 4104, 4112, 4616]
+             4100, 4104, 4112, 4616, 2180, 2184, 2192]
 # 128|t software-pipelined, 64|t group-refill, 256|t lane-queue, 512|... length-sorted rows,
 # 1024|... image-selected displacement, 2048|... exact fixed-point displacement,
-# 4096|... fixed point with the margin entries compacted away
+# 4096|... fixed point with the margin entries compacted away; 2048|128|t fixed point,
+# two entries per lane
 
 
 def _run(lj, s, half, precision, tpi, dt=0.01, eps=1.0, sigma=1.0, p0=None, rc=None, pl=None):
@@ -171,6 +172,43 @@ def test_fp64_compact_long_rows(cuda_lib, oracle_lib, tpi):
         assert _relerr(got, want) <= FP64_TOL
 
 
+def test_fp64_box_wider_than_1024_cutoffs(cuda_lib, oracle_lib):
+    """L = 4000 > 1024 r_c: the default FP64 schedule, the force+energy pass,
+    the adjoint and the batched launch take image selection (the fixed point
+    would resolve only 2^-41), and agree with the oracle; an explicit
+    fixed-point schedule is refused."""
+    from paper_1806_05713_gb300.batch import Batch
+    lj = cuda_lib
+    rng = np.random.default_rng(11)
+    centres = np.array([[1.0, 2000.0, 3999.0], [3998.6, 1.2, 0.4], [2000.0, 2000.0, 2000.0]])
+    pts = []
+    for c in centres:
+        for _ in range(6):
+            pts.append(np.mod(c + rng.uniform(-1.2, 1.2, 3), 4000.0))
+    q = np.zeros((len(pts), 4))
+    q[:, :3] = pts
+    s = inputs.LJSystem(q=q, box=np.array([4000.0] * 3), rho=0.0)
+    qd = to_dev(s.q)
+    for half in (True, False):
+        want = _oracle(oracle_lib, s, half)
+        got, pl = _run(lj, s, half, 0, 0)
+        assert _relerr(got, want) <= FP64_TOL
+        p = torch.zeros_like(qd)
+        e = lj.lj_force_energy(qd, p, pl, 0.01, 3.0, s.box).item()
+        rp, col = oracle_lib.pairlist(s.q, s.box, s.rs, half)
+        assert abs(e - oracle_lib.energy(s.q, rp, col, half, 3.0, s.box)) <= 1e-12 * abs(e)
+        assert _relerr(p.cpu().numpy()[:, :3], want) <= FP64_TOL
+        with pytest.raises(lj.LJError):
+            lj.lj_force(qd, torch.zeros_like(qd), pl, 0.01, 3.0, s.box, tpi=lj.LJ_SCHED_FIXED | 8)
+    b = Batch([s, s], 0.01, 0, True, tpi=8, rows_per_item=8, plan_rows_min=8)
+    b.force()
+    torch.cuda.synchronize()
+    want = _oracle(oracle_lib, s, True)
+    out = b.p4.cpu().numpy()
+    for k in range(2):
+        assert _relerr(out[k * s.n:(k + 1) * s.n, :3], want) <= FP64_TOL
+
+
 def test_newton_third_law_half_list(cuda_lib, small):
     got, _ = _run(cuda_lib, small, True, 0, 64)
     assert np.max(np.abs(got.sum(axis=0))) < 1e-12 * np.abs(got).sum()
@@ -195,7 +233,7 @@ def test_fp64_paper_size(cuda_lib, oracle_lib, order, half):
     want = _oracle(oracle_lib, s, half)
     pl = None
     for tpi in (64, 8, 32, 136, 72, 200, 258, 260, 264, 648, 1160, 1672, 2052, 2056, 2568, 4104,
-                4100):
+                4100, 2184, 2180):
         got, pl = _run(cuda_lib, s, half, 0, tpi, pl=pl)
         assert _relerr(got, want) <= FP64_TOL, tpi
 

@@ -40,6 +40,27 @@ def test_vjp_fp64_matches_oracle(cuda_lib, oracle_lib, half):
 
 
 @pytest.mark.parametrize("half", [True, False])
+def test_vjp_fp64_box_wider_than_1024_cutoffs(cuda_lib, oracle_lib, half):
+    """L = 4000: the FP64 adjoint takes image selection there."""
+    lj = cuda_lib
+    rng = np.random.default_rng(12)
+    pts = [np.mod(c + rng.uniform(-1.2, 1.2, 3), 4000.0)
+           for c in ([0.5, 2000.0, 3999.5], [3999.0, 1.0, 0.2]) for _ in range(7)]
+    q4 = np.zeros((len(pts), 4))
+    q4[:, :3] = pts
+    s = inputs.LJSystem(q=q4, box=np.array([4000.0] * 3), rho=0.0)
+    q, pl, rp, col, _ = _setup(lj, oracle_lib, s, half)
+    R = np.random.default_rng(5).normal(size=(s.n, 4))
+    gq, ges = lj.lj_force_vjp(q, to_dev(R), pl, s.rc, s.box, EPS_M, SIG_M, lj.LJ_FP64)
+    torch.cuda.synchronize()
+    want_q, want_e, want_s = oracle_lib.force_vjp(s.q, R, rp, col, half, s.rc, s.box, EPS_M, SIG_M)
+    assert np.max(np.abs(gq.cpu().numpy()[:, :3] - want_q)) <= 1e-11 * np.max(np.abs(want_q))
+    e, sg = ges.cpu().numpy()
+    assert abs(e - want_e) <= 1e-10 * max(1.0, abs(want_e))
+    assert abs(sg - want_s) <= 1e-10 * max(1.0, abs(want_s))
+
+
+@pytest.mark.parametrize("half", [True, False])
 def test_vjp_mixed_within_stated_error(cuda_lib, oracle_lib, half):
     lj = cuda_lib
     s = inputs.fcc_system(8, 1.0, 0.1, seed=4)
