@@ -151,6 +151,65 @@ __device__ __forceinline__ double fixed128_to_f64(unsigned long long hi, unsigne
     return assemble_f64(round53(top, rem, half), n, k2, 0ull);
 }
 
+// 1/a in double for 2^-69 <= a < 2^120 from a seed good to ~2^-45 and one
+// Newton step (two FP64 instructions instead of rcp_fp64's three).  The
+// seed is built off the FP64 pipe: a split by its bits into a head float
+// (24 leading bits) and a tail float (the next 29 bits, rounded), the
+// head's FP32 reciprocal y refined on the FP32 pipe to y + y (t + t^2) with
+// t = 1 - a y (the reciprocal of a double-float number), and y and its
+// correction joined into one double with integer instructions.  Outside
+// the range the caller divides (a warp-uniform branch).
+__device__ __forceinline__ double rcp_fp64_seeded(double a, bool &ok)
+{
+    const long long b = __double_as_longlong(a);
+    const int ea = static_cast<int>((b >> 52) & 0x7ff) - 1023;  // a in [2^ea, 2^(ea+1))
+    ok = ea > -70 && ea < 120;  // head, tail and y stay normal floats
+    const int e = ok ? ea : 0;
+    const unsigned long long mant = static_cast<unsigned long long>(b) & 0xfffffffffffffull;
+    // head: 1.m[51:29] 2^e exactly; tail: m[28:0] 2^(e-52)
+    const float head = __uint_as_float(static_cast<unsigned>((e + 127) << 23) |
+                                       static_cast<unsigned>(mant >> 29));
+    const float tail = __fmul_rn(__uint2float_rn(static_cast<unsigned>(mant & 0x1fffffffull)),
+                                 __uint_as_float(static_cast<unsigned>((e - 52 + 127) << 23)));
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(head));
+    float t = __fmaf_rn(-head, y, 1.0f);
+    t = __fmaf_rn(-tail, y, t);
+    const float q = __fmul_rn(y, t);
+    const float l = __fmaf_rn(q, t, q);  // 1/a ~ y + l, |l| < 2^-21 y
+    // y + l as a double: y's 24-bit significand at bit 52, l added at its
+    // binary point (integer add of the two aligned significands).
+    const unsigned uy = __float_as_uint(y), ul = __float_as_uint(l);
+    const int ey = static_cast<int>((uy >> 23) & 0xff);
+    const int el = static_cast<int>((ul >> 23) & 0xff);
+    long long my = static_cast<long long>((uy & 0x7fffffu) | 0x800000u) << 29;
+    const int sh = 29 - (ey - el);  // where l's significand lands (<= 8)
+    long long ml = static_cast<long long>((ul & 0x7fffffu) | (el ? 0x800000u : 0u));
+    ml = el == 0 ? 0 : (sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> -sh) : 0));
+    my += (ul >> 31) ? -ml : ml;
+    long long eb = static_cast<long long>(ey) - 127 + 1023;
+    if (my >= (1ll << 53)) {
+        my >>= 1;
+        ++eb;
+    } else if (my < (1ll << 52)) {
+        my <<= 1;
+        --eb;
+    }
+    const double x0 = __longlong_as_double((eb << 52) | (my & 0xfffffffffffffll));
+    const double r = fma(-a, x0, 1.0);
+    return fma(x0, r, x0);
+}
+
+__device__ __forceinline__ double rcp_fp64_fixed(double a, unsigned mask)
+{
+    bool ok;
+    double x = rcp_fp64_seeded(a, ok);
+    if (__any_sync(mask, !ok)) {
+        if (!ok) x = 1.0 / a;
+    }
+    return x;
+}
+
 // |D|^2 summed over three axes as a 128-bit integer (|D| <= 2^60 each).
 __device__ __forceinline__ void norm2_fixed(long long dx, long long dy, long long dz,
                                             unsigned long long &hi, unsigned long long &lo)
@@ -236,7 +295,7 @@ __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
         const bool in = fixed_entry(q4, xi, yi, zi, xj, yj, zj, valid, i, j, P, F, gm, dx, dy, dz, r2);
         if (__any_sync(gm, in)) {
             if (!in) r2 = 1.0;
-            const double w = rcp_fp64(r2, gm);
+            const double w = rcp_fp64_fixed(r2, gm);
             const double w2 = w * w;
             const double w4 = w2 * w2;
             const double w3 = w2 * w;
