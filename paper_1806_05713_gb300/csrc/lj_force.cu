@@ -62,7 +62,7 @@ force_fp64_kernel(const double *__restrict__ q4, double *__restrict__ p4, int n,
 // FP64 form with the exact fixed-point displacement (LJ_SCHED_FIXED; U = 2:
 // | LJ_SCHED_SWP2).
 template <int TPI, bool HALF, int U>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, U == 1 ? 6 : 1)
 force_fixed_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
                    double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
                    const int *__restrict__ col, Fp64Params P, FixParams F,
