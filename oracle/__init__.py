@@ -17,5 +17,10 @@ Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
 * energy: pinned -- V(2^(1/6) sigma) = -eps, V(sigma) = 0, the shift.
 * force_vjp: pinned -- central finite differences of the loss (h = 1e-6)
   built from ``forces`` alone.
+* force_fs, energy_fs (force-shifted truncation): pinned -- sympy's
+  derivative of V(r) - V(r_c) - (r - r_c) V'(r_c) for two-body pairs; force
+  and energy vanish at r_c (linearly, quadratically); F = -grad E_fs by
+  central differences; Newton's third law; half list == full list.
 """
-from .oracle import build, energy, force, force_vjp, forces, pairlist  # noqa: F401
+from .oracle import (build, energy, energy_fs, force, force_fs, force_vjp, forces,  # noqa: F401
+                     pairlist)

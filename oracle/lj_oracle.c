@@ -274,6 +274,84 @@ double oracle_energy(int64_t n, const double *q, int64_t qstride, const int32_t 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Force-shifted truncation                                                  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The smooth truncation the paper recommends for energy conservation but
+ * does not use (section "Lennard-Jones Potential"): for r < r_c
+ *   V_fs(r) = V(r) - V(r_c) - (r - r_c) V'(r_c),
+ * whose pair force -V_fs'(r) = -V'(r) + V'(r_c) goes to zero at r_c.  With
+ * F_c = -V'(r_c) = 24 eps (2 sigma^12 / r_c^13 - sigma^6 / r_c^7), the
+ * impulse coefficient of a pair is the plain one minus F_c dt / r:
+ *   df_fs = df - F_c dt / r,   p_i -= df_fs r_vec,  p_j += df_fs r_vec.
+ */
+static double lj_fc(double rc, double eps, double sigma)
+{
+    double sr = sigma / rc;
+    double sr2 = sr * sr;
+    double sr6 = sr2 * sr2 * sr2;
+    return 24.0 * eps * (2.0 * sr6 * sr6 - sr6) / rc;
+}
+
+void oracle_force_fs(int64_t n, const double *q, int64_t qstride, double *p, int64_t pstride,
+                     const int32_t *row_ptr, const int32_t *col, int half, double dt, double rc,
+                     const double *L, double eps, double sigma)
+{
+    double rc2 = rc * rc;
+    double s2 = sigma * sigma;
+    double s6 = s2 * s2 * s2;
+    double s12 = s6 * s6;
+    double c48 = 48.0 * eps * s12;
+    double c24 = 24.0 * eps * s6;
+    double fc = lj_fc(rc, eps, sigma);
+    double r[3];
+    for (int64_t i = 0; i < n; ++i) {
+        const double *qi = q + i * qstride;
+        double pi[3] = {p[i * pstride + 0], p[i * pstride + 1], p[i * pstride + 2]};
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int64_t j = col[k];
+            double r2 = displacement(qi, q + j * qstride, L, r);
+            if (r2 < rc2) {
+                double r6 = r2 * r2 * r2;
+                double r14 = r6 * r6 * r2;
+                double df = (c48 - c24 * r6) * dt / r14 - fc * dt / sqrt(r2);
+                for (int a = 0; a < 3; ++a)
+                    pi[a] -= df * r[a];
+                if (half)
+                    for (int a = 0; a < 3; ++a)
+                        p[j * pstride + a] += df * r[a];
+            }
+        }
+        for (int a = 0; a < 3; ++a)
+            p[i * pstride + a] = pi[a];
+    }
+}
+
+/* Sum over unique pairs with r < r_c of V_fs(r). */
+double oracle_energy_fs(int64_t n, const double *q, int64_t qstride, const int32_t *row_ptr,
+                        const int32_t *col, int half, double rc, const double *L, double eps,
+                        double sigma)
+{
+    double rc2 = rc * rc;
+    double vc = lj_v(rc2, eps, sigma);
+    double fc = lj_fc(rc, eps, sigma);
+    double e = 0.0;
+    double r[3];
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int64_t j = col[k];
+            if (!half && j < i)
+                continue;
+            double r2 = displacement(q + i * qstride, q + j * qstride, L, r);
+            if (r2 < rc2)
+                e += lj_v(r2, eps, sigma) - vc + (sqrt(r2) - rc) * fc;
+        }
+    }
+    return e;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Adjoint of the force map                                                  */
 /* ------------------------------------------------------------------------ */
 

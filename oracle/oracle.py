@@ -70,6 +70,11 @@ def _load():
         lib.oracle_energy.restype = _dbl
         lib.oracle_energy.argtypes = [_i64, _vp, _i64, _vp, _vp, _int, _dbl, _vp, _dbl, _dbl,
                                       _int]
+        lib.oracle_force_fs.restype = None
+        lib.oracle_force_fs.argtypes = [_i64, _vp, _i64, _vp, _i64, _vp, _vp, _int, _dbl, _dbl,
+                                        _vp, _dbl, _dbl]
+        lib.oracle_energy_fs.restype = _dbl
+        lib.oracle_energy_fs.argtypes = [_i64, _vp, _i64, _vp, _vp, _int, _dbl, _vp, _dbl, _dbl]
         lib.oracle_force_vjp.restype = None
         lib.oracle_force_vjp.argtypes = [_i64, _vp, _i64, _vp, _i64, _vp, _vp, _int, _dbl, _vp,
                                          _dbl, _dbl, _vp, _vp]
@@ -139,6 +144,36 @@ def energy(q, row_ptr, col, half: bool, rc: float, box, eps: float = 1.0, sigma:
     return float(lib.oracle_energy(q.shape[0], _ptr(q), q.shape[1], _ptr(row_ptr), _ptr(col),
                                    int(bool(half)), float(rc), _ptr(L), float(eps),
                                    float(sigma), int(bool(shifted))))
+
+
+def force_fs(q, p, row_ptr, col, half: bool, dt: float, rc: float, box, eps: float = 1.0,
+             sigma: float = 1.0) -> np.ndarray:
+    """Momenta after one force call with the force-shifted truncation (the
+    pair force -V'(r) + V'(r_c), zero at r_c); p is not modified."""
+    lib = _load()
+    q = _rows(q, "q")
+    out = _rows(p, "p").copy()
+    L = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    lib.oracle_force_fs(q.shape[0], _ptr(q), q.shape[1], _ptr(out), out.shape[1], _ptr(row_ptr),
+                        _ptr(col), int(bool(half)), float(dt), float(rc), _ptr(L), float(eps),
+                        float(sigma))
+    return out
+
+
+def energy_fs(q, row_ptr, col, half: bool, rc: float, box, eps: float = 1.0,
+              sigma: float = 1.0) -> float:
+    """Force-shifted potential energy: sum of V(r) - V(r_c) - (r - r_c) V'(r_c)
+    over unique pairs with r < r_c."""
+    lib = _load()
+    q = _rows(q, "q")
+    L = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    return float(lib.oracle_energy_fs(q.shape[0], _ptr(q), q.shape[1], _ptr(row_ptr), _ptr(col),
+                                      int(bool(half)), float(rc), _ptr(L), float(eps),
+                                      float(sigma)))
 
 
 def force_vjp(q, R, row_ptr, col, half: bool, rc: float, box, eps: float = 1.0,

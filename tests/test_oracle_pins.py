@@ -351,3 +351,83 @@ def test_vjp_matches_central_differences(oracle_lib, half):
         qm[i, a] -= h
         fd = (L(q=qp) - L(q=qm)) / (2 * h)
         assert abs(fd - gq[i, a]) < 1e-5 * scale, (i, a, fd, gq[i, a])
+
+
+# --------------------------------------------------------------------------
+# Force-shifted truncation
+# --------------------------------------------------------------------------
+
+def _two_body(r):
+    q = np.zeros((2, 4))
+    q[:, :3] = 10.0
+    q[1, 0] += r
+    return q
+
+
+def test_fs_matches_symbolic_definition(oracle_lib):
+    """V_fs(r) = V(r) - V(r_c) - (r - r_c) V'(r_c), differentiated by sympy:
+    the impulse on the second atom of a pair along x is -V_fs'(r) dt, and
+    the pair energy is V_fs(r)."""
+    sympy = pytest.importorskip("sympy")
+    r, rc, e, s = sympy.symbols("r r_c epsilon sigma", positive=True)
+    V = 4 * e * ((s / r) ** 12 - (s / r) ** 6)
+    Vfs = V - V.subs(r, rc) - (r - rc) * sympy.diff(V, r).subs(r, rc)
+    F = sympy.lambdify((r, rc, e, s), -sympy.diff(Vfs, r))
+    E = sympy.lambdify((r, rc, e, s), Vfs)
+    box = np.array([20.0] * 3)
+    for rv, rcv, ev, sv in [(1.0, 3.0, 1.0, 1.0), (1.3, 2.5, 1.2, 0.9), (2.9, 3.0, 1.0, 1.0),
+                            (0.95, 4.0, 0.7, 1.1)]:
+        q = _two_body(rv)
+        rp, col = oracle_lib.pairlist(q, box, rcv + 0.3, True)
+        p = oracle_lib.force_fs(q, np.zeros((2, 3)), rp, col, True, 0.01, rcv, box, ev, sv)
+        want = float(F(rv, rcv, ev, sv)) * 0.01
+        assert abs(p[1, 0] - want) <= 1e-12 * max(1.0, abs(want))
+        assert abs(p[0, 0] + want) <= 1e-12 * max(1.0, abs(want))
+        got_e = oracle_lib.energy_fs(q, rp, col, True, rcv, box, ev, sv)
+        assert abs(got_e - float(E(rv, rcv, ev, sv))) <= 1e-12 * max(1.0, abs(got_e))
+
+
+def test_fs_force_and_energy_vanish_at_the_cutoff(oracle_lib):
+    """The shifted force goes to zero linearly and the shifted energy
+    quadratically as r -> r_c; the plain truncation jumps."""
+    box = np.array([20.0] * 3)
+    f, en, fp = [], [], []
+    for d in (1e-2, 1e-3, 1e-4):
+        q = _two_body(3.0 - d)
+        rp, col = oracle_lib.pairlist(q, box, 3.3, True)
+        f.append(abs(oracle_lib.force_fs(q, np.zeros((2, 3)), rp, col, True, 1.0, 3.0, box)[1, 0]))
+        fp.append(abs(oracle_lib.force(q, np.zeros((2, 3)), rp, col, True, 1.0, 3.0, box)[1, 0]))
+        en.append(abs(oracle_lib.energy_fs(q, rp, col, True, 3.0, box)))
+    assert 8 < f[0] / f[1] < 12 and 8 < f[1] / f[2] < 12
+    assert 80 < en[0] / en[1] < 120 and 80 < en[1] / en[2] < 120
+    assert min(fp) > 1e-3   # the plain force does not vanish at r_c
+    q = _two_body(3.0)      # at r_c exactly: excluded
+    rp, col = oracle_lib.pairlist(q, box, 3.3, True)
+    assert oracle_lib.energy_fs(q, rp, col, True, 3.0, box) == 0.0
+
+
+def test_fs_force_is_minus_gradient_of_fs_energy(oracle_lib):
+    s = inputs.fcc_system(5, 1.0, 0.08, seed=22)
+    rp, col = oracle_lib.pairlist(s.q, s.box, 3.3, True)
+    F = oracle_lib.force_fs(s.q, np.zeros((s.n, 3)), rp, col, True, 1.0, 3.0, s.box)
+    h = 1e-5
+    rng = np.random.default_rng(1)
+    for _ in range(12):
+        i, a = int(rng.integers(s.n)), int(rng.integers(3))
+        qp, qm = s.q.copy(), s.q.copy()
+        qp[i, a] += h
+        qm[i, a] -= h
+        fd = -(oracle_lib.energy_fs(qp, rp, col, True, 3.0, s.box) -
+               oracle_lib.energy_fs(qm, rp, col, True, 3.0, s.box)) / (2 * h)
+        assert abs(fd - F[i, a]) < 1e-6 * max(1.0, abs(F[i, a])), (i, a, fd, F[i, a])
+
+
+def test_fs_newton_and_half_equals_full(oracle_lib, small):
+    s, (rp, col), (rpf, colf) = small
+    ph = oracle_lib.force_fs(s.q, np.zeros((s.n, 3)), rp, col, True, 0.01, 3.0, s.box)
+    pf = oracle_lib.force_fs(s.q, np.zeros((s.n, 3)), rpf, colf, False, 0.01, 3.0, s.box)
+    assert np.max(np.abs(ph.sum(axis=0))) < 1e-12 * np.abs(ph).sum()
+    assert np.max(np.abs(ph - pf)) <= 1e-13 * np.max(np.abs(ph))
+    eh = oracle_lib.energy_fs(s.q, rp, col, True, 3.0, s.box)
+    ef = oracle_lib.energy_fs(s.q, rpf, colf, False, 3.0, s.box)
+    assert abs(eh - ef) <= 1e-12 * abs(eh)
