@@ -357,7 +357,7 @@ def test_vjp_matches_central_differences(oracle_lib, half):
 # Force-shifted truncation
 # --------------------------------------------------------------------------
 
-def _two_body(r):
+def _pair_at(r):
     q = np.zeros((2, 4))
     q[:, :3] = 10.0
     q[1, 0] += r
@@ -377,7 +377,7 @@ def test_fs_matches_symbolic_definition(oracle_lib):
     box = np.array([20.0] * 3)
     for rv, rcv, ev, sv in [(1.0, 3.0, 1.0, 1.0), (1.3, 2.5, 1.2, 0.9), (2.9, 3.0, 1.0, 1.0),
                             (0.95, 4.0, 0.7, 1.1)]:
-        q = _two_body(rv)
+        q = _pair_at(rv)
         rp, col = oracle_lib.pairlist(q, box, rcv + 0.3, True)
         p = oracle_lib.force_fs(q, np.zeros((2, 3)), rp, col, True, 0.01, rcv, box, ev, sv)
         want = float(F(rv, rcv, ev, sv)) * 0.01
@@ -393,7 +393,7 @@ def test_fs_force_and_energy_vanish_at_the_cutoff(oracle_lib):
     box = np.array([20.0] * 3)
     f, en, fp = [], [], []
     for d in (1e-2, 1e-3, 1e-4):
-        q = _two_body(3.0 - d)
+        q = _pair_at(3.0 - d)
         rp, col = oracle_lib.pairlist(q, box, 3.3, True)
         f.append(abs(oracle_lib.force_fs(q, np.zeros((2, 3)), rp, col, True, 1.0, 3.0, box)[1, 0]))
         fp.append(abs(oracle_lib.force(q, np.zeros((2, 3)), rp, col, True, 1.0, 3.0, box)[1, 0]))
@@ -401,7 +401,7 @@ def test_fs_force_and_energy_vanish_at_the_cutoff(oracle_lib):
     assert 8 < f[0] / f[1] < 12 and 8 < f[1] / f[2] < 12
     assert 80 < en[0] / en[1] < 120 and 80 < en[1] / en[2] < 120
     assert min(fp) > 1e-3   # the plain force does not vanish at r_c
-    q = _two_body(3.0)      # at r_c exactly: excluded
+    q = _pair_at(3.0)      # at r_c exactly: excluded
     rp, col = oracle_lib.pairlist(q, box, 3.3, True)
     assert oracle_lib.energy_fs(q, rp, col, True, 3.0, box) == 0.0
 
