@@ -58,7 +58,7 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
 # schedule, from ncu (cold cache), with the profile that records them.
 TRAFFIC_PER_LAUNCH = {
     1032: (41903872.0 + 1280.0, "profiles/force_fp64_images_tpi8_half_N119164.md"),
-    2056: (41909760.0, "profiles/force_fp64_fixed_tpi8_half_N119164.md"),
+    2056: (41911040.0 + 2560.0, "profiles/force_fp64_fixed_tpi8_half_N119164.md"),
     4104: (41915904.0, "profiles/force_fp64_compact_tpi8_half_N119164.md"),
 }
 
@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--profile", choices=["fp64", "fp64-full", "mixed", "mixed-full", "dfloat",
                                           "dfloat-full", "list", "vjp", "batched", "batched-dfloat"],
                     help="no timing: build the list and run a few calls of one kernel (for ncu)")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="FP64 schedule for the timed steps (0 = the library's autotuner picks)")
     ap.add_argument("--profile-atoms", choices=["paper", "million"], default="paper")
     ap.add_argument("--profile-tpi", type=int, default=0, help="schedule for --profile (0 = auto)")
     return ap.parse_args()
@@ -320,7 +322,10 @@ def main():
 
     pl = lj.lj_build_pairlist(q, box, s.rs, True)
     # schedule picked by the library's autotuner on this system and list
-    best_tpi, _, tune_table = lj.lj_autotune_force(q, pl, DT, s.rc, box, reps=5)
+    if args.schedule:
+        best_tpi, tune_table = args.schedule, {}
+    else:
+        best_tpi, _, tune_table = lj.lj_autotune_force(q, pl, DT, s.rc, box, reps=5)
     force = lj.lj_force_prepared(q, p, pl, DT, s.rc, box, precision=lj.LJ_FP64, tpi=best_tpi)
     nnz = pl.nnz
     n_cut = count_in_cutoff(q, pl, box, s.rc)

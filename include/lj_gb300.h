@@ -290,6 +290,29 @@ int lj_force_energy(const double *q4_dev, double *p4_dev, int64_t n, const int32
                     const double box[3], double eps, double sigma, int shifted, double *e_out_dev,
                     void *workspace_dev, size_t workspace_bytes, void *stream);
 
+/* Bytes of device workspace lj_force_shifted needs. */
+size_t lj_force_shifted_workspace_bytes(int64_t n);
+
+/*
+ * The momentum update with the force-shifted truncation the paper recommends
+ * for energy conservation but does not use (section "Lennard-Jones
+ * Potential"): for r < r_c the pair potential is
+ *   V_fs(r) = V(r) - V(r_c) - (r - r_c) V'(r_c),
+ * so the pair force -V'(r) + V'(r_c) falls continuously to zero at r_c; the
+ * impulse coefficient is lj_force's df minus F_c dt / r with
+ * F_c = -V'(r_c).  FP64 (the fixed-point rows of LJ_SCHED_FIXED | 8, plus an
+ * FP64 reciprocal square root per pair).  If e_out_dev (device, one double)
+ * is not NULL it receives the force-shifted energy sum of V_fs over unique
+ * pairs, computed in the same pass (deterministic reduction).  Other
+ * arguments as lj_force_energy.  Boxes up to 1024 r_c wide (else
+ * LJ_ERR_ARG).  Asynchronous.  Errors: LJ_ERR_ARG, LJ_ERR_BOX,
+ * LJ_ERR_CAPACITY, LJ_ERR_CUDA.
+ */
+int lj_force_shifted(const double *q4_dev, double *p4_dev, int64_t n, const int32_t *row_ptr_dev,
+                     const int32_t *col_dev, int64_t nnz, int half, double dt, double r_cut,
+                     const double box[3], double eps, double sigma, double *e_out_dev,
+                     void *workspace_dev, size_t workspace_bytes, void *stream);
+
 /* ======================================================================== */
 /* Energy (Eq. 1, truncated at r_c, optionally shifted)                     */
 /* ======================================================================== */

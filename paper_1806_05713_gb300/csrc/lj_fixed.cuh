@@ -200,6 +200,25 @@ __device__ __forceinline__ double rcp_fp64_seeded(double a, bool &ok)
     return fma(x0, r, x0);
 }
 
+// 1/sqrt(a) in double for 2^-120 < a < 2^120: the FP32 approximation of the
+// head of a, then two Newton steps y (3/2 - a y^2 / 2) in FP64 (2^-23 ->
+// 2^-46 -> below an ulp).  Outside the range, 1/sqrt by division.
+__device__ __forceinline__ double rsqrt_fp64(double a)
+{
+    const long long b = __double_as_longlong(a);
+    const int ea = static_cast<int>((b >> 52) & 0x7ff) - 1023;
+    if (!(ea > -120 && ea < 120)) return 1.0 / sqrt(a);
+    const float head = __uint_as_float(static_cast<unsigned>((ea + 127) << 23) |
+                                       static_cast<unsigned>((b >> 29) & 0x7fffff));
+    float y0;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(head));
+    double y = f32_to_f64(y0);
+    const double h = 0.5 * a;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) y = fma(y, fma(-h, y * y, 0.5), y);
+    return y;
+}
+
 __device__ __forceinline__ double rcp_fp64_fixed(double a, unsigned mask)
 {
     bool ok;
@@ -270,8 +289,9 @@ __device__ __forceinline__ bool fixed_entry(const double *__restrict__ q4, long 
 // One row of the FP64 form with the exact fixed-point displacement (see the
 // header comment); the arithmetic after r^2 is fp64_row's.  EN: also sum the
 // pair energy 4 eps [(sigma/r)^12 - (sigma/r)^6] of every interacting entry
-// into *ev and count them in *ecount.
-template <int TPI, bool HALF, bool EN = false>
+// into *ev and count them in *ecount.  FS: the force-shifted truncation --
+// df - F_c dt / r, and (EN) the pair energy V(r) - V(r_c) + (r - r_c) F_c.
+template <int TPI, bool HALF, bool EN = false, bool FS = false>
 __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
                                                const longlong4 *__restrict__ X,
                                                double *__restrict__ p4,
@@ -299,10 +319,17 @@ __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
             const double w2 = w * w;
             const double w4 = w2 * w2;
             const double w3 = w2 * w;
-            const double fn = w4 * fma(P.B, w3, -P.A);  // -df: p_i -= fn d, p_j += fn d
+            double fn = w4 * fma(P.B, w3, -P.A);  // -df: p_i -= fn d, p_j += fn d
+            double inv_r = 0.0;
+            if (FS) {
+                inv_r = rsqrt_fp64(r2);
+                fn = fma(-P.fs_c, inv_r, fn);  // the shifted coefficient: fn - F_c dt / r
+            }
             if (in) {
                 if (EN) {
-                    *ev += w3 * fma(P.C12, w3, -P.C6);
+                    double v = w3 * fma(P.C12, w3, -P.C6);
+                    if (FS) v += fma(r2, inv_r, -P.rc) * P.Fc - P.Vc;
+                    *ev += v;
                     ++*ecount;
                 }
                 if (HALF) {

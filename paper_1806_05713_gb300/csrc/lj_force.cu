@@ -112,7 +112,9 @@ force_mixed_kernel(const double *__restrict__ q4, const uint4 *__restrict__ rel,
 // Force and potential energy in one pass (FP64, 8 lanes per row, exact
 // fixed-point displacement): each thread keeps its row's pair-energy sum and
 // in-cutoff count; a fixed-order block reduction writes one partial per
-// block (the final sum is taken by energy_partials_kernel).
+// block (the final sum is taken by energy_partials_kernel).  FS: the
+// force-shifted truncation (fixed-point rows only).
+template <bool FS>
 __global__ void __launch_bounds__(256)
 force_energy_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
                          double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
@@ -126,13 +128,13 @@ force_energy_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restr
     double ev = 0.0;
     int cnt = 0;
     if (gid < n) {
-        if (X) {
+        if (FS || X) {
             if (half)
-                fp64_fixed_row<TPI, true, true>(q4, X, p4, row_ptr, col, gid, P, F, group_mask<TPI>(),
-                                                &ev, &cnt);
+                fp64_fixed_row<TPI, true, true, FS>(q4, X, p4, row_ptr, col, gid, P, F,
+                                                    group_mask<TPI>(), &ev, &cnt);
             else
-                fp64_fixed_row<TPI, false, true>(q4, X, p4, row_ptr, col, gid, P, F, group_mask<TPI>(),
-                                                 &ev, &cnt);
+                fp64_fixed_row<TPI, false, true, FS>(q4, X, p4, row_ptr, col, gid, P, F,
+                                                     group_mask<TPI>(), &ev, &cnt);
         } else {  // a box wider than 1024 r_c: image-selected rows
             if (half)
                 fp64_row<TPI, true, 1, true, 0, true>(q4, p4, row_ptr, col, gid, P, group_mask<TPI>(),
@@ -163,6 +165,19 @@ force_energy_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restr
         partial[2 * blockIdx.x] = se;
         partial[2 * blockIdx.x + 1] = static_cast<double>(sc);
     }
+}
+
+// The force-shifted truncation without the energy (8 lanes per row).
+template <bool HALF>
+__global__ void __launch_bounds__(256)
+force_fs_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
+                double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
+                const int *__restrict__ col, Fp64Params P, FixParams F)
+{
+    constexpr int TPI = 8;
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
+    if (gid >= n) return;
+    fp64_fixed_row<TPI, HALF, false, true>(q4, X, p4, row_ptr, col, gid, P, F, group_mask<TPI>());
 }
 
 // E = scale * (sum of pair energies - vshift * number of in-cutoff entries).
@@ -542,8 +557,8 @@ extern "C" int lj_force_energy(const double *q4_dev, double *p4_dev, int64_t n,
     } else {
         X = nullptr;
     }
-    force_energy_fp64_kernel<<<blocks, 256, 0, st>>>(q4_dev, X, p4_dev, static_cast<int>(n), row_ptr_dev,
-                                                     col_dev, P, F, half, partial);
+    force_energy_fp64_kernel<false><<<blocks, 256, 0, st>>>(q4_dev, X, p4_dev, static_cast<int>(n),
+                                                            row_ptr_dev, col_dev, P, F, half, partial);
     LJ_TRY_LAUNCH("force_energy_fp64_kernel");
     double vshift = 0.0;
     if (shifted) {
@@ -552,6 +567,54 @@ extern "C" int lj_force_energy(const double *q4_dev, double *p4_dev, int64_t n,
     }
     energy_partials_kernel<<<1, 1024, 0, st>>>(partial, blocks, half ? 1.0 : 0.5, vshift, e_out_dev);
     LJ_TRY_LAUNCH("energy_partials_kernel");
+    return LJ_OK;
+}
+
+extern "C" size_t lj_force_shifted_workspace_bytes(int64_t n)
+{
+    return lj_force_energy_workspace_bytes(n);
+}
+
+extern "C" int lj_force_shifted(const double *q4_dev, double *p4_dev, int64_t n,
+                                const int32_t *row_ptr_dev, const int32_t *col_dev, int64_t nnz,
+                                int half, double dt, double r_cut, const double box[3], double eps,
+                                double sigma, double *e_out_dev, void *workspace_dev,
+                                size_t workspace_bytes, void *stream)
+{
+    using namespace lj;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_force_args(q4_dev, p4_dev, n, row_ptr_dev, col_dev, nnz, r_cut, box, eps, sigma,
+                              dt);
+    if (rc != LJ_OK) return rc;
+    if (e_out_dev && (reinterpret_cast<uintptr_t>(e_out_dev) & 7u)) return LJ_ERR_ARG;
+    if (!fixed_point_ok(box, r_cut)) return LJ_ERR_ARG;
+    if (n == 0 || nnz == 0) {
+        if (e_out_dev) LJ_TRY_CUDA(cudaMemsetAsync(e_out_dev, 0, sizeof(double), st));
+        return LJ_OK;
+    }
+    if (!workspace_dev || workspace_bytes < lj_force_shifted_workspace_bytes(n)) return LJ_ERR_CAPACITY;
+    const Fp64Params P = make_fp64_params(box, dt, r_cut, eps, sigma);
+    const FixParams F = make_fix_params(box);
+    const int ni = static_cast<int>(n);
+    const int blocks = static_cast<int>((n * 8 + 255) / 256);
+    Carver c(workspace_dev);
+    double *partial = c.take<double>(2 * size_t(blocks));
+    longlong4 *X = c.take<longlong4>(size_t(n));
+    fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, ni, F, X);
+    LJ_TRY_LAUNCH("fixed_prepass_kernel");
+    if (e_out_dev) {
+        force_energy_fp64_kernel<true><<<blocks, 256, 0, st>>>(q4_dev, X, p4_dev, ni, row_ptr_dev,
+                                                               col_dev, P, F, half, partial);
+        LJ_TRY_LAUNCH("force_energy_fp64_kernel");
+        energy_partials_kernel<<<1, 1024, 0, st>>>(partial, blocks, half ? 1.0 : 0.5, 0.0, e_out_dev);
+        LJ_TRY_LAUNCH("energy_partials_kernel");
+    } else {
+        if (half)
+            force_fs_kernel<true><<<blocks, 256, 0, st>>>(q4_dev, X, p4_dev, ni, row_ptr_dev, col_dev, P, F);
+        else
+            force_fs_kernel<false><<<blocks, 256, 0, st>>>(q4_dev, X, p4_dev, ni, row_ptr_dev, col_dev, P, F);
+        LJ_TRY_LAUNCH("force_fs_kernel");
+    }
     return LJ_OK;
 }
 

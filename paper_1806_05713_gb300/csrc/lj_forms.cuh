@@ -17,6 +17,8 @@ struct Fp64Params {
     double rc2;
     double A, B;  // df = u^4 (A - B u^3): A = 24 eps sigma^6 dt, B = 48 eps sigma^12 dt
     double C12, C6;  // V = u^3 (C12 u^3 - C6): C12 = 4 eps sigma^12, C6 = 4 eps sigma^6
+    // force-shifted truncation: F_c = -V'(r_c), fs_c = F_c dt, V_c = V(r_c)
+    double rc, Fc, fs_c, Vc;
 };
 
 struct MixedParams {
@@ -164,6 +166,11 @@ Fp64Params make_fp64_params(const double box[3], double dt, double rc, double ep
     P.B = 48.0 * eps * s12 * dt;
     P.C12 = 4.0 * eps * s12;
     P.C6 = 4.0 * eps * s6;
+    const double sr = sigma / rc, sr2 = sr * sr, sr6 = sr2 * sr2 * sr2;
+    P.rc = rc;
+    P.Fc = 24.0 * eps * (2.0 * sr6 * sr6 - sr6) / rc;
+    P.fs_c = P.Fc * dt;
+    P.Vc = 4.0 * eps * (sr6 * sr6 - sr6);
     return P;
 }
 

@@ -98,6 +98,9 @@ SIGNATURES = {
     "lj_force_energy_workspace_bytes": (_sz, [_i64]),
     "lj_force_energy": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl, _dbl3, _dbl, _dbl,
                                _int, _vp, _vp, _sz, _vp]),
+    "lj_force_shifted_workspace_bytes": (_sz, [_i64]),
+    "lj_force_shifted": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl, _dbl3, _dbl, _dbl,
+                                _vp, _vp, _sz, _vp]),
     "lj_energy_workspace_bytes": (_sz, [_i64]),
     "lj_energy": (_int, [_vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl3, _dbl, _dbl, _int, _vp, _vp,
                          _sz, _vp]),
@@ -439,6 +442,31 @@ def lj_force_energy(q4: torch.Tensor, p4: torch.Tensor, plist: PairList, dt: flo
                              _dev(out, torch.float64, "out"), workspace.data_ptr(),
                              workspace.numel(), _stream(stream))
     _check(st, "lj_force_energy")
+    return out
+
+
+def lj_force_shifted_workspace_bytes(n: int) -> int:
+    return int(load().lj_force_shifted_workspace_bytes(int(n)))
+
+
+def lj_force_shifted(q4: torch.Tensor, p4: torch.Tensor, plist: PairList, dt: float,
+                     r_cut: float, box, eps: float = 1.0, sigma: float = 1.0,
+                     out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor | None:
+    """p4 += impulses with the force-shifted truncation (FP64); if `out` (a
+    1-element float64 device tensor) is given it receives the force-shifted
+    potential energy.  Returns `out`."""
+    lib = load()
+    n = plist.n
+    if workspace is None:
+        workspace = _workspace(lib.lj_force_shifted_workspace_bytes(n), q4.device)
+    st = lib.lj_force_shifted(_dev(q4, torch.float64, "q4", (n, 4)),
+                              _dev(p4, torch.float64, "p4", (n, 4)), n, plist.row_ptr.data_ptr(),
+                              plist.col.data_ptr(), plist.nnz, int(plist.half), float(dt),
+                              float(r_cut), _box3(box), float(eps), float(sigma),
+                              _dev(out, torch.float64, "out") if out is not None else None,
+                              workspace.data_ptr(), workspace.numel(), _stream(stream))
+    _check(st, "lj_force_shifted")
     return out
 
 

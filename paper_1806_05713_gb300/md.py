@@ -25,7 +25,14 @@ class VelocityVerlet:
 
     def __init__(self, q4: torch.Tensor, p4: torch.Tensor, box, r_cut: float, margin: float,
                  dt: float, eps: float = 1.0, sigma: float = 1.0, precision: int = lj.LJ_FP64,
-                 tpi: int = lj.LJ_TPI_AUTO, half: bool = True):
+                 tpi: int = lj.LJ_TPI_AUTO, half: bool = True, truncation: str = "plain"):
+        """truncation: "plain" (Eq. (1) cut at r_c, the paper's choice) or
+        "force_shifted" (the pair force taken to zero at r_c; FP64 only)."""
+        if truncation not in ("plain", "force_shifted"):
+            raise ValueError("truncation must be 'plain' or 'force_shifted'")
+        if truncation == "force_shifted" and precision != lj.LJ_FP64:
+            raise ValueError("the force-shifted truncation is FP64 only")
+        self.truncation = truncation
         self.q4, self.p4 = q4, p4
         self.box = [float(x) for x in box]
         self.r_cut, self.margin, self.dt = float(r_cut), float(margin), float(dt)
@@ -37,6 +44,8 @@ class VelocityVerlet:
         self.max_disp2 = torch.zeros(1, dtype=torch.float64, device=q4.device)
         self.ws = lj._workspace(lj.lj_force_workspace_bytes(q4.shape[0], self.box, self.precision),
                                 q4.device)
+        self._fsws = (lj._workspace(lj.lj_force_shifted_workspace_bytes(q4.shape[0]), q4.device)
+                      if truncation == "force_shifted" else None)
         self._half_kicked = False
         self._rebuild()
 
@@ -47,7 +56,10 @@ class VelocityVerlet:
         self.moved = 0.0
 
     def _kick(self, h: float, energy_out: torch.Tensor | None = None):
-        if energy_out is not None:
+        if self.truncation == "force_shifted":
+            lj.lj_force_shifted(self.q4, self.p4, self.plist, h, self.r_cut, self.box, self.eps,
+                                self.sigma, out=energy_out, workspace=self._fsws)
+        elif energy_out is not None:
             # the FP64 force pass that also returns U(q) (shifted potential)
             lj.lj_force_energy(self.q4, self.p4, self.plist, h, self.r_cut, self.box, self.eps,
                                self.sigma, True, out=energy_out, workspace=self._ews)
@@ -58,8 +70,8 @@ class VelocityVerlet:
     def run(self, steps: int, energies: torch.Tensor | None = None):
         """Advance `steps` steps; p4 ends at the same time as q4.  If
         `energies` (a device tensor of `steps` doubles) is given, the force
-        passes also write the shifted potential energy U(q(t_k)) of each new
-        position into it (FP64 form)."""
+        passes also write the potential energy U(q(t_k)) of each new position
+        into it (FP64 form; shifted, or force-shifted with that truncation)."""
         if steps <= 0:
             return
         if energies is not None:
@@ -81,5 +93,12 @@ class VelocityVerlet:
         return 0.5 * float((self.p4[:, :3] ** 2).sum())
 
     def potential_energy(self, shifted: bool = True) -> float:
+        """The truncated potential energy (shifted by V(r_c) or not); with the
+        force-shifted truncation, its energy (a force pass with dt = 0)."""
+        if self.truncation == "force_shifted":
+            out = torch.empty(1, dtype=torch.float64, device=self.q4.device)
+            lj.lj_force_shifted(self.q4, torch.zeros_like(self.p4), self.plist, 0.0, self.r_cut,
+                                self.box, self.eps, self.sigma, out=out, workspace=self._fsws)
+            return float(out.item())
         return float(lj.lj_energy(self.q4, self.plist, self.r_cut, self.box, self.eps, self.sigma,
                                   shifted).item())
