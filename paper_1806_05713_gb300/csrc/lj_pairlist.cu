@@ -7,16 +7,24 @@
 // "Data layout of a pair list" (b), (c) is this CSR).
 //
 // GB300 design:
-//   1. bin:      one thread per atom -> cell id (cells of side >= r_s) and a
-//                slot inside the cell (atomic counter); validates q in [0, L).
+//   1. bin:      one thread per atom -> cell id (cells of side >= r_s / 2,
+//                so every partner within r_s lies in the 5 x 5 x 5 cells
+//                around an atom's own) and a slot inside the cell (atomic
+//                counter); validates q in [0, L).
 //   2. scan:     exclusive prefix sum of the cell counts -> cell_start.
 //   3. scatter:  atoms in cell order, with an FP32 copy {x, y, z, id} so that
 //                the candidate loops below stream 16-byte records.
 //   4. count:    one warp per row (rows taken in cell order, so neighbouring
-//                warps share their 27 neighbour cells in L1/L2); candidates
-//                are screened in FP32 against r_s^2 (1 +- delta) with a proven
-//                error bound delta, and only the rare candidates inside the
-//                band are decided by the exact FP64 definition.
+//                warps share their neighbour cells in L1/L2); the five cells
+//                of a row of the stencil along x are consecutive in the cell
+//                order, so they are walked as one run of candidates (two
+//                where the stencil wraps around the box) -- 25 runs of ~27
+//                atoms at density 1 instead of 27 cells of ~43, about half
+//                the candidate slots of a stencil of r_s-sized cells;
+//                candidates are screened in FP32 against r_s^2 (1 +- delta)
+//                with a proven error bound delta, and only the rare
+//                candidates inside the band are decided by the exact FP64
+//                definition.
 //   5. scan:     row counts -> row_ptr; total and longest row read back.
 //   6. fill:     the same walk compacts the j of the row into shared memory
 //                (ballot + popc), ranks them (all j are distinct) and writes
@@ -47,7 +55,7 @@ struct ListStats {
 struct Grid {
     int nc[3];
     int noff[3];
-    int off[3][3];
+    int off[3][5];
     double L[3];
     long long half_bits[3];
     float Lf[3];
@@ -58,10 +66,12 @@ struct Grid {
     int ncell;
 };
 
+// Cells of side >= r_s / 2.
 int cells_per_axis(double L, double rs)
 {
-    int nc = static_cast<int>(std::floor(L / rs));
-    while (nc > 1 && L / nc < rs * (1.0 + 1e-12)) --nc;
+    const double side = 0.5 * rs;
+    int nc = static_cast<int>(std::floor(L / side));
+    while (nc > 1 && L / nc < side * (1.0 + 1e-12)) --nc;
     return nc < 1 ? 1 : nc;
 }
 
@@ -81,18 +91,14 @@ Grid make_grid(int64_t n, const double box[3], double rs)
     double Lmax = 0.0;
     for (int a = 0; a < 3; ++a) {
         const int nc = g.nc[a];
-        if (nc == 1) {
-            g.noff[a] = 1;
-            g.off[a][0] = 0;
-        } else if (nc == 2) {
-            g.noff[a] = 2;
-            g.off[a][0] = 0;
-            g.off[a][1] = 1;
+        // Offsets -2..2; with fewer than five cells on the axis every cell
+        // is a neighbour and each is listed once (offsets 0..nc-1).
+        if (nc < 5) {
+            g.noff[a] = nc;
+            for (int o = 0; o < nc; ++o) g.off[a][o] = o;
         } else {
-            g.noff[a] = 3;
-            g.off[a][0] = -1;
-            g.off[a][1] = 0;
-            g.off[a][2] = 1;
+            g.noff[a] = 5;
+            for (int o = 0; o < 5; ++o) g.off[a][o] = o - 2;
         }
         g.L[a] = box[a];
         const double h = 0.5 * box[a];
@@ -227,17 +233,37 @@ __device__ __forceinline__ void walk_row(const double *__restrict__ q4, const Gr
     const int cz = cell_i / (g.nc[0] * g.nc[1]);
     bool have_exact = false;
     double xi = 0.0, yi = 0.0, zi = 0.0;
+    // The x-neighbours of a stencil row: cells x0..x1 (consecutive in the
+    // cell order), plus x2..x3 where the stencil wraps (empty otherwise).
+    int x0, x1, x2 = 0, x3 = -1;
+    if (g.noff[0] < 5) {
+        x0 = 0;
+        x1 = g.nc[0] - 1;
+    } else if (cx - 2 < 0) {
+        x0 = 0;
+        x1 = cx + 2;
+        x2 = g.nc[0] + cx - 2;
+        x3 = g.nc[0] - 1;
+    } else if (cx + 2 >= g.nc[0]) {
+        x0 = cx - 2;
+        x1 = g.nc[0] - 1;
+        x2 = 0;
+        x3 = cx + 2 - g.nc[0];
+    } else {
+        x0 = cx - 2;
+        x1 = cx + 2;
+    }
     for (int oz = 0; oz < g.noff[2]; ++oz) {
         int nz = cz + g.off[2][oz];
         nz = nz < 0 ? nz + g.nc[2] : (nz >= g.nc[2] ? nz - g.nc[2] : nz);
         for (int oy = 0; oy < g.noff[1]; ++oy) {
             int ny = cy + g.off[1][oy];
             ny = ny < 0 ? ny + g.nc[1] : (ny >= g.nc[1] ? ny - g.nc[1] : ny);
-            for (int ox = 0; ox < g.noff[0]; ++ox) {
-                int nx = cx + g.off[0][ox];
-                nx = nx < 0 ? nx + g.nc[0] : (nx >= g.nc[0] ? nx - g.nc[0] : nx);
-                const int cell = (nz * g.nc[1] + ny) * g.nc[0] + nx;
-                const int s = cell_start[cell], e = cell_start[cell + 1];
+            const int rowc = (nz * g.nc[1] + ny) * g.nc[0];
+            for (int run = 0; run < 2; ++run) {
+                const int xa = run == 0 ? x0 : x2, xb = run == 0 ? x1 : x3;
+                if (xb < xa) continue;  // no second run (warp-uniform)
+                const int s = cell_start[rowc + xa], e = cell_start[rowc + xb + 1];
                 for (int base = s; base < e; base += 32) {
                     const int k = base + lane;
                     bool in = false;
