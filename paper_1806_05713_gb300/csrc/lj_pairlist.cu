@@ -356,6 +356,78 @@ fill_kernel(const double *__restrict__ q4, int n, Grid g, const int *__restrict_
     }
 }
 
+// One-walk build: the row's accepted j, in walk order, into its slab
+// tmp[i * cap .. i * cap + cap) (rows longer than cap are only counted and
+// flagged; the caller then finishes with fill_kernel).
+template <bool HALF>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+walk_store_kernel(const double *__restrict__ q4, int n, Grid g, const int *__restrict__ cell_of,
+                  const int *__restrict__ cell_start, const int *__restrict__ cell_atoms,
+                  const float4 *__restrict__ pos_f, int *__restrict__ tmp, int cap,
+                  int *__restrict__ row_cnt, ListStats *__restrict__ stats)
+{
+    const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (w >= n) return;
+    const int i = cell_atoms[w];
+    const float4 pi = pos_f[w];
+    int *dst = tmp + static_cast<size_t>(i) * cap;
+    int cnt = 0;
+    walk_row<HALF>(q4, g, cell_start, pos_f, i, pi, cell_of[i],
+                   [&](unsigned mask, bool in, int j) {
+                       const int pos = cnt + __popc(mask & lanemask_lt());
+                       if (in && pos < cap) dst[pos] = j;
+                       cnt += __popc(mask);
+                   });
+    if ((threadIdx.x & 31) == 0) {
+        row_cnt[i] = cnt;
+        atomicMax(&stats->max_row, cnt);
+        if (cnt > cap) atomicOr(&stats->err, 4);
+    }
+}
+
+// Row i's slab, staged in shared memory, rank-sorted into col (the j of a
+// row are distinct: rank(v) = #{m : buf[m] < v}).
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+sort_rows_kernel(const int *__restrict__ tmp, int cap, int n, const int32_t *__restrict__ row_ptr,
+                 int32_t *__restrict__ col)
+{
+    extern __shared__ int smem[];
+    const int wib = threadIdx.x >> 5;
+    const int i = blockIdx.x * kWarpsPerBlock + wib;
+    if (i >= n) return;
+    const int lane = threadIdx.x & 31;
+    int *buf = smem + size_t(wib) * cap;
+    const int start = row_ptr[i];
+    const int len = row_ptr[i + 1] - start;
+    const int *src = tmp + static_cast<size_t>(i) * cap;
+    for (int e = lane; e < len; e += 32) buf[e] = src[e];
+    __syncwarp();
+    for (int e = lane; e < len; e += 32) {
+        const int v = buf[e];
+        int r = 0;
+        int m = 0;
+        for (; m + 4 <= len; m += 4)
+            r += (buf[m] < v) + (buf[m + 1] < v) + (buf[m + 2] < v) + (buf[m + 3] < v);
+        for (; m < len; ++m) r += buf[m] < v;
+        col[start + r] = v;
+    }
+}
+
+// Slab width of the one-walk build: 1.5 times the mean full-list row of a
+// uniform system of this density, plus 32, rounded up to 32 (rows beyond it
+// make the build finish with the two-walk path); 0 -- no one-walk build --
+// above kMaxSlab, where eight slabs would not fit the sort's shared memory.
+constexpr int kMaxSlab = 4096;
+
+int slab_cap(int64_t n, const double box[3], double rs)
+{
+    const double vol = box[0] * box[1] * box[2];
+    const double mean = (vol > 0.0 ? double(n) / vol : 0.0) * (4.0 / 3.0) * 3.14159265358979 * rs * rs * rs;
+    const double c = 1.5 * mean + 32.0;
+    if (!(c <= double(kMaxSlab))) return 0;
+    return (static_cast<int>(c) + 31) & ~31;
+}
+
 }  // namespace
 
 int build_pairlist_impl(const double *q4, int64_t n, const double box[3], double rs, int half,
@@ -393,15 +465,32 @@ int build_pairlist_impl(const double *q4, int64_t n, const double box[3], double
                                        w.cell_atoms, w.pos_f);
     LJ_TRY_LAUNCH("scatter_kernel");
     const unsigned gw = unsigned((n + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    if (half)
-        count_kernel<true><<<gw, kWarpsPerBlock * 32, 0, st>>>(q4, ni, g, w.cell_of, w.cell_start,
-                                                               w.cell_atoms, w.pos_f, w.row_cnt,
-                                                               w.stats);
-    else
-        count_kernel<false><<<gw, kWarpsPerBlock * 32, 0, st>>>(q4, ni, g, w.cell_of, w.cell_start,
-                                                                w.cell_atoms, w.pos_f, w.row_cnt,
-                                                                w.stats);
-    LJ_TRY_LAUNCH("count_kernel");
+    // One walk (rows stored in slabs, then sorted into place) when the
+    // workspace holds the slabs; otherwise count, then fill (two walks).
+    const int cap_slab = slab_cap(n, box, rs);
+    const size_t base_bytes = carve_bytes(n, g.ncell);
+    int *slabs = nullptr;
+    if (cap_slab > 0 && ws_bytes >= base_bytes + 256 + size_t(n) * size_t(cap_slab) * sizeof(int))
+        slabs = reinterpret_cast<int *>((reinterpret_cast<uintptr_t>(ws) + base_bytes + 255) & ~uintptr_t(255));
+    if (slabs) {
+        if (half)
+            walk_store_kernel<true><<<gw, kWarpsPerBlock * 32, 0, st>>>(
+                q4, ni, g, w.cell_of, w.cell_start, w.cell_atoms, w.pos_f, slabs, cap_slab, w.row_cnt, w.stats);
+        else
+            walk_store_kernel<false><<<gw, kWarpsPerBlock * 32, 0, st>>>(
+                q4, ni, g, w.cell_of, w.cell_start, w.cell_atoms, w.pos_f, slabs, cap_slab, w.row_cnt, w.stats);
+        LJ_TRY_LAUNCH("walk_store_kernel");
+    } else {
+        if (half)
+            count_kernel<true><<<gw, kWarpsPerBlock * 32, 0, st>>>(q4, ni, g, w.cell_of, w.cell_start,
+                                                                   w.cell_atoms, w.pos_f, w.row_cnt,
+                                                                   w.stats);
+        else
+            count_kernel<false><<<gw, kWarpsPerBlock * 32, 0, st>>>(q4, ni, g, w.cell_of, w.cell_start,
+                                                                    w.cell_atoms, w.pos_f, w.row_cnt,
+                                                                    w.stats);
+        LJ_TRY_LAUNCH("count_kernel");
+    }
     rc = scan_exclusive<int, int32_t>(w.row_cnt, row_ptr, n, &w.stats->nnz, w.scan_scratch, st);
     if (rc != LJ_OK) return rc;
     ListStats hs{};
@@ -419,6 +508,16 @@ int build_pairlist_impl(const double *q4, int64_t n, const double box[3], double
         return LJ_ERR_CAPACITY;
     }
     if (hs.nnz == 0) {
+        LJ_TRY_CUDA(cudaStreamSynchronize(st));
+        return LJ_OK;
+    }
+    if (slabs && !(hs.err & 4)) {
+        const size_t smem_sort = size_t(kWarpsPerBlock) * cap_slab * sizeof(int);
+        if (smem_sort > 48 * 1024)
+            LJ_TRY_CUDA(cudaFuncSetAttribute(sort_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smem_sort)));
+        sort_rows_kernel<<<gw, kWarpsPerBlock * 32, smem_sort, st>>>(slabs, cap_slab, ni, row_ptr, col);
+        LJ_TRY_LAUNCH("sort_rows_kernel");
         LJ_TRY_CUDA(cudaStreamSynchronize(st));
         return LJ_OK;
     }
@@ -448,12 +547,22 @@ int build_pairlist_impl(const double *q4, int64_t n, const double box[3], double
     return LJ_OK;
 }
 
+// The two-walk path's workspace plus the one-walk slabs (n x slab_cap ints);
+// a workspace of only carve_bytes() selects the two-walk path.
 size_t pairlist_workspace_bytes_impl(int64_t n, const double box[3], double rs)
 {
     if (n < 0 || !box || !(rs > 0.0)) return 0;
     if (check_box(box, rs) != LJ_OK) return 256;
     const Grid g = make_grid(n, box, rs);
-    return carve_bytes(n, g.ncell);
+    return carve_bytes(n, g.ncell) + 256 + size_t(n > 0 ? n : 1) * size_t(slab_cap(n, box, rs)) * sizeof(int);
+}
+
+// The two-walk path's workspace alone.
+size_t pairlist_workspace_bytes_min_impl(int64_t n, const double box[3], double rs)
+{
+    if (n < 0 || !box || !(rs > 0.0)) return 0;
+    if (check_box(box, rs) != LJ_OK) return 256;
+    return carve_bytes(n, make_grid(n, box, rs).ncell);
 }
 
 }  // namespace lj

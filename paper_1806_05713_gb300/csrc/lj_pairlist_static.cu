@@ -26,7 +26,7 @@ namespace lj {
 int build_pairlist_impl(const double *q4, int64_t n, const double box[3], double rs, int half,
                         int32_t *row_ptr, int32_t *col, int64_t cap, void *ws, size_t ws_bytes,
                         int64_t *nnz_out, int64_t *max_row_out, cudaStream_t st);
-size_t pairlist_workspace_bytes_impl(int64_t n, const double box[3], double rs);
+size_t pairlist_workspace_bytes_min_impl(int64_t n, const double box[3], double rs);
 }  // namespace lj
 
 static __device__ __align__(256) unsigned char lj_static_scratch[LJ_STATIC_SCRATCH_BYTES];
@@ -46,7 +46,8 @@ extern "C" int lj_build_pairlist_static(const double *q4_dev, int64_t n, const d
     if (max_row_out) *max_row_out = 0;
     if (n < 0 || !box || !nnz_out) return LJ_ERR_ARG;
     if (n > LJ_STATIC_MAX_ATOMS) return LJ_ERR_CAPACITY;
-    const size_t need = lj::pairlist_workspace_bytes_impl(n, box, r_search);
+    // the builder's two-walk path (no row slabs) fits the static scratch
+    const size_t need = lj::pairlist_workspace_bytes_min_impl(n, box, r_search);
     if (need > LJ_STATIC_SCRATCH_BYTES) return LJ_ERR_CAPACITY;
     int dev = 0;
     LJ_TRY_CUDA(cudaGetDevice(&dev));

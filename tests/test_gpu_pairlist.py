@@ -96,6 +96,21 @@ def test_isolated_atoms_give_empty_rows(cuda_lib):
     assert pl.nnz == 0 and np.all(rp == 0)
 
 
+@pytest.mark.parametrize("half", [True, False])
+def test_dense_cluster_overflows_the_row_slabs(cuda_lib, oracle_lib, half):
+    """A gas with a dense cluster: the cluster's rows exceed the one-walk
+    builder's slab (sized from the mean density), so the build finishes with
+    the two-walk path; the list is still the oracle's."""
+    rng = np.random.default_rng(9)
+    box = np.array([15.0, 15.0, 15.0])
+    gas = rng.random((1500, 3)) * box
+    cluster = 7.0 + rng.random((600, 3)) * 2.2
+    q = np.zeros((2100, 4))
+    q[:, :3] = np.concatenate([gas, cluster])
+    pl = _assert_same(cuda_lib, oracle_lib, q, box, 3.3, half)
+    assert pl.max_row > 400
+
+
 def test_errors(cuda_lib):
     lj = cuda_lib
     s = inputs.workload_small()
