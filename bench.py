@@ -576,7 +576,7 @@ def extra_adjoint(lj, dev, stream, flush):
     Ft = torch.zeros_like(q)
     lj.lj_force(q, Ft, big, 1.0, reps[0].rc, box, 1.0, 1.0)
     res = {"replicas": len(reps), "atoms": int(q.shape[0]), "pairs": off // 2}
-    for name, prec in (("fp64", lj.LJ_FP64), ("mixed", lj.LJ_MIXED)):
+    for name, prec in (("fp64", lj.LJ_FP64), ("mixed", lj.LJ_MIXED), ("dfloat", lj.LJ_DFLOAT)):
         eps = torch.tensor(1.1, dtype=torch.float64, device=dev, requires_grad=True)
         sig = torch.tensor(0.97, dtype=torch.float64, device=dev, requires_grad=True)
 

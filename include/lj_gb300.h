@@ -479,8 +479,10 @@ size_t lj_force_vjp_workspace_bytes(int64_t n, int precision);
  *                       dLoss/dsigma = sum dg/dsigma (d.w).
  * Full lists gather per row without atomics (deterministic); half lists
  * scatter dLoss/dq_j with FP64 atomics.  The scalar sums use a fixed-order
- * reduction.  precision: LJ_FP64 or LJ_MIXED (FP32 pair arithmetic,
- * compensated FP32 sums, FP64 outputs).  Asynchronous.  Errors as lj_force.
+ * reduction.  precision: LJ_FP64, LJ_MIXED (FP32 pair arithmetic,
+ * compensated FP32 sums, FP64 outputs) or LJ_DFLOAT (double-float pair
+ * arithmetic on the FP32 pipe, FP64-class results; needs |dLoss/dF| within
+ * the FP32 range).  Asynchronous.  Errors as lj_force.
  */
 int lj_force_vjp(const double *q4_dev, const double *gradF4_dev, int64_t n,
                  const int32_t *row_ptr_dev, const int32_t *col_dev, int64_t nnz, int half,

@@ -349,6 +349,11 @@ int check_force_args(const double *q4, const double *p4, int64_t n, const int32_
                      const int32_t *col, int64_t nnz, double r_cut, const double box[3], double eps,
                      double sigma, double dt);
 
+size_t vjp_dfloat_extra_bytes(int64_t n);
+int vjp_dfloat(const double *q4, const double *R4, int n, const int *row_ptr, const int *col,
+               int half, double rc, const double box[3], double eps, double sigma, double *gq4,
+               double *partial, int blocks, void *extra, cudaStream_t st);
+
 }  // namespace lj
 
 extern "C" size_t lj_force_vjp_workspace_bytes(int64_t n, int precision)
@@ -357,6 +362,7 @@ extern "C" size_t lj_force_vjp_workspace_bytes(int64_t n, int precision)
     size_t bytes = 2 * blocks * sizeof(double) + 256;
     if (precision == LJ_MIXED) bytes += size_t(n > 0 ? n : 1) * sizeof(uint4) + 256;
     if (precision == LJ_FP64) bytes += size_t(n > 0 ? n : 1) * sizeof(longlong4) + 256;
+    if (precision == LJ_DFLOAT) bytes += lj::vjp_dfloat_extra_bytes(n) + 256;
     return bytes;
 }
 
@@ -373,7 +379,7 @@ extern "C" int lj_force_vjp(const double *q4_dev, const double *gradF4_dev, int6
     if (rc != LJ_OK) return rc;
     if (!grad_eps_sigma_dev || (n > 0 && !gradF4_dev)) return LJ_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(gradF4_dev) & 31u) return LJ_ERR_ARG;
-    if (precision != LJ_FP64 && precision != LJ_MIXED) return LJ_ERR_ARG;
+    if (precision != LJ_FP64 && precision != LJ_MIXED && precision != LJ_DFLOAT) return LJ_ERR_ARG;
     if (n == 0) {
         LJ_TRY_CUDA(cudaMemsetAsync(grad_eps_sigma_dev, 0, 2 * sizeof(double), st));
         return LJ_OK;
@@ -386,7 +392,12 @@ extern "C" int lj_force_vjp(const double *q4_dev, const double *gradF4_dev, int6
     double *partial = c.take<double>(2 * size_t(blocks));
     if (half || nnz == 0)
         LJ_TRY_CUDA(cudaMemsetAsync(gradq4_dev, 0, size_t(n) * 4 * sizeof(double), st));
-    if (precision == LJ_FP64) {
+    if (precision == LJ_DFLOAT) {
+        void *extra = c.take<char>(vjp_dfloat_extra_bytes(n));
+        rc = vjp_dfloat(q4_dev, gradF4_dev, ni, row_ptr_dev, col_dev, half, r_cut, box, eps, sigma,
+                        gradq4_dev, partial, blocks, extra, st);
+        if (rc != LJ_OK) return rc;
+    } else if (precision == LJ_FP64) {
         const Fp64Params P = make_fp64_params(box, 1.0, r_cut, eps, sigma);
         const FixParams F = make_fix_params(box);
         const VjpCoef C = make_coef(eps, sigma);

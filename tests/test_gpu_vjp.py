@@ -137,3 +137,65 @@ def test_autograd_mixed_vs_oracle(cuda_lib, oracle_lib):
     oq, oe, os_ = oracle_lib.force_vjp(s.q, R, rp, col, False, s.rc, s.box, EPS_M, SIG_M)
     assert np.max(np.abs(gq - oq)) <= 1e-4 * np.max(np.abs(oq))
     assert abs(ge - oe) <= 1e-4 * abs(oe) and abs(gs - os_) <= 1e-4 * abs(os_)
+
+
+# --------------------------------------------------------------------------
+# The double-float form, held to the FP64 tolerances
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("half", [True, False])
+@pytest.mark.parametrize("stretch", [(1.0, 1.0, 1.0), (1.0, 1.1, 1.2)])
+def test_vjp_dfloat_matches_oracle(cuda_lib, oracle_lib, half, stretch):
+    lj = cuda_lib
+    s = inputs.fcc_system(8, 1.0, 0.1, seed=4)
+    st = np.array(stretch)
+    s.q[:, :3] *= st
+    s.box = s.box * st
+    q, pl, rp, col, _ = _setup(lj, oracle_lib, s, half)
+    R = np.random.default_rng(3).normal(size=(s.n, 4))
+    gq, ges = lj.lj_force_vjp(q, to_dev(R), pl, s.rc, s.box, EPS_M, SIG_M, lj.LJ_DFLOAT)
+    torch.cuda.synchronize()
+    want_q, want_e, want_s = oracle_lib.force_vjp(s.q, R, rp, col, half, s.rc, s.box, EPS_M, SIG_M)
+    got = gq.cpu().numpy()
+    assert np.all(got[:, 3] == 0.0)
+    assert np.max(np.abs(got[:, :3] - want_q)) <= 1e-11 * np.max(np.abs(want_q))
+    e, sg = ges.cpu().numpy()
+    assert abs(e - want_e) <= 1e-10 * max(1.0, abs(want_e))
+    assert abs(sg - want_s) <= 1e-10 * max(1.0, abs(want_s))
+
+
+def test_vjp_dfloat_close_pair_takes_fp64(cuda_lib, oracle_lib):
+    """A pair at 0.02 sigma (u^8 beyond the double-float range) and pairs on
+    the cutoff take the FP64 formulas."""
+    lj = cuda_lib
+    q4 = np.zeros((6, 4))
+    q4[:, :3] = [[5.0, 5.0, 5.0], [5.02, 5.0, 5.0], [6.1, 5.3, 5.0], [5.0, 6.2, 5.9],
+                 [12.0, 12.0, 12.0], [15.0, 12.0, 12.0]]
+    s = inputs.LJSystem(q=q4, box=np.array([20.0] * 3), rho=0.0)
+    for half in (True, False):
+        q, pl, rp, col, _ = _setup(lj, oracle_lib, s, half)
+        R = np.random.default_rng(8).normal(size=(s.n, 4))
+        gq, ges = lj.lj_force_vjp(q, to_dev(R), pl, s.rc, s.box, EPS_M, SIG_M, lj.LJ_DFLOAT)
+        want_q, want_e, want_s = oracle_lib.force_vjp(s.q, R, rp, col, half, s.rc, s.box,
+                                                      EPS_M, SIG_M)
+        got = gq.cpu().numpy()[:, :3]
+        assert np.all(np.isfinite(got))
+        assert np.max(np.abs(got - want_q)) <= 1e-11 * np.max(np.abs(want_q))
+        e, sg = ges.cpu().numpy()
+        assert abs(e - want_e) <= 1e-10 * max(1.0, abs(want_e))
+        assert abs(sg - want_s) <= 1e-10 * max(1.0, abs(want_s))
+
+
+def test_autograd_dfloat_vs_oracle(cuda_lib, oracle_lib):
+    lj = cuda_lib
+    s = inputs.fcc_system(16, 1.0, 0.1, seed=1)
+    q, pl, rp, col, Ft = _setup(lj, oracle_lib, s, False)
+    Ft_dev = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
+    Ft_dev[:, :3] = torch.from_numpy(Ft).cuda()
+    loss, gq, ge, gs = _loss_and_grads(lj, q, pl, s, Ft_dev, lj.LJ_DFLOAT)
+    Fm = oracle_lib.forces(s.q, rp, col, False, s.rc, s.box, EPS_M, SIG_M)
+    R = 2.0 * (Fm - Ft) / Fm.size
+    oq, oe, os_ = oracle_lib.force_vjp(s.q, R, rp, col, False, s.rc, s.box, EPS_M, SIG_M)
+    assert abs(loss - np.mean((Fm - Ft) ** 2)) <= 1e-11 * loss
+    assert np.max(np.abs(gq - oq)) <= 1e-10 * np.max(np.abs(oq))
+    assert abs(ge - oe) <= 1e-9 * abs(oe) and abs(gs - os_) <= 1e-9 * abs(os_)
