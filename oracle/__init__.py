@@ -5,7 +5,9 @@ anything here; only the tests, the smoke check and the benchmark's CPU
 baseline do.  See ``lj_oracle.c`` for the passages of the paper each function
 follows and the readings taken where the paper is silent.
 
-Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
+Parity status of each function (what pins it, in ``tests/test_oracle_*.py``;
+``test_oracle_properties.py`` repeats the list, force, momentum, translation
+and force-shifted pins on random gases in random boxes with hypothesis):
 
 * pairlist (brute, cells): pinned -- the two independent routes agree as
   sets; mean row length against the closed-form sphere volume; the paper's
