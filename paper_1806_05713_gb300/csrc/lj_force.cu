@@ -335,6 +335,11 @@ int force_queue_fp64(const double *q4, double *p4, int n, const int *row_ptr, co
                      int half, const double box[3], double dt, double rc, double eps, double sigma,
                      int sched, void *ws, size_t ws_bytes, cudaStream_t st);
 
+int force_fixed_refill_fp64(const double *q4, const longlong4 *X, double *p4, int n,
+                            const int *row_ptr, const int *col, int half, const double box[3],
+                            double dt, double rc, double eps, double sigma, int sched, void *ws,
+                            size_t ws_bytes, cudaStream_t st);
+
 size_t dfloat_record_bytes(int64_t n);
 int force_dfloat(const double *q4, double *p4, int n, const int *row_ptr, const int *col, int half,
                  const double box[3], double dt, double rc, double eps, double sigma, int tpi,
@@ -387,6 +392,9 @@ bool valid_schedule(int s, int precision)
 {
     const int t = s & 63;
     const bool pow2 = t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32;
+    if ((s & LJ_SCHED_FIXED) && (s & LJ_SCHED_REFILL))
+        return precision == LJ_FP64 && (s & ~(LJ_SCHED_FIXED | LJ_SCHED_REFILL | 63)) == 0 &&
+               (t == 4 || t == 8);
     if (s & LJ_SCHED_QUEUE)
         return precision == LJ_FP64 && (s & ~(LJ_SCHED_QUEUE | 63)) == 0 && (t <= 8) && (t == 0 || pow2);
     if (s & LJ_SCHED_REFILL)
@@ -442,7 +450,7 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
         return force_queue_fp64(q4, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma, tpi,
                                 W.counter, 256, st);
     }
-    if (tpi & LJ_SCHED_REFILL) {
+    if ((tpi & LJ_SCHED_REFILL) && !(tpi & LJ_SCHED_FIXED)) {
         if (precision != LJ_FP64) return LJ_ERR_ARG;
         return force_refill_fp64(q4, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma, tpi,
                                  W.counter, 256, st);
@@ -463,6 +471,9 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
         longlong4 *X = static_cast<longlong4 *>(W.rec);
         fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4, ni, F, X);
         LJ_TRY_LAUNCH("fixed_prepass_kernel");
+        if (tpi & LJ_SCHED_REFILL)
+            return force_fixed_refill_fp64(q4, X, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma,
+                                           tpi, W.counter, 256, st);
         if (tpi & LJ_SCHED_COMPACT) {
             switch (tpi & 63) {
                 case 4: return launch_compact<4>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "lj_fixed.cuh"
 #include "lj_rows.cuh"
 
 namespace lj {
@@ -164,6 +165,129 @@ force_refill_kernel(const double *__restrict__ q4, double *__restrict__ p4, int 
     }
 }
 
+// The group-refill walk with the exact fixed-point displacement of
+// LJ_SCHED_FIXED (LJ_SCHED_FIXED | LJ_SCHED_REFILL | t): a group's row
+// switch costs integer loads only (no FP64 set-up), so refilling the groups
+// of a warp as their rows end takes the rows' unequal lengths off the FP64
+// pipe.  p_i is handed to L2 per lane and component with FP64 atomics for
+// both list kinds (so a full list's rounding order varies between calls).
+template <int TPI>
+__global__ void __launch_bounds__(kRefillThreads)
+force_fixed_refill_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
+                          double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
+                          const int *__restrict__ col, Fp64Params P, FixParams F, int half,
+                          unsigned *__restrict__ counter)
+{
+    constexpr int G = 32 / TPI;
+    constexpr int kChunk = 4 * G;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (TPI - 1);
+    const int leader = lane & ~(TPI - 1);
+    const unsigned below_leader = (1u << leader) - 1u;
+    int chunk_next = 0, chunk_end = 0;   // warp-uniform
+    bool exhausted = false;              // warp-uniform
+    int row = -1, k = 0, ke = 0;         // group-uniform
+    long long xi = 0, yi = 0, zi = 0;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    while (true) {
+        bool need = k >= ke;
+        if (need && row >= 0) {
+            double *pi = p4 + 4 * static_cast<int64_t>(row);
+            atomicAdd(pi + 0, ax);
+            atomicAdd(pi + 1, ay);
+            atomicAdd(pi + 2, az);
+            row = -1;
+        }
+        unsigned want = __ballot_sync(0xffffffffu, need && sub == 0);
+        while (want && !exhausted) {
+            if (chunk_next >= chunk_end) {
+                unsigned c = 0;
+                if (lane == 0) c = atomicAdd(counter, static_cast<unsigned>(kChunk));
+                c = __shfl_sync(0xffffffffu, c, 0);
+                if (c >= static_cast<unsigned>(n)) {
+                    exhausted = true;
+                    break;
+                }
+                chunk_next = static_cast<int>(c);
+                chunk_end = min(n, chunk_next + kChunk);
+            }
+            const int avail = chunk_end - chunk_next;
+            const int rank = __popc(want & below_leader);
+            if (need && rank < avail) {
+                row = chunk_next + rank;
+                k = row_ptr[row];
+                ke = row_ptr[row + 1];
+                load_fixed(X, row, xi, yi, zi);
+                ax = ay = az = 0.0;
+                need = false;
+            }
+            chunk_next += min(avail, __popc(want));
+            want = __ballot_sync(0xffffffffu, need && sub == 0);
+        }
+        if (!__any_sync(0xffffffffu, k < ke)) {
+            if (exhausted) break;
+            continue;  // only empty rows were handed out: hand them in, refill
+        }
+        const int kk = k + sub;
+        const bool valid = kk < ke;
+        const int j = valid ? col[kk] : (row >= 0 ? row : 0);
+        long long xj, yj, zj;
+        load_fixed(X, j, xj, yj, zj);
+        double dx, dy, dz, r2;
+        const bool in = fixed_entry(q4, xi, yi, zi, xj, yj, zj, valid, row >= 0 ? row : 0, j, P, F,
+                                    0xffffffffu, dx, dy, dz, r2);
+        if (__any_sync(0xffffffffu, in)) {
+            const double w = rcp_fp64_fixed(in ? r2 : 1.0, 0xffffffffu);
+            const double w2 = w * w;
+            const double w4 = w2 * w2;
+            const double w3 = w2 * w;
+            const double fn = w4 * fma(P.B, w3, -P.A);  // -df: p_i -= fn d, p_j += fn d
+            if (in) {
+                if (half) {
+                    const double fx = fn * dx, fy = fn * dy, fz = fn * dz;
+                    double *pj = p4 + 4 * static_cast<int64_t>(j);
+                    atomicAdd(pj + 0, fx);
+                    atomicAdd(pj + 1, fy);
+                    atomicAdd(pj + 2, fz);
+                    ax -= fx;
+                    ay -= fy;
+                    az -= fz;
+                } else {
+                    ax = fma(-fn, dx, ax);
+                    ay = fma(-fn, dy, ay);
+                    az = fma(-fn, dz, az);
+                }
+            }
+        }
+        if (k < ke) k += TPI;
+    }
+}
+
+template <int TPI>
+int launch_fixed_refill(const double *q4, const longlong4 *X, double *p4, int n, const int *rp,
+                        const int *col, int half, const Fp64Params &P, const FixParams &F,
+                        unsigned *counter, cudaStream_t st)
+{
+    static int max_blocks = 0;
+    if (max_blocks == 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, force_fixed_refill_kernel<TPI>,
+                                                          kRefillThreads, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 2;
+        max_blocks = per_sm * num_sms();
+    }
+    constexpr int G = 32 / TPI;
+    constexpr int warps_per_block = kRefillThreads / 32;
+    const long long want_warps = std::max<long long>(1, n / (G * kRowsPerGroupTarget));
+    int blocks = static_cast<int>((want_warps + warps_per_block - 1) / warps_per_block);
+    blocks = std::max(std::min(blocks, max_blocks), std::min(max_blocks, 2 * num_sms()));
+    force_fixed_refill_kernel<TPI><<<blocks, kRefillThreads, 0, st>>>(q4, X, p4, n, rp, col, P, F,
+                                                                      half, counter);
+    LJ_TRY_LAUNCH("force_fixed_refill_kernel");
+    return LJ_OK;
+}
+
 template <int TPI, bool HALF, int U>
 int launch_refill(const double *q4, double *p4, int n, const int *rp, const int *col,
                   const Fp64Params &P, unsigned *counter, cudaStream_t st)
@@ -191,6 +315,25 @@ int launch_refill(const double *q4, double *p4, int n, const int *rp, const int 
 }  // namespace
 
 size_t force_refill_workspace_bytes() { return 256; }
+
+// sched: LJ_SCHED_FIXED | LJ_SCHED_REFILL | tpi (tpi 4 or 8); X: the
+// fixed-point positions (already written by the caller's pre-pass).
+int force_fixed_refill_fp64(const double *q4, const longlong4 *X, double *p4, int n,
+                            const int *row_ptr, const int *col, int half, const double box[3],
+                            double dt, double rc, double eps, double sigma, int sched, void *ws,
+                            size_t ws_bytes, cudaStream_t st)
+{
+    if (!ws || ws_bytes < force_refill_workspace_bytes()) return LJ_ERR_CAPACITY;
+    const Fp64Params P = make_fp64_params(box, dt, rc, eps, sigma);
+    const FixParams F = make_fix_params(box);
+    unsigned *counter = static_cast<unsigned *>(ws);
+    LJ_TRY_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+    switch (sched & 63) {
+        case 4: return launch_fixed_refill<4>(q4, X, p4, n, row_ptr, col, half, P, F, counter, st);
+        case 8: return launch_fixed_refill<8>(q4, X, p4, n, row_ptr, col, half, P, F, counter, st);
+        default: return LJ_ERR_ARG;
+    }
+}
 
 // sched: LJ_SCHED_REFILL | tpi (tpi 0 or 1: one lane per row), optionally
 // | LJ_SCHED_SWP2 for two entries per lane and iteration.

@@ -15,7 +15,7 @@ FP64_TOL = 1e-12
 MIXED_TOL = 1e-5
 SCHEDULES = [1, 2, 4, 8, 16, 32, 132, 136, 144, 64, 68, 72, 196, 200, 257, 258, 260, 264, 520,
              644, 648, 656, 1028, 1032, 1040, 1156, 1160, 1168, 1672, 1544, 2052, 2056, 2064, 2568,
-             4100, 4104, 4112, 4616, 2180, 2184, 2192]
+             4100, 4104, 4112, 4616, 2180, 2184, 2192, 2116, 2120]
 # 128|t software-pipelined, 64|t group-refill, 256|t lane-queue, 512|... length-sorted rows,
 # 1024|... image-selected displacement, 2048|... exact fixed-point displacement,
 # 4096|... fixed point with the margin entries compacted away; 2048|128|t fixed point,
