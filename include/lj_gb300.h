@@ -82,7 +82,10 @@ extern "C" {
  * soon as its own ends (rows are handed to warps in chunks from a counter in
  * the workspace), so no group waits for a longer row of its warp; a
  * persistent grid of one launch.  Half lists add each lane's partial sums to
- * p_i with FP64 atomics. */
+ * p_i with FP64 atomics.  With LJ_SCHED_FIXED (t = 4 or 8): the same over
+ * the exact fixed-point displacement; both list kinds then add each lane's
+ * partial sums to p_i with atomics (the full list's sums are then not
+ * deterministic). */
 #define LJ_SCHED_REFILL 64
 /* LJ_SCHED_SWP2 | tpi (tpi = 4, 8 or 16, or with LJ_SCHED_REFILL | 1, 4, 8;
  * FP64 only): software pipelining, the paper's section "Software

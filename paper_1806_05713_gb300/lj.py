@@ -369,7 +369,8 @@ def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float
                        S | I | 8, S | I | 16, F | 4, F | 8, F | 16, S | F | 8, C | 4, C | 8, C | 16,
                        LJ_SCHED_REFILL | W | 8, LJ_SCHED_QUEUE | 8]
                       if precision == LJ_FP64 else
-                      [4, 8, 16, S | 4, S | 8, S | 16] if precision == LJ_DFLOAT else
+                      [W | 8, W | 4, W | 16, S | W | 8, 4, 8, 16, S | 4, S | 8]
+                      if precision == LJ_DFLOAT else
                       [2, 4, 8, 16, S | 4, S | 8, S | 16])
     n = plist.n
     scratch = torch.zeros((n, 4), dtype=torch.float64, device=q4.device)
