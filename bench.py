@@ -14,8 +14,9 @@ so each step credits 100 * nnz(half list).
 
 Timing: inputs resident in HBM; L2 flushed (256 MiB write) before every
 step, outside the timed events; each step timed with CUDA events on the
-launching stream; W warm-up steps; the max over ranks of the summed step
-times.  `e2e` repeats the step with the positions and momenta copied from
+launching stream (three events a step: start, list built, end; the force
+call's duration is the span after the list over the 100 calls); W warm-up
+steps; the max over ranks of the summed step times.  `e2e` repeats the step with the positions and momenta copied from
 pinned host memory and the momenta copied back inside the timed region.
 
 `--impl reference` times the CPU oracle (the plain double-precision C
@@ -330,25 +331,18 @@ def main():
     nnz = pl.nnz
     n_cut = count_in_cutoff(q, pl, box, s.rc)
 
-    def one_step(ev):
+    def one_step(list_done):
         lj.lj_build_pairlist(q, box, s.rs, True, reuse=pl)
-        ev[1].record(stream)
+        list_done.record(stream)
         for c in range(FORCE_CALLS):
-            ev[2][c].record(stream)
             force()
-            ev[3][c].record(stream)
 
     def new_events():
-        return ([torch.cuda.Event(enable_timing=True) for _ in range(2)],
-                [torch.cuda.Event(enable_timing=True) for _ in range(2)],
-                [torch.cuda.Event(enable_timing=True) for _ in range(FORCE_CALLS)],
-                [torch.cuda.Event(enable_timing=True) for _ in range(FORCE_CALLS)])
+        return [torch.cuda.Event(enable_timing=True) for _ in range(3)]
 
     for _ in range(args.warmup):
         flush.zero_()
-        ev = new_events()
-        ev[0][0].record(stream)
-        one_step((None, ev[1][0], ev[2], ev[3]))
+        one_step(new_events()[1])
     torch.cuda.synchronize()
 
     step_ms, list_ms, force_ms = [], [], []
@@ -359,15 +353,15 @@ def main():
     with ClockSampler(dev.index if dev.index is not None else 0) as clk:
         for _ in range(args.steps):
             flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ev = new_events()
+            e0, e_list, e1 = new_events()
             e0.record(stream)
-            one_step((None, ev[1][0], ev[2], ev[3]))
+            one_step(e_list)
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
-            list_ms.append(e0.elapsed_time(ev[1][0]))
-            force_ms.extend(a.elapsed_time(b) for a, b in zip(ev[2], ev[3]))
+            list_ms.append(e0.elapsed_time(e_list))
+            # the average force call (fixed-point pre-pass + force kernel)
+            force_ms.append(e_list.elapsed_time(e1) / FORCE_CALLS)
         torch.cuda.synchronize()
     launches = lib.lj_kernel_launch_count() - launches0
     if world > 1:
@@ -597,7 +591,9 @@ def extra_md(lj, dev, stream):
     """Velocity Verlet on the N = 119,164 workload with random initial momenta
     (T ~ 1): one drift and one force call per step, the list rebuilt by the
     fastest-atom bookkeeping rule; reports steps/s and pairs/s including the
-    rebuilds, with the FP64 and the double-float force."""
+    rebuilds, with the FP64 and the double-float force.  The default driver
+    queues steps through lj_md_steps (validity test on the device); the
+    host-checked loop (one host read per step) is timed beside it."""
     import torch
     from paper_1806_05713_gb300 import inputs
     from paper_1806_05713_gb300.md import VelocityVerlet
@@ -606,10 +602,12 @@ def extra_md(lj, dev, stream):
     g[:, 3] = 0.0
     g[:, :3] -= g[:, :3].mean(axis=0)
     res = {"n_atoms": s.n, "dt": 0.005}
-    for name, prec in (("fp64", lj.LJ_FP64), ("dfloat", lj.LJ_DFLOAT)):
+    for name, prec, driver in (("fp64", lj.LJ_FP64, "device"), ("dfloat", lj.LJ_DFLOAT, "device"),
+                               ("fp64_host_driver", lj.LJ_FP64, "host"),
+                               ("dfloat_host_driver", lj.LJ_DFLOAT, "host")):
         q = torch.from_numpy(s.q).to(dev)
         p = torch.from_numpy(g).to(dev)
-        vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, 0.005, precision=prec)
+        vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, 0.005, precision=prec, driver=driver)
         vv.run(20)
         e0 = vv.kinetic_energy() + vv.potential_energy()
         r0 = vv.rebuilds

@@ -353,6 +353,45 @@ int lj_energy(const double *q4_dev, int64_t n, const int32_t *row_ptr_dev,
 int lj_drift(double *q4_dev, const double *p4_dev, int64_t n, double dt, const double box[3],
              double *max_disp2_dev, void *stream);
 
+/* Bookkeeping state of lj_md_steps, in device memory (caller-owned, 8-byte
+ * aligned).  Zero all of it whenever the list is (re)built. */
+typedef struct lj_md_state {
+    double moved;          /* sum over the steps since the build of the largest |dt p| */
+    double max_disp2;      /* scratch: the current step's largest |dt p|^2 */
+    double last_disp2;     /* the largest |dt p|^2 of the last step that moved the atoms */
+    int32_t stale;         /* 1 once 2 moved >= r_search - r_cut (see lj_md_steps) */
+    int32_t steps;         /* steps completed (drift and kick) since the state was zeroed */
+    uint32_t blocks_done;  /* scratch of the drift kernel */
+    int32_t reserved;
+} lj_md_state;
+
+/*
+ * Enqueue `steps` leapfrog steps of velocity Verlet (unit mass) with the
+ * bookkeeping method of section "Verlet List and Bookkeeping Method", the
+ * validity test taken on the device so that no step waits for the host.
+ * Each step, unless state->stale is already set:
+ *   1. the drift of lj_drift (q += dt p, wrapped) and its largest |dt p|^2;
+ *   2. moved += sqrt(that); if 2 moved >= r_search - r_cut the list may have
+ *      lost a pair: stale = 1 and row_ptr_dev[0..n] is zeroed -- the list is
+ *      emptied on the device, so the kick of this step and every later step
+ *      of the call do nothing; otherwise steps += 1;
+ *   3. the kick p += impulses(q) of lj_force with this dt.
+ * After the call the host reads the state: `steps` steps are complete; if
+ * stale is 1, the positions are one drift ahead of the momenta -- rebuild
+ * the list from q4_dev (lj_build_pairlist), zero the state and apply the
+ * kick that step owes with lj_force (same dt), then continue.  The force
+ * arguments (precision, tpi, workspace) are those of lj_force and are all
+ * checked before anything is enqueued.  Asynchronous; one small kernel for
+ * the drift and bookkeeping, one for the emptying, and lj_force's launches,
+ * per step.  Errors: LJ_ERR_ARG (also r_search <= r_cut, steps < 0, state
+ * NULL or not 8-byte aligned), LJ_ERR_BOX, LJ_ERR_CAPACITY, LJ_ERR_CUDA.
+ */
+int lj_md_steps(double *q4_dev, double *p4_dev, int64_t n, int32_t *row_ptr_dev,
+                const int32_t *col_dev, int64_t nnz, int half, double dt, double r_cut,
+                double r_search, const double box[3], double eps, double sigma, int precision,
+                int tpi, int64_t steps, lj_md_state *state_dev, void *workspace_dev,
+                size_t workspace_bytes, void *stream);
+
 /* ======================================================================== */
 /* Batched systems: many independent LJ systems in one persistent launch    */
 /* (the Algorithm 3 loop of each system, work-shared across the GPU)        */

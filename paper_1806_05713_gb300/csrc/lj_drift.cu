@@ -21,9 +21,9 @@ constexpr int kDriftThreads = 256;
 // q += dt p with round-to-nearest double operations (no fused multiply-add),
 // then one periodic wrap per axis; *max_d2 = max over atoms of |dt p|^2 (as
 // the ordered bit pattern of a non-negative double).
-__global__ void __launch_bounds__(kDriftThreads)
-drift_kernel(double *__restrict__ q4, const double *__restrict__ p4, int n, double dt, double Lx,
-             double Ly, double Lz, unsigned long long *__restrict__ max_d2)
+__device__ __forceinline__ void drift_block(double *__restrict__ q4, const double *__restrict__ p4,
+                                            int n, double dt, double Lx, double Ly, double Lz,
+                                            unsigned long long *__restrict__ max_d2)
 {
     __shared__ double red[kDriftThreads / 32];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -54,6 +54,54 @@ drift_kernel(double *__restrict__ q4, const double *__restrict__ p4, int n, doub
     }
 }
 
+__global__ void __launch_bounds__(kDriftThreads)
+drift_kernel(double *__restrict__ q4, const double *__restrict__ p4, int n, double dt, double Lx,
+             double Ly, double Lz, unsigned long long *__restrict__ max_d2)
+{
+    drift_block(q4, p4, n, dt, Lx, Ly, Lz, max_d2);
+}
+
+// One step of lj_md_steps, part 1: nothing once the state is stale (every
+// block reads the flag before the last block can write it); else the
+// drift, and the block that finishes last folds the step into the state:
+// moved += sqrt(max |dt p|^2), then the validity test 2 moved < margin.
+__global__ void __launch_bounds__(kDriftThreads)
+md_drift_kernel(double *__restrict__ q4, const double *__restrict__ p4, int n, double dt, double Lx,
+                double Ly, double Lz, double margin, lj_md_state *__restrict__ S)
+{
+    if (*reinterpret_cast<volatile int32_t *>(&S->stale)) return;
+    drift_block(q4, p4, n, dt, Lx, Ly, Lz, reinterpret_cast<unsigned long long *>(&S->max_disp2));
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();  // this block's maximum before its count
+        last = atomicAdd(&S->blocks_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();  // every block's maximum is visible
+        volatile lj_md_state *V = S;
+        const double d2 = V->max_disp2;
+        const double moved = __dadd_rn(V->moved, sqrt(d2));
+        V->moved = moved;
+        V->last_disp2 = d2;
+        V->max_disp2 = 0.0;
+        V->blocks_done = 0u;
+        if (__dmul_rn(2.0, moved) >= margin)
+            V->stale = 1;
+        else
+            V->steps = V->steps + 1;
+    }
+}
+
+// Part 2: a stale list is emptied (row_ptr[0..n] = 0), so that the force
+// calls enqueued after it add nothing until the host rebuilds it.
+__global__ void __launch_bounds__(kDriftThreads)
+md_empty_kernel(int32_t *__restrict__ row_ptr, int n, const lj_md_state *__restrict__ S)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n && *reinterpret_cast<const volatile int32_t *>(&S->stale)) row_ptr[i] = 0;
+}
+
 }  // namespace
 }  // namespace lj
 
@@ -76,5 +124,37 @@ extern "C" int lj_drift(double *q4_dev, const double *p4_dev, int64_t n, double 
         q4_dev, p4_dev, static_cast<int>(n), dt, box[0], box[1], box[2],
         reinterpret_cast<unsigned long long *>(max_disp2_dev));
     LJ_TRY_LAUNCH("drift_kernel");
+    return LJ_OK;
+}
+
+extern "C" int lj_md_steps(double *q4_dev, double *p4_dev, int64_t n, int32_t *row_ptr_dev,
+                           const int32_t *col_dev, int64_t nnz, int half, double dt, double r_cut,
+                           double r_search, const double box[3], double eps, double sigma,
+                           int precision, int tpi, int64_t steps, lj_md_state *state_dev,
+                           void *workspace_dev, size_t workspace_bytes, void *stream)
+{
+    using namespace lj;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (steps < 0 || !state_dev || (reinterpret_cast<uintptr_t>(state_dev) & 7u)) return LJ_ERR_ARG;
+    if (!std::isfinite(r_search) || !(r_search > r_cut)) return LJ_ERR_ARG;
+    int t = tpi;
+    const int rc = force_check(q4_dev, p4_dev, n, row_ptr_dev, col_dev, nnz, dt, r_cut, box, eps,
+                               sigma, precision, &t, workspace_dev, workspace_bytes);
+    if (rc != LJ_OK) return rc;
+    if (n == 0 || steps == 0) return LJ_OK;
+    const int ni = static_cast<int>(n);
+    const double margin = r_search - r_cut;
+    const unsigned gd = unsigned((n + kDriftThreads - 1) / kDriftThreads);
+    const unsigned ge = unsigned((n + 1 + kDriftThreads - 1) / kDriftThreads);
+    for (int64_t s = 0; s < steps; ++s) {
+        md_drift_kernel<<<gd, kDriftThreads, 0, st>>>(q4_dev, p4_dev, ni, dt, box[0], box[1], box[2],
+                                                      margin, state_dev);
+        LJ_TRY_LAUNCH("md_drift_kernel");
+        md_empty_kernel<<<ge, kDriftThreads, 0, st>>>(row_ptr_dev, ni, state_dev);
+        LJ_TRY_LAUNCH("md_empty_kernel");
+        const int r = lj_force(q4_dev, p4_dev, n, row_ptr_dev, col_dev, nnz, half, dt, r_cut, box, eps,
+                               sigma, precision, t, workspace_dev, workspace_bytes, stream);
+        if (r != LJ_OK) return r;
+    }
     return LJ_OK;
 }

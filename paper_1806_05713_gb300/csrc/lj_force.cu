@@ -341,6 +341,7 @@ int force_fixed_refill_fp64(const double *q4, const longlong4 *X, double *p4, in
                             size_t ws_bytes, cudaStream_t st);
 
 size_t dfloat_record_bytes(int64_t n);
+bool dfloat_params_ok(const double box[3], double dt, double rc, double eps, double sigma);
 int force_dfloat(const double *q4, double *p4, int n, const int *row_ptr, const int *col, int half,
                  const double box[3], double dt, double rc, double eps, double sigma, int tpi,
                  const int *order, void *rec_ws, cudaStream_t st);
@@ -429,21 +430,37 @@ size_t force_workspace_bytes_impl(int64_t n, int precision)
     return c.used + 256;
 }
 
-int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, const int32_t *col,
-               int64_t nnz, int half, double dt, double rc, const double box[3], double eps,
-               double sigma, int precision, int tpi, void *ws, size_t ws_bytes, cudaStream_t st)
+// Every host-side check of lj_force, with no launch: the arguments, the
+// form, the schedule (LJ_TPI_AUTO resolved into *tpi) and the workspace.
+int force_check(const double *q4, const double *p4, int64_t n, const int32_t *row_ptr,
+                const int32_t *col, int64_t nnz, double dt, double rc, const double box[3],
+                double eps, double sigma, int precision, int *tpi, const void *ws, size_t ws_bytes)
 {
     int rcode = check_force_args(q4, p4, n, row_ptr, col, nnz, rc, box, eps, sigma, dt);
     if (rcode != LJ_OK) return rcode;
     if (precision != LJ_FP64 && precision != LJ_MIXED && precision != LJ_DFLOAT) return LJ_ERR_ARG;
     if (n == 0 || nnz == 0) return LJ_OK;
-    const int ni = static_cast<int>(n);
-    if (tpi == LJ_TPI_AUTO)
-        tpi = precision == LJ_FP64 ? (fixed_point_ok(box, rc) ? (LJ_SCHED_FIXED | 8) : (LJ_SCHED_IMAGES | 8))
-              : precision == LJ_DFLOAT ? (LJ_SCHED_SWP2 | 8) : 8;
-    if ((tpi & (LJ_SCHED_FIXED | LJ_SCHED_COMPACT)) && !fixed_point_ok(box, rc)) return LJ_ERR_ARG;
-    if (!valid_schedule(tpi, precision)) return LJ_ERR_ARG;
+    int t = *tpi;
+    if (t == LJ_TPI_AUTO)
+        t = precision == LJ_FP64 ? (fixed_point_ok(box, rc) ? (LJ_SCHED_FIXED | 8) : (LJ_SCHED_IMAGES | 8))
+            : precision == LJ_DFLOAT ? (LJ_SCHED_SWP2 | 8) : 8;
+    if ((t & (LJ_SCHED_FIXED | LJ_SCHED_COMPACT)) && !fixed_point_ok(box, rc)) return LJ_ERR_ARG;
+    if (!valid_schedule(t, precision)) return LJ_ERR_ARG;
     if (!ws || ws_bytes < force_workspace_bytes_impl(n, precision)) return LJ_ERR_CAPACITY;
+    if (precision == LJ_DFLOAT && !dfloat_params_ok(box, dt, rc, eps, sigma)) return LJ_ERR_ARG;
+    *tpi = t;
+    return LJ_OK;
+}
+
+int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, const int32_t *col,
+               int64_t nnz, int half, double dt, double rc, const double box[3], double eps,
+               double sigma, int precision, int tpi, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    const int rcode = force_check(q4, p4, n, row_ptr, col, nnz, dt, rc, box, eps, sigma, precision,
+                                  &tpi, ws, ws_bytes);
+    if (rcode != LJ_OK) return rcode;
+    if (n == 0 || nnz == 0) return LJ_OK;
+    const int ni = static_cast<int>(n);
     const ForceWs W = carve_force_ws(ws, n, precision);
     if (tpi & LJ_SCHED_QUEUE) {
         if (precision != LJ_FP64) return LJ_ERR_ARG;

@@ -51,6 +51,13 @@ int launch_dfloat_t(const double *q4, const DfRec *rec, double *p4, int n, const
 
 }  // namespace
 
+// K_e (the exponent the double-float impulses are scaled by) within range.
+bool dfloat_params_ok(const double box[3], double dt, double rc, double eps, double sigma)
+{
+    const DfParams P = make_dfloat_params(box, dt, rc, eps, sigma);
+    return P.k_exp >= -700 && P.k_exp <= 700;
+}
+
 size_t dfloat_record_bytes(int64_t n)
 {
     return sizeof(DfRec) * size_t(n > 0 ? n : 1);

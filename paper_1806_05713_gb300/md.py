@@ -4,12 +4,20 @@ Bookkeeping Method".
 
 The list is built with search length r_s = r_c + margin and reused while
 twice the accumulated fastest-atom displacement (the sum over steps of the
-largest |dt p|, reported by ``lj_drift``) stays below the margin; then it is
-rebuilt.  The kick and drift of consecutive steps are merged (leapfrog form
-of velocity Verlet), so each step is one ``lj_drift`` and one ``lj_force``
-call -- the force kernel applies the kick directly (Algorithm 1 updates the
-momenta with dt).  Host-side orchestration only: every step of the
-computation runs in the library's kernels.
+largest |dt p|) stays below the margin; then it is rebuilt.  The kick and
+drift of consecutive steps are merged (leapfrog form of velocity Verlet),
+so each step is one drift and one force call -- the force kernel applies
+the kick directly (Algorithm 1 updates the momenta with dt).
+
+Two drivers.  The plain truncation without per-step energies runs its
+steps through ``lj_md_steps``: batches of steps enqueued at once, the
+validity test taken on the device (a list whose margin is used up is
+emptied there, so the steps queued after it do nothing), and one read of
+the bookkeeping state per batch; the batch length is predicted from the
+last step's displacement so that few queued steps go unused.  The other
+cases take one ``lj_drift`` and one force call per step with the test on
+the host.  Host-side orchestration only: every step of the computation
+runs in the library's kernels.
 """
 from __future__ import annotations
 
@@ -25,17 +33,25 @@ class VelocityVerlet:
 
     def __init__(self, q4: torch.Tensor, p4: torch.Tensor, box, r_cut: float, margin: float,
                  dt: float, eps: float = 1.0, sigma: float = 1.0, precision: int = lj.LJ_FP64,
-                 tpi: int = lj.LJ_TPI_AUTO, half: bool = True, truncation: str = "plain"):
+                 tpi: int = lj.LJ_TPI_AUTO, half: bool = True, truncation: str = "plain",
+                 driver: str = "device"):
         """truncation: "plain" (Eq. (1) cut at r_c, the paper's choice) or
-        "force_shifted" (the pair force taken to zero at r_c; FP64 only)."""
+        "force_shifted" (the pair force taken to zero at r_c; FP64 only).
+        driver: "device" (batches through lj_md_steps where it applies) or
+        "host" (the validity test on the host after every drift)."""
         if truncation not in ("plain", "force_shifted"):
             raise ValueError("truncation must be 'plain' or 'force_shifted'")
+        if driver not in ("device", "host"):
+            raise ValueError("driver must be 'device' or 'host'")
+        self.driver = driver
         if truncation == "force_shifted" and precision != lj.LJ_FP64:
             raise ValueError("the force-shifted truncation is FP64 only")
         self.truncation = truncation
         self.q4, self.p4 = q4, p4
         self.box = [float(x) for x in box]
-        self.r_cut, self.margin, self.dt = float(r_cut), float(margin), float(dt)
+        self.r_cut, self.dt = float(r_cut), float(dt)
+        self.r_search = self.r_cut + float(margin)
+        self.margin = self.r_search - self.r_cut   # the margin the built list has
         self.eps, self.sigma = float(eps), float(sigma)
         self.precision, self.tpi, self.half = int(precision), int(tpi), bool(half)
         self.plist = None
@@ -47,13 +63,16 @@ class VelocityVerlet:
         self._fsws = (lj._workspace(lj.lj_force_shifted_workspace_bytes(q4.shape[0]), q4.device)
                       if truncation == "force_shifted" else None)
         self._half_kicked = False
+        self._md_state = lj.lj_md_state_new(q4.device)
+        self.max_batch = 64       # steps enqueued per read of the device state, at most
         self._rebuild()
 
     def _rebuild(self):
-        self.plist = lj.lj_build_pairlist(self.q4, self.box, self.r_cut + self.margin, self.half,
+        self.plist = lj.lj_build_pairlist(self.q4, self.box, self.r_search, self.half,
                                           reuse=self.plist)
         self.rebuilds += 1
         self.moved = 0.0
+        self._md_state.zero_()
 
     def _kick(self, h: float, energy_out: torch.Tensor | None = None):
         if self.truncation == "force_shifted":
@@ -79,6 +98,43 @@ class VelocityVerlet:
                                       self.q4.device)
         if not self._half_kicked:
             self._kick(0.5 * self.dt)              # p(t + dt/2)
+        if self.driver == "device" and energies is None and self.truncation == "plain" and steps > 1:
+            self._run_on_device(steps - 1)         # all but the last step (a half kick)
+            steps_left = 1
+        else:
+            steps_left = steps
+        self._run_host_checked(steps_left, energies)
+
+    def _run_on_device(self, steps: int):
+        """`steps` full leapfrog steps through lj_md_steps."""
+        # the device state starts from the host's bound (steps may have run host-checked)
+        self._md_state.zero_()
+        self._md_state[0] = self.moved
+        done, base, batch = 0, 0, 8
+        while done < steps:
+            k = min(batch, steps - done)
+            lj.lj_md_steps(self.q4, self.p4, self.plist, k, self.dt, self.r_cut, self.r_search,
+                           self.box, self.eps, self.sigma, self.precision, self.tpi,
+                           state=self._md_state, workspace=self.ws)
+            st = lj.lj_md_state_read(self._md_state)
+            done += st["steps"] - base
+            base = st["steps"]
+            if st["stale"]:
+                # positions one drift ahead: rebuild, then the kick that step owes
+                self._rebuild()
+                self._kick(self.dt)
+                done += 1
+                base = 0
+                self.moved = 0.0
+            else:
+                self.moved = st["moved"]
+            # steps until the margin is used up at the last step's pace, plus one
+            step = math.sqrt(st["last_disp2"])
+            left = 0.5 * self.margin - self.moved
+            batch = self.max_batch if step == 0.0 else int(min(self.max_batch, left / step + 2))
+            batch = max(1, batch)
+
+    def _run_host_checked(self, steps: int, energies: torch.Tensor | None):
         for s in range(steps):
             lj.lj_drift(self.q4, self.p4, self.dt, self.box, self.max_disp2)
             self.moved += math.sqrt(float(self.max_disp2.item()))

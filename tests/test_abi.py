@@ -110,6 +110,24 @@ def test_host_argument_checks_without_gpu():
     assert force(tpi=lj.LJ_SCHED_FIXED | 2, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG
     # empty work is a no-op that succeeds
     assert force(n=0, nnz=0) == lj.LJ_OK
+    # lj_md_steps: its own arguments, then every force check, before any launch
+
+    def md(steps=3, state=fake, rs=3.3, ws=fake, wsb=1 << 40, **k):
+        a = args(**k)
+        return L.lj_md_steps(a["q"], a["p"], a["n"], a["rp"], a["col"], a["nnz"], a["half"],
+                             a["dt"], a["rc"], rs, a["box"], a["eps"], a["sig"], a["prec"],
+                             a["tpi"], steps, state, ws, wsb, None)
+    assert md(steps=-1) == lj.LJ_ERR_ARG
+    assert md(state=None) == lj.LJ_ERR_ARG
+    assert md(state=ctypes.c_void_p(260)) == lj.LJ_ERR_ARG
+    assert md(rs=3.0) == lj.LJ_ERR_ARG
+    assert md(rs=float("nan")) == lj.LJ_ERR_ARG
+    assert md(prec=7) == lj.LJ_ERR_ARG
+    assert md(tpi=3) == lj.LJ_ERR_ARG
+    assert md(rc=6.0, rs=6.3) == lj.LJ_ERR_BOX
+    assert md(ws=None, wsb=0) == lj.LJ_ERR_CAPACITY
+    assert md(prec=2, dt=1e-250) == lj.LJ_ERR_ARG
+    assert md(steps=0) == lj.LJ_OK
 
 
 def test_workspace_sizes_are_sane():

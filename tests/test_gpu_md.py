@@ -110,3 +110,91 @@ def test_energies_from_the_force_pass(cuda_lib):
     u_last = float(U[-1])
     assert abs(u_last - vv.potential_energy(shifted=True)) <= 1e-12 * abs(u_last)
     assert torch.all(U < 0)
+
+
+def _hot_system(seed=2):
+    s = inputs.fcc_system(10, 0.8, 0.05, seed=seed)
+    p0 = np.random.default_rng(5).normal(size=(s.n, 4)) * 1.2
+    p0[:, 3] = 0.0
+    p0[:, :3] -= p0[:, :3].mean(axis=0)
+    return s, p0
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_device_driver_equals_host_driver(cuda_lib, precision):
+    """lj_md_steps (the validity test on the device, steps queued in batches)
+    against the host-checked loop: with the full list (no atomics, so every
+    kernel is deterministic) the trajectories agree bit for bit and the list
+    is rebuilt at the same steps."""
+    from paper_1806_05713_gb300.md import VelocityVerlet
+    s, p0 = _hot_system()
+    out = {}
+    for driver in ("device", "host"):
+        q, p = to_dev(s.q), to_dev(p0)
+        vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, 0.002, precision=precision, half=False,
+                            driver=driver)
+        vv.run(150)
+        vv.run(60)
+        torch.cuda.synchronize()
+        out[driver] = (q.cpu().numpy(), p.cpu().numpy(), vv.rebuilds)
+    qd, pd, rd = out["device"]
+    qh, ph, rh = out["host"]
+    assert rd == rh and rd >= 3
+    assert np.array_equal(qd, qh)
+    assert np.array_equal(pd, ph)
+
+
+def test_device_driver_half_list(cuda_lib):
+    """Half list (FP64 atomics, so sums in any order): the two drivers agree
+    to rounding and the list in use still holds every pair within r_c."""
+    from paper_1806_05713_gb300.md import VelocityVerlet
+    lj = cuda_lib
+    s, p0 = _hot_system(seed=7)
+    res = {}
+    for driver in ("device", "host"):
+        q, p = to_dev(s.q), to_dev(p0)
+        vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, 0.002, driver=driver)
+        vv.run(120)
+        torch.cuda.synchronize()
+        res[driver] = (q, p, vv)
+    q, p, vv = res["device"]
+    assert vv.rebuilds >= 3
+    dq = q.cpu().numpy()[:, :3] - res["host"][0].cpu().numpy()[:, :3]
+    dq -= s.box * np.round(dq / s.box)
+    assert np.max(np.abs(dq)) < 1e-10
+    F_old = torch.zeros_like(q)
+    lj.lj_force(q, F_old, vv.plist, 1.0, s.rc, s.box)
+    fresh = lj.lj_build_pairlist(q, s.box, s.rs, True)
+    F_new = torch.zeros_like(q)
+    lj.lj_force(q, F_new, fresh, 1.0, s.rc, s.box)
+    assert float((F_old - F_new).abs().max()) <= 1e-12 * float(F_new.abs().max())
+
+
+def test_md_steps_stale_state_does_nothing(cuda_lib):
+    """A state already marked stale: no drift, no kick, the list's rows
+    emptied; a margin used up inside the call stops the steps after it."""
+    lj = cuda_lib
+    s, p0 = _hot_system()
+    q, p = to_dev(s.q), to_dev(p0)
+    pl = lj.lj_build_pairlist(q, s.box, s.rs, True)
+    state = lj.lj_md_state_new(q.device)
+    ints = state.view(torch.int32)
+    ints[6] = 1                                   # stale
+    q0, p0d = q.clone(), p.clone()
+    lj.lj_md_steps(q, p, pl, 5, 0.002, s.rc, s.rs, s.box, state=state)
+    torch.cuda.synchronize()
+    assert torch.equal(q, q0) and torch.equal(p, p0d)
+    assert int(pl.row_ptr.abs().sum()) == 0
+    st = lj.lj_md_state_read(state)
+    assert st["stale"] == 1 and st["steps"] == 0
+    # a tiny margin: the first drift uses it up; only that drift happens
+    pl = lj.lj_build_pairlist(q, s.box, s.rs, True)
+    state = lj.lj_md_state_new(q.device)
+    lj.lj_md_steps(q, p, pl, 4, 0.002, s.rc, s.rc + 1e-6, s.box, state=state)
+    st = lj.lj_md_state_read(state)
+    assert st["stale"] == 1 and st["steps"] == 0
+    want, want_d2 = _np_drift(q0.cpu().numpy(), p0d.cpu().numpy(), 0.002, s.box)
+    assert np.array_equal(q.cpu().numpy(), want)
+    assert torch.equal(p, p0d)
+    assert st["last_disp2"] == want_d2
+    assert st["moved"] == np.sqrt(want_d2)
