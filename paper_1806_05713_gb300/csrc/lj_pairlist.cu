@@ -385,6 +385,14 @@ walk_store_kernel(const double *__restrict__ q4, int n, Grid g, const int *__res
     }
 }
 
+// row_ptr[n] = nnz, the total of the row-length scan (clamped to int32; a
+// larger total is refused on the host).
+__global__ void set_total_kernel(int32_t *__restrict__ row_end, const ListStats *__restrict__ stats)
+{
+    const int64_t t = stats->nnz;
+    *row_end = static_cast<int32_t>(t < INT32_MAX ? t : INT32_MAX);
+}
+
 // Row i's slab, staged in shared memory, rank-sorted into col (the j of a
 // row are distinct: rank(v) = #{m : buf[m] < v}).
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
@@ -493,6 +501,9 @@ int build_pairlist_impl(const double *q4, int64_t n, const double box[3], double
     }
     rc = scan_exclusive<int, int32_t>(w.row_cnt, row_ptr, n, &w.stats->nnz, w.scan_scratch, st);
     if (rc != LJ_OK) return rc;
+    // row_ptr[n] = nnz (the scan writes only the first n entries)
+    set_total_kernel<<<1, 1, 0, st>>>(row_ptr + n, w.stats);
+    LJ_TRY_LAUNCH("set_total_kernel");
     ListStats hs{};
     LJ_TRY_CUDA(cudaMemcpyAsync(&hs, w.stats, sizeof(ListStats), cudaMemcpyDeviceToHost, st));
     LJ_TRY_CUDA(cudaStreamSynchronize(st));
@@ -500,17 +511,8 @@ int build_pairlist_impl(const double *q4, int64_t n, const double box[3], double
     *nnz_out = hs.nnz;
     if (max_row_out) *max_row_out = hs.max_row;
     if (hs.nnz >= (int64_t(1) << 31) - 1) return LJ_ERR_CAPACITY;
-    // row_ptr[n] = nnz (the scan writes only the first n entries).
-    const int32_t total32 = static_cast<int32_t>(hs.nnz);
-    LJ_TRY_CUDA(cudaMemcpyAsync(row_ptr + n, &total32, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    if (hs.nnz > cap || hs.max_row > kMaxRowSmem) {
-        LJ_TRY_CUDA(cudaStreamSynchronize(st));
-        return LJ_ERR_CAPACITY;
-    }
-    if (hs.nnz == 0) {
-        LJ_TRY_CUDA(cudaStreamSynchronize(st));
-        return LJ_OK;
-    }
+    if (hs.nnz > cap || hs.max_row > kMaxRowSmem) return LJ_ERR_CAPACITY;
+    if (hs.nnz == 0) return LJ_OK;
     if (slabs && !(hs.err & 4)) {
         const size_t smem_sort = size_t(kWarpsPerBlock) * cap_slab * sizeof(int);
         if (smem_sort > 48 * 1024)
@@ -518,7 +520,6 @@ int build_pairlist_impl(const double *q4, int64_t n, const double box[3], double
                                              int(smem_sort)));
         sort_rows_kernel<<<gw, kWarpsPerBlock * 32, smem_sort, st>>>(slabs, cap_slab, ni, row_ptr, col);
         LJ_TRY_LAUNCH("sort_rows_kernel");
-        LJ_TRY_CUDA(cudaStreamSynchronize(st));
         return LJ_OK;
     }
     const int cap_row = std::max(1, hs.max_row);
@@ -542,8 +543,6 @@ int build_pairlist_impl(const double *q4, int64_t n, const double box[3], double
                                                         wpb, w.stats);
     }
     LJ_TRY_LAUNCH("fill_kernel");
-    // The copy of the host-stack total above must finish before returning.
-    LJ_TRY_CUDA(cudaStreamSynchronize(st));
     return LJ_OK;
 }
 
