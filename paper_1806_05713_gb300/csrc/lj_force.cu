@@ -12,11 +12,16 @@
 //
 // Forms:
 //  * FP64: every step in IEEE double precision.  GB300 issues FP64 at a
-//    small fraction of its FP32 rate, so the kernel spends FP64 operations
-//    only where the value needs them: the minimum-image tests and the cutoff
-//    test are integer compares of IEEE bit patterns, the division is an FP32
-//    seed plus one third-order FP64 correction, and
-//    df = u^4 (A - B u^3) with u = 1/r^2 takes five FP64 operations.
+//    small fraction of its FP32 rate, so the kernels spend FP64 operations
+//    only where the value needs them.  The default schedule (LJ_SCHED_FIXED,
+//    lj_fixed.cuh) takes the minimum-image displacement and r^2 exactly in
+//    integer fixed point and the reciprocal from a double-float seed built
+//    on the FP32 pipe plus one FP64 Newton step: 13 FP64 instructions per
+//    entry.  The older schedules (fp64_row in lj_rows.cuh) test the minimum
+//    image and the cutoff by integer compares of IEEE bit patterns and take
+//    the division as an FP32 seed plus one third-order FP64 correction.  In
+//    all of them df = u^4 (A - B u^3) with u = 1/r^2 takes five FP64
+//    operations after the reciprocal.
 //  * MIXED: a pre-pass turns each FP64 position into a 32-bit fixed-point
 //    fraction of the box side (X = floor(x 2^32 / L), computed in FP64), so
 //    X_j - X_i in wrapping integer arithmetic is the minimum-image
@@ -27,7 +32,9 @@
 //    transformations and added to the FP64 momentum once per row (head and
 //    compensation as two FP64 additions in L2); half-list p_j updates are
 //    FP64 atomics of exactly converted FP32 values.
-// In both forms a pair whose r^2 lies within a proven error band of r_c^2
+//  * DFLOAT (lj_force_dfloat.cu): the pair arithmetic in double-float on
+//    the FP32 pipe, held to the FP64 tolerance.
+// In every form a pair whose r^2 lies within a proven error band of r_c^2
 // is re-decided with the exact FP64 definition, so the set of interacting
 // pairs is the same as in double precision.
 #include <algorithm>
