@@ -402,7 +402,7 @@ __device__ __forceinline__ void fp64_fixed_row2(const double *__restrict__ q4,
             double fn[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                const double w = rcp_fp64(in[u] ? r2[u] : 1.0, gm);
+                const double w = rcp_fp64_fixed(in[u] ? r2[u] : 1.0, gm);
                 const double w2 = w * w;
                 const double w4 = w2 * w2;
                 const double w3 = w2 * w;

@@ -67,9 +67,11 @@ force_fp64_kernel(const double *__restrict__ q4, double *__restrict__ p4, int n,
 }
 
 // FP64 form with the exact fixed-point displacement (LJ_SCHED_FIXED; U = 2:
-// | LJ_SCHED_SWP2).
+// | LJ_SCHED_SWP2).  U = 1 fits six blocks an SM in 40 registers; U = 2
+// three in 74 (0.298 ms against 0.263 for U = 1 at N = 119,164: the
+// occupancy hides the FP64 latency better than the second chain).
 template <int TPI, bool HALF, int U>
-__global__ void __launch_bounds__(256, U == 1 ? 6 : 1)
+__global__ void __launch_bounds__(256, U == 1 ? 6 : 3)
 force_fixed_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
                    double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
                    const int *__restrict__ col, Fp64Params P, FixParams F,
