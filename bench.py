@@ -76,7 +76,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (1M atoms, 512-system batch, 64-replica adjoint)")
     ap.add_argument("--profile", choices=["fp64", "fp64-full", "mixed", "mixed-full", "dfloat",
-                                          "dfloat-full", "list", "vjp", "batched", "batched-dfloat"],
+                                          "dfloat-full", "list", "vjp", "vjp-dfloat", "batched",
+                                          "batched-mixed", "batched-dfloat"],
                     help="no timing: build the list and run a few calls of one kernel (for ncu)")
     ap.add_argument("--schedule", type=int, default=0,
                     help="FP64 schedule for the timed steps (0 = the library's autotuner picks)")
@@ -258,21 +259,23 @@ def run_profile(args):
     if args.profile.startswith("batched"):
         from paper_1806_05713_gb300.batch import Batch
         systems = inputs.batched_systems(nsys=64, seed=0)
-        prec = lj.LJ_DFLOAT if args.profile == "batched-dfloat" else lj.LJ_FP64
+        prec = {"batched": lj.LJ_FP64, "batched-mixed": lj.LJ_MIXED,
+                "batched-dfloat": lj.LJ_DFLOAT}[args.profile]
         b = Batch(systems, DT, prec, True, tpi=8 if prec == lj.LJ_FP64 else 4, rows_per_item=16)
         for _ in range(5):
             b.force()
         torch.cuda.synchronize()
         print(json.dumps({"profile": args.profile, "systems": len(systems), "atoms": b.total_atoms}))
         return
-    if args.profile == "vjp":
+    if args.profile.startswith("vjp"):
         half = False
     pl = lj.lj_build_pairlist(q, box, s.rs, half)
     pl = lj.lj_build_pairlist(q, box, s.rs, half, reuse=pl)
-    if args.profile == "vjp":
+    if args.profile.startswith("vjp"):
         R = torch.ones((s.n, 4), dtype=torch.float64, device="cuda")
+        prec = lj.LJ_DFLOAT if args.profile == "vjp-dfloat" else lj.LJ_FP64
         for _ in range(5):
-            lj.lj_force_vjp(q, R, pl, s.rc, box, 1.1, 0.97, lj.LJ_FP64)
+            lj.lj_force_vjp(q, R, pl, s.rc, box, 1.1, 0.97, prec)
     elif args.profile == "list":
         for _ in range(3):
             lj.lj_build_pairlist(q, box, s.rs, half, reuse=pl)
