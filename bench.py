@@ -596,7 +596,9 @@ def extra_md(lj, dev, stream):
     fastest-atom bookkeeping rule; reports steps/s and pairs/s including the
     rebuilds, with the FP64 and the double-float force.  The default driver
     queues steps through lj_md_steps (validity test on the device); the
-    host-checked loop (one host read per step) is timed beside it."""
+    host-checked loop (one host read per step) is timed beside it, and so is
+    the displacement criterion (rebuild when 2 max |q - q_build| reaches the
+    margin) beside the paper's fastest-atom bound."""
     import torch
     from paper_1806_05713_gb300 import inputs
     from paper_1806_05713_gb300.md import VelocityVerlet
@@ -605,12 +607,17 @@ def extra_md(lj, dev, stream):
     g[:, 3] = 0.0
     g[:, :3] -= g[:, :3].mean(axis=0)
     res = {"n_atoms": s.n, "dt": 0.005}
-    for name, prec, driver in (("fp64", lj.LJ_FP64, "device"), ("dfloat", lj.LJ_DFLOAT, "device"),
-                               ("fp64_host_driver", lj.LJ_FP64, "host"),
-                               ("dfloat_host_driver", lj.LJ_DFLOAT, "host")):
+    for name, prec, driver, crit in (
+            ("fp64", lj.LJ_FP64, "device", "fastest_atom"),
+            ("dfloat", lj.LJ_DFLOAT, "device", "fastest_atom"),
+            ("fp64_host_driver", lj.LJ_FP64, "host", "fastest_atom"),
+            ("dfloat_host_driver", lj.LJ_DFLOAT, "host", "fastest_atom"),
+            ("fp64_displacement_criterion", lj.LJ_FP64, "device", "displacement"),
+            ("dfloat_displacement_criterion", lj.LJ_DFLOAT, "device", "displacement")):
         q = torch.from_numpy(s.q).to(dev)
         p = torch.from_numpy(g).to(dev)
-        vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, 0.005, precision=prec, driver=driver)
+        vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, 0.005, precision=prec, driver=driver,
+                            criterion=crit)
         vv.run(20)
         e0 = vv.kinetic_energy() + vv.potential_energy()
         r0 = vv.rebuilds

@@ -357,40 +357,59 @@ int lj_drift(double *q4_dev, const double *p4_dev, int64_t n, double dt, const d
 /* Bookkeeping state of lj_md_steps, in device memory (caller-owned, 8-byte
  * aligned).  Zero all of it whenever the list is (re)built. */
 typedef struct lj_md_state {
-    double moved;          /* sum over the steps since the build of the largest |dt p| */
+    double moved;          /* the displacement bound since the build (see lj_md_steps) */
     double max_disp2;      /* scratch: the current step's largest |dt p|^2 */
     double last_disp2;     /* the largest |dt p|^2 of the last step that moved the atoms */
+    double max_dev2;       /* scratch: the current step's largest |q - q_build|^2 */
     int32_t stale;         /* 1 once 2 moved >= r_search - r_cut (see lj_md_steps) */
     int32_t steps;         /* steps completed (drift and kick) since the state was zeroed */
     uint32_t blocks_done;  /* scratch of the drift kernel */
     int32_t reserved;
 } lj_md_state;
 
+/* lj_md_steps flag: the last step of the call kicks by dt / 2 (the closing
+ * half kick of velocity Verlet). */
+#define LJ_MD_LAST_HALF_KICK 1
+
 /*
  * Enqueue `steps` leapfrog steps of velocity Verlet (unit mass) with the
  * bookkeeping method of section "Verlet List and Bookkeeping Method", the
  * validity test taken on the device so that no step waits for the host.
  * Each step, unless state->stale is already set:
- *   1. the drift of lj_drift (q += dt p, wrapped) and its largest |dt p|^2;
- *   2. moved += sqrt(that); if 2 moved >= r_search - r_cut the list may have
- *      lost a pair: stale = 1 and row_ptr_dev[0..n] is zeroed -- the list is
- *      emptied on the device, so the kick of this step and every later step
- *      of the call do nothing; otherwise steps += 1;
- *   3. the kick p += impulses(q) of lj_force with this dt.
+ *   1. the drift of lj_drift (q += dt p, wrapped);
+ *   2. the displacement bound: with q4_build_dev NULL, moved += the step's
+ *      largest |dt p| (the fastest atom's step, summed over the steps since
+ *      the build); with q4_build_dev (n x 4, the positions the list was
+ *      built from), moved = the largest |q - q_build| over the atoms, each
+ *      axis as its minimum image -- the tighter bound, since a pair moves
+ *      closer by at most the two atoms' displacements.  If 2 moved >=
+ *      r_search - r_cut the list may have lost a pair: stale = 1 and
+ *      row_ptr_dev[0..n] is zeroed -- the list is emptied on the device, so
+ *      the kick of this step and every later step of the call do nothing;
+ *      otherwise steps += 1;
+ *   3. the kick p += impulses(q) of lj_force with this dt (dt / 2 on the
+ *      call's last step with LJ_MD_LAST_HALF_KICK); with energies_dev
+ *      (FP64 only) the kick is lj_force_energy's and writes the shifted
+ *      potential energy U(q) of step s to energies_dev[s].
  * After the call the host reads the state: `steps` steps are complete; if
  * stale is 1, the positions are one drift ahead of the momenta -- rebuild
  * the list from q4_dev (lj_build_pairlist), zero the state and apply the
- * kick that step owes with lj_force (same dt), then continue.  The force
- * arguments (precision, tpi, workspace) are those of lj_force and are all
- * checked before anything is enqueued.  Asynchronous; one small kernel for
- * the drift and bookkeeping, one for the emptying, and lj_force's launches,
- * per step.  Errors: LJ_ERR_ARG (also r_search <= r_cut, steps < 0, state
- * NULL or not 8-byte aligned), LJ_ERR_BOX, LJ_ERR_CAPACITY, LJ_ERR_CUDA.
+ * kick that step owes with lj_force (same dt, or dt / 2 if it was the last
+ * step of a half-kick call), then continue.  The force arguments
+ * (precision, tpi, workspace: at least lj_force_workspace_bytes, and with
+ * energies also lj_force_energy_workspace_bytes) are all checked before
+ * anything is enqueued.  Asynchronous; one small kernel for the drift and
+ * bookkeeping, one for the emptying, and the force call's launches, per
+ * step.  Errors: LJ_ERR_ARG (also r_search <= r_cut, steps < 0, unknown
+ * flags, state NULL or not 8-byte aligned, q4_build_dev not 32-byte
+ * aligned, energies with a form other than LJ_FP64), LJ_ERR_BOX,
+ * LJ_ERR_CAPACITY, LJ_ERR_CUDA.
  */
 int lj_md_steps(double *q4_dev, double *p4_dev, int64_t n, int32_t *row_ptr_dev,
                 const int32_t *col_dev, int64_t nnz, int half, double dt, double r_cut,
                 double r_search, const double box[3], double eps, double sigma, int precision,
-                int tpi, int64_t steps, lj_md_state *state_dev, void *workspace_dev,
+                int tpi, int64_t steps, int flags, const double *q4_build_dev,
+                double *energies_dev, lj_md_state *state_dev, void *workspace_dev,
                 size_t workspace_bytes, void *stream);
 
 /* ======================================================================== */

@@ -18,16 +18,35 @@ namespace {
 
 constexpr int kDriftThreads = 256;
 
-// q += dt p with round-to-nearest double operations (no fused multiply-add),
-// then one periodic wrap per axis; *max_d2 = max over atoms of |dt p|^2 (as
-// the ordered bit pattern of a non-negative double).
-__device__ __forceinline__ void drift_block(double *__restrict__ q4, const double *__restrict__ p4,
-                                            int n, double dt, double Lx, double Ly, double Lz,
-                                            unsigned long long *__restrict__ max_d2)
+// The block's maximum of v >= 0 into *dst (the ordered bit pattern of a
+// non-negative double).
+__device__ __forceinline__ void block_max_into(double v, unsigned long long *dst)
 {
     __shared__ double red[kDriftThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();  // red is reused by a second call
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < kDriftThreads / 32; ++w) m = fmax(m, red[w]);
+        atomicMax(dst, static_cast<unsigned long long>(__double_as_longlong(m)));
+    }
+}
+
+// q += dt p with round-to-nearest double operations (no fused multiply-add),
+// then one periodic wrap per axis; *max_d2 = max over atoms of |dt p|^2.
+// With qb (the positions of the last list build): *max_dev2 = max over
+// atoms of |q - qb|^2, each axis taken as its minimum image.
+__device__ __forceinline__ void drift_block(double *__restrict__ q4, const double *__restrict__ p4,
+                                            int n, double dt, double Lx, double Ly, double Lz,
+                                            unsigned long long *__restrict__ max_d2,
+                                            const double *__restrict__ qb = nullptr,
+                                            unsigned long long *__restrict__ max_dev2 = nullptr)
+{
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double d2 = 0.0;
+    double d2 = 0.0, e2 = 0.0;
     if (i < n) {
         double *q = q4 + 4 * static_cast<int64_t>(i);
         const double *p = p4 + 4 * static_cast<int64_t>(i);
@@ -41,17 +60,17 @@ __device__ __forceinline__ void drift_block(double *__restrict__ q4, const doubl
             if (!(x < L[a])) x = 0.0;  // x == L after rounding
             q[a] = x;
             d2 = __dadd_rn(d2, __dmul_rn(dq, dq));
+            if (qb) {
+                double e = __dsub_rn(x, qb[4 * static_cast<int64_t>(i) + a]);
+                const double h = 0.5 * L[a];
+                if (e > h) e = __dsub_rn(e, L[a]);
+                else if (e < -h) e = __dadd_rn(e, L[a]);
+                e2 = __dadd_rn(e2, __dmul_rn(e, e));
+            }
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d2 = fmax(d2, __shfl_xor_sync(0xffffffffu, d2, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d2;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int w = 0; w < kDriftThreads / 32; ++w) m = fmax(m, red[w]);
-        atomicMax(max_d2, static_cast<unsigned long long>(__double_as_longlong(m)));
-    }
+    block_max_into(d2, max_d2);
+    if (qb) block_max_into(e2, max_dev2);
 }
 
 __global__ void __launch_bounds__(kDriftThreads)
@@ -64,13 +83,17 @@ drift_kernel(double *__restrict__ q4, const double *__restrict__ p4, int n, doub
 // One step of lj_md_steps, part 1: nothing once the state is stale (every
 // block reads the flag before the last block can write it); else the
 // drift, and the block that finishes last folds the step into the state:
-// moved += sqrt(max |dt p|^2), then the validity test 2 moved < margin.
+// moved += sqrt(max |dt p|^2) (the fastest-atom bound), or with qb
+// moved = sqrt(max |q - qb|^2) (the largest displacement since the build),
+// then the validity test 2 moved < margin.
 __global__ void __launch_bounds__(kDriftThreads)
 md_drift_kernel(double *__restrict__ q4, const double *__restrict__ p4, int n, double dt, double Lx,
-                double Ly, double Lz, double margin, lj_md_state *__restrict__ S)
+                double Ly, double Lz, double margin, const double *__restrict__ qb,
+                lj_md_state *__restrict__ S)
 {
     if (*reinterpret_cast<volatile int32_t *>(&S->stale)) return;
-    drift_block(q4, p4, n, dt, Lx, Ly, Lz, reinterpret_cast<unsigned long long *>(&S->max_disp2));
+    drift_block(q4, p4, n, dt, Lx, Ly, Lz, reinterpret_cast<unsigned long long *>(&S->max_disp2), qb,
+                reinterpret_cast<unsigned long long *>(&S->max_dev2));
     __shared__ bool last;
     if (threadIdx.x == 0) {
         __threadfence();  // this block's maximum before its count
@@ -81,10 +104,11 @@ md_drift_kernel(double *__restrict__ q4, const double *__restrict__ p4, int n, d
         __threadfence();  // every block's maximum is visible
         volatile lj_md_state *V = S;
         const double d2 = V->max_disp2;
-        const double moved = __dadd_rn(V->moved, sqrt(d2));
+        const double moved = qb ? sqrt(V->max_dev2) : __dadd_rn(V->moved, sqrt(d2));
         V->moved = moved;
         V->last_disp2 = d2;
         V->max_disp2 = 0.0;
+        V->max_dev2 = 0.0;
         V->blocks_done = 0u;
         if (__dmul_rn(2.0, moved) >= margin)
             V->stale = 1;
@@ -130,17 +154,25 @@ extern "C" int lj_drift(double *q4_dev, const double *p4_dev, int64_t n, double 
 extern "C" int lj_md_steps(double *q4_dev, double *p4_dev, int64_t n, int32_t *row_ptr_dev,
                            const int32_t *col_dev, int64_t nnz, int half, double dt, double r_cut,
                            double r_search, const double box[3], double eps, double sigma,
-                           int precision, int tpi, int64_t steps, lj_md_state *state_dev,
-                           void *workspace_dev, size_t workspace_bytes, void *stream)
+                           int precision, int tpi, int64_t steps, int flags,
+                           const double *q4_build_dev, double *energies_dev,
+                           lj_md_state *state_dev, void *workspace_dev, size_t workspace_bytes,
+                           void *stream)
 {
     using namespace lj;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (steps < 0 || !state_dev || (reinterpret_cast<uintptr_t>(state_dev) & 7u)) return LJ_ERR_ARG;
+    if (flags & ~LJ_MD_LAST_HALF_KICK) return LJ_ERR_ARG;
     if (!std::isfinite(r_search) || !(r_search > r_cut)) return LJ_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(q4_build_dev) & 31u) ||
+        (reinterpret_cast<uintptr_t>(energies_dev) & 7u))
+        return LJ_ERR_ARG;
+    if (energies_dev && precision != LJ_FP64) return LJ_ERR_ARG;
     int t = tpi;
     const int rc = force_check(q4_dev, p4_dev, n, row_ptr_dev, col_dev, nnz, dt, r_cut, box, eps,
                                sigma, precision, &t, workspace_dev, workspace_bytes);
     if (rc != LJ_OK) return rc;
+    if (energies_dev && workspace_bytes < lj_force_energy_workspace_bytes(n)) return LJ_ERR_CAPACITY;
     if (n == 0 || steps == 0) return LJ_OK;
     const int ni = static_cast<int>(n);
     const double margin = r_search - r_cut;
@@ -148,12 +180,18 @@ extern "C" int lj_md_steps(double *q4_dev, double *p4_dev, int64_t n, int32_t *r
     const unsigned ge = unsigned((n + 1 + kDriftThreads - 1) / kDriftThreads);
     for (int64_t s = 0; s < steps; ++s) {
         md_drift_kernel<<<gd, kDriftThreads, 0, st>>>(q4_dev, p4_dev, ni, dt, box[0], box[1], box[2],
-                                                      margin, state_dev);
+                                                      margin, q4_build_dev, state_dev);
         LJ_TRY_LAUNCH("md_drift_kernel");
         md_empty_kernel<<<ge, kDriftThreads, 0, st>>>(row_ptr_dev, ni, state_dev);
         LJ_TRY_LAUNCH("md_empty_kernel");
-        const int r = lj_force(q4_dev, p4_dev, n, row_ptr_dev, col_dev, nnz, half, dt, r_cut, box, eps,
-                               sigma, precision, t, workspace_dev, workspace_bytes, stream);
+        const double h = (s == steps - 1 && (flags & LJ_MD_LAST_HALF_KICK)) ? 0.5 * dt : dt;
+        const int r = energies_dev
+                          ? lj_force_energy(q4_dev, p4_dev, n, row_ptr_dev, col_dev, nnz, half, h,
+                                            r_cut, box, eps, sigma, 1, energies_dev + s,
+                                            workspace_dev, workspace_bytes, stream)
+                          : lj_force(q4_dev, p4_dev, n, row_ptr_dev, col_dev, nnz, half, h, r_cut,
+                                     box, eps, sigma, precision, t, workspace_dev, workspace_bytes,
+                                     stream);
         if (r != LJ_OK) return r;
     }
     return LJ_OK;

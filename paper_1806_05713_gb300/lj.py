@@ -35,6 +35,7 @@ LJ_SCHED_SORTED = 512
 LJ_SCHED_IMAGES = 1024
 LJ_SCHED_FIXED = 2048
 LJ_SCHED_COMPACT = 4096
+LJ_MD_LAST_HALF_KICK = 1
 LJ_STATIC_MAX_ATOMS = 131072
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liblj_gb300.so")
@@ -91,7 +92,7 @@ SIGNATURES = {
                                    _vp, _vp, _sz, _vp, _sz, _int, _intp, _intp, _fltp, _vp]),
     "lj_drift": (_int, [_vp, _vp, _i64, _dbl, _dbl3, _vp, _vp]),
     "lj_md_steps": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl, _dbl, _dbl3, _dbl, _dbl,
-                           _int, _int, _i64, _vp, _vp, _sz, _vp]),
+                           _int, _int, _i64, _int, _vp, _vp, _vp, _vp, _sz, _vp]),
     "lj_force_vjp_workspace_bytes": (_sz, [_i64, _int]),
     "lj_force_vjp": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl3, _dbl, _dbl, _int,
                             _vp, _vp, _vp, _sz, _vp]),
@@ -406,39 +407,53 @@ def lj_drift(q4: torch.Tensor, p4: torch.Tensor, dt: float, box,
 
 
 def lj_md_state_new(device) -> torch.Tensor:
-    """A zeroed lj_md_state (40 bytes) in device memory."""
-    return torch.zeros(5, dtype=torch.float64, device=device)
+    """A zeroed lj_md_state (48 bytes) in device memory."""
+    return torch.zeros(6, dtype=torch.float64, device=device)
 
 
 def lj_md_state_read(state: torch.Tensor) -> dict:
     """The fields of an lj_md_state (one device-to-host copy; synchronises)."""
     a = state.cpu().numpy()
     ints = a.view(np.int32)
-    return {"moved": float(a[0]), "last_disp2": float(a[2]), "stale": int(ints[6]),
-            "steps": int(ints[7])}
+    return {"moved": float(a[0]), "last_disp2": float(a[2]), "stale": int(ints[8]),
+            "steps": int(ints[9])}
 
 
 def lj_md_steps(q4: torch.Tensor, p4: torch.Tensor, plist: PairList, steps: int, dt: float,
                 r_cut: float, r_search: float, box, eps: float = 1.0, sigma: float = 1.0,
                 precision: int = LJ_FP64, tpi: int = LJ_TPI_AUTO, state: torch.Tensor | None = None,
-                workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """Enqueue `steps` leapfrog steps (drift, then a kick by dt) with the
-    bookkeeping test on the device; returns the lj_md_state tensor.  Once the
-    margin is used up the library empties plist's rows and the remaining
-    steps do nothing: read the state, rebuild, kick once, continue."""
+                workspace: torch.Tensor | None = None, last_half_kick: bool = False,
+                q_build: torch.Tensor | None = None, energies: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """Enqueue `steps` leapfrog steps (drift, then a kick by dt; dt/2 on the
+    last one with last_half_kick) with the bookkeeping test on the device;
+    returns the lj_md_state tensor.  q_build: the positions the list was
+    built from (the displacement bound) or None (the summed fastest-atom
+    bound).  energies: a device tensor of `steps` doubles for U(q) of each
+    step (FP64).  Once the margin is used up the library empties plist's
+    rows and the remaining steps do nothing: read the state, rebuild, kick
+    once, continue."""
     lib = load()
     n = int(q4.shape[0])
     if state is None:
         state = lj_md_state_new(q4.device)
-    if state.dtype != torch.float64 or state.numel() != 5 or not state.is_cuda:
-        raise TypeError("state must be a 5-element CUDA float64 tensor (lj_md_state_new)")
+    if state.dtype != torch.float64 or state.numel() != 6 or not state.is_cuda:
+        raise TypeError("state must be a 6-element CUDA float64 tensor (lj_md_state_new)")
     if workspace is None:
-        workspace = _workspace(lj_force_workspace_bytes(n, box, precision), q4.device)
+        nb = lj_force_workspace_bytes(n, box, precision)
+        if energies is not None:
+            nb = max(nb, lj_force_energy_workspace_bytes(n))
+        workspace = _workspace(nb, q4.device)
+    qb = 0 if q_build is None else _dev(q_build, torch.float64, "q_build", (n, 4))
+    if energies is not None and energies.numel() < int(steps):
+        raise ValueError("energies must hold one double per step")
+    ep = 0 if energies is None else _dev(energies, torch.float64, "energies")
     st = lib.lj_md_steps(_dev(q4, torch.float64, "q4", (n, 4)), _dev(p4, torch.float64, "p4", (n, 4)),
                          n, plist.row_ptr.data_ptr(), plist.col.data_ptr(), plist.nnz,
                          int(plist.half), float(dt), float(r_cut), float(r_search), _box3(box),
                          float(eps), float(sigma), int(precision), int(tpi), int(steps),
-                         state.data_ptr(), workspace.data_ptr(), workspace.numel(), _stream(stream))
+                         LJ_MD_LAST_HALF_KICK if last_half_kick else 0, qb, ep, state.data_ptr(),
+                         workspace.data_ptr(), workspace.numel(), _stream(stream))
     _check(st, "lj_md_steps")
     return state
 

@@ -3,21 +3,23 @@ with the bookkeeping method of the paper's section "Verlet List and
 Bookkeeping Method".
 
 The list is built with search length r_s = r_c + margin and reused while
-twice the accumulated fastest-atom displacement (the sum over steps of the
-largest |dt p|) stays below the margin; then it is rebuilt.  The kick and
-drift of consecutive steps are merged (leapfrog form of velocity Verlet),
-so each step is one drift and one force call -- the force kernel applies
-the kick directly (Algorithm 1 updates the momenta with dt).
+twice a bound on the largest displacement since the build stays below the
+margin; then it is rebuilt.  The bound is the paper's fastest-atom one
+(the sum over steps of the largest |dt p|) or, optionally, the largest
+displacement |q - q_build| itself.  The kick and drift of consecutive
+steps are merged (leapfrog form of velocity Verlet), so each step is one
+drift and one force call -- the force kernel applies the kick directly
+(Algorithm 1 updates the momenta with dt).
 
-Two drivers.  The plain truncation without per-step energies runs its
-steps through ``lj_md_steps``: batches of steps enqueued at once, the
-validity test taken on the device (a list whose margin is used up is
-emptied there, so the steps queued after it do nothing), and one read of
-the bookkeeping state per batch; the batch length is predicted from the
-last step's displacement so that few queued steps go unused.  The other
-cases take one ``lj_drift`` and one force call per step with the test on
-the host.  Host-side orchestration only: every step of the computation
-runs in the library's kernels.
+Two drivers.  The device driver (the plain truncation) runs the steps
+through ``lj_md_steps``: batches of steps enqueued at once, the validity
+test taken on the device (a list whose margin is used up is emptied there,
+so the steps queued after it do nothing), and one read of the bookkeeping
+state per batch; the batch length is predicted from the last step's
+displacement so that few queued steps go unused.  The host driver (and the
+force-shifted truncation) takes one ``lj_drift`` and one force call per
+step with the test on the host.  Host-side orchestration only: every step
+of the computation runs in the library's kernels.
 """
 from __future__ import annotations
 
@@ -34,16 +36,27 @@ class VelocityVerlet:
     def __init__(self, q4: torch.Tensor, p4: torch.Tensor, box, r_cut: float, margin: float,
                  dt: float, eps: float = 1.0, sigma: float = 1.0, precision: int = lj.LJ_FP64,
                  tpi: int = lj.LJ_TPI_AUTO, half: bool = True, truncation: str = "plain",
-                 driver: str = "device"):
+                 driver: str = "device", criterion: str = "fastest_atom"):
         """truncation: "plain" (Eq. (1) cut at r_c, the paper's choice) or
         "force_shifted" (the pair force taken to zero at r_c; FP64 only).
-        driver: "device" (batches through lj_md_steps where it applies) or
-        "host" (the validity test on the host after every drift)."""
+        driver: "device" (steps queued in batches through lj_md_steps; the
+        plain truncation) or "host" (the validity test on the host after
+        every drift).  criterion: "fastest_atom" (the paper's: the sum over
+        steps of the fastest atom's step) or "displacement" (the largest
+        displacement of any atom since the build, a tighter bound; device
+        driver only)."""
         if truncation not in ("plain", "force_shifted"):
             raise ValueError("truncation must be 'plain' or 'force_shifted'")
         if driver not in ("device", "host"):
             raise ValueError("driver must be 'device' or 'host'")
-        self.driver = driver
+        if criterion not in ("fastest_atom", "displacement"):
+            raise ValueError("criterion must be 'fastest_atom' or 'displacement'")
+        if truncation == "force_shifted":
+            driver = "host"
+        if criterion == "displacement" and driver != "device":
+            raise ValueError("the displacement criterion needs the device driver and the plain "
+                             "truncation")
+        self.driver, self.criterion = driver, criterion
         if truncation == "force_shifted" and precision != lj.LJ_FP64:
             raise ValueError("the force-shifted truncation is FP64 only")
         self.truncation = truncation
@@ -64,6 +77,8 @@ class VelocityVerlet:
                       if truncation == "force_shifted" else None)
         self._half_kicked = False
         self._md_state = lj.lj_md_state_new(q4.device)
+        self._q_build = q4.clone() if criterion == "displacement" else None
+        self._mdws = None         # lj_md_steps workspace with per-step energies
         self.max_batch = 64       # steps enqueued per read of the device state, at most
         self._rebuild()
 
@@ -73,6 +88,8 @@ class VelocityVerlet:
         self.rebuilds += 1
         self.moved = 0.0
         self._md_state.zero_()
+        if self._q_build is not None:
+            self._q_build.copy_(self.q4)
 
     def _kick(self, h: float, energy_out: torch.Tensor | None = None):
         if self.truncation == "force_shifted":
@@ -98,31 +115,41 @@ class VelocityVerlet:
                                       self.q4.device)
         if not self._half_kicked:
             self._kick(0.5 * self.dt)              # p(t + dt/2)
-        if self.driver == "device" and energies is None and self.truncation == "plain" and steps > 1:
-            self._run_on_device(steps - 1)         # all but the last step (a half kick)
-            steps_left = 1
+        if self.driver == "device":
+            self._run_on_device(steps, energies)
         else:
-            steps_left = steps
-        self._run_host_checked(steps_left, energies)
+            self._run_host_checked(steps, energies)
+        self._half_kicked = False
 
-    def _run_on_device(self, steps: int):
-        """`steps` full leapfrog steps through lj_md_steps."""
-        # the device state starts from the host's bound (steps may have run host-checked)
+    def _run_on_device(self, steps: int, energies: torch.Tensor | None):
+        """`steps` leapfrog steps through lj_md_steps, the last with a half kick."""
+        # the device state continues the host's bound across run() calls
         self._md_state.zero_()
         self._md_state[0] = self.moved
+        prec, tpi, ws = self.precision, self.tpi, self.ws
+        if energies is not None:                # the FP64 force-and-energy pass, as _kick's
+            prec, tpi = lj.LJ_FP64, lj.LJ_TPI_AUTO
+            if self._mdws is None:
+                n = self.q4.shape[0]
+                self._mdws = lj._workspace(max(lj.lj_force_workspace_bytes(n, self.box, prec),
+                                               lj.lj_force_energy_workspace_bytes(n)),
+                                           self.q4.device)
+            ws = self._mdws
         done, base, batch = 0, 0, 8
         while done < steps:
             k = min(batch, steps - done)
             lj.lj_md_steps(self.q4, self.p4, self.plist, k, self.dt, self.r_cut, self.r_search,
-                           self.box, self.eps, self.sigma, self.precision, self.tpi,
-                           state=self._md_state, workspace=self.ws)
+                           self.box, self.eps, self.sigma, prec, tpi, state=self._md_state,
+                           workspace=ws, last_half_kick=done + k == steps, q_build=self._q_build,
+                           energies=None if energies is None else energies[done:done + k])
             st = lj.lj_md_state_read(self._md_state)
             done += st["steps"] - base
             base = st["steps"]
             if st["stale"]:
                 # positions one drift ahead: rebuild, then the kick that step owes
                 self._rebuild()
-                self._kick(self.dt)
+                self._kick(0.5 * self.dt if done + 1 == steps else self.dt,
+                           None if energies is None else energies[done:done + 1])
                 done += 1
                 base = 0
                 self.moved = 0.0
@@ -143,7 +170,6 @@ class VelocityVerlet:
             last = s == steps - 1
             self._kick(0.5 * self.dt if last else self.dt,
                        None if energies is None else energies[s:s + 1])
-        self._half_kicked = False
 
     def kinetic_energy(self) -> float:
         return 0.5 * float((self.p4[:, :3] ** 2).sum())

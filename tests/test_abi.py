@@ -112,11 +112,11 @@ def test_host_argument_checks_without_gpu():
     assert force(n=0, nnz=0) == lj.LJ_OK
     # lj_md_steps: its own arguments, then every force check, before any launch
 
-    def md(steps=3, state=fake, rs=3.3, ws=fake, wsb=1 << 40, **k):
+    def md(steps=3, state=fake, rs=3.3, ws=fake, wsb=1 << 40, flags=0, qb=None, en=None, **k):
         a = args(**k)
         return L.lj_md_steps(a["q"], a["p"], a["n"], a["rp"], a["col"], a["nnz"], a["half"],
                              a["dt"], a["rc"], rs, a["box"], a["eps"], a["sig"], a["prec"],
-                             a["tpi"], steps, state, ws, wsb, None)
+                             a["tpi"], steps, flags, qb, en, state, ws, wsb, None)
     assert md(steps=-1) == lj.LJ_ERR_ARG
     assert md(state=None) == lj.LJ_ERR_ARG
     assert md(state=ctypes.c_void_p(260)) == lj.LJ_ERR_ARG
@@ -127,7 +127,12 @@ def test_host_argument_checks_without_gpu():
     assert md(rc=6.0, rs=6.3) == lj.LJ_ERR_BOX
     assert md(ws=None, wsb=0) == lj.LJ_ERR_CAPACITY
     assert md(prec=2, dt=1e-250) == lj.LJ_ERR_ARG
+    assert md(flags=2) == lj.LJ_ERR_ARG
+    assert md(qb=ctypes.c_void_p(264)) == lj.LJ_ERR_ARG
+    assert md(en=ctypes.c_void_p(260)) == lj.LJ_ERR_ARG
+    assert md(en=fake, prec=2) == lj.LJ_ERR_ARG
     assert md(steps=0) == lj.LJ_OK
+    assert md(steps=0, flags=lj.LJ_MD_LAST_HALF_KICK, qb=fake, en=fake) == lj.LJ_OK
 
 
 def test_workspace_sizes_are_sane():

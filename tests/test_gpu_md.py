@@ -120,6 +120,42 @@ def _hot_system(seed=2):
     return s, p0
 
 
+def test_device_driver_energies_and_displacement_criterion(cuda_lib):
+    """Per-step energies through lj_md_steps equal the host-checked loop's
+    (full list: bit for bit); the displacement criterion rebuilds no more
+    often than the fastest-atom bound, keeps every pair within r_c in the
+    list, and follows the same trajectory to rounding."""
+    from paper_1806_05713_gb300.md import VelocityVerlet
+    lj = cuda_lib
+    s, p0 = _hot_system(seed=11)
+    res = {}
+    for name, driver, crit in (("host", "host", "fastest_atom"), ("device", "device", "fastest_atom"),
+                               ("disp", "device", "displacement")):
+        q, p = to_dev(s.q), to_dev(p0)
+        vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, 0.002, half=False, driver=driver,
+                            criterion=crit)
+        U = torch.zeros(90, dtype=torch.float64, device="cuda")
+        vv.run(90, energies=U)
+        torch.cuda.synchronize()
+        res[name] = (q, p, U, vv)
+    qh, ph, Uh, vh = res["host"]
+    qd, pd, Ud, vd = res["device"]
+    assert vd.rebuilds == vh.rebuilds >= 2
+    assert torch.equal(Ud, Uh) and torch.equal(qd, qh) and torch.equal(pd, ph)
+    qx, px, Ux, vx = res["disp"]
+    assert vx.rebuilds <= vh.rebuilds
+    dq = qx.cpu().numpy()[:, :3] - qh.cpu().numpy()[:, :3]
+    dq -= s.box * np.round(dq / s.box)
+    assert np.max(np.abs(dq)) < 1e-10
+    assert float((Ux - Uh).abs().max()) <= 1e-10 * float(Uh.abs().max())
+    F_old = torch.zeros_like(qx)
+    lj.lj_force(qx, F_old, vx.plist, 1.0, s.rc, s.box)
+    fresh = lj.lj_build_pairlist(qx, s.box, s.rs, False)
+    F_new = torch.zeros_like(qx)
+    lj.lj_force(qx, F_new, fresh, 1.0, s.rc, s.box)
+    assert float((F_old - F_new).abs().max()) <= 1e-12 * float(F_new.abs().max())
+
+
 @pytest.mark.parametrize("precision", [0, 2])
 def test_device_driver_equals_host_driver(cuda_lib, precision):
     """lj_md_steps (the validity test on the device, steps queued in batches)
@@ -179,7 +215,7 @@ def test_md_steps_stale_state_does_nothing(cuda_lib):
     pl = lj.lj_build_pairlist(q, s.box, s.rs, True)
     state = lj.lj_md_state_new(q.device)
     ints = state.view(torch.int32)
-    ints[6] = 1                                   # stale
+    ints[8] = 1                                   # stale
     q0, p0d = q.clone(), p.clone()
     lj.lj_md_steps(q, p, pl, 5, 0.002, s.rc, s.rs, s.box, state=state)
     torch.cuda.synchronize()
