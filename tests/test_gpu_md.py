@@ -156,7 +156,7 @@ def test_device_driver_energies_and_displacement_criterion(cuda_lib):
     assert float((F_old - F_new).abs().max()) <= 1e-12 * float(F_new.abs().max())
 
 
-@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_device_driver_equals_host_driver(cuda_lib, precision):
     """lj_md_steps (the validity test on the device, steps queued in batches)
     against the host-checked loop: with the full list (no atomics, so every
