@@ -14,21 +14,28 @@
 //   2. scan:     exclusive prefix sum of the cell counts -> cell_start.
 //   3. scatter:  atoms in cell order, with an FP32 copy {x, y, z, id} so that
 //                the candidate loops below stream 16-byte records.
-//   4. count:    one warp per row (rows taken in cell order, so neighbouring
-//                warps share their neighbour cells in L1/L2); the five cells
-//                of a row of the stencil along x are consecutive in the cell
-//                order, so they are walked as one run of candidates (two
-//                where the stencil wraps around the box) -- 25 runs of ~27
-//                atoms at density 1 instead of 27 cells of ~43, about half
-//                the candidate slots of a stencil of r_s-sized cells;
-//                candidates are screened in FP32 against r_s^2 (1 +- delta)
-//                with a proven error bound delta, and only the rare
+//   4. walk:     one warp per atom (atoms taken in cell order, so
+//                neighbouring warps share their neighbour cells in L1/L2);
+//                the five cells of a row of the stencil along x are
+//                consecutive in the cell order, so they are walked as one
+//                run of candidates (two where the stencil wraps around the
+//                box) -- runs of ~27 atoms at density 1 instead of cells of
+//                ~5; candidates are screened in FP32 against r_s^2 (1 +-
+//                delta) with a proven error bound delta, and only the rare
 //                candidates inside the band are decided by the exact FP64
-//                definition.
+//                definition.  Default (five or more cells on every axis and
+//                room for the row slabs): the FORWARD half of the stencil
+//                only -- 12.5 runs instead of 25 -- each pair met once and
+//                appended, through a per-row atomic slot counter, to the
+//                slab of its smaller index (half list) or to both slabs
+//                (full list).  Otherwise the full stencil per row i, either
+//                into row i's slab or, with no room for slabs, counted
+//                first and filled later (the two-walk path).
 //   5. scan:     row counts -> row_ptr; total and longest row read back.
-//   6. fill:     the same walk compacts the j of the row into shared memory
-//                (ballot + popc), ranks them (all j are distinct) and writes
-//                the sorted row.
+//   6. sort:     each slab rank-sorted into its place in col (all j of a
+//                row are distinct); the two-walk path instead walks again,
+//                compacts the j of the row into shared memory (ballot +
+//                popc), ranks them and writes the sorted row.
 // The result is bit-exact against the FP64 definition because every
 // decision is either certain from the FP32 bound or taken with the exact
 // IEEE operations (d = q_j - q_i, minimum image, (dx*dx + dy*dy) + dz*dz,
@@ -385,6 +392,136 @@ walk_store_kernel(const double *__restrict__ q4, int n, Grid g, const int *__res
     }
 }
 
+// One walk over HALF the stencil (every axis with at least five cells, so
+// each neighbour cell is one offset in -2..2): the warp of atom a
+// (cell-order position w) takes the 62 forward cells -- offset dz > 0, or
+// dz = 0 and dy > 0, or dz = dy = 0 and dx > 0 -- and the atoms after it in
+// its own cell, so every unordered pair of atoms within reach is met once
+// instead of twice.  A pair found closer than r_s goes, for the half list,
+// to the row of its smaller index (the larger index into that row's slab),
+// for the full list to both rows; each store takes its slot from an atomic
+// counter of the row, and the rows are sorted afterwards.  The exact
+// decision is the definition's: d = q_b - q_a is the negation of q_a - q_b,
+// and the minimum image and the squares are symmetric under it.
+__device__ __forceinline__ void append_slab(int row, int val, int *__restrict__ tmp, int cap,
+                                            int *__restrict__ row_cnt, ListStats *__restrict__ stats)
+{
+    const int slot = atomicAdd(&row_cnt[row], 1);
+    if (slot < cap)
+        tmp[static_cast<size_t>(row) * cap + slot] = val;
+    else
+        atomicOr(&stats->err, 4);
+}
+
+template <bool HALF>
+__device__ __forceinline__ void forward_run(const double *__restrict__ q4, const Grid &g,
+                                         const float4 *__restrict__ pos_f, int s, int e, int ia,
+                                         float4 pa, bool &have_exact, double &xa, double &ya,
+                                         double &za, int *__restrict__ tmp, int cap,
+                                         int *__restrict__ row_cnt, ListStats *__restrict__ stats)
+{
+    const int lane = threadIdx.x & 31;
+    for (int base = s; base < e; base += 32) {
+        const int k = base + lane;
+        if (k >= e) break;
+        const float4 pj = pos_f[k];
+        const int jb = __float_as_int(pj.w);
+        float dx = pj.x - pa.x, dy = pj.y - pa.y, dz = pj.z - pa.z;
+        if (fabsf(dx) > g.hLf[0]) dx -= copysignf(g.Lf[0], dx);
+        if (fabsf(dy) > g.hLf[1]) dy -= copysignf(g.Lf[1], dy);
+        if (fabsf(dz) > g.hLf[2]) dz -= copysignf(g.Lf[2], dz);
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        bool in = r2 < g.lo;
+        if (!in && r2 < g.hi) {
+            if (!have_exact) {
+                load_xyz(q4, ia, xa, ya, za);
+                have_exact = true;
+            }
+            in = exact_within(q4, jb, xa, ya, za, g);
+        }
+        if (in) {
+            if (HALF) {
+                append_slab(ia < jb ? ia : jb, ia < jb ? jb : ia, tmp, cap, row_cnt, stats);
+            } else {
+                append_slab(ia, jb, tmp, cap, row_cnt, stats);
+                append_slab(jb, ia, tmp, cap, row_cnt, stats);
+            }
+        }
+    }
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+walk_forward_store_kernel(const double *__restrict__ q4, int n, Grid g, const int *__restrict__ cell_of,
+                       const int *__restrict__ cell_start, const int *__restrict__ cell_atoms,
+                       const float4 *__restrict__ pos_f, int *__restrict__ tmp, int cap,
+                       int *__restrict__ row_cnt, ListStats *__restrict__ stats)
+{
+    const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (w >= n) return;
+    const int ia = cell_atoms[w];
+    const float4 pa = pos_f[w];
+    const int cell_a = cell_of[ia];
+    const int cx = cell_a % g.nc[0];
+    const int cy = (cell_a / g.nc[0]) % g.nc[1];
+    const int cz = cell_a / (g.nc[0] * g.nc[1]);
+    bool have_exact = false;
+    double xa = 0.0, ya = 0.0, za = 0.0;
+    auto wrap = [](int c, int nc) { return c < 0 ? c + nc : (c >= nc ? c - nc : c); };
+    // x-cells cx-2..cx+2 of a stencil row as up to two consecutive runs
+    int x0, x1, x2 = 0, x3 = -1;
+    if (cx - 2 < 0) {
+        x0 = 0;
+        x1 = cx + 2;
+        x2 = g.nc[0] + cx - 2;
+        x3 = g.nc[0] - 1;
+    } else if (cx + 2 >= g.nc[0]) {
+        x0 = cx - 2;
+        x1 = g.nc[0] - 1;
+        x2 = 0;
+        x3 = cx + 2 - g.nc[0];
+    } else {
+        x0 = cx - 2;
+        x1 = cx + 2;
+    }
+    for (int dz = 0; dz <= 2; ++dz) {
+        const int nz = wrap(cz + dz, g.nc[2]);
+        for (int dy = (dz == 0 ? 0 : -2); dy <= 2; ++dy) {
+            const int ny = wrap(cy + dy, g.nc[1]);
+            const int rowc = (nz * g.nc[1] + ny) * g.nc[0];
+            if (dz == 0 && dy == 0) {
+                // own row: the atoms after a in its cell, then cells cx+1, cx+2
+                if (cx + 2 < g.nc[0]) {
+                    forward_run<HALF>(q4, g, pos_f, w + 1, cell_start[rowc + cx + 3], ia, pa, have_exact, xa,
+                             ya, za, tmp, cap, row_cnt, stats);
+                } else {
+                    forward_run<HALF>(q4, g, pos_f, w + 1, cell_start[rowc + g.nc[0]], ia, pa, have_exact,
+                             xa, ya, za, tmp, cap, row_cnt, stats);
+                    forward_run<HALF>(q4, g, pos_f, cell_start[rowc], cell_start[rowc + cx + 3 - g.nc[0]], ia,
+                             pa, have_exact, xa, ya, za, tmp, cap, row_cnt, stats);
+                }
+                continue;
+            }
+            forward_run<HALF>(q4, g, pos_f, cell_start[rowc + x0], cell_start[rowc + x1 + 1], ia, pa,
+                     have_exact, xa, ya, za, tmp, cap, row_cnt, stats);
+            if (x3 >= x2)
+                forward_run<HALF>(q4, g, pos_f, cell_start[rowc + x2], cell_start[rowc + x3 + 1], ia, pa,
+                         have_exact, xa, ya, za, tmp, cap, row_cnt, stats);
+        }
+    }
+}
+
+// stats->max_row = the longest row (row_cnt filled by atomic slots).
+__global__ void max_row_kernel(const int *__restrict__ row_cnt, int n, ListStats *__restrict__ stats)
+{
+    int m = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m = max(m, row_cnt[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&stats->max_row, m);
+}
+
 // row_ptr[n] = nnz, the total of the row-length scan (clamped to int32; a
 // larger total is refused on the host).
 __global__ void set_total_kernel(int32_t *__restrict__ row_end, const ListStats *__restrict__ stats)
@@ -480,8 +617,20 @@ int build_pairlist_impl(const double *q4, int64_t n, const double box[3], double
     int *slabs = nullptr;
     if (cap_slab > 0 && ws_bytes >= base_bytes + 256 + size_t(n) * size_t(cap_slab) * sizeof(int))
         slabs = reinterpret_cast<int *>((reinterpret_cast<uintptr_t>(ws) + base_bytes + 255) & ~uintptr_t(255));
+    const bool forward_stencil = g.noff[0] == 5 && g.noff[1] == 5 && g.noff[2] == 5;
     if (slabs) {
-        if (half)
+        if (forward_stencil) {
+            LJ_TRY_CUDA(cudaMemsetAsync(w.row_cnt, 0, sizeof(int) * size_t(n), st));
+            if (half)
+                walk_forward_store_kernel<true><<<gw, kWarpsPerBlock * 32, 0, st>>>(
+                    q4, ni, g, w.cell_of, w.cell_start, w.cell_atoms, w.pos_f, slabs, cap_slab, w.row_cnt, w.stats);
+            else
+                walk_forward_store_kernel<false><<<gw, kWarpsPerBlock * 32, 0, st>>>(
+                    q4, ni, g, w.cell_of, w.cell_start, w.cell_atoms, w.pos_f, slabs, cap_slab, w.row_cnt, w.stats);
+            LJ_TRY_LAUNCH("walk_forward_store_kernel");
+            max_row_kernel<<<unsigned(std::min<int64_t>((n + 255) / 256, 4 * 152)), 256, 0, st>>>(
+                w.row_cnt, ni, w.stats);
+        } else if (half)
             walk_store_kernel<true><<<gw, kWarpsPerBlock * 32, 0, st>>>(
                 q4, ni, g, w.cell_of, w.cell_start, w.cell_atoms, w.pos_f, slabs, cap_slab, w.row_cnt, w.stats);
         else
