@@ -530,13 +530,43 @@ __global__ void set_total_kernel(int32_t *__restrict__ row_end, const ListStats 
     *row_end = static_cast<int32_t>(t < INT32_MAX ? t : INT32_MAX);
 }
 
+// Ranks of a row of len <= 32 E entries: each lane holds E of them and
+// compares every 16-byte group of the row (padded with INT_MAX, which no
+// index reaches) against all E at once, so each shared-memory load serves E
+// ranks.
+template <int E>
+__device__ __forceinline__ void rank_row(const int *__restrict__ buf, int len, int lane,
+                                         int32_t *__restrict__ out)
+{
+    int v[E], r[E];
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+        const int e = lane + 32 * u;
+        v[u] = e < len ? buf[e] : INT32_MAX;
+        r[u] = 0;
+    }
+    const int4 *b4 = reinterpret_cast<const int4 *>(buf);
+    const int len4 = (len + 3) >> 2;
+    for (int m = 0; m < len4; ++m) {
+        const int4 w = b4[m];
+#pragma unroll
+        for (int u = 0; u < E; ++u)
+            r[u] += (w.x < v[u]) + (w.y < v[u]) + (w.z < v[u]) + (w.w < v[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < E; ++u)
+        if (lane + 32 * u < len) out[r[u]] = v[u];
+}
+
 // Row i's slab, staged in shared memory, rank-sorted into col (the j of a
-// row are distinct: rank(v) = #{m : buf[m] < v}).
+// row are distinct: rank(v) = #{m : buf[m] < v}).  cap is a multiple of 32,
+// so each warp's buffer is 16-byte aligned and holds the padding.
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 sort_rows_kernel(const int *__restrict__ tmp, int cap, int n, const int32_t *__restrict__ row_ptr,
                  int32_t *__restrict__ col)
 {
-    extern __shared__ int smem[];
+    extern __shared__ int4 smem4[];
+    int *smem = reinterpret_cast<int *>(smem4);
     const int wib = threadIdx.x >> 5;
     const int i = blockIdx.x * kWarpsPerBlock + wib;
     if (i >= n) return;
@@ -545,8 +575,20 @@ sort_rows_kernel(const int *__restrict__ tmp, int cap, int n, const int32_t *__r
     const int start = row_ptr[i];
     const int len = row_ptr[i + 1] - start;
     const int *src = tmp + static_cast<size_t>(i) * cap;
-    for (int e = lane; e < len; e += 32) buf[e] = src[e];
+    const int padded = (len + 3) & ~3;
+    for (int e = lane; e < padded; e += 32) buf[e] = e < len ? src[e] : INT32_MAX;
     __syncwarp();
+    int32_t *out = col + start;
+    switch ((len + 31) >> 5) {
+        case 0: return;
+        case 1: rank_row<1>(buf, len, lane, out); return;
+        case 2: rank_row<2>(buf, len, lane, out); return;
+        case 3: rank_row<3>(buf, len, lane, out); return;
+        case 4: rank_row<4>(buf, len, lane, out); return;
+        case 5: rank_row<5>(buf, len, lane, out); return;
+        case 6: rank_row<6>(buf, len, lane, out); return;
+        default: break;
+    }
     for (int e = lane; e < len; e += 32) {
         const int v = buf[e];
         int r = 0;
