@@ -57,6 +57,11 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
 # entry reports null.
 # DRAM bytes (read + write) of one launch of the FP64 force kernel per
 # schedule, from ncu (cold cache), with the profile that records them.
+# L2 read and reduction sectors per launch of the FP64 force kernel from the
+# same ncu capture (the gathered-bytes view), per schedule.
+LTS_SECTORS_PER_LAUNCH = {
+    2056: (11227842, 24806236, "profiles/force_fp64_fixed_tpi8_half_N119164.md"),
+}
 TRAFFIC_PER_LAUNCH = {
     1032: (41903872.0 + 1280.0, "profiles/force_fp64_images_tpi8_half_N119164.md"),
     2056: (41911040.0 + 2560.0, "profiles/force_fp64_fixed_tpi8_half_N119164.md"),
@@ -417,6 +422,18 @@ def main():
     hbm_view = {"achieved": alg_bytes / t_force / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "frac": alg_bytes / t_force / 1e9 / hbm_peak, "peak_source": hbm_src,
                 "bytes_per_pair": alg_bytes / nnz}
+    # the gathered-bytes view: what the kernel asks of L2 -- per entry its
+    # column index and q_j record, per row its row pointers and q_i, and the
+    # FP64 reductions (p_j per interacting entry, p_i per lane and row)
+    gathered_reads = 36.0 * nnz + 40.0 * s.n
+    reductions = 3.0 * n_cut + 3.0 * 8 * s.n
+    lts = LTS_SECTORS_PER_LAUNCH.get(best_tpi)
+    l2_view = {"gathered_read_bytes": gathered_reads, "reductions": reductions,
+               "gathered_read_GBps": gathered_reads / t_force / 1e9,
+               "reductions_per_s": reductions / t_force,
+               "lts_read_sectors": None if lts is None else lts[0],
+               "lts_red_sectors": None if lts is None else lts[1],
+               "lts_source": None if lts is None else lts[2]}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -430,7 +447,7 @@ def main():
         "list_build_ms": statistics.mean(list_ms),
         "force_ms_per_call": t_force * 1e3,
         "force_only_pairs_per_s": nnz / t_force,
-        "roofline": roof, "hbm_roofline": hbm_view,
+        "roofline": roof, "hbm_roofline": hbm_view, "l2_gather_view": l2_view,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 32 * s.n,
                 "d2h_bytes_per_step": 32 * s.n},
         "gpu_launches": int(launches),
