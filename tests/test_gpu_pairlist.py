@@ -52,6 +52,20 @@ def test_nonuniform_box_and_uniform_gas(cuda_lib, oracle_lib):
         _assert_same(cuda_lib, oracle_lib, q, box, 3.3, half, "brute")
 
 
+@pytest.mark.parametrize("box", [(9.9, 11.55, 14.85), (8.3, 8.3, 21.0), (16.6, 8.4, 8.5)])
+def test_forward_stencil_noncubic_boxes(cuda_lib, oracle_lib, box):
+    """Boxes with five or more cells on every axis (the forward-stencil
+    walk), with five exactly on some axes and unequal sides, against brute
+    force, half and full lists."""
+    rng = np.random.default_rng(int(sum(box) * 10))
+    box = np.array(box)
+    n = int(0.9 * np.prod(box))
+    q = np.zeros((n, 4))
+    q[:, :3] = rng.random((n, 3)) * box
+    for half in (True, False):
+        _assert_same(cuda_lib, oracle_lib, q, box, 3.3, half, "brute")
+
+
 def test_atoms_on_cell_and_box_faces(cuda_lib, oracle_lib):
     """Positions exactly on cell boundaries, at 0 and just below L."""
     L = 13.2  # 4 cells of exactly r_s = 3.3
