@@ -543,7 +543,9 @@ def extra_million(lj, dev, stream, flush):
 def extra_batched(lj, dev, stream, flush):
     """512 systems, N log-uniform in 500..32000, rho in 0.8..1.2, rc 2.5 or
     3.0: one persistent launch replayed from a CUDA graph vs one launch per
-    system, FP64, mixed and double-float, half lists."""
+    system, FP64, mixed and double-float; the autotuner picks lanes per row,
+    rows per work item and the list layout (half list with atomics or full
+    list without)."""
     import torch
     from paper_1806_05713_gb300 import inputs
     from paper_1806_05713_gb300.batch import Batch
@@ -551,12 +553,14 @@ def extra_batched(lj, dev, stream, flush):
     res = {"n_systems": len(systems), "total_atoms": int(sum(s.n for s in systems))}
     for name, prec in (("fp64", lj.LJ_FP64), ("mixed", lj.LJ_MIXED), ("dfloat", lj.LJ_DFLOAT)):
         b = Batch(systems, DT, prec, True, tpi=8, rows_per_item=64, plan_rows_min=16)
-        tpi, rows, _ = b.autotune(tpis=(4, 8, 16), rows=(16, 32, 64, 128), reps=3)
+        tpi, rows, _ = b.autotune(tpis=(4, 8, 16), rows=(16, 32, 64, 128), reps=3,
+                                  layouts=(True, False))
         g = b.capture_graph()
         t_graph = time_calls(g.replay, stream, flush, 10, 2)
         t_sep = time_calls(lambda: b.force_per_system(tpi=lj.LJ_TPI_AUTO),
                            stream, flush, 5, 1)
-        res[name] = {"tpi": tpi, "rows_per_item": rows, "pairs_per_call": b.pairs,
+        res[name] = {"tpi": tpi, "rows_per_item": rows, "list": "half" if b.half else "full",
+                     "pairs_per_call": b.pairs,
                      "graph_persistent_ms": t_graph,
                      "graph_persistent_pairs_per_s": b.pairs / (t_graph / 1e3),
                      "per_system_launches_ms": t_sep,

@@ -38,10 +38,20 @@ class Batch:
         self.q4 = torch.from_numpy(q).to(self.device)
         self.p4 = torch.zeros((total, 4), dtype=torch.float64, device=self.device)
         self.row_ptr = torch.empty(total + nsys, dtype=torch.int32, device=self.device)
-        st = lj._stream(None)
-        # pass 1: list sizes (capacity 0 reports the size needed)
         ws_bytes = max(lib.lj_pairlist_workspace_bytes(s.n, lj._box3(s.box), s.rs) for s in self.systems)
         self.list_ws = lj._workspace(ws_bytes, self.device)
+        self.eps, self.sigma = float(eps), float(sigma)
+        self.plan_rows_min = int(plan_rows_min)
+        self._build_lists(self.half)
+        self.c_batch = lj.LjBatch()
+        self.init(tpi, rows_per_item)
+
+    def _build_lists(self, half: bool):
+        """Every system's list (half or full) in place, and the host
+        descriptors and device plan for it."""
+        lib, st, nsys = self.lib, lj._stream(None), len(self.systems)
+        self.half = bool(half)
+        # pass 1: list sizes (capacity 0 reports the size needed)
         nnz = np.zeros(nsys, dtype=np.int64)
         qbase, rbase = self.q4.data_ptr(), self.row_ptr.data_ptr()
         for k, s in enumerate(self.systems):
@@ -73,12 +83,9 @@ class Batch:
             y.row_offset, y.entry_offset, y.nnz = int(self.row_offset[k]), int(self.entry_offset[k]), int(nnz[k])
             for a in range(3):
                 y.box[a] = float(s.box[a])
-            y.r_cut, y.eps, y.sigma, y.half = float(s.rc), float(eps), float(sigma), int(half)
-        self.plan = lj._workspace(lib.lj_batch_plan_bytes(self.c_systems, nsys, int(plan_rows_min)),
+            y.r_cut, y.eps, y.sigma, y.half = float(s.rc), self.eps, self.sigma, int(half)
+        self.plan = lj._workspace(lib.lj_batch_plan_bytes(self.c_systems, nsys, self.plan_rows_min),
                                   self.device)
-        self.plan_rows_min = int(plan_rows_min)
-        self.c_batch = lj.LjBatch()
-        self.init(tpi, rows_per_item)
 
     @property
     def pairs(self) -> int:
@@ -140,8 +147,25 @@ class Batch:
             self.force(p4)
         return g
 
-    def autotune(self, tpis=None, rows=(16, 32, 64, 128), reps: int = 5):
-        """Pick lanes-per-row and rows-per-item by timing; applies and returns them."""
+    def autotune(self, tpis=None, rows=(16, 32, 64, 128), reps: int = 5, layouts=None):
+        """Pick lanes-per-row and rows-per-item -- and, with layouts=(True,
+        False), the list layout (half list with p_j atomics, or full list
+        without) -- by timing; applies them and returns (tpi, rows, ms)."""
+        layouts = (self.half,) if layouts is None else tuple(bool(h) for h in layouts)
+        best = None
+        for half in layouts:
+            if half != self.half:
+                self._build_lists(half)
+                self.init(self.c_batch.tpi, self.c_batch.rows_per_item)
+            t, r, ms = self._autotune_layout(tpis, rows, reps)
+            if best is None or ms < best[3]:
+                best = (half, t, r, ms)
+        if best[0] != self.half:
+            self._build_lists(best[0])
+        self.init(best[1], best[2])
+        return best[1], best[2], best[3]
+
+    def _autotune_layout(self, tpis, rows, reps):
         if tpis is None:
             tpis = (4, 8, 16) if self.precision == lj.LJ_DFLOAT else (2, 4, 8, 16)
         scratch = torch.zeros_like(self.p4)
@@ -156,5 +180,4 @@ class Batch:
                                                self.ws.data_ptr(), self.ws.numel(), int(reps),
                                                ctypes.byref(bt), ctypes.byref(br), ctypes.byref(bm),
                                                lj._stream(None)), "lj_autotune_batched")
-        self.init(bt.value, br.value)
         return bt.value, br.value, bm.value

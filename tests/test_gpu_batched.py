@@ -115,6 +115,26 @@ def test_autotune_picks_a_valid_schedule(cuda_lib, oracle_lib, systems):
     assert np.max(np.abs(got - want)) <= FP64_TOL * np.max(np.abs(want))
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_autotune_picks_the_list_layout(cuda_lib, oracle_lib, systems, precision):
+    """With both layouts offered the tuner times the half list (p_j atomics)
+    and the full list and keeps the faster; the batch then gives the
+    oracle's momenta with the kept layout."""
+    from paper_1806_05713_gb300.batch import Batch
+    b = Batch(systems, 0.01, precision, True, tpi=8, rows_per_item=64, plan_rows_min=16)
+    tpi, rows, ms = b.autotune(tpis=(4, 8), rows=(16, 64), reps=2, layouts=(True, False))
+    assert tpi in (4, 8) and rows in (16, 64) and 0 < ms < 1e3
+    assert b.pairs == (int(b.nnz.sum()) if b.half else int(b.nnz.sum()) // 2)
+    b.p4.zero_()
+    b.force()
+    torch.cuda.synchronize()
+    tol = FP64_TOL if precision != 1 else MIXED_TOL
+    for k in (0, 3):
+        got = _per_system(b, b.p4)[k]
+        want = _oracle_dp(oracle_lib, systems[k], 0.01, True)
+        assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
 def test_autotune_force_single_system(cuda_lib):
     lj = cuda_lib
     s = inputs.workload_small()
