@@ -663,7 +663,9 @@ def forms(lj, q, pl, box, s, best_tpi, flops, dev, stream, flush):
     """The three arithmetic forms on the headline workload (half list, one
     force call, L2 flushed): time, pair interactions/s, FP64-equivalent
     TFLOP/s (the paper's 28 flops per in-cutoff pair), error vs the FP64
-    kernel (itself within 1e-12 of the oracle in the tests)."""
+    kernel (itself within 1e-12 of the oracle in the tests); and each form
+    again with the list layout (half or full) chosen by measurement, its
+    pairs still counted as unique half-list entries."""
     import torch
     res, ref = {}, None
     for name, prec, tpis in (("fp64", lj.LJ_FP64, (best_tpi,)), ("mixed", lj.LJ_MIXED, (8, 16)),
@@ -689,6 +691,17 @@ def forms(lj, q, pl, box, s, best_tpi, flops, dev, stream, flush):
             r["rms_err_rel_vs_fp64"] = float(err.pow(2).mean().sqrt() / ref.pow(2).mean().sqrt())
             r["speedup_vs_fp64"] = res["fp64"]["ms_per_call"] / ms
         res[name] = r
+    # each form with the list layout and schedule chosen by measurement
+    # (lj_autotune_layout: half list with p_j atomics, or full list)
+    for name, prec in (("fp64", lj.LJ_FP64), ("mixed", lj.LJ_MIXED), ("dfloat", lj.LJ_DFLOAT)):
+        plb, t, _, _ = lj.lj_autotune_layout(q, box, s.rs, DT, s.rc, precision=prec, reps=3)
+        pp = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
+        ms = time_calls(lj.lj_force_prepared(q, pp, plb, DT, s.rc, box, precision=prec, tpi=t),
+                        stream, flush)
+        res[name]["best_layout"] = {"list": "half" if plb.half else "full",
+                                    "schedule": schedule_name(t), "ms_per_call": ms,
+                                    "pairs_per_s": pl.nnz / (ms / 1e3)}
+        del plb, pp
     res["note"] = ("dfloat: pair arithmetic in double-float on the FP32 pipe, exact fixed-point "
                    "displacement; mixed: FP32 pair arithmetic; both add into FP64 momenta")
     return res

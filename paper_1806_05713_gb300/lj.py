@@ -392,6 +392,24 @@ def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float
     return int(best.value), float(best_ms.value), {c: float(m) for c, m in zip(candidates, ms)}
 
 
+def lj_autotune_layout(q4: torch.Tensor, box, r_search: float, dt: float, r_cut: float,
+                       eps: float = 1.0, sigma: float = 1.0, precision: int = LJ_FP64,
+                       reps: int = 5, stream=None):
+    """The list layout chosen by measurement: builds the half list (p_j by
+    atomics) and the full list (no p_j writes), tunes the schedule on each
+    with lj_autotune_force and keeps the faster.  Returns (plist, tpi, ms,
+    {(half, tpi): ms})."""
+    best, table = None, {}
+    for half in (True, False):
+        pl = lj_build_pairlist(q4, box, r_search, half, stream=stream)
+        t, ms, tab = lj_autotune_force(q4, pl, dt, r_cut, box, eps, sigma, precision, reps=reps,
+                                       stream=stream)
+        table.update({(half, c): m for c, m in tab.items()})
+        if best is None or ms < best[2]:
+            best = (pl, t, ms)
+    return best[0], best[1], best[2], table
+
+
 def lj_drift(q4: torch.Tensor, p4: torch.Tensor, dt: float, box,
              max_disp2: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """q += dt p (wrapped); returns the 1-element device tensor max |dt p|^2."""

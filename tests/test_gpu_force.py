@@ -256,3 +256,20 @@ def test_million_atoms_fp64_and_mixed(cuda_lib, oracle_lib):
     assert _relerr(got, want) <= FP64_TOL
     got, _ = _run(cuda_lib, s, True, 1, 8, pl=pl)
     assert _relerr(got, want) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL), (2, FP64_TOL)])
+def test_autotune_layout(cuda_lib, oracle_lib, small, precision, tol):
+    """The layout chosen by measurement (half or full list) and its schedule
+    give the oracle's momenta."""
+    lj = cuda_lib
+    q = to_dev(small.q)
+    pl, tpi, ms, table = lj.lj_autotune_layout(q, small.box, small.rs, 0.01, small.rc,
+                                               precision=precision, reps=2)
+    assert (pl.half, tpi) in table and ms == min(table.values())
+    assert {h for h, _ in table} == {True, False}
+    p = torch.zeros_like(q)
+    lj.lj_force(q, p, pl, 0.01, small.rc, small.box, precision=precision, tpi=tpi)
+    torch.cuda.synchronize()
+    want = _oracle(oracle_lib, small, True)
+    assert _relerr(p.cpu().numpy()[:, :3], want) <= tol
