@@ -60,11 +60,11 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
 # L2 read and reduction sectors per launch of the FP64 force kernel from the
 # same ncu capture (the gathered-bytes view), per schedule.
 LTS_SECTORS_PER_LAUNCH = {
-    2056: (11227842, 24806236, "profiles/force_fp64_fixed_tpi8_half_N119164.md"),
+    2056: (11254023, 24806804, "profiles/force_fp64_fixed_tpi8_half_N119164.md"),
 }
 TRAFFIC_PER_LAUNCH = {
     1032: (41903872.0 + 1280.0, "profiles/force_fp64_images_tpi8_half_N119164.md"),
-    2056: (41911040.0 + 2560.0, "profiles/force_fp64_fixed_tpi8_half_N119164.md"),
+    2056: (41910784.0 + 5632.0, "profiles/force_fp64_fixed_tpi8_half_N119164.md"),
     4104: (41915904.0, "profiles/force_fp64_compact_tpi8_half_N119164.md"),
 }
 
