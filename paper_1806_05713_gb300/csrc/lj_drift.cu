@@ -8,7 +8,10 @@
 // fastest atom (the criterion the paper cites) bounds that distance by the
 // sum over steps of the largest per-step displacement.  lj_drift moves the
 // atoms, q += dt p, wrapped back into [0, L), and reports that largest
-// per-step displacement.
+// per-step displacement.  lj_md_steps queues whole leapfrog steps (drift,
+// the bound and its test, kick) with the test taken on the device, the
+// bound either that sum or the largest displacement since the build
+// measured against the positions the list was built from.
 #include <cmath>
 
 #include "lj_internal.cuh"
