@@ -149,9 +149,11 @@ size_t lj_pairlist_workspace_bytes(int64_t n, const double box[3], double r_sear
  * all (i, j), j != i (j > i if half != 0), with minimum-image
  * r^2 < r_search^2, where r^2 = (dx*dx + dy*dy) + dz*dz in round-to-nearest
  * double arithmetic without fused multiply-adds (the list is bit-exact
- * against that definition).  Atoms are binned into cells of side >= r_search
- * (the linked-list cell method), candidates are screened in FP32 with a
- * proven error bound and decided in FP64, and each row is sorted.
+ * against that definition).  Atoms are binned into cells of side
+ * >= r_search / 2 (the linked-list cell method with a 5 x 5 x 5 stencil; with
+ * five or more cells on every axis each pair is met once, over the forward
+ * half of the stencil), candidates are screened in FP32 with a proven error
+ * bound and decided in FP64, and each row is sorted by j.
  *
  *  q4_dev        n x 4 doubles, positions in [0, L).
  *  n             number of atoms (>= 0; n = 0 gives an empty list).
