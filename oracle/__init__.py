@@ -17,6 +17,9 @@ and force-shifted pins on random gases in random boxes with hypothesis):
   F = -grad E by central differences; half list == full list; invariance
   under permutation and translation; the eps/sigma scaling law.
 * energy: pinned -- V(2^(1/6) sigma) = -eps, V(sigma) = 0, the shift.
+* virial: pinned -- minus the derivative of the energy under a uniform
+  scaling of coordinates and box (central differences); two-body closed
+  forms (zero at 2^(1/6) sigma, 24 eps at r = sigma).
 * force_vjp: pinned -- central finite differences of the loss (h = 1e-6)
   built from ``forces`` alone.
 * force_fs, energy_fs (force-shifted truncation): pinned -- sympy's
@@ -25,4 +28,4 @@ and force-shifted pins on random gases in random boxes with hypothesis):
   central differences; Newton's third law; half list == full list.
 """
 from .oracle import (build, energy, energy_fs, force, force_fs, force_vjp, forces,  # noqa: F401
-                     pairlist)
+                     pairlist, virial)

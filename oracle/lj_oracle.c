@@ -273,6 +273,35 @@ double oracle_energy(int64_t n, const double *q, int64_t qstride, const int32_t 
     return e;
 }
 
+/*
+ * The pair virial of the truncated Eq. (1): W = sum over unique pairs with
+ * r < r_c of r F(r), F(r) = -dV/dr = 24 eps (2 (sigma/r)^12 - (sigma/r)^6) / r
+ * (positive when repulsive), so W = sum 24 eps (2 (sigma/r)^12 - (sigma/r)^6).
+ * With the kinetic energy K, the pressure of the box is (2 K + W) / (3 V).
+ */
+double oracle_virial(int64_t n, const double *q, int64_t qstride, const int32_t *row_ptr,
+                     const int32_t *col, int half, double rc, const double *L, double eps,
+                     double sigma)
+{
+    double rc2 = rc * rc;
+    double w = 0.0;
+    double r[3];
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int64_t j = col[k];
+            if (!half && j < i)
+                continue;
+            double r2 = displacement(q + i * qstride, q + j * qstride, L, r);
+            if (r2 < rc2) {
+                double sr2 = sigma * sigma / r2;
+                double sr6 = sr2 * sr2 * sr2;
+                w += 24.0 * eps * (2.0 * sr6 * sr6 - sr6);
+            }
+        }
+    }
+    return w;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Force-shifted truncation                                                  */
 /* ------------------------------------------------------------------------ */

@@ -15,6 +15,7 @@ follow:
 * ``force``: Algorithm 3 (sorted list) with Algorithm 1 per pair; the
   momentum change of one call, p_i -= df r, p_j += df r (half list).
 * ``energy``: Eq. (1) truncated at r_c, optionally shifted to V(r_c) = 0.
+* ``virial``: the pair virial sum r F(r) of the same truncated Eq. (1).
 * ``force_vjp``: the adjoint of the force map F(q; eps, sigma), derived from
   Eq. (1).
 """
@@ -70,6 +71,8 @@ def _load():
         lib.oracle_energy.restype = _dbl
         lib.oracle_energy.argtypes = [_i64, _vp, _i64, _vp, _vp, _int, _dbl, _vp, _dbl, _dbl,
                                       _int]
+        lib.oracle_virial.restype = _dbl
+        lib.oracle_virial.argtypes = [_i64, _vp, _i64, _vp, _vp, _int, _dbl, _vp, _dbl, _dbl]
         lib.oracle_force_fs.restype = None
         lib.oracle_force_fs.argtypes = [_i64, _vp, _i64, _vp, _i64, _vp, _vp, _int, _dbl, _dbl,
                                         _vp, _dbl, _dbl]
@@ -144,6 +147,19 @@ def energy(q, row_ptr, col, half: bool, rc: float, box, eps: float = 1.0, sigma:
     return float(lib.oracle_energy(q.shape[0], _ptr(q), q.shape[1], _ptr(row_ptr), _ptr(col),
                                    int(bool(half)), float(rc), _ptr(L), float(eps),
                                    float(sigma), int(bool(shifted))))
+
+
+def virial(q, row_ptr, col, half: bool, rc: float, box, eps: float = 1.0,
+           sigma: float = 1.0) -> float:
+    """Pair virial W = sum over unique pairs with r < r_c of r F(r),
+    F = -dV/dr of Eq. (1)."""
+    lib = _load()
+    q = _rows(q, "q")
+    L = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    return float(lib.oracle_virial(q.shape[0], _ptr(q), q.shape[1], _ptr(row_ptr), _ptr(col),
+                                   int(bool(half)), float(rc), _ptr(L), float(eps), float(sigma)))
 
 
 def force_fs(q, p, row_ptr, col, half: bool, dt: float, rc: float, box, eps: float = 1.0,

@@ -318,6 +318,36 @@ def test_force_is_minus_gradient_of_energy(oracle_lib):
         assert abs(fd - F[i, a]) < 1e-6 * max(1.0, abs(F[i, a])), (i, a, fd, F[i, a])
 
 
+@pytest.mark.parametrize("half", [True, False])
+def test_virial_is_minus_scaling_derivative_of_energy(oracle_lib, half):
+    """W = sum r F(r) = -dU/dlambda at lambda = 1 when every coordinate and
+    the box are scaled by lambda (central differences of the shifted energy,
+    whose pair set and shift stay fixed for small h)."""
+    s = inputs.fcc_system(5, 0.9, 0.08, seed=23)
+    rp, col = oracle_lib.pairlist(s.q, s.box, 3.3, half)
+    W = oracle_lib.virial(s.q, rp, col, half, 3.0, s.box, 1.1, 0.95)
+    h = 1e-6
+
+    def U(lam):
+        q = s.q.copy()
+        q[:, :3] *= lam
+        return oracle_lib.energy(q, rp, col, half, 3.0, np.asarray(s.box) * lam, 1.1, 0.95,
+                                 shifted=True)
+    fd = -(U(1 + h) - U(1 - h)) / (2 * h)
+    assert abs(fd - W) < 1e-6 * abs(W), (fd, W)
+
+
+def test_virial_closed_forms(oracle_lib):
+    """One pair: r F(r) is zero at the potential minimum 2^(1/6) sigma and
+    24 eps at r = sigma; beyond r_c it is not counted."""
+    for r, want in ((2 ** (1 / 6), 0.0), (1.0, 24.0), (0.9, 24.0 * (2 * 0.9 ** -12 - 0.9 ** -6)),
+                    (3.05, 0.0)):
+        q, box = _two_body(r)
+        rp, col = oracle_lib.pairlist(q, box, 3.3, True)
+        W = oracle_lib.virial(q, rp, col, True, 3.0, box)
+        assert abs(W - want) < 1e-12 * max(1.0, abs(want)), (r, W, want)
+
+
 # --------------------------------------------------------------------------
 # Adjoint
 # --------------------------------------------------------------------------
