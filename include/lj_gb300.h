@@ -281,20 +281,36 @@ int lj_force_strided(const double *q_dev, double *p_dev, int64_t n, int64_t row_
 size_t lj_force_energy_workspace_bytes(int64_t n);
 
 /*
- * lj_force (FP64 form, 8 lanes per row, image-selected displacement) that
- * also returns the potential energy of the same configuration, Eq. (1)
- * truncated at r_cut and, if shifted != 0, shifted so that V(r_cut) = 0 --
- * the energy a velocity-Verlet loop monitors, as a by-product of the force
- * pass (the pair energy reuses the pass's 1/r^2: three extra FP64
- * instructions per pair).  e_out_dev: one device double, overwritten; a
- * full list counts each pair once (half of its entries' sum).  The energy
- * sum is deterministic (fixed-order reduction).  Asynchronous.  Errors as
- * lj_force and lj_energy.
+ * lj_force (FP64 form, 8 lanes per row; the exact fixed-point displacement,
+ * or image selection for boxes wider than 1024 r_cut) that also returns the
+ * potential energy of the same configuration, Eq. (1) truncated at r_cut
+ * and, if shifted != 0, shifted so that V(r_cut) = 0 -- the energy a
+ * velocity-Verlet loop monitors, as a by-product of the force pass (the pair
+ * energy reuses the pass's 1/r^2: three extra FP64 instructions per pair).
+ * e_out_dev: one device double, overwritten; a full list counts each pair
+ * once (half of its entries' sum).  The energy sum is deterministic
+ * (fixed-order reduction).  Asynchronous.  Errors as lj_force and lj_energy.
  */
 int lj_force_energy(const double *q4_dev, double *p4_dev, int64_t n, const int32_t *row_ptr_dev,
                     const int32_t *col_dev, int64_t nnz, int half, double dt, double r_cut,
                     const double box[3], double eps, double sigma, int shifted, double *e_out_dev,
                     void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/*
+ * lj_force_energy that also returns the pair virial of the same pass,
+ *   W = sum over unique pairs with r < r_cut of r F(r),
+ *   F(r) = -dV/dr = 24 eps (2 (sigma/r)^12 - (sigma/r)^6) / r
+ * (unaffected by the energy shift; positive when the pairs repel), so that
+ * with the kinetic energy K the pressure of the box is (2 K + W) / (3 V).
+ * w_out_dev: one device double (8-byte aligned), overwritten.  Same
+ * workspace (lj_force_energy_workspace_bytes), semantics and errors as
+ * lj_force_energy; LJ_ERR_ARG if w_out_dev is NULL.
+ */
+int lj_force_energy_virial(const double *q4_dev, double *p4_dev, int64_t n,
+                           const int32_t *row_ptr_dev, const int32_t *col_dev, int64_t nnz,
+                           int half, double dt, double r_cut, const double box[3], double eps,
+                           double sigma, int shifted, double *e_out_dev, double *w_out_dev,
+                           void *workspace_dev, size_t workspace_bytes, void *stream);
 
 /* Bytes of device workspace lj_force_shifted needs. */
 size_t lj_force_shifted_workspace_bytes(int64_t n);

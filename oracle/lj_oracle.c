@@ -274,6 +274,7 @@ double oracle_energy(int64_t n, const double *q, int64_t qstride, const int32_t 
 }
 
 /*
+ * (Not in the paper; the by-product its bookkeeping MD needs for pressure.)
  * The pair virial of the truncated Eq. (1): W = sum over unique pairs with
  * r < r_c of r F(r), F(r) = -dV/dr = 24 eps (2 (sigma/r)^12 - (sigma/r)^6) / r
  * (positive when repulsive), so W = sum 24 eps (2 (sigma/r)^12 - (sigma/r)^6).

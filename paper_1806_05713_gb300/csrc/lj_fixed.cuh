@@ -289,8 +289,9 @@ __device__ __forceinline__ bool fixed_entry(const double *__restrict__ q4, long 
 // One row of the FP64 form with the exact fixed-point displacement (see the
 // header comment); the arithmetic after r^2 is fp64_row's.  EN: also sum the
 // pair energy 4 eps [(sigma/r)^12 - (sigma/r)^6] of every interacting entry
-// into *ev and count them in *ecount.  FS: the force-shifted truncation --
-// df - F_c dt / r, and (EN) the pair energy V(r) - V(r_c) + (r - r_c) F_c.
+// into *ev, its pair virial r F(r) into *wv, and count them in *ecount.
+// FS: the force-shifted truncation -- df - F_c dt / r, and (EN) the pair
+// energy V(r) - V(r_c) + (r - r_c) F_c and virial r F(r) - r F_c.
 template <int TPI, bool HALF, bool EN = false, bool FS = false>
 __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
                                                const longlong4 *__restrict__ X,
@@ -298,7 +299,8 @@ __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
                                                const int *__restrict__ row_ptr,
                                                const int *__restrict__ col, int i,
                                                const Fp64Params &P, const FixParams &F, unsigned gm,
-                                               double *ev = nullptr, int *ecount = nullptr)
+                                               double *ev = nullptr, int *ecount = nullptr,
+                                               double *wv = nullptr)
 {
     const int sub = threadIdx.x & (TPI - 1);
     long long xi, yi, zi;
@@ -328,8 +330,13 @@ __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
             if (in) {
                 if (EN) {
                     double v = w3 * fma(P.C12, w3, -P.C6);
-                    if (FS) v += fma(r2, inv_r, -P.rc) * P.Fc - P.Vc;
+                    double vir = w3 * fma(P.W12, w3, -P.W6);
+                    if (FS) {
+                        v += fma(r2, inv_r, -P.rc) * P.Fc - P.Vc;
+                        vir = fma(-P.Fc, r2 * inv_r, vir);
+                    }
                     *ev += v;
+                    *wv += vir;
                     ++*ecount;
                 }
                 if (HALF) {

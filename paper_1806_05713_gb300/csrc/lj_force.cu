@@ -133,48 +133,52 @@ force_energy_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restr
                          double *__restrict__ partial)
 {
     constexpr int TPI = 8;
-    __shared__ double red_e[8];
+    __shared__ double red_e[8], red_w[8];
     __shared__ long long red_c[8];
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
-    double ev = 0.0;
+    double ev = 0.0, wv = 0.0;
     int cnt = 0;
     if (gid < n) {
         if (FS || X) {
             if (half)
                 fp64_fixed_row<TPI, true, true, FS>(q4, X, p4, row_ptr, col, gid, P, F,
-                                                    group_mask<TPI>(), &ev, &cnt);
+                                                    group_mask<TPI>(), &ev, &cnt, &wv);
             else
                 fp64_fixed_row<TPI, false, true, FS>(q4, X, p4, row_ptr, col, gid, P, F,
-                                                     group_mask<TPI>(), &ev, &cnt);
+                                                     group_mask<TPI>(), &ev, &cnt, &wv);
         } else {  // a box wider than 1024 r_c: image-selected rows
             if (half)
                 fp64_row<TPI, true, 1, true, 0, true>(q4, p4, row_ptr, col, gid, P, group_mask<TPI>(),
-                                                      Layout{4, 1}, &ev, &cnt);
+                                                      Layout{4, 1}, &ev, &cnt, &wv);
             else
                 fp64_row<TPI, false, 1, true, 0, true>(q4, p4, row_ptr, col, gid, P, group_mask<TPI>(),
-                                                       Layout{4, 1}, &ev, &cnt);
+                                                       Layout{4, 1}, &ev, &cnt, &wv);
         }
     }
     long long c = cnt;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ev += __shfl_xor_sync(0xffffffffu, ev, o);
+        wv += __shfl_xor_sync(0xffffffffu, wv, o);
         c += __shfl_xor_sync(0xffffffffu, c, o);
     }
     if ((threadIdx.x & 31) == 0) {
         red_e[threadIdx.x >> 5] = ev;
+        red_w[threadIdx.x >> 5] = wv;
         red_c[threadIdx.x >> 5] = c;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double se = 0.0;
+        double se = 0.0, sw = 0.0;
         long long sc = 0;
         for (int w = 0; w < 8; ++w) {
             se += red_e[w];
+            sw += red_w[w];
             sc += red_c[w];
         }
-        partial[2 * blockIdx.x] = se;
-        partial[2 * blockIdx.x + 1] = static_cast<double>(sc);
+        partial[3 * blockIdx.x] = se;
+        partial[3 * blockIdx.x + 1] = static_cast<double>(sc);
+        partial[3 * blockIdx.x + 2] = sw;
     }
 }
 
@@ -191,33 +195,40 @@ force_fs_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
     fp64_fixed_row<TPI, HALF, false, true>(q4, X, p4, row_ptr, col, gid, P, F, group_mask<TPI>());
 }
 
-// E = scale * (sum of pair energies - vshift * number of in-cutoff entries).
+// E = scale * (sum of pair energies - vshift * number of in-cutoff entries)
+// and, with wout, W = scale * (sum of pair virials); fixed-order sums.
 __global__ void energy_partials_kernel(const double *__restrict__ partial, int blocks, double scale,
-                                       double vshift, double *__restrict__ out)
+                                       double vshift, double *__restrict__ out,
+                                       double *__restrict__ wout)
 {
-    __shared__ double se[32], sc[32];
-    double e = 0.0, c = 0.0;
+    __shared__ double se[32], sc[32], sw[32];
+    double e = 0.0, c = 0.0, v = 0.0;
     for (int t = threadIdx.x; t < blocks; t += blockDim.x) {
-        e += partial[2 * t];
-        c += partial[2 * t + 1];
+        e += partial[3 * t];
+        c += partial[3 * t + 1];
+        v += partial[3 * t + 2];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         e += __shfl_xor_sync(0xffffffffu, e, o);
         c += __shfl_xor_sync(0xffffffffu, c, o);
+        v += __shfl_xor_sync(0xffffffffu, v, o);
     }
     if ((threadIdx.x & 31) == 0) {
         se[threadIdx.x >> 5] = e;
         sc[threadIdx.x >> 5] = c;
+        sw[threadIdx.x >> 5] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double te = 0.0, tc = 0.0;
+        double te = 0.0, tc = 0.0, tw = 0.0;
         for (int w = 0; w < int(blockDim.x / 32); ++w) {
             te += se[w];
             tc += sc[w];
+            tw += sw[w];
         }
         *out = scale * (te - vshift * tc);
+        if (wout) *wout = scale * tw;
     }
 }
 
@@ -562,25 +573,28 @@ extern "C" size_t lj_force_energy_workspace_bytes(int64_t n)
 {
     const int64_t blocks = (std::max<int64_t>(n, 1) * 8 + 255) / 256;
     lj::Carver c(nullptr);
-    c.take<double>(2 * size_t(blocks));
+    c.take<double>(3 * size_t(blocks));
     c.take<longlong4>(size_t(std::max<int64_t>(n, 1)));
     return c.used + 256;
 }
 
-extern "C" int lj_force_energy(const double *q4_dev, double *p4_dev, int64_t n,
-                               const int32_t *row_ptr_dev, const int32_t *col_dev, int64_t nnz,
-                               int half, double dt, double r_cut, const double box[3], double eps,
-                               double sigma, int shifted, double *e_out_dev, void *workspace_dev,
-                               size_t workspace_bytes, void *stream)
+namespace lj {
+namespace {
+
+int force_energy_impl(const double *q4_dev, double *p4_dev, int64_t n, const int32_t *row_ptr_dev,
+                      const int32_t *col_dev, int64_t nnz, int half, double dt, double r_cut,
+                      const double box[3], double eps, double sigma, int shifted, double *e_out_dev,
+                      double *w_out_dev, void *workspace_dev, size_t workspace_bytes,
+                      cudaStream_t st)
 {
-    using namespace lj;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = check_force_args(q4_dev, p4_dev, n, row_ptr_dev, col_dev, nnz, r_cut, box, eps, sigma,
                               dt);
     if (rc != LJ_OK) return rc;
     if (!e_out_dev || (reinterpret_cast<uintptr_t>(e_out_dev) & 7u)) return LJ_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(w_out_dev) & 7u) return LJ_ERR_ARG;
     if (n == 0 || nnz == 0) {
         LJ_TRY_CUDA(cudaMemsetAsync(e_out_dev, 0, sizeof(double), st));
+        if (w_out_dev) LJ_TRY_CUDA(cudaMemsetAsync(w_out_dev, 0, sizeof(double), st));
         return LJ_OK;
     }
     if (!workspace_dev || workspace_bytes < lj_force_energy_workspace_bytes(n)) return LJ_ERR_CAPACITY;
@@ -588,7 +602,7 @@ extern "C" int lj_force_energy(const double *q4_dev, double *p4_dev, int64_t n,
     const FixParams F = make_fix_params(box);
     const int blocks = static_cast<int>((n * 8 + 255) / 256);
     Carver c(workspace_dev);
-    double *partial = c.take<double>(2 * size_t(blocks));
+    double *partial = c.take<double>(3 * size_t(blocks));
     longlong4 *X = c.take<longlong4>(size_t(n));
     if (fixed_point_ok(box, r_cut)) {
         fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, static_cast<int>(n), F, X);
@@ -604,9 +618,37 @@ extern "C" int lj_force_energy(const double *q4_dev, double *p4_dev, int64_t n,
         const double sr2 = sigma * sigma / (r_cut * r_cut), sr6 = sr2 * sr2 * sr2;
         vshift = 4.0 * eps * (sr6 * sr6 - sr6);
     }
-    energy_partials_kernel<<<1, 1024, 0, st>>>(partial, blocks, half ? 1.0 : 0.5, vshift, e_out_dev);
+    energy_partials_kernel<<<1, 1024, 0, st>>>(partial, blocks, half ? 1.0 : 0.5, vshift, e_out_dev,
+                                               w_out_dev);
     LJ_TRY_LAUNCH("energy_partials_kernel");
     return LJ_OK;
+}
+
+}  // namespace
+}  // namespace lj
+
+extern "C" int lj_force_energy(const double *q4_dev, double *p4_dev, int64_t n,
+                               const int32_t *row_ptr_dev, const int32_t *col_dev, int64_t nnz,
+                               int half, double dt, double r_cut, const double box[3], double eps,
+                               double sigma, int shifted, double *e_out_dev, void *workspace_dev,
+                               size_t workspace_bytes, void *stream)
+{
+    return lj::force_energy_impl(q4_dev, p4_dev, n, row_ptr_dev, col_dev, nnz, half, dt, r_cut, box,
+                                 eps, sigma, shifted, e_out_dev, nullptr, workspace_dev,
+                                 workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int lj_force_energy_virial(const double *q4_dev, double *p4_dev, int64_t n,
+                                      const int32_t *row_ptr_dev, const int32_t *col_dev,
+                                      int64_t nnz, int half, double dt, double r_cut,
+                                      const double box[3], double eps, double sigma, int shifted,
+                                      double *e_out_dev, double *w_out_dev, void *workspace_dev,
+                                      size_t workspace_bytes, void *stream)
+{
+    if (!w_out_dev) return LJ_ERR_ARG;
+    return lj::force_energy_impl(q4_dev, p4_dev, n, row_ptr_dev, col_dev, nnz, half, dt, r_cut, box,
+                                 eps, sigma, shifted, e_out_dev, w_out_dev, workspace_dev,
+                                 workspace_bytes, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" size_t lj_force_shifted_workspace_bytes(int64_t n)
@@ -637,7 +679,7 @@ extern "C" int lj_force_shifted(const double *q4_dev, double *p4_dev, int64_t n,
     const int ni = static_cast<int>(n);
     const int blocks = static_cast<int>((n * 8 + 255) / 256);
     Carver c(workspace_dev);
-    double *partial = c.take<double>(2 * size_t(blocks));
+    double *partial = c.take<double>(3 * size_t(blocks));
     longlong4 *X = c.take<longlong4>(size_t(n));
     fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, ni, F, X);
     LJ_TRY_LAUNCH("fixed_prepass_kernel");
@@ -645,7 +687,8 @@ extern "C" int lj_force_shifted(const double *q4_dev, double *p4_dev, int64_t n,
         force_energy_fp64_kernel<true><<<blocks, 256, 0, st>>>(q4_dev, X, p4_dev, ni, row_ptr_dev,
                                                                col_dev, P, F, half, partial);
         LJ_TRY_LAUNCH("force_energy_fp64_kernel");
-        energy_partials_kernel<<<1, 1024, 0, st>>>(partial, blocks, half ? 1.0 : 0.5, 0.0, e_out_dev);
+        energy_partials_kernel<<<1, 1024, 0, st>>>(partial, blocks, half ? 1.0 : 0.5, 0.0, e_out_dev,
+                                                   nullptr);
         LJ_TRY_LAUNCH("energy_partials_kernel");
     } else {
         if (half)

@@ -17,6 +17,7 @@ struct Fp64Params {
     double rc2;
     double A, B;  // df = u^4 (A - B u^3): A = 24 eps sigma^6 dt, B = 48 eps sigma^12 dt
     double C12, C6;  // V = u^3 (C12 u^3 - C6): C12 = 4 eps sigma^12, C6 = 4 eps sigma^6
+    double W12, W6;  // r F(r) = u^3 (W12 u^3 - W6): W12 = 48 eps sigma^12, W6 = 24 eps sigma^6
     // force-shifted truncation: F_c = -V'(r_c), fs_c = F_c dt, V_c = V(r_c)
     double rc, Fc, fs_c, Vc;
 };
@@ -166,6 +167,8 @@ Fp64Params make_fp64_params(const double box[3], double dt, double rc, double ep
     P.B = 48.0 * eps * s12 * dt;
     P.C12 = 4.0 * eps * s12;
     P.C6 = 4.0 * eps * s6;
+    P.W12 = 48.0 * eps * s12;
+    P.W6 = 24.0 * eps * s6;
     const double sr = sigma / rc, sr2 = sr * sr, sr6 = sr2 * sr2 * sr2;
     P.rc = rc;
     P.Fc = 24.0 * eps * (2.0 * sr6 * sr6 - sr6) / rc;

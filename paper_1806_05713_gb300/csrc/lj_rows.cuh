@@ -52,14 +52,16 @@ __device__ __forceinline__ double *mom_at(double *__restrict__ p, int i, int a, 
 // so the long dependent FP64 chains of two pairs are in flight together).
 // Pointers are the system's own arrays (local indices).
 // EN: also accumulate the pair energy 4 eps [(sigma/r)^12 - (sigma/r)^6] of
-// every in-cutoff entry into *ev and count the entries into *ecount (the
-// caller applies the shift and, for a full list, the factor 1/2).
+// every in-cutoff entry into *ev, its pair virial r F(r) into *wv, and
+// count the entries into *ecount (the caller applies the shift and, for a
+// full list, the factor 1/2).
 template <int TPI, bool HALF, int U, bool IMG = false, int LAY = 0, bool EN = false>
 __device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *__restrict__ p4,
                                          const int *__restrict__ row_ptr,
                                          const int *__restrict__ col, int i, const Fp64Params &P,
                                          unsigned gm, const Layout &Lay = Layout{4, 1},
-                                         double *ev = nullptr, int *ecount = nullptr)
+                                         double *ev = nullptr, int *ecount = nullptr,
+                                         double *wv = nullptr)
 {
     const int sub = threadIdx.x & (TPI - 1);
     double xi, yi, zi;
@@ -161,6 +163,7 @@ __device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *
                 fn[u] = w4 * fma(P.B, w3, -P.A);  // -df: p_i -= fn d, p_j += fn d
                 if (EN && in[u]) {
                     *ev += w3 * fma(P.C12, w3, -P.C6);  // 4 eps [(s/r)^12 - (s/r)^6]
+                    *wv += w3 * fma(P.W12, w3, -P.W6);  // 24 eps [2 (s/r)^12 - (s/r)^6]
                     ++*ecount;
                 }
             }

@@ -101,6 +101,8 @@ SIGNATURES = {
     "lj_force_energy_workspace_bytes": (_sz, [_i64]),
     "lj_force_energy": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl, _dbl3, _dbl, _dbl,
                                _int, _vp, _vp, _sz, _vp]),
+    "lj_force_energy_virial": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl, _dbl3, _dbl,
+                                      _dbl, _int, _vp, _vp, _vp, _sz, _vp]),
     "lj_force_shifted_workspace_bytes": (_sz, [_i64]),
     "lj_force_shifted": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl, _dbl3, _dbl, _dbl,
                                 _vp, _vp, _sz, _vp]),
@@ -516,6 +518,31 @@ def lj_force_energy(q4: torch.Tensor, p4: torch.Tensor, plist: PairList, dt: flo
                              _dev(out, torch.float64, "out"), workspace.data_ptr(),
                              workspace.numel(), _stream(stream))
     _check(st, "lj_force_energy")
+    return out
+
+
+def lj_force_energy_virial(q4: torch.Tensor, p4: torch.Tensor, plist: PairList, dt: float,
+                           r_cut: float, box, eps: float = 1.0, sigma: float = 1.0,
+                           shifted: bool = False, out: torch.Tensor | None = None,
+                           workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """p4 += impulses (FP64); returns a 2-element tensor (potential energy,
+    pair virial sum r F(r))."""
+    lib = load()
+    n = plist.n
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=q4.device)
+    if out.numel() < 2:
+        raise ValueError("out must hold two doubles (energy, virial)")
+    if workspace is None:
+        workspace = _workspace(lib.lj_force_energy_workspace_bytes(n), q4.device)
+    ep = _dev(out, torch.float64, "out")
+    st = lib.lj_force_energy_virial(_dev(q4, torch.float64, "q4", (n, 4)),
+                                    _dev(p4, torch.float64, "p4", (n, 4)), n,
+                                    plist.row_ptr.data_ptr(), plist.col.data_ptr(), plist.nnz,
+                                    int(plist.half), float(dt), float(r_cut), _box3(box),
+                                    float(eps), float(sigma), int(bool(shifted)), ep, ep + 8,
+                                    workspace.data_ptr(), workspace.numel(), _stream(stream))
+    _check(st, "lj_force_energy_virial")
     return out
 
 
