@@ -174,6 +174,15 @@ class VelocityVerlet:
     def kinetic_energy(self) -> float:
         return 0.5 * float((self.p4[:, :3] ** 2).sum())
 
+    def pressure(self) -> float:
+        """(2 K + W) / (3 V) with the pair virial W of the plain truncation
+        (one FP64 force-and-energy pass with dt = 0 on scratch momenta)."""
+        out = lj.lj_force_energy_virial(self.q4, torch.zeros_like(self.p4), self.plist, 0.0,
+                                        self.r_cut, self.box, self.eps, self.sigma)
+        W = float(out[1].item())
+        V = self.box[0] * self.box[1] * self.box[2]
+        return (2.0 * self.kinetic_energy() + W) / (3.0 * V)
+
     def potential_energy(self, shifted: bool = True) -> float:
         """The truncated potential energy (shifted by V(r_c) or not); with the
         force-shifted truncation, its energy (a force pass with dt = 0)."""

@@ -234,3 +234,28 @@ def test_md_steps_stale_state_does_nothing(cuda_lib):
     assert torch.equal(p, p0d)
     assert st["last_disp2"] == want_d2
     assert st["moved"] == np.sqrt(want_d2)
+
+
+def test_pressure(cuda_lib, oracle_lib):
+    """VelocityVerlet.pressure: (2 K + W) / 3V with the oracle's virial; a
+    dilute gas is close to the ideal-gas value 2 K / 3V."""
+    from paper_1806_05713_gb300.md import VelocityVerlet
+    s, p0 = _hot_system()
+    q, p = to_dev(s.q), to_dev(p0)
+    vv = VelocityVerlet(q, p, s.box, s.rc, s.margin, 0.002)
+    P = vv.pressure()
+    K = vv.kinetic_energy()
+    V = float(np.prod(s.box))
+    rp, col = oracle_lib.pairlist(s.q, s.box, s.rs, True)
+    W = oracle_lib.virial(s.q, rp, col, True, s.rc, s.box)
+    want = (2 * K + W) / (3 * V)
+    assert abs(P - want) <= 1e-12 * abs(want)
+    rng = np.random.default_rng(4)
+    L = 60.0
+    gas = np.zeros((300, 4))
+    gas[:, :3] = rng.random((300, 3)) * L
+    pg = np.zeros((300, 4))
+    pg[:, :3] = rng.normal(size=(300, 3))
+    vg = VelocityVerlet(to_dev(gas), to_dev(pg), [L, L, L], 3.0, 0.3, 0.002)
+    ideal = 2 * vg.kinetic_energy() / (3 * L ** 3)
+    assert abs(vg.pressure() - ideal) < 0.05 * ideal
