@@ -250,12 +250,14 @@ def test_pressure(cuda_lib, oracle_lib):
     W = oracle_lib.virial(s.q, rp, col, True, s.rc, s.box)
     want = (2 * K + W) / (3 * V)
     assert abs(P - want) <= 1e-12 * abs(want)
+    # no pair within r_c (a jittered lattice of spacing 8): the ideal-gas value exactly
     rng = np.random.default_rng(4)
-    L = 60.0
-    gas = np.zeros((300, 4))
-    gas[:, :3] = rng.random((300, 3)) * L
-    pg = np.zeros((300, 4))
-    pg[:, :3] = rng.normal(size=(300, 3))
+    g = (np.arange(7) + 0.5) * 8.0
+    L = 56.0
+    gas = np.zeros((343, 4))
+    gas[:, :3] = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    gas[:, :3] += rng.uniform(-0.5, 0.5, (343, 3))
+    pg = np.zeros((343, 4))
+    pg[:, :3] = rng.normal(size=(343, 3))
     vg = VelocityVerlet(to_dev(gas), to_dev(pg), [L, L, L], 3.0, 0.3, 0.002)
-    ideal = 2 * vg.kinetic_energy() / (3 * L ** 3)
-    assert abs(vg.pressure() - ideal) < 0.05 * ideal
+    assert vg.pressure() == 2 * vg.kinetic_energy() / (3 * L ** 3)
