@@ -1,8 +1,9 @@
 """Property-based pins of the CPU oracle (hypothesis): random small systems
 in random boxes, each checked against a route that does not share the
 oracle's code path -- brute force against the cell method, forces against
-central differences of the energy, conservation of momentum, invariance
-under translation across the periodic boundary."""
+central differences of the energy, the virial against the derivative of
+the energy under scaling, conservation of momentum, invariance under
+translation across the periodic boundary."""
 import numpy as np
 import pytest
 
@@ -114,3 +115,24 @@ def test_force_shifted_is_minus_its_energy_gradient(oracle_lib, g):
             fd = -(oracle_lib.energy_fs(qp, rp, col, True, rc, box) -
                    oracle_lib.energy_fs(qm, rp, col, True, rc, box)) / (2 * h)
             assert abs(fd - F[i, a]) <= 1e-5 * max(1.0, np.max(np.abs(F))), (i, a)
+
+
+@settings(**SETTINGS)
+@given(gas(min_n=3, max_n=30), st.floats(0.85, 1.2), st.floats(0.8, 1.3), st.booleans())
+def test_virial_is_minus_scaling_derivative(oracle_lib, g, eps, sigma, half):
+    """W = -dU/dlambda for coordinates and box scaled by lambda (the shifted
+    energy, so that the pair set and the shift stay fixed for small h)."""
+    q, box, rs = g
+    q = _spread(q, box, 0.75 * sigma)
+    rc = 0.9 * rs
+    rp, col = oracle_lib.pairlist(q, box, rs, half)
+    W = oracle_lib.virial(q, rp, col, half, rc, box, eps, sigma)
+    h = 1e-7
+
+    def U(lam):
+        qs = q.copy()
+        qs[:, :3] *= lam
+        return oracle_lib.energy(qs, rp, col, half, rc, box * lam, eps, sigma, shifted=True)
+    fd = -(U(1 + h) - U(1 - h)) / (2 * h)
+    scale = max(1.0, abs(W))
+    assert abs(fd - W) < 1e-5 * scale, (fd, W)
