@@ -225,7 +225,10 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_name(args.order)},
+        "data": "synthetic",
+        "config": {"workload": workload_name(args.order), "n_atoms": s.n, "pairs_per_call": nnz,
+                   "force_calls_per_step": CPU_FORCE_CALLS, "list_builds_per_step": 1,
+                   "parallelism": "one CPU thread"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
