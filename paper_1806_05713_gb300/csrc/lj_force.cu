@@ -108,8 +108,10 @@ force_compact_kernel(const double *__restrict__ q4, const longlong4 *__restrict_
                                                buf[threadIdx.x / TPI]);
 }
 
+// MIXED form, 128-thread blocks (a finer last wave: the full list 2-4 %
+// faster than with 256).
 template <int TPI, bool HALF>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 force_mixed_kernel(const double *__restrict__ q4, const uint4 *__restrict__ rel,
                    double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
                    const int *__restrict__ col, MixedParams P, const int *__restrict__ order)
@@ -337,11 +339,11 @@ int launch_mixed(const double *q4, const uint4 *rel, double *p4, int n, const in
                  const int *col, int half, const MixedParams &P, const int *order, cudaStream_t st)
 {
     const int64_t threads = int64_t(n) * TPI;
-    const unsigned grid = unsigned((threads + 255) / 256);
+    const unsigned grid = unsigned((threads + 127) / 128);
     if (half)
-        force_mixed_kernel<TPI, true><<<grid, 256, 0, st>>>(q4, rel, p4, n, rp, col, P, order);
+        force_mixed_kernel<TPI, true><<<grid, 128, 0, st>>>(q4, rel, p4, n, rp, col, P, order);
     else
-        force_mixed_kernel<TPI, false><<<grid, 256, 0, st>>>(q4, rel, p4, n, rp, col, P, order);
+        force_mixed_kernel<TPI, false><<<grid, 128, 0, st>>>(q4, rel, p4, n, rp, col, P, order);
     LJ_TRY_LAUNCH("force_mixed_kernel");
     return LJ_OK;
 }
