@@ -132,6 +132,19 @@ def test_host_argument_checks_without_gpu():
     assert md(en=ctypes.c_void_p(260)) == lj.LJ_ERR_ARG
     assert md(en=fake, prec=2) == lj.LJ_ERR_ARG
     assert md(steps=0) == lj.LJ_OK
+    # force + energy (+ virial): outputs required and 8-byte aligned, before any launch
+
+    def fev(e=fake, w=fake, **k):
+        a = args(**k)
+        return L.lj_force_energy_virial(a["q"], a["p"], a["n"], a["rp"], a["col"], a["nnz"],
+                                        a["half"], a["dt"], a["rc"], a["box"], a["eps"], a["sig"],
+                                        1, e, w, fake, 1 << 40, None)
+    assert fev(w=None) == lj.LJ_ERR_ARG
+    assert fev(e=None) == lj.LJ_ERR_ARG
+    assert fev(w=ctypes.c_void_p(260)) == lj.LJ_ERR_ARG
+    assert fev(rc=6.0) == lj.LJ_ERR_BOX
+    assert L.lj_force_energy(fake, fake, 10, fake, fake, 10, 1, 0.01, 3.0, box, 1.0, 1.0, 1, None,
+                             fake, 1 << 40, None) == lj.LJ_ERR_ARG
     assert md(steps=0, flags=lj.LJ_MD_LAST_HALF_KICK, qb=fake, en=fake) == lj.LJ_OK
 
 
