@@ -415,10 +415,10 @@ __device__ __forceinline__ void append_slab(int row, int val, int *__restrict__ 
 
 template <bool HALF>
 __device__ __forceinline__ void forward_run(const double *__restrict__ q4, const Grid &g,
-                                         const float4 *__restrict__ pos_f, int s, int e, int ia,
-                                         float4 pa, bool &have_exact, double &xa, double &ya,
-                                         double &za, int *__restrict__ tmp, int cap,
-                                         int *__restrict__ row_cnt, ListStats *__restrict__ stats)
+                                            const float4 *__restrict__ pos_f, int s, int e, int ia,
+                                            float4 pa, bool &have_exact, double &xa, double &ya,
+                                            double &za, int *__restrict__ tmp, int cap,
+                                            int *__restrict__ row_cnt, ListStats *__restrict__ stats)
 {
     const int lane = threadIdx.x & 31;
     for (int base = s; base < e; base += 32) {
@@ -452,10 +452,11 @@ __device__ __forceinline__ void forward_run(const double *__restrict__ q4, const
 
 template <bool HALF>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-walk_forward_store_kernel(const double *__restrict__ q4, int n, Grid g, const int *__restrict__ cell_of,
-                       const int *__restrict__ cell_start, const int *__restrict__ cell_atoms,
-                       const float4 *__restrict__ pos_f, int *__restrict__ tmp, int cap,
-                       int *__restrict__ row_cnt, ListStats *__restrict__ stats)
+walk_forward_store_kernel(const double *__restrict__ q4, int n, Grid g,
+                          const int *__restrict__ cell_of, const int *__restrict__ cell_start,
+                          const int *__restrict__ cell_atoms, const float4 *__restrict__ pos_f,
+                          int *__restrict__ tmp, int cap, int *__restrict__ row_cnt,
+                          ListStats *__restrict__ stats)
 {
     const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (w >= n) return;
@@ -492,21 +493,22 @@ walk_forward_store_kernel(const double *__restrict__ q4, int n, Grid g, const in
             if (dz == 0 && dy == 0) {
                 // own row: the atoms after a in its cell, then cells cx+1, cx+2
                 if (cx + 2 < g.nc[0]) {
-                    forward_run<HALF>(q4, g, pos_f, w + 1, cell_start[rowc + cx + 3], ia, pa, have_exact, xa,
-                             ya, za, tmp, cap, row_cnt, stats);
+                    forward_run<HALF>(q4, g, pos_f, w + 1, cell_start[rowc + cx + 3], ia, pa,
+                                      have_exact, xa, ya, za, tmp, cap, row_cnt, stats);
                 } else {
-                    forward_run<HALF>(q4, g, pos_f, w + 1, cell_start[rowc + g.nc[0]], ia, pa, have_exact,
-                             xa, ya, za, tmp, cap, row_cnt, stats);
-                    forward_run<HALF>(q4, g, pos_f, cell_start[rowc], cell_start[rowc + cx + 3 - g.nc[0]], ia,
-                             pa, have_exact, xa, ya, za, tmp, cap, row_cnt, stats);
+                    forward_run<HALF>(q4, g, pos_f, w + 1, cell_start[rowc + g.nc[0]], ia, pa,
+                                      have_exact, xa, ya, za, tmp, cap, row_cnt, stats);
+                    forward_run<HALF>(q4, g, pos_f, cell_start[rowc],
+                                      cell_start[rowc + cx + 3 - g.nc[0]], ia, pa, have_exact, xa,
+                                      ya, za, tmp, cap, row_cnt, stats);
                 }
                 continue;
             }
-            forward_run<HALF>(q4, g, pos_f, cell_start[rowc + x0], cell_start[rowc + x1 + 1], ia, pa,
-                     have_exact, xa, ya, za, tmp, cap, row_cnt, stats);
+            forward_run<HALF>(q4, g, pos_f, cell_start[rowc + x0], cell_start[rowc + x1 + 1], ia,
+                              pa, have_exact, xa, ya, za, tmp, cap, row_cnt, stats);
             if (x3 >= x2)
-                forward_run<HALF>(q4, g, pos_f, cell_start[rowc + x2], cell_start[rowc + x3 + 1], ia, pa,
-                         have_exact, xa, ya, za, tmp, cap, row_cnt, stats);
+                forward_run<HALF>(q4, g, pos_f, cell_start[rowc + x2], cell_start[rowc + x3 + 1],
+                                  ia, pa, have_exact, xa, ya, za, tmp, cap, row_cnt, stats);
         }
     }
 }
