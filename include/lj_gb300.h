@@ -170,8 +170,10 @@ size_t lj_pairlist_workspace_bytes(int64_t n, const double box[3], double r_sear
  *  max_row_out   host out (may be NULL): longest row.
  *  stream        cudaStream_t.
  * Blocks the calling thread until the list size is known (one small
- * device-to-host copy), then enqueues the rest of the build and returns:
- * the list is complete in stream order, not yet on return.
+ * device-to-host copy, read on an internal stream of the library -- one per
+ * host thread and device, created on first use -- that waits for the size
+ * only, while the rows are sorted on `stream`), and returns: the list is
+ * complete in stream order, not yet on return.
  * Errors: LJ_ERR_ARG, LJ_ERR_BOX, LJ_ERR_RANGE (a position outside [0, L) or
  * not finite), LJ_ERR_CAPACITY (col_capacity too small, nnz >= 2^31, or a
  * row longer than the 56,000 entries one warp's shared memory can sort),

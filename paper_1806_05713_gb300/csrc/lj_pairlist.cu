@@ -565,8 +565,16 @@ __device__ __forceinline__ void rank_row(const int *__restrict__ buf, int len, i
 // so each warp's buffer is 16-byte aligned and holds the padding.
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 sort_rows_kernel(const int *__restrict__ tmp, int cap, int n, const int32_t *__restrict__ row_ptr,
-                 int32_t *__restrict__ col)
+                 int32_t *__restrict__ col, const ListStats *__restrict__ stats, int64_t col_cap)
 {
+    // launched before the host has read the list size: nothing to do if the
+    // walk overflowed a slab, met a position out of range, or the list does
+    // not fit col (the host then reports it or takes the two-walk path)
+    {
+        const int err = stats->err;
+        const int64_t nnz = stats->nnz;
+        if ((err & 5) || nnz > col_cap || nnz >= INT32_MAX) return;
+    }
     extern __shared__ int4 smem4[];
     int *smem = reinterpret_cast<int *>(smem4);
     const int wib = threadIdx.x >> 5;
@@ -618,6 +626,36 @@ int slab_cap(int64_t n, const double box[3], double rs)
 }
 
 }  // namespace
+
+// A stream and an event per host thread and device, on which the builder
+// reads the list size back while the row sort runs on the caller's stream.
+// Created on first use and kept for the life of the thread.
+int side_stream(cudaStream_t &side, cudaEvent_t &ev)
+{
+    struct Side {
+        int dev;
+        cudaStream_t s;
+        cudaEvent_t e;
+    };
+    static thread_local Side cache[16] = {};
+    static thread_local int used = 0;
+    int dev = 0;
+    LJ_TRY_CUDA(cudaGetDevice(&dev));
+    for (int k = 0; k < used; ++k)
+        if (cache[k].dev == dev) {
+            side = cache[k].s;
+            ev = cache[k].e;
+            return LJ_OK;
+        }
+    if (used == 16) return LJ_ERR_ARG;
+    Side x{dev, nullptr, nullptr};
+    LJ_TRY_CUDA(cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking));
+    LJ_TRY_CUDA(cudaEventCreateWithFlags(&x.e, cudaEventDisableTiming));
+    cache[used++] = x;
+    side = x.s;
+    ev = x.e;
+    return LJ_OK;
+}
 
 int build_pairlist_impl(const double *q4, int64_t n, const double box[3], double rs, int half,
                         int32_t *row_ptr, int32_t *col, int64_t cap, void *ws, size_t ws_bytes,
@@ -698,23 +736,42 @@ int build_pairlist_impl(const double *q4, int64_t n, const double box[3], double
     set_total_kernel<<<1, 1, 0, st>>>(row_ptr + n, w.stats);
     LJ_TRY_LAUNCH("set_total_kernel");
     ListStats hs{};
-    LJ_TRY_CUDA(cudaMemcpyAsync(&hs, w.stats, sizeof(ListStats), cudaMemcpyDeviceToHost, st));
-    LJ_TRY_CUDA(cudaStreamSynchronize(st));
+    if (slabs) {
+        // One-walk path: the list size is read on a side stream that waits
+        // for the scan only, while the row sort -- which checks the same
+        // figures itself and does nothing unless the list fits col -- runs
+        // on the caller's stream; the host blocks for the small copy, not
+        // for the sort.
+        cudaStream_t side;
+        cudaEvent_t scanned;
+        rc = side_stream(side, scanned);
+        if (rc != LJ_OK) return rc;
+        LJ_TRY_CUDA(cudaEventRecord(scanned, st));
+        if (col && cap > 0) {
+            const size_t smem_sort = size_t(kWarpsPerBlock) * cap_slab * sizeof(int);
+            if (smem_sort > 48 * 1024)
+                LJ_TRY_CUDA(cudaFuncSetAttribute(sort_rows_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 int(smem_sort)));
+            sort_rows_kernel<<<gw, kWarpsPerBlock * 32, smem_sort, st>>>(slabs, cap_slab, ni, row_ptr,
+                                                                         col, w.stats, cap);
+            LJ_TRY_LAUNCH("sort_rows_kernel");
+        }
+        LJ_TRY_CUDA(cudaStreamWaitEvent(side, scanned, 0));
+        LJ_TRY_CUDA(cudaMemcpyAsync(&hs, w.stats, sizeof(ListStats), cudaMemcpyDeviceToHost, side));
+        LJ_TRY_CUDA(cudaStreamSynchronize(side));
+    } else {
+        // two-walk path (and the allocation-free builder): no side stream
+        LJ_TRY_CUDA(cudaMemcpyAsync(&hs, w.stats, sizeof(ListStats), cudaMemcpyDeviceToHost, st));
+        LJ_TRY_CUDA(cudaStreamSynchronize(st));
+    }
     if (hs.err & 1) return LJ_ERR_RANGE;
     *nnz_out = hs.nnz;
     if (max_row_out) *max_row_out = hs.max_row;
     if (hs.nnz >= (int64_t(1) << 31) - 1) return LJ_ERR_CAPACITY;
     if (hs.nnz > cap || hs.max_row > kMaxRowSmem) return LJ_ERR_CAPACITY;
     if (hs.nnz == 0) return LJ_OK;
-    if (slabs && !(hs.err & 4)) {
-        const size_t smem_sort = size_t(kWarpsPerBlock) * cap_slab * sizeof(int);
-        if (smem_sort > 48 * 1024)
-            LJ_TRY_CUDA(cudaFuncSetAttribute(sort_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem_sort)));
-        sort_rows_kernel<<<gw, kWarpsPerBlock * 32, smem_sort, st>>>(slabs, cap_slab, ni, row_ptr, col);
-        LJ_TRY_LAUNCH("sort_rows_kernel");
-        return LJ_OK;
-    }
+    if (slabs && !(hs.err & 4)) return LJ_OK;  // sorted into col by the kernel above
     const int cap_row = std::max(1, hs.max_row);
     int wpb = kWarpsPerBlock;
     while (wpb > 1 && size_t(wpb) * cap_row * sizeof(int) > 200 * 1024) wpb >>= 1;
