@@ -560,6 +560,54 @@ __device__ __forceinline__ void rank_row(const int *__restrict__ buf, int len, i
         if (lane + 32 * u < len) out[r[u]] = v[u];
 }
 
+// A row of len <= 32 E entries (E = 4 or 8) sorted by a bitonic network
+// held in registers: entry index u 32 + lane lives in v[u] of that lane,
+// pairs 32 or more apart are compared inside a lane, nearer ones across
+// lanes with shuffles; padding INT_MAX sorts last.  For long rows it takes
+// fewer instructions than ranking every entry against the whole row.
+template <int E>
+__device__ __forceinline__ void bitonic_row(const int *__restrict__ buf, int len, int lane,
+                                            int32_t *__restrict__ out)
+{
+    constexpr int N = 32 * E;
+    int v[E];
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+        const int e = lane + 32 * u;
+        v[u] = e < len ? buf[e] : INT32_MAX;
+    }
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int u = 0; u < E; ++u) {
+                    const int pu = u ^ (j >> 5);
+                    if (pu > u) {
+                        const bool asc = ((u * 32) & k) == 0;  // k > 32: set by u alone
+                        const int a = v[u], b = v[pu];
+                        const bool swap = asc ? (a > b) : (a < b);
+                        v[u] = swap ? b : a;
+                        v[pu] = swap ? a : b;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < E; ++u) {
+                    const int other = __shfl_xor_sync(0xffffffffu, v[u], j);
+                    const bool asc = ((u * 32 + lane) & k) == 0;
+                    const bool lower = (lane & j) == 0;
+                    v[u] = (lower == asc) ? min(v[u], other) : max(v[u], other);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < E; ++u)
+        if (lane + 32 * u < len) out[lane + 32 * u] = v[u];
+}
+
 // Row i's slab, staged in shared memory, rank-sorted into col (the j of a
 // row are distinct: rank(v) = #{m : buf[m] < v}).  cap is a multiple of 32,
 // so each warp's buffer is 16-byte aligned and holds the padding.
@@ -594,9 +642,11 @@ sort_rows_kernel(const int *__restrict__ tmp, int cap, int n, const int32_t *__r
         case 1: rank_row<1>(buf, len, lane, out); return;
         case 2: rank_row<2>(buf, len, lane, out); return;
         case 3: rank_row<3>(buf, len, lane, out); return;
-        case 4: rank_row<4>(buf, len, lane, out); return;
-        case 5: rank_row<5>(buf, len, lane, out); return;
-        case 6: rank_row<6>(buf, len, lane, out); return;
+        case 4: bitonic_row<4>(buf, len, lane, out); return;
+        case 5:
+        case 6:
+        case 7:
+        case 8: bitonic_row<8>(buf, len, lane, out); return;
         default: break;
     }
     for (int e = lane; e < len; e += 32) {
