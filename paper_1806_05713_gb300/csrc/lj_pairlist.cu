@@ -560,7 +560,7 @@ __device__ __forceinline__ void rank_row(const int *__restrict__ buf, int len, i
         if (lane + 32 * u < len) out[r[u]] = v[u];
 }
 
-// A row of len <= 32 E entries (E = 4 or 8) sorted by a bitonic network
+// A row of len <= 32 E entries (E = 2, 4 or 8) sorted by a bitonic network
 // held in registers: entry index u 32 + lane lives in v[u] of that lane,
 // pairs 32 or more apart are compared inside a lane, nearer ones across
 // lanes with shuffles; padding INT_MAX sorts last.  For long rows it takes
@@ -640,8 +640,8 @@ sort_rows_kernel(const int *__restrict__ tmp, int cap, int n, const int32_t *__r
     switch ((len + 31) >> 5) {
         case 0: return;
         case 1: rank_row<1>(buf, len, lane, out); return;
-        case 2: rank_row<2>(buf, len, lane, out); return;
-        case 3: rank_row<3>(buf, len, lane, out); return;
+        case 2: bitonic_row<2>(buf, len, lane, out); return;
+        case 3:
         case 4: bitonic_row<4>(buf, len, lane, out); return;
         case 5:
         case 6:
