@@ -32,7 +32,9 @@
 //                into row i's slab or, with no room for slabs, counted
 //                first and filled later (the two-walk path).
 //   5. scan:     row counts -> row_ptr; total and longest row read back.
-//   6. sort:     each slab rank-sorted into its place in col (all j of a
+//   6. sort:     each slab sorted into its place in col -- a bitonic
+//                network in the warp's registers for rows of up to 256
+//                entries, a rank sort in shared memory beyond (all j of a
 //                row are distinct); the two-walk path instead walks again,
 //                compacts the j of the row into shared memory (ballot +
 //                popc), ranks them and writes the sorted row.
@@ -532,35 +534,7 @@ __global__ void set_total_kernel(int32_t *__restrict__ row_end, const ListStats 
     *row_end = static_cast<int32_t>(t < INT32_MAX ? t : INT32_MAX);
 }
 
-// Ranks of a row of len <= 32 E entries: each lane holds E of them and
-// compares every 16-byte group of the row (padded with INT_MAX, which no
-// index reaches) against all E at once, so each shared-memory load serves E
-// ranks.
-template <int E>
-__device__ __forceinline__ void rank_row(const int *__restrict__ buf, int len, int lane,
-                                         int32_t *__restrict__ out)
-{
-    int v[E], r[E];
-#pragma unroll
-    for (int u = 0; u < E; ++u) {
-        const int e = lane + 32 * u;
-        v[u] = e < len ? buf[e] : INT32_MAX;
-        r[u] = 0;
-    }
-    const int4 *b4 = reinterpret_cast<const int4 *>(buf);
-    const int len4 = (len + 3) >> 2;
-    for (int m = 0; m < len4; ++m) {
-        const int4 w = b4[m];
-#pragma unroll
-        for (int u = 0; u < E; ++u)
-            r[u] += (w.x < v[u]) + (w.y < v[u]) + (w.z < v[u]) + (w.w < v[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < E; ++u)
-        if (lane + 32 * u < len) out[r[u]] = v[u];
-}
-
-// A row of len <= 32 E entries (E = 2, 4 or 8) sorted by a bitonic network
+// A row of len <= 32 E entries (E = 1, 2, 4 or 8) sorted by a bitonic network
 // held in registers: entry index u 32 + lane lives in v[u] of that lane,
 // pairs 32 or more apart are compared inside a lane, nearer ones across
 // lanes with shuffles; padding INT_MAX sorts last.  For long rows it takes
@@ -608,9 +582,9 @@ __device__ __forceinline__ void bitonic_row(const int *__restrict__ buf, int len
         if (lane + 32 * u < len) out[lane + 32 * u] = v[u];
 }
 
-// Row i's slab, staged in shared memory, rank-sorted into col (the j of a
-// row are distinct: rank(v) = #{m : buf[m] < v}).  cap is a multiple of 32,
-// so each warp's buffer is 16-byte aligned and holds the padding.
+// Row i's slab sorted into col: rows of up to 256 entries by the bitonic
+// network above, longer ones staged in shared memory and ranked (the j of
+// a row are distinct: rank(v) = #{m : buf[m] < v}).
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 sort_rows_kernel(const int *__restrict__ tmp, int cap, int n, const int32_t *__restrict__ row_ptr,
                  int32_t *__restrict__ col, const ListStats *__restrict__ stats, int64_t col_cap)
@@ -629,26 +603,27 @@ sort_rows_kernel(const int *__restrict__ tmp, int cap, int n, const int32_t *__r
     const int i = blockIdx.x * kWarpsPerBlock + wib;
     if (i >= n) return;
     const int lane = threadIdx.x & 31;
-    int *buf = smem + size_t(wib) * cap;
     const int start = row_ptr[i];
     const int len = row_ptr[i + 1] - start;
     const int *src = tmp + static_cast<size_t>(i) * cap;
-    const int padded = (len + 3) & ~3;
-    for (int e = lane; e < padded; e += 32) buf[e] = e < len ? src[e] : INT32_MAX;
-    __syncwarp();
     int32_t *out = col + start;
+    // rows of up to 256 entries: a bitonic network straight from the slab
     switch ((len + 31) >> 5) {
         case 0: return;
-        case 1: rank_row<1>(buf, len, lane, out); return;
-        case 2: bitonic_row<2>(buf, len, lane, out); return;
+        case 1: bitonic_row<1>(src, len, lane, out); return;
+        case 2: bitonic_row<2>(src, len, lane, out); return;
         case 3:
-        case 4: bitonic_row<4>(buf, len, lane, out); return;
+        case 4: bitonic_row<4>(src, len, lane, out); return;
         case 5:
         case 6:
         case 7:
-        case 8: bitonic_row<8>(buf, len, lane, out); return;
+        case 8: bitonic_row<8>(src, len, lane, out); return;
         default: break;
     }
+    // longer rows: staged in shared memory and ranked
+    int *buf = smem + size_t(wib) * cap;
+    for (int e = lane; e < len; e += 32) buf[e] = src[e];
+    __syncwarp();
     for (int e = lane; e < len; e += 32) {
         const int v = buf[e];
         int r = 0;
