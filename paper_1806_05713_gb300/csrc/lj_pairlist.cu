@@ -37,7 +37,7 @@
 //                entries, a rank sort in shared memory beyond (all j of a
 //                row are distinct); the two-walk path instead walks again,
 //                compacts the j of the row into shared memory (ballot +
-//                popc), ranks them and writes the sorted row.
+//                popc), sorts them the same way and writes the sorted row.
 // The result is bit-exact against the FP64 definition because every
 // decision is either certain from the FP32 bound or taken with the exact
 // IEEE operations (d = q_j - q_i, minimum image, (dx*dx + dy*dy) + dz*dz,
@@ -304,6 +304,74 @@ __device__ __forceinline__ void walk_row(const double *__restrict__ q4, const Gr
     }
 }
 
+// A row of len <= 32 E entries (E = 1, 2, 4 or 8) sorted by a bitonic network
+// held in registers: entry index u 32 + lane lives in v[u] of that lane,
+// pairs 32 or more apart are compared inside a lane, nearer ones across
+// lanes with shuffles; padding INT_MAX sorts last.  For long rows it takes
+// fewer instructions than ranking every entry against the whole row.
+template <int E>
+__device__ __forceinline__ void bitonic_row(const int *__restrict__ buf, int len, int lane,
+                                            int32_t *__restrict__ out)
+{
+    constexpr int N = 32 * E;
+    int v[E];
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+        const int e = lane + 32 * u;
+        v[u] = e < len ? buf[e] : INT32_MAX;
+    }
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int u = 0; u < E; ++u) {
+                    const int pu = u ^ (j >> 5);
+                    if (pu > u) {
+                        const bool asc = ((u * 32) & k) == 0;  // k > 32: set by u alone
+                        const int a = v[u], b = v[pu];
+                        const bool swap = asc ? (a > b) : (a < b);
+                        v[u] = swap ? b : a;
+                        v[pu] = swap ? a : b;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < E; ++u) {
+                    const int other = __shfl_xor_sync(0xffffffffu, v[u], j);
+                    const bool asc = ((u * 32 + lane) & k) == 0;
+                    const bool lower = (lane & j) == 0;
+                    v[u] = (lower == asc) ? min(v[u], other) : max(v[u], other);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < E; ++u)
+        if (lane + 32 * u < len) out[lane + 32 * u] = v[u];
+}
+
+// Sorts row `buf` (len distinct j) into out with a bitonic network when it
+// has at most 256 entries; returns false for a longer row (left to the
+// caller's rank sort).
+__device__ __forceinline__ bool bitonic_sort_row(const int *__restrict__ buf, int len, int lane,
+                                                 int32_t *__restrict__ out)
+{
+    switch ((len + 31) >> 5) {
+        case 0: return true;
+        case 1: bitonic_row<1>(buf, len, lane, out); return true;
+        case 2: bitonic_row<2>(buf, len, lane, out); return true;
+        case 3:
+        case 4: bitonic_row<4>(buf, len, lane, out); return true;
+        case 5:
+        case 6:
+        case 7:
+        case 8: bitonic_row<8>(buf, len, lane, out); return true;
+        default: return false;
+    }
+}
+
 template <bool HALF>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 count_kernel(const double *__restrict__ q4, int n, Grid g, const int *__restrict__ cell_of,
@@ -353,6 +421,7 @@ fill_kernel(const double *__restrict__ q4, int n, Grid g, const int *__restrict_
         if (lane == 0) atomicOr(&stats->err, 2);
         return;
     }
+    if (bitonic_sort_row(buf, cnt, lane, col + start)) return;
     // Rank sort: the j of a row are distinct, so rank(v) = #{m : buf[m] < v}.
     for (int e = lane; e < cnt; e += 32) {
         const int v = buf[e];
@@ -534,54 +603,6 @@ __global__ void set_total_kernel(int32_t *__restrict__ row_end, const ListStats 
     *row_end = static_cast<int32_t>(t < INT32_MAX ? t : INT32_MAX);
 }
 
-// A row of len <= 32 E entries (E = 1, 2, 4 or 8) sorted by a bitonic network
-// held in registers: entry index u 32 + lane lives in v[u] of that lane,
-// pairs 32 or more apart are compared inside a lane, nearer ones across
-// lanes with shuffles; padding INT_MAX sorts last.  For long rows it takes
-// fewer instructions than ranking every entry against the whole row.
-template <int E>
-__device__ __forceinline__ void bitonic_row(const int *__restrict__ buf, int len, int lane,
-                                            int32_t *__restrict__ out)
-{
-    constexpr int N = 32 * E;
-    int v[E];
-#pragma unroll
-    for (int u = 0; u < E; ++u) {
-        const int e = lane + 32 * u;
-        v[u] = e < len ? buf[e] : INT32_MAX;
-    }
-#pragma unroll
-    for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= 32) {
-#pragma unroll
-                for (int u = 0; u < E; ++u) {
-                    const int pu = u ^ (j >> 5);
-                    if (pu > u) {
-                        const bool asc = ((u * 32) & k) == 0;  // k > 32: set by u alone
-                        const int a = v[u], b = v[pu];
-                        const bool swap = asc ? (a > b) : (a < b);
-                        v[u] = swap ? b : a;
-                        v[pu] = swap ? a : b;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int u = 0; u < E; ++u) {
-                    const int other = __shfl_xor_sync(0xffffffffu, v[u], j);
-                    const bool asc = ((u * 32 + lane) & k) == 0;
-                    const bool lower = (lane & j) == 0;
-                    v[u] = (lower == asc) ? min(v[u], other) : max(v[u], other);
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < E; ++u)
-        if (lane + 32 * u < len) out[lane + 32 * u] = v[u];
-}
-
 // Row i's slab sorted into col: rows of up to 256 entries by the bitonic
 // network above, longer ones staged in shared memory and ranked (the j of
 // a row are distinct: rank(v) = #{m : buf[m] < v}).
@@ -608,18 +629,7 @@ sort_rows_kernel(const int *__restrict__ tmp, int cap, int n, const int32_t *__r
     const int *src = tmp + static_cast<size_t>(i) * cap;
     int32_t *out = col + start;
     // rows of up to 256 entries: a bitonic network straight from the slab
-    switch ((len + 31) >> 5) {
-        case 0: return;
-        case 1: bitonic_row<1>(src, len, lane, out); return;
-        case 2: bitonic_row<2>(src, len, lane, out); return;
-        case 3:
-        case 4: bitonic_row<4>(src, len, lane, out); return;
-        case 5:
-        case 6:
-        case 7:
-        case 8: bitonic_row<8>(src, len, lane, out); return;
-        default: break;
-    }
+    if (bitonic_sort_row(src, len, lane, out)) return;
     // longer rows: staged in shared memory and ranked
     int *buf = smem + size_t(wib) * cap;
     for (int e = lane; e < len; e += 32) buf[e] = src[e];
