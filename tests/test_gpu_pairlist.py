@@ -165,3 +165,28 @@ def test_million_atoms_bit_exact(cuda_lib, oracle_lib):
     pl = _assert_same(cuda_lib, oracle_lib, s.q, s.box, s.rs, True)
     mean = pl.nnz / s.n
     assert abs(mean - 0.5 * 4 / 3 * math.pi * 3.3 ** 3) < 6
+
+
+def test_build_on_a_side_stream_then_force_on_it(cuda_lib, oracle_lib):
+    """The builder returns before its row sort ends; on the caller's own
+    (non-default) stream the list is complete in stream order: a force call
+    queued right behind it on that stream sees the finished list."""
+    lj = cuda_lib
+    s = inputs.workload_paper(order="random")
+    q = to_dev(s.q)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        pl = lj.lj_build_pairlist(q, s.box, s.rs, True, stream=side)
+        p = torch.zeros_like(q)
+        lj.lj_force(q, p, pl, 0.01, s.rc, s.box, stream=side)
+        rp_dev = pl.row_ptr.clone()
+        col_dev = pl.col_view.clone()
+    side.synchronize()
+    orp, ocol = oracle_lib.pairlist(s.q, s.box, s.rs, True)
+    assert np.array_equal(rp_dev.cpu().numpy(), orp)
+    assert np.array_equal(col_dev.cpu().numpy(), ocol)
+    ref = torch.zeros_like(q)
+    lj.lj_force(q, ref, lj.lj_build_pairlist(q, s.box, s.rs, True), 0.01, s.rc, s.box)
+    torch.cuda.synchronize()
+    assert float((p - ref).abs().max()) <= 1e-13 * float(ref.abs().max())
