@@ -26,6 +26,13 @@ and force-shifted pins on random gases in random boxes with hypothesis):
   derivative of V(r) - V(r_c) - (r - r_c) V'(r_c) for two-body pairs; force
   and energy vanish at r_c (linearly, quadratically); F = -grad E_fs by
   central differences; Newton's third law; half list == full list.
+* pairlist_rows, force_rows (a block of rows, for the bounded CPU timing
+  sample): pinned -- the rows equal those of the O(N^2) definition; the
+  momentum changes of a partition of the rows add up to the whole call.
+* force_atoms (per-atom sum over every other atom, no list; for sampled
+  checks of systems too large to list on the CPU): pinned -- equals the
+  list-based call on sampled atoms (half and full lists); the two-body
+  closed form at r = sigma; atoms beyond r_c contribute nothing.
 """
-from .oracle import (build, energy, energy_fs, force, force_fs, force_vjp, forces,  # noqa: F401
-                     pairlist, virial)
+from .oracle import (build, energy, energy_fs, force, force_atoms, force_fs,  # noqa: F401
+                     force_rows, force_vjp, forces, pairlist, pairlist_rows, virial)

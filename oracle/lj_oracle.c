@@ -129,10 +129,14 @@ static int axis_offsets(int nc, int off[3])
  * each i scans the atoms of its own and neighbouring cells.  The j of each
  * row are then sorted (the paper's counting sort groups by i; within a row
  * the oracle orders by j so that the list is a canonical sorted set).
- * Same output contract as oracle_pairlist_brute.
+ * Same output contract as oracle_pairlist_brute, for the rows i0 .. i1-1
+ * only: row_ptr has i1 - i0 + 1 entries (starting at 0) and col the j of
+ * those rows (global atom indices).  Every atom is binned; only the listed
+ * rows are walked (a bounded sample of a large system).
  */
-int64_t oracle_pairlist_cells(int64_t n, const double *q, int64_t stride, const double *L,
-                              double rs, int half, int32_t *row_ptr, int32_t *col, int64_t cap)
+int64_t oracle_pairlist_cells_rows(int64_t n, const double *q, int64_t stride, const double *L,
+                                   double rs, int half, int64_t i0, int64_t i1, int32_t *row_ptr,
+                                   int32_t *col, int64_t cap)
 {
     double rs2 = rs * rs;
     int nc[3], off[3][3], noff[3];
@@ -162,8 +166,8 @@ int64_t oracle_pairlist_cells(int64_t n, const double *q, int64_t stride, const 
     }
     int64_t nnz = 0;
     double r[3];
-    for (int64_t i = 0; i < n; ++i) {
-        row_ptr[i] = (int32_t)nnz;
+    for (int64_t i = i0; i < i1; ++i) {
+        row_ptr[i - i0] = (int32_t)nnz;
         int64_t len = 0;
         for (int oz = 0; oz < noff[2]; ++oz)
             for (int oy = 0; oy < noff[1]; ++oy)
@@ -187,12 +191,19 @@ int64_t oracle_pairlist_cells(int64_t n, const double *q, int64_t stride, const 
         }
         nnz += len;
     }
-    row_ptr[n] = (int32_t)nnz;
+    row_ptr[i1 - i0] = (int32_t)nnz;
     free(head);
     free(next);
     free(cell);
     free(row);
     return nnz;
+}
+
+/* The whole list: rows 0 .. n-1 of the cell method above. */
+int64_t oracle_pairlist_cells(int64_t n, const double *q, int64_t stride, const double *L,
+                              double rs, int half, int32_t *row_ptr, int32_t *col, int64_t cap)
+{
+    return oracle_pairlist_cells_rows(n, q, stride, L, rs, half, 0, n, row_ptr, col, cap);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -205,9 +216,9 @@ int64_t oracle_pairlist_cells(int64_t n, const double *q, int64_t stride, const 
  * appears again in row j).  Pairs with r^2 >= r_c^2 (the bookkeeping margin)
  * are skipped.
  */
-void oracle_force(int64_t n, const double *q, int64_t qstride, double *p, int64_t pstride,
-                  const int32_t *row_ptr, const int32_t *col, int half, double dt, double rc,
-                  const double *L, double eps, double sigma)
+void oracle_force_rows(int64_t n, const double *q, int64_t qstride, double *p, int64_t pstride,
+                       int64_t i0, int64_t i1, const int32_t *row_ptr, const int32_t *col,
+                       int half, double dt, double rc, const double *L, double eps, double sigma)
 {
     double rc2 = rc * rc;
     double s2 = sigma * sigma;
@@ -216,10 +227,11 @@ void oracle_force(int64_t n, const double *q, int64_t qstride, double *p, int64_
     double c48 = 48.0 * eps * s12;
     double c24 = 24.0 * eps * s6;
     double r[3];
-    for (int64_t i = 0; i < n; ++i) {
+    (void)n;
+    for (int64_t i = i0; i < i1; ++i) {
         const double *qi = q + i * qstride;
         double pi[3] = {p[i * pstride + 0], p[i * pstride + 1], p[i * pstride + 2]};
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+        for (int64_t k = row_ptr[i - i0]; k < row_ptr[i - i0 + 1]; ++k) {
             int64_t j = col[k];
             double r2 = displacement(qi, q + j * qstride, L, r);
             if (r2 < rc2) {
@@ -235,6 +247,55 @@ void oracle_force(int64_t n, const double *q, int64_t qstride, double *p, int64_
         }
         for (int a = 0; a < 3; ++a)
             p[i * pstride + a] = pi[a];
+    }
+}
+
+/* One force call over the whole list (rows 0 .. n-1). */
+void oracle_force(int64_t n, const double *q, int64_t qstride, double *p, int64_t pstride,
+                  const int32_t *row_ptr, const int32_t *col, int half, double dt, double rc,
+                  const double *L, double eps, double sigma)
+{
+    oracle_force_rows(n, q, qstride, p, pstride, 0, n, row_ptr, col, half, dt, rc, L, eps, sigma);
+}
+
+/*
+ * The momentum change of selected atoms straight from the definition, with
+ * no pair list: for each atom i = idx[m], the sum over every other atom j
+ * with minimum-image r^2 < r_c^2 of -df r (r = q_j - q_i, Algorithm 1's
+ * arithmetic), i.e. what one force call over a complete list adds to p_i,
+ * whichever of i and j owns the pair in a half list.  O(n) per atom: it
+ * checks sampled atoms of systems too large for the O(N) list to be built
+ * on the CPU in seconds.  out: m rows of 3 doubles.
+ */
+void oracle_force_atoms(int64_t n, const double *q, int64_t qstride, const double *L, double dt,
+                        double rc, double eps, double sigma, const int64_t *idx, int64_t m,
+                        double *out)
+{
+    double rc2 = rc * rc;
+    double s2 = sigma * sigma;
+    double s6 = s2 * s2 * s2;
+    double s12 = s6 * s6;
+    double c48 = 48.0 * eps * s12;
+    double c24 = 24.0 * eps * s6;
+    double r[3];
+    for (int64_t t = 0; t < m; ++t) {
+        int64_t i = idx[t];
+        const double *qi = q + i * qstride;
+        double pi[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i)
+                continue;
+            double r2 = displacement(qi, q + j * qstride, L, r);
+            if (r2 < rc2) {
+                double r6 = r2 * r2 * r2;
+                double r14 = r6 * r6 * r2;
+                double df = (c48 - c24 * r6) * dt / r14;
+                for (int a = 0; a < 3; ++a)
+                    pi[a] -= df * r[a];
+            }
+        }
+        for (int a = 0; a < 3; ++a)
+            out[3 * t + a] = pi[a];
     }
 }
 

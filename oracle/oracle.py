@@ -14,6 +14,11 @@ follow:
   section; must give the identical list.
 * ``force``: Algorithm 3 (sorted list) with Algorithm 1 per pair; the
   momentum change of one call, p_i -= df r, p_j += df r (half list).
+* ``pairlist_rows`` / ``force_rows``: the same two functions restricted to
+  a block of rows (a bounded sample of a large system for CPU timing).
+* ``force_atoms``: the momentum change of chosen atoms straight from the
+  definition, summed over every other atom (no list; checks sampled atoms
+  of systems too large to list on the CPU quickly).
 * ``energy``: Eq. (1) truncated at r_c, optionally shifted to V(r_c) = 0.
 * ``virial``: the pair virial sum r F(r) of the same truncated Eq. (1).
 * ``force_vjp``: the adjoint of the force map F(q; eps, sigma), derived from
@@ -65,6 +70,15 @@ def _load():
         lib.oracle_pairlist_brute.argtypes = [_i64, _vp, _i64, _vp, _dbl, _int, _vp, _vp, _i64]
         lib.oracle_pairlist_cells.restype = _i64
         lib.oracle_pairlist_cells.argtypes = [_i64, _vp, _i64, _vp, _dbl, _int, _vp, _vp, _i64]
+        lib.oracle_pairlist_cells_rows.restype = _i64
+        lib.oracle_pairlist_cells_rows.argtypes = [_i64, _vp, _i64, _vp, _dbl, _int, _i64, _i64,
+                                                   _vp, _vp, _i64]
+        lib.oracle_force_rows.restype = None
+        lib.oracle_force_rows.argtypes = [_i64, _vp, _i64, _vp, _i64, _i64, _i64, _vp, _vp, _int,
+                                          _dbl, _dbl, _vp, _dbl, _dbl]
+        lib.oracle_force_atoms.restype = None
+        lib.oracle_force_atoms.argtypes = [_i64, _vp, _i64, _vp, _dbl, _dbl, _dbl, _dbl, _vp, _i64,
+                                           _vp]
         lib.oracle_force.restype = None
         lib.oracle_force.argtypes = [_i64, _vp, _i64, _vp, _i64, _vp, _vp, _int, _dbl, _dbl,
                                      _vp, _dbl, _dbl]
@@ -112,6 +126,61 @@ def pairlist(q, box, rs: float, half: bool = True, method: str = "cells"):
         if nnz <= cap:
             return row_ptr, col[:nnz].copy()
         cap = int(nnz)
+
+
+def pairlist_rows(q, box, rs: float, half: bool, i0: int, i1: int):
+    """Rows i0 .. i1-1 of the cell-method list: (row_ptr int32[i1-i0+1]
+    starting at 0, col int32 with global atom indices)."""
+    lib = _load()
+    q = _rows(q, "q")
+    L = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+    n = q.shape[0]
+    if not 0 <= i0 <= i1 <= n:
+        raise ValueError("row range outside the system")
+    row_ptr = np.zeros(i1 - i0 + 1, dtype=np.int32)
+    cap = max(1, (160 if half else 320) * (i1 - i0))
+    while True:
+        col = np.empty(cap, dtype=np.int32)
+        nnz = lib.oracle_pairlist_cells_rows(n, _ptr(q), q.shape[1], _ptr(L), float(rs),
+                                             int(bool(half)), int(i0), int(i1), _ptr(row_ptr),
+                                             _ptr(col), cap)
+        if nnz <= cap:
+            return row_ptr, col[:nnz].copy()
+        cap = int(nnz)
+
+
+def force_rows(q, p, row_ptr, col, half: bool, dt: float, rc: float, box, i0: int, i1: int,
+               eps: float = 1.0, sigma: float = 1.0) -> np.ndarray:
+    """Momenta after one force call over rows i0 .. i1-1 of a list given in
+    the pairlist_rows form; p is not modified."""
+    lib = _load()
+    q = _rows(q, "q")
+    out = _rows(p, "p").copy()
+    L = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    if row_ptr.size != i1 - i0 + 1 or not 0 <= i0 <= i1 <= q.shape[0]:
+        raise ValueError("row_ptr does not match the row range")
+    lib.oracle_force_rows(q.shape[0], _ptr(q), q.shape[1], _ptr(out), out.shape[1], int(i0),
+                          int(i1), _ptr(row_ptr), _ptr(col), int(bool(half)), float(dt), float(rc),
+                          _ptr(L), float(eps), float(sigma))
+    return out
+
+
+def force_atoms(q, idx, dt: float, rc: float, box, eps: float = 1.0,
+                sigma: float = 1.0) -> np.ndarray:
+    """Momentum change (m, 3) of the atoms idx in one force call, from the
+    definition over all atoms (no list)."""
+    lib = _load()
+    q = _rows(q, "q")
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    if idx.size and (idx.min() < 0 or idx.max() >= q.shape[0]):
+        raise ValueError("atom index outside the system")
+    L = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+    out = np.zeros((idx.size, 3))
+    lib.oracle_force_atoms(q.shape[0], _ptr(q), q.shape[1], _ptr(L), float(dt), float(rc),
+                           float(eps), float(sigma), _ptr(idx), idx.size, _ptr(out))
+    return out
 
 
 def force(q, p, row_ptr, col, half: bool, dt: float, rc: float, box, eps: float = 1.0,

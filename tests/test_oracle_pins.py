@@ -461,3 +461,78 @@ def test_fs_newton_and_half_equals_full(oracle_lib, small):
     eh = oracle_lib.energy_fs(s.q, rp, col, True, 3.0, s.box)
     ef = oracle_lib.energy_fs(s.q, rpf, colf, False, 3.0, s.box)
     assert abs(eh - ef) <= 1e-12 * abs(eh)
+
+
+# --------------------------------------------------------------------------
+# Row blocks and per-atom sums (the bounded CPU sample and the sampled
+# parity checks at full size)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("half", [True, False])
+def test_pairlist_rows_equal_brute_force_rows(oracle_lib, small, half):
+    """A block of rows from the cell method equals the same rows of the
+    O(N^2) definition; blocks of a partition concatenate to the whole list."""
+    s = small[0]
+    brute_rp, brute_col = oracle_lib.pairlist(s.q, s.box, 3.3, half, "brute")
+    cuts = [0, 1, 997, 1500, 3999, s.n]
+    cols = []
+    for i0, i1 in zip(cuts[:-1], cuts[1:]):
+        rp, col = oracle_lib.pairlist_rows(s.q, s.box, 3.3, half, i0, i1)
+        want_rp = brute_rp[i0:i1 + 1] - brute_rp[i0]
+        assert np.array_equal(rp, want_rp)
+        assert np.array_equal(col, brute_col[brute_rp[i0]:brute_rp[i1]])
+        cols.append(col)
+    assert np.array_equal(np.concatenate(cols), brute_col)
+    empty_rp, empty_col = oracle_lib.pairlist_rows(s.q, s.box, 3.3, half, 17, 17)
+    assert empty_rp.tolist() == [0] and empty_col.size == 0
+
+
+@pytest.mark.parametrize("half", [True, False])
+def test_force_over_row_blocks_sums_to_whole_call(oracle_lib, small, half):
+    """The momentum changes of a partition of the rows, each from zero, add up
+    to the change of one call over the whole list (momentum changes add)."""
+    s, lh, lf = small
+    rp_all, col_all = lh if half else lf
+    whole = oracle_lib.force(s.q, np.zeros((s.n, 3)), rp_all, col_all, half, 0.01, 3.0, s.box)
+    total = np.zeros((s.n, 3))
+    cuts = [0, 640, 2222, 3001, s.n]
+    for i0, i1 in zip(cuts[:-1], cuts[1:]):
+        rp, col = oracle_lib.pairlist_rows(s.q, s.box, 3.3, half, i0, i1)
+        part = oracle_lib.force_rows(s.q, np.zeros((s.n, 3)), rp, col, half, 0.01, 3.0, s.box,
+                                     i0, i1)
+        if not half:   # a full-list block changes only its own rows
+            outside = np.ones(s.n, dtype=bool)
+            outside[i0:i1] = False
+            assert not part[outside].any()
+        total += part
+    assert np.max(np.abs(total - whole)) <= 1e-13 * np.max(np.abs(whole))
+
+
+def test_force_atoms_equals_list_force(oracle_lib, small):
+    """The per-atom sum over all atoms equals the list-based call (half and
+    full lists) on sampled atoms: two routes to the same definition."""
+    s, (rph, ch), (rpf, cf) = small
+    ph = oracle_lib.force(s.q, np.zeros((s.n, 3)), rph, ch, True, 0.01, 3.0, s.box)
+    pf = oracle_lib.force(s.q, np.zeros((s.n, 3)), rpf, cf, False, 0.01, 3.0, s.box)
+    idx = np.array([0, 1, 2, 1234, 2999, s.n - 1] +
+                   list(np.random.default_rng(4).choice(s.n, 40, replace=False)))
+    got = oracle_lib.force_atoms(s.q, idx, 0.01, 3.0, s.box)
+    scale = np.max(np.abs(ph))
+    assert np.max(np.abs(got - ph[idx])) <= 1e-13 * scale
+    assert np.max(np.abs(got - pf[idx])) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_force_atoms_two_body_closed_form(oracle_lib, axis):
+    """At r = sigma the impulse on atom 0 is -24 dt eps / sigma along d
+    (repulsive), and nothing beyond r_c contributes."""
+    q, box = _two_body(1.0, axis=axis)
+    far = np.zeros((1, 4))
+    far[0, :3] = 5.0
+    far[0, axis] = 5.0 + 4.5          # 4.5 and 3.5 from the pair: beyond r_c = 3
+    q3 = np.vstack([q, far])
+    got = oracle_lib.force_atoms(q3, [0, 1], 0.01, 3.0, box)
+    want = np.zeros(3)
+    want[axis] = -24.0 * 0.01
+    assert np.allclose(got[0], want, rtol=1e-15, atol=0)
+    assert np.allclose(got[1], -want, rtol=1e-15, atol=0)
