@@ -86,6 +86,8 @@ def parse():
                     help="no timing: build the list and run a few calls of one kernel (for ncu)")
     ap.add_argument("--schedule", type=int, default=0,
                     help="FP64 schedule for the timed steps (0 = the library's autotuner picks)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="only measure the FP64 / FP32 / packed-FP32 / L2-read ceilings and print them")
     ap.add_argument("--profile-atoms", choices=["paper", "million"], default="paper")
     ap.add_argument("--profile-tpi", type=int, default=0, help="schedule for --profile (0 = auto)")
     return ap.parse_args()
@@ -98,6 +100,50 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
     except Exception:
         return 6800.0, "fallback (profiling recipe)"
+
+
+def measure_ceilings(lj, dev, target_ms: float = 40.0, reps: int = 3):
+    """The roofline denominators of the force kernels, measured on this GPU
+    with the library's probe kernels (lj_measure_peak): DFMA, FFMA and
+    packed-FFMA throughput (TFLOP/s) and L2 read bandwidth of a 32 MiB
+    resident buffer (GB/s).  Each probe is sized to run ~target_ms and the
+    best of `reps` runs is kept."""
+    import torch
+    buf = torch.zeros(32 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, kind, scale in (("fp64_fma_tflops", lj.LJ_PEAK_DFMA, 1e12),
+                              ("fp32_fma_tflops", lj.LJ_PEAK_FFMA, 1e12),
+                              ("fp32x2_fma_tflops", lj.LJ_PEAK_FFMA2, 1e12),
+                              ("l2_read_gbs", lj.LJ_PEAK_L2_READ, 1e9)):
+        b = buf if kind == lj.LJ_PEAK_L2_READ else None
+        work = 4
+        _, ms = lj.lj_measure_peak(kind, work, b)
+        work = max(1, int(work * target_ms / max(ms, 1e-3)))
+        best, best_ms = 0.0, 0.0
+        for _ in range(reps):
+            rate, ms = lj.lj_measure_peak(kind, work, b)
+            if rate > best:
+                best, best_ms = rate, ms
+        out[name] = best / scale
+        out[name.rsplit("_", 1)[0] + "_ms"] = best_ms
+    del buf
+    return out
+
+
+def run_peaks(args):
+    import torch
+    from paper_1806_05713_gb300 import build as lib_build
+    from paper_1806_05713_gb300 import lj
+    lib_build.build()
+    dev = torch.device("cuda", 0)
+    lj.load()
+    with ClockSampler(0) as clk:
+        res = measure_ceilings(lj, dev)
+    res["clocks"] = clk.summary()
+    res["sm_count"] = torch.cuda.get_device_properties(dev).multi_processor_count
+    res["derived_fp64_tflops"] = FP64_PEAK_TFLOPS
+    res["derived_fp32_tflops"] = FP32_PEAK_TFLOPS
+    print(json.dumps(res))
 
 
 class ClockSampler:
@@ -307,6 +353,9 @@ def main():
         return
     if args.profile:
         run_profile(args)
+        return
+    if args.peaks:
+        run_peaks(args)
         return
 
     import torch

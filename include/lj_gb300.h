@@ -201,7 +201,12 @@ int lj_build_pairlist(const double *q4_dev, int64_t n, const double box[3], doub
  *    device current; make that first call before any stream capture.
  *  - All calls share the one array and each call clears what it needs zeroed:
  *    calls whose GPU work overlaps (other streams or host threads) race on it
- *    and must be serialised by the caller.
+ *    and must be serialised by the caller.  The array is in use until the
+ *    call's work on `stream` has completed -- after the call returns, since
+ *    the last kernels still read it -- so serialise through that stream or an
+ *    event, not by the order of the host calls alone.
+ *  - It always takes the builder's two-walk path (count, scan, fill), and
+ *    every operation it enqueues goes on `stream` (no internal stream).
  * Arguments, outputs, blocking behaviour and the other errors are those of
  * lj_build_pairlist.
  */

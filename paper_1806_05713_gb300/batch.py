@@ -147,6 +147,23 @@ class Batch:
             self.force(p4)
         return g
 
+    def capture_per_system_graph(self, p4: torch.Tensor | None = None,
+                                 tpi: int = lj.LJ_TPI_AUTO) -> torch.cuda.CUDAGraph:
+        """A CUDA graph of the per-system calls (force_per_system): replaying
+        it issues the same kernels as the separate lj_force calls with no
+        host work between them, so its time against the persistent launch's
+        is the GPU-side difference of the two ways of running the batch."""
+        p4 = self.p4 if p4 is None else p4
+        side = torch.cuda.Stream(device=self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            self.force_per_system(p4, tpi=tpi)  # sizes the workspace outside capture
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.force_per_system(p4, tpi=tpi)
+        return g
+
     def autotune(self, tpis=None, rows=(16, 32, 64, 128), reps: int = 5, layouts=None):
         """Pick lanes-per-row and rows-per-item -- and, with layouts=(True,
         False), the list layout (half list with p_j atomics, or full list

@@ -178,14 +178,19 @@ __device__ __forceinline__ double rcp_fp64_seeded(double a, bool &ok)
     const float q = __fmul_rn(y, t);
     const float l = __fmaf_rn(q, t, q);  // 1/a ~ y + l, |l| < 2^-21 y
     // y + l as a double: y's 24-bit significand at bit 52, l added at its
-    // binary point (integer add of the two aligned significands).
+    // binary point (integer add of the two aligned significands).  For large
+    // a the correction l is a subnormal float (|l| ~ 2^-22 / a falls below
+    // 2^-126 once a passes ~2^104, earlier when y is already close): it then
+    // has no implicit bit and the exponent of the smallest normal, and its
+    // absolute resolution 2^-149 still leaves the seed within 2^-31 of 1/a
+    // up to a < 2^120, which the Newton step squares to below an ulp.
     const unsigned uy = __float_as_uint(y), ul = __float_as_uint(l);
     const int ey = static_cast<int>((uy >> 23) & 0xff);
     const int el = static_cast<int>((ul >> 23) & 0xff);
     long long my = static_cast<long long>((uy & 0x7fffffu) | 0x800000u) << 29;
-    const int sh = 29 - (ey - el);  // where l's significand lands (<= 8)
+    const int sh = 29 - (ey - (el ? el : 1));  // where l's significand lands
     long long ml = static_cast<long long>((ul & 0x7fffffu) | (el ? 0x800000u : 0u));
-    ml = el == 0 ? 0 : (sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> -sh) : 0));
+    ml = sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> -sh) : 0);
     my += (ul >> 31) ? -ml : ml;
     long long eb = static_cast<long long>(ey) - 127 + 1023;
     if (my >= (1ll << 53)) {

@@ -1,0 +1,275 @@
+// lj_measure.cu -- measured ceilings for the roofline of the force kernels,
+// and direct evaluation of their reciprocal approximations.
+//
+// The paper costs one pair at 27 additions or multiplications and one
+// division (section "Lennard-Jones Potential") and proposes replacing the
+// division by a reciprocal approximation plus a correction (section
+// "Summary and Discussion").  lj_measure_peak times the units that bound the
+// GB300 kernels (the FP64 pipe, the FP32 pipe in its scalar and packed
+// forms, L2 reads), so the kernels' fractions rest on measured numbers;
+// lj_eval_reciprocal runs, element by element, the reciprocal functions the
+// kernels inline, so their error can be checked against IEEE division.
+#include <cmath>
+
+#include "lj_dfloat.cuh"
+#include "lj_fixed.cuh"
+#include "lj_measure.h"
+
+namespace lj {
+namespace {
+
+constexpr int kChains = 8;   // independent FMA chains per thread
+constexpr int kUnroll = 16;  // FMAs per chain per loop trip
+constexpr int kPeakThreads = 256;
+constexpr int kPeakBlocksPerSm = 8;
+
+// Each chain is x <- x m + k with |m| < 1, so the values stay bounded and
+// finite; m and k are kernel arguments, so nothing folds at compile time.
+// The result is written only if it equals an impossible value, which keeps
+// the chains live without a store per thread.
+__global__ void __launch_bounds__(kPeakThreads)
+peak_dfma_kernel(double m, double k, long long trips, double *__restrict__ sink)
+{
+    double x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = 1.0 + 1e-3 * c + 1e-9 * threadIdx.x;
+    for (long long t = 0; t < trips; ++t) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], m, k);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    if (s == -1234.5) sink[threadIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kPeakThreads)
+peak_ffma_kernel(float m, float k, long long trips, double *__restrict__ sink)
+{
+    float x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = 1.0f + 1e-3f * c + 1e-6f * threadIdx.x;
+    for (long long t = 0; t < trips; ++t) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) x[c] = __fmaf_rn(x[c], m, k);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    if (s == -1234.5f) sink[threadIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kPeakThreads)
+peak_ffma2_kernel(float m, float k, long long trips, double *__restrict__ sink)
+{
+    f2 x[kChains];
+    const f2 mm = pk2(m, m), kk = pk2(k, k);
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = pk2(1.0f + 1e-3f * c, 1.0f + 1e-6f * threadIdx.x);
+    for (long long t = 0; t < trips; ++t) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) x[c] = fma2(x[c], mm, kk);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+        float a, b;
+        up2(x[c], a, b);
+        s += a + b;
+    }
+    if (s == -1234.5f) sink[threadIdx.x] = s;
+}
+
+// Grid-stride 16-byte reads of the whole buffer, `passes` times.  The XOR
+// of everything read decides a store (never taken for the zero-filled
+// buffer the caller passes), so the compiler must keep every load.
+__global__ void __launch_bounds__(kPeakThreads)
+peak_l2_read_kernel(const uint4 *__restrict__ buf, long long count, long long passes,
+                    unsigned *__restrict__ sink)
+{
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    unsigned acc = 0u;
+    for (long long p = 0; p < passes; ++p) {
+        for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+             e < count; e += stride) {
+            uint4 v;
+            asm volatile("ld.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                         : "l"(buf + e));
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    }
+    if (acc == 0x9e3779b9u) sink[0] = acc;
+}
+
+int launch_peak(int kind, const void *buf, size_t buf_bytes, long long work, double *sink,
+                unsigned grid, cudaStream_t st)
+{
+    switch (kind) {
+        case LJ_PEAK_DFMA:
+            peak_dfma_kernel<<<grid, kPeakThreads, 0, st>>>(0.9999999, 1e-7, work, sink);
+            break;
+        case LJ_PEAK_FFMA:
+            peak_ffma_kernel<<<grid, kPeakThreads, 0, st>>>(0.99999f, 1e-5f, work, sink);
+            break;
+        case LJ_PEAK_FFMA2:
+            peak_ffma2_kernel<<<grid, kPeakThreads, 0, st>>>(0.99999f, 1e-5f, work, sink);
+            break;
+        case LJ_PEAK_L2_READ:
+            peak_l2_read_kernel<<<grid, kPeakThreads, 0, st>>>(
+                static_cast<const uint4 *>(buf), static_cast<long long>(buf_bytes / 16), work,
+                reinterpret_cast<unsigned *>(sink));
+            break;
+        default:
+            return LJ_ERR_ARG;
+    }
+    LJ_TRY_LAUNCH("peak kernel");
+    return LJ_OK;
+}
+
+// ---- reciprocal evaluation -------------------------------------------------
+
+__global__ void eval_reciprocal_kernel(int kind, const double *__restrict__ a, long long n,
+                                       double *__restrict__ out, unsigned char *__restrict__ ok)
+{
+    const long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (kind == LJ_RCP_DF2) {
+        // two entries per lane: elements 2t and 2t + 1 (the last one twice
+        // when n is odd)
+        const long long k0 = 2 * t, k1 = 2 * t + 1 < n ? 2 * t + 1 : 2 * t;
+        if (k0 >= n) return;
+        const double a0 = a[k0], a1 = a[k1];
+        const float h0 = __double2float_rn(a0), h1 = __double2float_rn(a1);
+        const float l0 = __double2float_rn(a0 - static_cast<double>(h0));
+        const float l1 = __double2float_rn(a1 - static_cast<double>(h1));
+        const df2 r = df2_rcp(df2{pk2(h0, h1), pk2(l0, l1)});
+        float rh0, rh1, rl0, rl1;
+        up2(r.h, rh0, rh1);
+        up2(r.l, rl0, rl1);
+        out[2 * k0] = static_cast<double>(rh0);
+        out[2 * k0 + 1] = static_cast<double>(rl0);
+        if (ok) ok[k0] = 1;
+        if (k1 != k0) {
+            out[2 * k1] = static_cast<double>(rh1);
+            out[2 * k1 + 1] = static_cast<double>(rl1);
+            if (ok) ok[k1] = 1;
+        }
+        return;
+    }
+    if (t >= n) return;
+    const double x = a[t];
+    double v = 0.0, w = 0.0;
+    bool in_range = true;
+    switch (kind) {
+        case LJ_RCP_FP64_SEEDED:
+            v = rcp_fp64_seeded(x, in_range);
+            break;
+        case LJ_RCP_FP64_FAST:
+            v = rcp_fp64_fast(x, in_range);
+            break;
+        case LJ_RSQRT_FP64: {
+            v = rsqrt_fp64(x);
+            const int ea = static_cast<int>((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+            in_range = ea > -120 && ea < 120;
+            break;
+        }
+        case LJ_RCP_DF: {
+            const float h = __double2float_rn(x);
+            const float l = __double2float_rn(x - static_cast<double>(h));
+            const df r = df_rcp(df{h, l});
+            v = static_cast<double>(r.h);
+            w = static_cast<double>(r.l);
+            break;
+        }
+        case LJ_RCP_FP32:
+            v = static_cast<double>(rcp_fp32(__double2float_rn(x)));
+            break;
+        default:
+            break;
+    }
+    out[2 * t] = v;
+    out[2 * t + 1] = w;
+    if (ok) ok[t] = in_range ? 1 : 0;
+}
+
+}  // namespace
+}  // namespace lj
+
+extern "C" int lj_measure_peak(int kind, void *buf_dev, size_t buf_bytes, int64_t work,
+                               double *rate_out, double *ms_out, void *stream)
+{
+    using namespace lj;
+    if (rate_out) *rate_out = 0.0;
+    if (ms_out) *ms_out = 0.0;
+    if (!rate_out || !ms_out || work < 1) return LJ_ERR_ARG;
+    if (kind < LJ_PEAK_DFMA || kind > LJ_PEAK_L2_READ) return LJ_ERR_ARG;
+    if (kind == LJ_PEAK_L2_READ &&
+        (!buf_dev || buf_bytes == 0 || (buf_bytes % 4096) != 0 ||
+         (reinterpret_cast<uintptr_t>(buf_dev) & 255u)))
+        return LJ_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned grid = unsigned(num_sms() * kPeakBlocksPerSm);
+    // The sink is never written: the probe kernels store to it only under a
+    // condition their values cannot meet (it may be null for the FMA kinds).
+    double *sink = static_cast<double *>(buf_dev);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LJ_TRY_CUDA(cudaEventCreate(&e0));
+    const cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        record_cuda_error(ce, "cudaEventCreate");
+        return LJ_ERR_CUDA;
+    }
+    int rc = launch_peak(kind, buf_dev, buf_bytes, kind == LJ_PEAK_L2_READ ? 1 : work, sink, grid,
+                         st);  // warm-up (and, for L2, the pass that loads the buffer)
+    cudaError_t err = cudaSuccess;
+    if (rc == LJ_OK) err = cudaEventRecord(e0, st);
+    if (rc == LJ_OK && err == cudaSuccess) rc = launch_peak(kind, buf_dev, buf_bytes, work, sink, grid, st);
+    if (rc == LJ_OK && err == cudaSuccess) err = cudaEventRecord(e1, st);
+    if (rc == LJ_OK && err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (rc == LJ_OK && err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) {
+        record_cuda_error(err, "lj_measure_peak timing");
+        return LJ_ERR_CUDA;
+    }
+    if (rc != LJ_OK) return rc;
+    const double threads = double(grid) * kPeakThreads;
+    const double fmas = threads * kChains * kUnroll * double(work);
+    double amount = 0.0;
+    switch (kind) {
+        case LJ_PEAK_DFMA:
+        case LJ_PEAK_FFMA: amount = 2.0 * fmas; break;
+        case LJ_PEAK_FFMA2: amount = 4.0 * fmas; break;
+        default: amount = double(buf_bytes) * double(work); break;
+    }
+    *ms_out = ms;
+    *rate_out = ms > 0.0f ? amount / (double(ms) * 1e-3) : 0.0;
+    return LJ_OK;
+}
+
+extern "C" int lj_eval_reciprocal(int kind, const double *a_dev, int64_t n, double *out_dev,
+                                  uint8_t *ok_dev, void *stream)
+{
+    using namespace lj;
+    if (kind < LJ_RCP_FP64_SEEDED || kind > LJ_RCP_FP32 || n < 0) return LJ_ERR_ARG;
+    if (n == 0) return LJ_OK;
+    if (!a_dev || !out_dev) return LJ_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(a_dev) | reinterpret_cast<uintptr_t>(out_dev)) & 7u)
+        return LJ_ERR_ARG;
+    if (n >= (int64_t(1) << 40)) return LJ_ERR_ARG;
+    const long long lanes = kind == LJ_RCP_DF2 ? (n + 1) / 2 : n;
+    const unsigned grid = unsigned((lanes + 255) / 256);
+    eval_reciprocal_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        kind, a_dev, n, out_dev, ok_dev);
+    LJ_TRY_LAUNCH("eval_reciprocal_kernel");
+    return LJ_OK;
+}

@@ -45,6 +45,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "lj_internal.cuh"
 #include "lj_scan.cuh"
@@ -417,6 +418,12 @@ fill_kernel(const double *__restrict__ q4, int n, Grid g, const int *__restrict_
     __syncwarp();
     const int start = row_ptr[i];
     const int len = row_ptr[i + 1] - start;
+    // Unreachable by construction: the count and the fill run the same walk
+    // (walk_row, same arithmetic, same inputs), so the fill meets exactly
+    // the row's counted entries, and cap is the longest counted row.  Only a
+    // caller writing q between the two kernels could break it; the row is
+    // then left unwritten and the bit recorded, but the host has already
+    // read the statistics, so nothing reports it.
     if (cnt != len || cnt > cap) {
         if (lane == 0) atomicOr(&stats->err, 2);
         return;
@@ -664,29 +671,52 @@ int slab_cap(int64_t n, const double box[3], double rs)
 
 // A stream and an event per host thread and device, on which the builder
 // reads the list size back while the row sort runs on the caller's stream.
-// Created on first use and kept for the life of the thread.
-int side_stream(cudaStream_t &side, cudaEvent_t &ev)
-{
+// Created on first use and destroyed when the thread exits (a thread-local
+// holder's destructor; errors there are ignored, since the CUDA runtime may
+// already be shutting down at process exit).  No limit on the number of
+// devices a thread uses.
+namespace {
+struct SideStreams {
     struct Side {
         int dev;
         cudaStream_t s;
         cudaEvent_t e;
     };
-    static thread_local Side cache[16] = {};
-    static thread_local int used = 0;
+    std::vector<Side> sides;
+    ~SideStreams()
+    {
+        for (const Side &x : sides) {
+            int cur = 0;
+            if (cudaGetDevice(&cur) != cudaSuccess) break;
+            if (cudaSetDevice(x.dev) != cudaSuccess) continue;
+            cudaEventDestroy(x.e);
+            cudaStreamDestroy(x.s);
+            cudaSetDevice(cur);
+        }
+    }
+};
+}  // namespace
+
+int side_stream(cudaStream_t &side, cudaEvent_t &ev)
+{
+    static thread_local SideStreams cache;
     int dev = 0;
     LJ_TRY_CUDA(cudaGetDevice(&dev));
-    for (int k = 0; k < used; ++k)
-        if (cache[k].dev == dev) {
-            side = cache[k].s;
-            ev = cache[k].e;
+    for (const SideStreams::Side &x : cache.sides)
+        if (x.dev == dev) {
+            side = x.s;
+            ev = x.e;
             return LJ_OK;
         }
-    if (used == 16) return LJ_ERR_ARG;
-    Side x{dev, nullptr, nullptr};
+    SideStreams::Side x{dev, nullptr, nullptr};
     LJ_TRY_CUDA(cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking));
-    LJ_TRY_CUDA(cudaEventCreateWithFlags(&x.e, cudaEventDisableTiming));
-    cache[used++] = x;
+    const cudaError_t err = cudaEventCreateWithFlags(&x.e, cudaEventDisableTiming);
+    if (err != cudaSuccess) {
+        cudaStreamDestroy(x.s);
+        record_cuda_error(err, "cudaEventCreateWithFlags");
+        return LJ_ERR_CUDA;
+    }
+    cache.sides.push_back(x);
     side = x.s;
     ev = x.e;
     return LJ_OK;

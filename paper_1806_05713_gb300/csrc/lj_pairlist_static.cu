@@ -16,8 +16,15 @@
 // cudaGetSymbolAddress, with that device current, and caches it.  That first
 // call should therefore come before any stream capture.  All calls share the
 // one array: calls whose GPU work overlaps (on different streams or host
-// threads) race on it and must be serialised by the caller.  Everything the
-// builder needs zeroed is cleared at the start of each call.
+// threads) race on it and must be serialised by the caller: the array stays
+// in use until the call's work on its stream has completed, which is after
+// the call returns (the last kernels still read it), so order a second call
+// after the first through that stream or an event, not by host order alone.
+// Everything the builder needs zeroed is cleared at the start of each call.
+// The builder is handed exactly the two-walk workspace (count, scan, fill),
+// so this entry point never takes the one-walk path with its row slabs and
+// never creates or uses a side stream: every operation it enqueues goes on
+// the caller's stream.
 #include <mutex>
 
 #include "lj_internal.cuh"
@@ -62,7 +69,9 @@ extern "C" int lj_build_pairlist_static(const double *q4_dev, int64_t n, const d
         }
         scratch = g_static_addr[dev];
     }
+    // `need` bytes (not the whole array): the builder then takes its two-walk
+    // path, which has no row slabs and no side stream.
     return lj::build_pairlist_impl(q4_dev, n, box, r_search, half, row_ptr_dev, col_dev,
-                                   col_capacity, scratch, LJ_STATIC_SCRATCH_BYTES, nnz_out,
-                                   max_row_out, static_cast<cudaStream_t>(stream));
+                                   col_capacity, scratch, need, nnz_out, max_row_out,
+                                   static_cast<cudaStream_t>(stream));
 }

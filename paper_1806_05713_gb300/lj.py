@@ -36,6 +36,16 @@ LJ_SCHED_IMAGES = 1024
 LJ_SCHED_FIXED = 2048
 LJ_SCHED_COMPACT = 4096
 LJ_MD_LAST_HALF_KICK = 1
+LJ_PEAK_DFMA = 0
+LJ_PEAK_FFMA = 1
+LJ_PEAK_FFMA2 = 2
+LJ_PEAK_L2_READ = 3
+LJ_RCP_FP64_SEEDED = 0
+LJ_RCP_FP64_FAST = 1
+LJ_RSQRT_FP64 = 2
+LJ_RCP_DF = 3
+LJ_RCP_DF2 = 4
+LJ_RCP_FP32 = 5
 LJ_STATIC_MAX_ATOMS = 131072
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liblj_gb300.so")
@@ -106,6 +116,9 @@ SIGNATURES = {
     "lj_force_shifted_workspace_bytes": (_sz, [_i64]),
     "lj_force_shifted": (_int, [_vp, _vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl, _dbl3, _dbl, _dbl,
                                 _vp, _vp, _sz, _vp]),
+    "lj_measure_peak": (_int, [_int, _vp, _sz, _i64, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), _vp]),
+    "lj_eval_reciprocal": (_int, [_int, _vp, _i64, _vp, _vp, _vp]),
     "lj_energy_workspace_bytes": (_sz, [_i64]),
     "lj_energy": (_int, [_vp, _i64, _vp, _vp, _i64, _int, _dbl, _dbl3, _dbl, _dbl, _int, _vp, _vp,
                          _sz, _vp]),
@@ -630,3 +643,32 @@ def lj_autotune_batched(systems, dt: float, precision: int, tpis, rows_per_item,
                                       ctypes.byref(br), ctypes.byref(bm), _stream(stream)),
            "lj_autotune_batched")
     return bt.value, br.value, bm.value
+
+
+def lj_measure_peak(kind: int, work: int, buf: torch.Tensor | None = None, stream=None):
+    """One timed run of the ceiling probe ``kind`` (LJ_PEAK_*); returns
+    (rate, ms): flop/s for the FMA kinds, bytes/s for LJ_PEAK_L2_READ (which
+    reads ``buf``, a CUDA byte tensor)."""
+    lib = load()
+    rate, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    bp = buf.data_ptr() if buf is not None else None
+    nb = buf.numel() * buf.element_size() if buf is not None else 0
+    st = lib.lj_measure_peak(int(kind), bp, nb, int(work), ctypes.byref(rate), ctypes.byref(ms),
+                             _stream(stream))
+    _check(st, "lj_measure_peak")
+    return float(rate.value), float(ms.value)
+
+
+def lj_eval_reciprocal(kind: int, a: torch.Tensor, stream=None):
+    """Evaluate the reciprocal approximation ``kind`` (LJ_RCP_*, LJ_RSQRT_FP64)
+    on the float64 CUDA tensor ``a``; returns (out (n, 2) float64: value or
+    double-float head, and tail; ok (n,) uint8: 1 inside the function's
+    range)."""
+    lib = load()
+    n = int(a.numel())
+    ap = _dev(a, torch.float64, "a")
+    out = torch.empty((n, 2), dtype=torch.float64, device=a.device)
+    ok = torch.empty(n, dtype=torch.uint8, device=a.device)
+    st = lib.lj_eval_reciprocal(int(kind), ap, n, out.data_ptr(), ok.data_ptr(), _stream(stream))
+    _check(st, "lj_eval_reciprocal")
+    return out, ok

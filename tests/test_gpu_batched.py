@@ -69,6 +69,24 @@ def test_graph_replay(cuda_lib, systems, precision):
     assert torch.allclose(p, 2 * once, rtol=0, atol=1e-14 * float(once.abs().max()))
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_per_system_graph_equals_per_system_calls(cuda_lib, systems, precision):
+    """The CUDA graph of the per-system lj_force calls replays exactly the
+    calls it captured: on full lists (deterministic) its update is
+    bit-identical to the same calls issued from the host."""
+    from paper_1806_05713_gb300.batch import Batch
+    b = Batch(systems, 0.01, precision, False, tpi=8, rows_per_item=32)
+    direct = torch.zeros_like(b.p4)
+    b.force_per_system(direct)
+    p = torch.zeros_like(b.p4)
+    g = b.capture_per_system_graph(p)
+    torch.cuda.synchronize()
+    p.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(p, direct)
+
+
 def test_batched_dfloat_equals_per_system_launches_full_list(cuda_lib, systems):
     """The double-float row walk is the same in the persistent launch and in
     lj_force (two entries per lane, 8 lanes per row): same bits."""

@@ -5,8 +5,12 @@ their context, no workspace handed to them): its scratch is a fixed array in
 the library's device memory.  It must produce exactly the list of the
 regular entry point, lj_build_pairlist, call after call -- the shared array
 keeps the previous call's contents, so a second call on a different system
-checks that everything that must start at zero is cleared.  This file sorts
-last so that a run stopping at the first failure has run every other test.
+checks that everything that must start at zero is cleared.  Both calls (the
+paper-size system of 119,164 atoms, then the 4,000-atom one) go through the
+builder's two-walk path, count -> scan -> fill, the only path this entry
+point takes; the regular builder it is compared with takes its one-walk
+path, so the two routes check each other.  This file sorts last so that a
+run stopping at the first failure has run every other test.
 """
 import ctypes
 
