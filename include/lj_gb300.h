@@ -77,29 +77,11 @@ extern "C" {
  * (FP64: LJ_SCHED_FIXED | 8; mixed: 8 lanes per row; double-float:
  * LJ_SCHED_SWP2 | 8). */
 #define LJ_TPI_AUTO 0
-/* LJ_SCHED_REFILL | t (t = 1, 4 or 8; FP64 only): the group-refill schedule.
- * Each group of t lanes owns one row at a time and takes the next row as
- * soon as its own ends (rows are handed to warps in chunks from a counter in
- * the workspace), so no group waits for a longer row of its warp; a
- * persistent grid of one launch.  Half lists add each lane's partial sums to
- * p_i with FP64 atomics.  With LJ_SCHED_FIXED (t = 4 or 8): the same over
- * the exact fixed-point displacement; both list kinds then add each lane's
- * partial sums to p_i with atomics (the full list's sums are then not
- * deterministic). */
-#define LJ_SCHED_REFILL 64
-/* LJ_SCHED_SWP2 | tpi (tpi = 4, 8 or 16, or with LJ_SCHED_REFILL | 1, 4, 8;
- * FP64 only): software pipelining, the paper's section "Software
- * Pipelining" -- each lane carries two independent entries per iteration so
- * that their FP64 chains overlap. */
+/* LJ_SCHED_SWP2 | tpi (tpi = 4, 8 or 16; FP64 with the IEEE-bit-pattern
+ * displacement, and LJ_DFLOAT): software pipelining, the paper's section
+ * "Software Pipelining" -- each lane carries two independent entries per
+ * iteration so that their dependency chains overlap. */
 #define LJ_SCHED_SWP2 128
-/* LJ_SCHED_QUEUE | t (t = 1, 2, 4 or 8; FP64 only): the lane-queue schedule.
- * Groups of t lanes take rows as in LJ_SCHED_REFILL; each lane screens the
- * entries of its share of the row (d, r^2, cutoff) into its own FIFO of
- * in-cutoff pairs in shared memory, and the force arithmetic runs only when
- * every lane with work holds a queued pair, so no FP64 instruction is spent
- * on margin pairs, row tails or idle groups.  Half lists add p_i by FP64
- * atomics per lane and row. */
-#define LJ_SCHED_QUEUE 256
 /* LJ_SCHED_SORTED | (a row-group schedule, FP64 or mixed): rows are walked
  * in order of decreasing length (a counting sort of the row lengths in the
  * workspace, three small kernels per call), so the groups of a warp walk
@@ -119,12 +101,6 @@ extern "C" {
  * boxes return LJ_ERR_ARG, and the default schedule, lj_force_energy,
  * lj_force_vjp and lj_force_batched use image selection there. */
 #define LJ_SCHED_FIXED 2048
-/* LJ_SCHED_COMPACT | 4, 8, 16 (FP64 only; implies LJ_SCHED_FIXED, optionally
- * | LJ_SCHED_SORTED): each row is first screened on the integer pipe with
- * the exact fixed-point r^2 and its interacting entries compacted in
- * shared memory; the FP64 arithmetic then runs over those entries only
- * (no FP64 instruction for margin entries or ragged row tails). */
-#define LJ_SCHED_COMPACT 4096
 
 const char *lj_status_string(int status);
 /* Text of the last CUDA error seen by this library in this thread. */
@@ -221,9 +197,9 @@ int lj_build_pairlist_static(const double *q4_dev, int64_t n, const double box[3
 /* Force (Algorithm 1 inside Algorithm 3)                                    */
 /* ======================================================================== */
 
-/* Bytes of device workspace lj_force needs (about 8 n + 2.5 KB: a row
- * counter and the length-sorted row order; plus fixed-point positions,
- * 32 n for LJ_FP64 (LJ_SCHED_FIXED) and LJ_DFLOAT, 16 n for LJ_MIXED). */
+/* Bytes of device workspace lj_force needs (about 8 n + 2.5 KB for the
+ * length-sorted row order; plus fixed-point positions, 32 n for LJ_FP64
+ * and LJ_DFLOAT, 16 n for LJ_MIXED). */
 size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
 
 /*
@@ -241,20 +217,17 @@ size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
  *  box              host, 3 box sides.
  *  eps, sigma       Eq. (1) parameters (> 0).
  *  precision        LJ_FP64, LJ_MIXED or LJ_DFLOAT.
- *  tpi              LJ_TPI_AUTO, 1..32 (power of two; LJ_DFLOAT: 4, 8, 16,
- *                   optionally | LJ_SCHED_SORTED), LJ_SCHED_SWP2 | 4, 8,
- *                   16, LJ_SCHED_REFILL | 1, 4, 8 (optionally | SWP2), or
- *                   LJ_SCHED_QUEUE | 1, 2, 4, 8; the last three families
- *                   FP64 only.  LJ_SCHED_SORTED may be or-ed into the plain
- *                   and SWP2 schedules, LJ_SCHED_IMAGES into the FP64
- *                   4, 8, 16 and SWP2 schedules; LJ_SCHED_FIXED | 4, 8, 16
- *                   and LJ_SCHED_COMPACT | 4, 8, 16 (FP64, optionally |
+ *  tpi              LJ_TPI_AUTO, 1..32 (power of two; LJ_DFLOAT: 4, 8, 16),
+ *                   or LJ_SCHED_SWP2 | 4, 8, 16 (FP64 and LJ_DFLOAT).
+ *                   LJ_SCHED_SORTED may be or-ed into any of these,
+ *                   LJ_SCHED_IMAGES into the FP64 4, 8, 16 and SWP2
+ *                   schedules; LJ_SCHED_FIXED | 4, 8, 16 (FP64, optionally |
  *                   LJ_SCHED_SORTED).
  *  workspace_dev    scratch of lj_force_workspace_bytes() (NULL if 0).
  * Half lists add p_j with FP64 atomics, so their rounding order (not their
  * value beyond the last bits) varies between calls; full lists are
- * deterministic except under LJ_SCHED_REFILL | 1 and LJ_SCHED_QUEUE (and,
- * for LJ_DFLOAT, rows with two or more pairs that take the FP64 formula).
+ * deterministic (except, for LJ_DFLOAT, rows with two or more pairs that
+ * take the FP64 formula).
  * LJ_DFLOAT agrees with LJ_FP64 to ~1e-14 of max |dp|; it returns
  * LJ_ERR_ARG if 24 eps sigma^6 dt / r_c^7 is outside 2^-690 .. 2^690.
  * Asynchronous.  Errors: LJ_ERR_ARG, LJ_ERR_BOX, LJ_ERR_CAPACITY (workspace

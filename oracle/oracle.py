@@ -150,12 +150,20 @@ def pairlist_rows(q, box, rs: float, half: bool, i0: int, i1: int):
 
 
 def force_rows(q, p, row_ptr, col, half: bool, dt: float, rc: float, box, i0: int, i1: int,
-               eps: float = 1.0, sigma: float = 1.0) -> np.ndarray:
+               eps: float = 1.0, sigma: float = 1.0, inplace: bool = False) -> np.ndarray:
     """Momenta after one force call over rows i0 .. i1-1 of a list given in
-    the pairlist_rows form; p is not modified."""
+    the pairlist_rows form; p is not modified unless inplace (then p, a
+    C-contiguous float64 (n, >=3) array, is updated and returned -- the
+    timing loops use this so that no copy of p is made per call)."""
     lib = _load()
     q = _rows(q, "q")
-    out = _rows(p, "p").copy()
+    if inplace:
+        if not (isinstance(p, np.ndarray) and p.dtype == np.float64 and p.ndim == 2
+                and p.shape[1] >= 3 and p.flags["C_CONTIGUOUS"]):
+            raise ValueError("inplace needs a C-contiguous float64 (n, >=3) array")
+        out = p
+    else:
+        out = _rows(p, "p").copy()
     L = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col = np.ascontiguousarray(col, dtype=np.int32)

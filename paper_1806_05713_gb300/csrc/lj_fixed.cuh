@@ -380,213 +380,5 @@ __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
     }
 }
 
-// Two entries per lane and iteration (k and k + TPI; LJ_SCHED_FIXED |
-// LJ_SCHED_SWP2): the two FP64 dependency chains of Algorithm 1 in flight
-// together, the paper's software pipelining.
-template <int TPI, bool HALF>
-__device__ __forceinline__ void fp64_fixed_row2(const double *__restrict__ q4,
-                                                const longlong4 *__restrict__ X,
-                                                double *__restrict__ p4,
-                                                const int *__restrict__ row_ptr,
-                                                const int *__restrict__ col, int i,
-                                                const Fp64Params &P, const FixParams &F, unsigned gm)
-{
-    const int sub = threadIdx.x & (TPI - 1);
-    long long xi, yi, zi;
-    load_fixed(X, i, xi, yi, zi);
-    double ax = 0.0, ay = 0.0, az = 0.0;
-    const int kb = row_ptr[i], ke = row_ptr[i + 1];
-    for (int k0 = kb; k0 < ke; k0 += 2 * TPI) {
-        const int k[2] = {k0 + sub, k0 + sub + TPI};
-        bool in[2];
-        int j[2];
-        double dx[2], dy[2], dz[2], r2[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const bool valid = k[u] < ke;
-            j[u] = valid ? col[k[u]] : i;
-            long long xj, yj, zj;
-            load_fixed(X, j[u], xj, yj, zj);
-            in[u] = fixed_entry(q4, xi, yi, zi, xj, yj, zj, valid, i, j[u], P, F, gm, dx[u], dy[u],
-                                dz[u], r2[u]);
-        }
-        if (__any_sync(gm, in[0] || in[1])) {
-            double fn[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const double w = rcp_fp64_fixed(in[u] ? r2[u] : 1.0, gm);
-                const double w2 = w * w;
-                const double w4 = w2 * w2;
-                const double w3 = w2 * w;
-                fn[u] = w4 * fma(P.B, w3, -P.A);  // -df: p_i -= fn d, p_j += fn d
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                if (in[u]) {
-                    if (HALF) {
-                        const double fx = fn[u] * dx[u], fy = fn[u] * dy[u], fz = fn[u] * dz[u];
-                        double *pj = p4 + 4 * static_cast<int64_t>(j[u]);
-                        atomicAdd(pj + 0, fx);
-                        atomicAdd(pj + 1, fy);
-                        atomicAdd(pj + 2, fz);
-                        ax -= fx;
-                        ay -= fy;
-                        az -= fz;
-                    } else {
-                        ax = fma(-fn[u], dx[u], ax);
-                        ay = fma(-fn[u], dy[u], ay);
-                        az = fma(-fn[u], dz[u], az);
-                    }
-                }
-            }
-        }
-    }
-    double *pi = p4 + 4 * static_cast<int64_t>(i);
-    if (HALF) {
-        atomicAdd(pi + 0, ax);
-        atomicAdd(pi + 1, ay);
-        atomicAdd(pi + 2, az);
-    } else {
-        if (TPI > 1) {
-            ax = group_sum<TPI>(ax);
-            ay = group_sum<TPI>(ay);
-            az = group_sum<TPI>(az);
-        }
-        if (sub == 0) {
-            atomicAdd(pi + 0, ax);
-            atomicAdd(pi + 1, ay);
-            atomicAdd(pi + 2, az);
-        }
-    }
-}
-
-// LJ_SCHED_COMPACT: the row in chunks of up to C entries, each in two
-// phases.  A (integer pipe only): every entry's exact r^2 and decision (the
-// FP64 definition inside the 64-ulp band), the interacting entries' column
-// indices compacted into the group's shared-memory buffer.  B: the FP64
-// arithmetic over the compacted entries only, TPI at a time -- the margin
-// entries (~14 % of a list with a 0.3 sigma margin) and the ragged row tails
-// take no FP64 instruction.  The group's phases have group-uniform trip
-// counts, so the four groups of a warp run each phase together.
-constexpr unsigned kBandFlag = 0x80000000u;
-
-template <int TPI, bool HALF, int C>
-__device__ __forceinline__ void fp64_compact_row(const double *__restrict__ q4,
-                                                 const longlong4 *__restrict__ X,
-                                                 double *__restrict__ p4,
-                                                 const int *__restrict__ row_ptr,
-                                                 const int *__restrict__ col, int i,
-                                                 const Fp64Params &P, const FixParams &F,
-                                                 unsigned gm, int *__restrict__ gbuf)
-{
-    const int sub = threadIdx.x & (TPI - 1);
-    const unsigned below = (1u << (threadIdx.x & 31)) - 1u;
-    long long xi, yi, zi;
-    load_fixed(X, i, xi, yi, zi);
-    double ax = 0.0, ay = 0.0, az = 0.0;
-    const int kb = row_ptr[i], ke = row_ptr[i + 1];
-    for (int c0 = kb; c0 < ke; c0 += C) {
-        const int c1 = min(c0 + C, ke);
-        int cnt = 0;  // group-uniform
-        // ---- phase A: exact decisions on the integer pipe, compaction ----
-        for (int k0 = c0; k0 < c1; k0 += TPI) {
-            const int k = k0 + sub;
-            const bool valid = k < c1;
-            const int j = valid ? col[k] : i;
-            long long xj, yj, zj;
-            load_fixed(X, j, xj, yj, zj);
-            const long long Dx = wrap_fixed(xj - xi, F.M[0], F.Mh[0]);
-            const long long Dy = wrap_fixed(yj - yi, F.M[1], F.Mh[1]);
-            const long long Dz = wrap_fixed(zj - zi, F.M[2], F.Mh[2]);
-            unsigned long long hi, lo;
-            norm2_fixed(Dx, Dy, Dz, hi, lo);
-            const long long rb = __double_as_longlong(valid ? fixed128_to_f64(hi, lo, 2 * F.k) : 1.0);
-            bool in = valid && rb < P.rc2_bits;
-            const bool near = valid && static_cast<unsigned long long>(rb - P.rc2_bits + 64) < 128ull;
-            if (__any_sync(gm, near)) {
-                if (near) {
-                    double qxi, qyi, qzi, qxj, qyj, qzj;
-                    load_xyz(q4, i, qxi, qyi, qzi);
-                    load_xyz(q4, j, qxj, qyj, qzj);
-                    in = exact_in_cutoff(min_image(__dsub_rn(qxj, qxi), P.L[0], P.half_bits[0]),
-                                         min_image(__dsub_rn(qyj, qyi), P.L[1], P.half_bits[1]),
-                                         min_image(__dsub_rn(qzj, qzi), P.L[2], P.half_bits[2]), P.rc2);
-                }
-            }
-            const unsigned m = __ballot_sync(gm, in) & gm;
-            if (in) gbuf[cnt + __popc(m & below)] = j | (near ? static_cast<int>(kBandFlag) : 0);
-            cnt += __popc(m);
-        }
-        __syncwarp(gm);
-        // ---- phase B: the FP64 arithmetic over the compacted entries -------
-        for (int b0 = 0; b0 < cnt; b0 += TPI) {
-            const int b = b0 + sub;
-            const bool v = b < cnt;
-            const int e = v ? gbuf[b] : i;
-            const bool band = v && (e & static_cast<int>(kBandFlag));
-            const int j = e & ~static_cast<int>(kBandFlag);
-            long long xj, yj, zj;
-            load_fixed(X, j, xj, yj, zj);
-            const long long Dx = wrap_fixed(xj - xi, F.M[0], F.Mh[0]);
-            const long long Dy = wrap_fixed(yj - yi, F.M[1], F.Mh[1]);
-            const long long Dz = wrap_fixed(zj - zi, F.M[2], F.Mh[2]);
-            unsigned long long hi, lo;
-            norm2_fixed(Dx, Dy, Dz, hi, lo);
-            double r2 = v ? fixed128_to_f64(hi, lo, 2 * F.k) : 1.0;
-            double dx = fixed_to_f64(Dx, F.k), dy = fixed_to_f64(Dy, F.k), dz = fixed_to_f64(Dz, F.k);
-            if (__any_sync(gm, band)) {
-                if (band) {
-                    double qxi, qyi, qzi, qxj, qyj, qzj;
-                    load_xyz(q4, i, qxi, qyi, qzi);
-                    load_xyz(q4, j, qxj, qyj, qzj);
-                    dx = min_image(__dsub_rn(qxj, qxi), P.L[0], P.half_bits[0]);
-                    dy = min_image(__dsub_rn(qyj, qyi), P.L[1], P.half_bits[1]);
-                    dz = min_image(__dsub_rn(qzj, qzi), P.L[2], P.half_bits[2]);
-                    r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-                }
-            }
-            const double w = rcp_fp64(r2, gm);
-            const double w2 = w * w;
-            const double w4 = w2 * w2;
-            const double w3 = w2 * w;
-            const double fn = w4 * fma(P.B, w3, -P.A);  // -df: p_i -= fn d, p_j += fn d
-            if (v) {
-                if (HALF) {
-                    const double fx = fn * dx, fy = fn * dy, fz = fn * dz;
-                    double *pj = p4 + 4 * static_cast<int64_t>(j);
-                    atomicAdd(pj + 0, fx);
-                    atomicAdd(pj + 1, fy);
-                    atomicAdd(pj + 2, fz);
-                    ax -= fx;
-                    ay -= fy;
-                    az -= fz;
-                } else {
-                    ax = fma(-fn, dx, ax);
-                    ay = fma(-fn, dy, ay);
-                    az = fma(-fn, dz, az);
-                }
-            }
-        }
-        __syncwarp(gm);
-    }
-    double *pi = p4 + 4 * static_cast<int64_t>(i);
-    if (HALF) {
-        atomicAdd(pi + 0, ax);
-        atomicAdd(pi + 1, ay);
-        atomicAdd(pi + 2, az);
-    } else {
-        if (TPI > 1) {
-            ax = group_sum<TPI>(ax);
-            ay = group_sum<TPI>(ay);
-            az = group_sum<TPI>(az);
-        }
-        if (sub == 0) {
-            atomicAdd(pi + 0, ax);
-            atomicAdd(pi + 1, ay);
-            atomicAdd(pi + 2, az);
-        }
-    }
-}
-
 }  // namespace
 }  // namespace lj

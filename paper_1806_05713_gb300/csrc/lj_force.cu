@@ -66,14 +66,14 @@ force_fp64_kernel(const double *__restrict__ q4, double *__restrict__ p4, int n,
     fp64_row<TPI, HALF, U, IMG>(q4, p4, row_ptr, col, i, P, group_mask<TPI>());
 }
 
-// FP64 form with the exact fixed-point displacement (LJ_SCHED_FIXED; U = 2:
-// | LJ_SCHED_SWP2).  128-thread blocks (a finer last wave than 256 at the
-// same occupancy, about 1 % faster): U = 1 fits twelve blocks an SM in 40
-// registers; U = 2 six in 74 (0.298 ms against 0.263 for U = 1 at
-// N = 119,164: the occupancy hides the FP64 latency better than the second
-// chain).
-template <int TPI, bool HALF, int U>
-__global__ void __launch_bounds__(128, U == 1 ? 12 : 6)
+// FP64 form with the exact fixed-point displacement (LJ_SCHED_FIXED).
+// 128-thread blocks (a finer last wave than 256 at the same occupancy,
+// about 1 % faster), twelve blocks an SM in 40 registers.  (Two entries per
+// lane -- the paper's software pipelining on this row -- needed 74
+// registers, six blocks an SM, and ran 0.298 ms against 0.263 at
+// N = 119,164: the occupancy hides the FP64 latency better.)
+template <int TPI, bool HALF>
+__global__ void __launch_bounds__(128, 12)
 force_fixed_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
                    double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
                    const int *__restrict__ col, Fp64Params P, FixParams F,
@@ -82,30 +82,7 @@ force_fixed_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ 
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
     if (gid >= n) return;
     const int i = order ? order[gid] : gid;
-    if (U == 2)
-        fp64_fixed_row2<TPI, HALF>(q4, X, p4, row_ptr, col, i, P, F, group_mask<TPI>());
-    else
-        fp64_fixed_row<TPI, HALF>(q4, X, p4, row_ptr, col, i, P, F, group_mask<TPI>());
-}
-
-// FP64 form, exact fixed-point displacement, margin entries compacted away
-// (LJ_SCHED_COMPACT): one shared-memory buffer of kCompactChunk column
-// indices per group.
-constexpr int kCompactChunk = 128;
-
-template <int TPI, bool HALF>
-__global__ void __launch_bounds__(256)
-force_compact_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
-                     double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
-                     const int *__restrict__ col, Fp64Params P, FixParams F,
-                     const int *__restrict__ order)
-{
-    __shared__ int buf[256 / TPI][kCompactChunk];
-    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
-    if (gid >= n) return;
-    const int i = order ? order[gid] : gid;
-    fp64_compact_row<TPI, HALF, kCompactChunk>(q4, X, p4, row_ptr, col, i, P, F, group_mask<TPI>(),
-                                               buf[threadIdx.x / TPI]);
+    fp64_fixed_row<TPI, HALF>(q4, X, p4, row_ptr, col, i, P, F, group_mask<TPI>());
 }
 
 // MIXED form, 128-thread blocks (a finer last wave: the full list 2-4 %
@@ -304,7 +281,7 @@ int launch_fp64(const double *q4, double *p4, int n, const int *rp, const int *c
     return LJ_OK;
 }
 
-template <int TPI, int U = 1>
+template <int TPI>
 int launch_fixed(const double *q4, const longlong4 *X, double *p4, int n, const int *rp,
                  const int *col, int half, const Fp64Params &P, const FixParams &F, const int *order,
                  cudaStream_t st)
@@ -312,25 +289,10 @@ int launch_fixed(const double *q4, const longlong4 *X, double *p4, int n, const 
     const int64_t threads = int64_t(n) * TPI;
     const unsigned grid = unsigned((threads + 127) / 128);
     if (half)
-        force_fixed_kernel<TPI, true, U><<<grid, 128, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
+        force_fixed_kernel<TPI, true><<<grid, 128, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
     else
-        force_fixed_kernel<TPI, false, U><<<grid, 128, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
+        force_fixed_kernel<TPI, false><<<grid, 128, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
     LJ_TRY_LAUNCH("force_fixed_kernel");
-    return LJ_OK;
-}
-
-template <int TPI>
-int launch_compact(const double *q4, const longlong4 *X, double *p4, int n, const int *rp,
-                   const int *col, int half, const Fp64Params &P, const FixParams &F,
-                   const int *order, cudaStream_t st)
-{
-    const int64_t threads = int64_t(n) * TPI;
-    const unsigned grid = unsigned((threads + 255) / 256);
-    if (half)
-        force_compact_kernel<TPI, true><<<grid, 256, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
-    else
-        force_compact_kernel<TPI, false><<<grid, 256, 0, st>>>(q4, X, p4, n, rp, col, P, F, order);
-    LJ_TRY_LAUNCH("force_compact_kernel");
     return LJ_OK;
 }
 
@@ -349,20 +311,6 @@ int launch_mixed(const double *q4, const uint4 *rel, double *p4, int n, const in
 }
 
 }  // namespace
-
-size_t force_refill_workspace_bytes();
-int force_refill_fp64(const double *q4, double *p4, int n, const int *row_ptr, const int *col,
-                      int half, const double box[3], double dt, double rc, double eps,
-                      double sigma, int sched, void *ws, size_t ws_bytes, cudaStream_t st);
-
-int force_queue_fp64(const double *q4, double *p4, int n, const int *row_ptr, const int *col,
-                     int half, const double box[3], double dt, double rc, double eps, double sigma,
-                     int sched, void *ws, size_t ws_bytes, cudaStream_t st);
-
-int force_fixed_refill_fp64(const double *q4, const longlong4 *X, double *p4, int n,
-                            const int *row_ptr, const int *col, int half, const double box[3],
-                            double dt, double rc, double eps, double sigma, int sched, void *ws,
-                            size_t ws_bytes, cudaStream_t st);
 
 size_t dfloat_record_bytes(int64_t n);
 bool dfloat_params_ok(const double box[3], double dt, double rc, double eps, double sigma);
@@ -387,11 +335,11 @@ int check_force_args(const double *q4, const double *p4, int64_t n, const int32_
     return check_box(box, r_cut);
 }
 
-// Workspace: [256 B: refill/queue counter][order: n int][slot: n int]
-// [length histogram] and the fixed-point positions of the form (LJ_FP64:
-// 64-bit integers for LJ_SCHED_FIXED; LJ_MIXED: 32-bit; LJ_DFLOAT: chunks).
+// Workspace: [order: n int][slot: n int][length histogram] (the
+// length-sorted row order of LJ_SCHED_SORTED) and the fixed-point positions
+// of the form (LJ_FP64: 64-bit integers; LJ_MIXED: 32-bit; LJ_DFLOAT:
+// chunks).
 struct ForceWs {
-    unsigned *counter;
     int *order, *slot, *hist;
     uint4 *rel;
     void *rec;
@@ -402,7 +350,6 @@ ForceWs carve_force_ws(void *base, int64_t n, int precision)
     Carver c(base);
     ForceWs w;
     const size_t nn = size_t(n > 0 ? n : 1);
-    w.counter = c.take<unsigned>(64);
     w.order = c.take<int>(nn);
     w.slot = c.take<int>(nn);
     w.hist = c.take<int>(kLenBuckets);
@@ -417,21 +364,8 @@ bool valid_schedule(int s, int precision)
 {
     const int t = s & 63;
     const bool pow2 = t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32;
-    if ((s & LJ_SCHED_FIXED) && (s & LJ_SCHED_REFILL))
-        return precision == LJ_FP64 && (s & ~(LJ_SCHED_FIXED | LJ_SCHED_REFILL | 63)) == 0 &&
-               (t == 4 || t == 8);
-    if (s & LJ_SCHED_QUEUE)
-        return precision == LJ_FP64 && (s & ~(LJ_SCHED_QUEUE | 63)) == 0 && (t <= 8) && (t == 0 || pow2);
-    if (s & LJ_SCHED_REFILL)
-        return precision == LJ_FP64 && (s & ~(LJ_SCHED_REFILL | LJ_SCHED_SWP2 | 63)) == 0 &&
-               (t == 0 || t == 1 || t == 4 || t == 8);
-    if (s & LJ_SCHED_COMPACT)
-        return precision == LJ_FP64 &&
-               (s & ~(LJ_SCHED_FIXED | LJ_SCHED_COMPACT | LJ_SCHED_SORTED | 63)) == 0 &&
-               (t == 4 || t == 8 || t == 16);
     if (s & LJ_SCHED_FIXED)
-        return precision == LJ_FP64 &&
-               (s & ~(LJ_SCHED_FIXED | LJ_SCHED_SWP2 | LJ_SCHED_SORTED | 63)) == 0 &&
+        return precision == LJ_FP64 && (s & ~(LJ_SCHED_FIXED | LJ_SCHED_SORTED | 63)) == 0 &&
                (t == 4 || t == 8 || t == 16);
     if (s & ~(LJ_SCHED_SORTED | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES | 63)) return false;
     if (precision == LJ_DFLOAT) return (s & LJ_SCHED_IMAGES) == 0 && (t == 4 || t == 8 || t == 16);
@@ -444,7 +378,6 @@ size_t force_workspace_bytes_impl(int64_t n, int precision)
 {
     Carver c(nullptr);
     const size_t nn = size_t(n > 0 ? n : 1);
-    c.take<unsigned>(64);
     c.take<int>(nn);
     c.take<int>(nn);
     c.take<int>(kLenBuckets);
@@ -468,7 +401,7 @@ int force_check(const double *q4, const double *p4, int64_t n, const int32_t *ro
     if (t == LJ_TPI_AUTO)
         t = precision == LJ_FP64 ? (fixed_point_ok(box, rc) ? (LJ_SCHED_FIXED | 8) : (LJ_SCHED_IMAGES | 8))
             : precision == LJ_DFLOAT ? (LJ_SCHED_SWP2 | 8) : 8;
-    if ((t & (LJ_SCHED_FIXED | LJ_SCHED_COMPACT)) && !fixed_point_ok(box, rc)) return LJ_ERR_ARG;
+    if ((t & LJ_SCHED_FIXED) && !fixed_point_ok(box, rc)) return LJ_ERR_ARG;
     if (!valid_schedule(t, precision)) return LJ_ERR_ARG;
     if (!ws || ws_bytes < force_workspace_bytes_impl(n, precision)) return LJ_ERR_CAPACITY;
     if (precision == LJ_DFLOAT && !dfloat_params_ok(box, dt, rc, eps, sigma)) return LJ_ERR_ARG;
@@ -486,16 +419,6 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
     if (n == 0 || nnz == 0) return LJ_OK;
     const int ni = static_cast<int>(n);
     const ForceWs W = carve_force_ws(ws, n, precision);
-    if (tpi & LJ_SCHED_QUEUE) {
-        if (precision != LJ_FP64) return LJ_ERR_ARG;
-        return force_queue_fp64(q4, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma, tpi,
-                                W.counter, 256, st);
-    }
-    if ((tpi & LJ_SCHED_REFILL) && !(tpi & LJ_SCHED_FIXED)) {
-        if (precision != LJ_FP64) return LJ_ERR_ARG;
-        return force_refill_fp64(q4, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma, tpi,
-                                 W.counter, 256, st);
-    }
     const int *order = nullptr;
     if (tpi & LJ_SCHED_SORTED) {
         const int rc2 = sort_rows_by_length(row_ptr, ni, W.hist, W.slot, W.order, st);
@@ -506,30 +429,16 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
     if (precision == LJ_DFLOAT)
         return force_dfloat(q4, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma, tpi, order,
                             W.rec, st);
-    if (precision == LJ_FP64 && (tpi & (LJ_SCHED_FIXED | LJ_SCHED_COMPACT))) {
+    if (precision == LJ_FP64 && (tpi & LJ_SCHED_FIXED)) {
         const Fp64Params P = make_fp64_params(box, dt, rc, eps, sigma);
         const FixParams F = make_fix_params(box);
         longlong4 *X = static_cast<longlong4 *>(W.rec);
         fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4, ni, F, X);
         LJ_TRY_LAUNCH("fixed_prepass_kernel");
-        if (tpi & LJ_SCHED_REFILL)
-            return force_fixed_refill_fp64(q4, X, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma,
-                                           tpi, W.counter, 256, st);
-        if (tpi & LJ_SCHED_COMPACT) {
-            switch (tpi & 63) {
-                case 4: return launch_compact<4>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
-                case 8: return launch_compact<8>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
-                case 16: return launch_compact<16>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
-                default: return LJ_ERR_ARG;
-            }
-        }
-        switch (tpi & (63 | LJ_SCHED_SWP2)) {
+        switch (tpi & 63) {
             case 4: return launch_fixed<4>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
             case 8: return launch_fixed<8>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
             case 16: return launch_fixed<16>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
-            case LJ_SCHED_SWP2 | 4: return launch_fixed<4, 2>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
-            case LJ_SCHED_SWP2 | 8: return launch_fixed<8, 2>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
-            case LJ_SCHED_SWP2 | 16: return launch_fixed<16, 2>(q4, X, p4, ni, row_ptr, col, half, P, F, order, st);
             default: return LJ_ERR_ARG;
         }
     }

@@ -28,13 +28,10 @@ LJ_FP64 = 0
 LJ_MIXED = 1
 LJ_DFLOAT = 2
 LJ_TPI_AUTO = 0
-LJ_SCHED_REFILL = 64
 LJ_SCHED_SWP2 = 128
-LJ_SCHED_QUEUE = 256
 LJ_SCHED_SORTED = 512
 LJ_SCHED_IMAGES = 1024
 LJ_SCHED_FIXED = 2048
-LJ_SCHED_COMPACT = 4096
 LJ_MD_LAST_HALF_KICK = 1
 LJ_PEAK_DFMA = 0
 LJ_PEAK_FFMA = 1
@@ -381,11 +378,10 @@ def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float
     (best_tpi, best_ms, {tpi: ms})."""
     lib = load()
     if candidates is None:
-        S, W, I, F, C = (LJ_SCHED_SORTED, LJ_SCHED_SWP2, LJ_SCHED_IMAGES, LJ_SCHED_FIXED,
-                         LJ_SCHED_COMPACT)
-        candidates = ([8, W | 8, I | 4, I | 8, I | 16, I | W | 4, I | W | 8, S | I | 4,
-                       S | I | 8, S | I | 16, F | 4, F | 8, F | 16, S | F | 8, C | 4, C | 8, C | 16,
-                       LJ_SCHED_REFILL | W | 8, LJ_SCHED_QUEUE | 8]
+        S, W, I, F = LJ_SCHED_SORTED, LJ_SCHED_SWP2, LJ_SCHED_IMAGES, LJ_SCHED_FIXED
+        # the fixed-point schedules are refused (and skipped) for boxes wider
+        # than 1024 r_c, where the image-selected ones take over
+        candidates = ([F | 4, F | 8, F | 16, S | F | 8, I | 4, I | 8, I | 16, I | W | 8]
                       if precision == LJ_FP64 else
                       [W | 8, W | 4, W | 16, S | W | 8, 4, 8, 16, S | 4, S | 8]
                       if precision == LJ_DFLOAT else

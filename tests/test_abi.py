@@ -90,10 +90,13 @@ def test_host_argument_checks_without_gpu():
     assert force(eps=0.0) == lj.LJ_ERR_ARG
     assert force(q=None) == lj.LJ_ERR_ARG
     assert force(tpi=3) == lj.LJ_ERR_ARG
-    assert force(prec=1, tpi=lj.LJ_SCHED_REFILL) == lj.LJ_ERR_ARG
-    # mixed precision, or the FP64 refill schedule, without a workspace
+    # retired schedule codes (group refill 64, lane queue 256, compaction
+    # 4096, two entries per lane on the fixed-point rows) are refused
+    for retired in (64 | 8, 256 | 8, 4096 | 8, lj.LJ_SCHED_FIXED | lj.LJ_SCHED_SWP2 | 8):
+        assert force(prec=0, tpi=retired, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG
+    # mixed precision, or the FP64 fixed-point schedule, without a workspace
     assert force(prec=1, tpi=8) == lj.LJ_ERR_CAPACITY
-    assert force(prec=0, tpi=64) == lj.LJ_ERR_CAPACITY
+    assert force(prec=0, tpi=lj.LJ_SCHED_FIXED | 8) == lj.LJ_ERR_CAPACITY
     assert force(prec=0, tpi=8) == lj.LJ_ERR_CAPACITY
     # double-float form: 4, 8 or 16 lanes (optionally length-sorted), a
     # workspace with the fixed-point records, K = 24 eps sigma^6 dt / lambda^7
@@ -106,7 +109,6 @@ def test_host_argument_checks_without_gpu():
     # the fixed-point FP64 schedules need a box at most 1024 r_c wide
     wide = lj._box3([4000.0, 4000.0, 4000.0])
     assert force(tpi=lj.LJ_SCHED_FIXED | 8, box=wide, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG
-    assert force(tpi=lj.LJ_SCHED_COMPACT | 8, box=wide, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG
     assert force(tpi=lj.LJ_SCHED_FIXED | 2, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG
     # empty work is a no-op that succeeds
     assert force(n=0, nnz=0) == lj.LJ_OK

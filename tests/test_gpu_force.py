@@ -13,13 +13,11 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 MIXED_TOL = 1e-5
-SCHEDULES = [1, 2, 4, 8, 16, 32, 132, 136, 144, 64, 68, 72, 196, 200, 257, 258, 260, 264, 520,
-             644, 648, 656, 1028, 1032, 1040, 1156, 1160, 1168, 1672, 1544, 2052, 2056, 2064, 2568,
-             4100, 4104, 4112, 4616, 2180, 2184, 2192, 2116, 2120]
-# 128|t software-pipelined, 64|t group-refill, 256|t lane-queue, 512|... length-sorted rows,
-# 1024|... image-selected displacement, 2048|... exact fixed-point displacement,
-# 4096|... fixed point with the margin entries compacted away; 2048|128|t fixed point,
-# two entries per lane
+SCHEDULES = [1, 2, 4, 8, 16, 32, 132, 136, 144, 520, 644, 648, 656, 1028, 1032, 1040, 1156, 1160,
+             1168, 1544, 1672, 2052, 2056, 2064, 2568]
+# t lanes per row; 128|t two entries per lane (software-pipelined); 512|...
+# length-sorted rows; 1024|... image-selected displacement; 2048|... exact
+# fixed-point displacement (the default)
 
 
 def _run(lj, s, half, precision, tpi, dt=0.01, eps=1.0, sigma=1.0, p0=None, rc=None, pl=None):
@@ -71,7 +69,7 @@ def test_eps_sigma_dt_and_existing_momenta(cuda_lib, oracle_lib, precision, tol)
     p0 = np.random.default_rng(2).normal(size=(s.n, 4))
     kw = dict(dt=0.005, eps=1.3, sigma=1.1, rc=3.0)
     for half in (True, False):
-        for tpi in ((64, 8, 136, 200, 260, 1160, 2056) if precision == 0 else (8,)):
+        for tpi in ((8, 136, 1160, 2056, 2568) if precision == 0 else (8,)):
             got, _ = _run(cuda_lib, s, half, precision, tpi, p0=p0, **kw)
             want = _oracle(oracle_lib, s, half, p0=p0, **kw)
             assert _relerr(got - p0[:, :3], want - p0[:, :3]) <= tol
@@ -88,7 +86,7 @@ def test_two_body_closed_form(cuda_lib, precision):
         q[1, 0] += r
         s = inputs.LJSystem(q=q, box=np.array([20.0] * 3), rho=0.0)
         for half in (True, False):
-            for tpi in (1, 32) + ((64,) if precision == 0 else ()):
+            for tpi in (1, 32) + ((2056,) if precision == 0 else ()):
                 got, _ = _run(lj, s, half, precision, tpi, dt=dt)
                 tol = 1e-15 if precision == 0 else 1e-6
                 assert abs(got[1, 0] - want) <= tol * 24 * dt + 1e-14 * 48 * dt
@@ -118,7 +116,7 @@ def test_small_box_mixed_image_choice(cuda_lib, oracle_lib):
         assert _relerr(got, want) <= MIXED_TOL
 
 
-@pytest.mark.parametrize("tpi", [1032, 2056, 4104])
+@pytest.mark.parametrize("tpi", [1032, 2056, 2568])
 def test_fp64_pairs_on_the_cutoff(cuda_lib, oracle_lib, tpi):
     """Pairs at r_c and one ulp either side, along an axis and a diagonal:
     the FP64 schedules interact exactly the oracle's pairs."""
@@ -155,15 +153,15 @@ def test_fp64_fixed_point_box_sizes(cuda_lib, oracle_lib, scale):
     s.rc, s.margin = 3.0 * scale, 0.3 * scale
     for half in (True, False):
         want = _oracle(oracle_lib, s, half, p0=p0, **kw)
-        for tpi in (2056, 4104):
+        for tpi in (2056, 1032):
             got, _ = _run(cuda_lib, s, half, 0, tpi, p0=p0, **kw)
             assert _relerr(got - p0[:, :3], want - p0[:, :3]) <= FP64_TOL
 
 
-@pytest.mark.parametrize("tpi", [4100, 4104, 4112])
-def test_fp64_compact_long_rows(cuda_lib, oracle_lib, tpi):
-    """r_c = 4, full list: ~330 entries a row, so a row spans three chunks of
-    the compacted schedule's shared-memory buffer."""
+@pytest.mark.parametrize("tpi", [2052, 2056, 2064])
+def test_fp64_long_rows(cuda_lib, oracle_lib, tpi):
+    """r_c = 4, full list: ~330 entries a row, many strides of every group
+    size of the fixed-point schedule."""
     s = inputs.fcc_system(10, 1.0, 0.05, seed=8)
     s.rc, s.margin = 4.0, 0.3
     for half in (True, False):
@@ -210,7 +208,7 @@ def test_fp64_box_wider_than_1024_cutoffs(cuda_lib, oracle_lib):
 
 
 def test_newton_third_law_half_list(cuda_lib, small):
-    got, _ = _run(cuda_lib, small, True, 0, 64)
+    got, _ = _run(cuda_lib, small, True, 0, 2056)
     assert np.max(np.abs(got.sum(axis=0))) < 1e-12 * np.abs(got).sum()
 
 
@@ -219,7 +217,7 @@ def test_pad_column_untouched(cuda_lib, small):
     q = to_dev(small.q)
     pl = lj.lj_build_pairlist(q, small.box, small.rs, True)
     p = torch.full((small.n, 4), 7.0, dtype=torch.float64, device="cuda")
-    for prec, tpi in ((0, 64), (0, 8), (1, 8)):
+    for prec, tpi in ((0, 2056), (0, 8), (1, 8), (2, 136)):
         lj.lj_force(q, p, pl, 0.01, 3.0, small.box, precision=prec, tpi=tpi)
     torch.cuda.synchronize()
     assert torch.all(p[:, 3] == 7.0)
@@ -232,8 +230,7 @@ def test_fp64_paper_size(cuda_lib, oracle_lib, order, half):
     s = inputs.workload_paper(order=order)
     want = _oracle(oracle_lib, s, half)
     pl = None
-    for tpi in (64, 8, 32, 136, 72, 200, 258, 260, 264, 648, 1160, 1672, 2052, 2056, 2568, 4104,
-                4100, 2184, 2180):
+    for tpi in (8, 32, 136, 648, 1032, 1160, 1672, 2052, 2056, 2064, 2568):
         got, pl = _run(cuda_lib, s, half, 0, tpi, pl=pl)
         assert _relerr(got, want) <= FP64_TOL, tpi
 
@@ -248,14 +245,35 @@ def test_mixed_paper_size(cuda_lib, oracle_lib, half):
     assert np.sqrt(np.mean(err ** 2)) / np.sqrt(np.mean(want ** 2)) <= 2.5e-6
 
 
-@pytest.mark.slow
-def test_million_atoms_fp64_and_mixed(cuda_lib, oracle_lib):
+@pytest.fixture(scope="module")
+def million(oracle_lib):
+    """N = 1,048,576 (64^3 FCC): 384 sampled atoms and their momentum change
+    from the definition (every other atom, no list)."""
     s = inputs.workload_million()
-    want = _oracle(oracle_lib, s, True)
-    got, pl = _run(cuda_lib, s, True, 0, 64)
-    assert _relerr(got, want) <= FP64_TOL
-    got, _ = _run(cuda_lib, s, True, 1, 8, pl=pl)
-    assert _relerr(got, want) <= MIXED_TOL
+    g = np.random.default_rng(17)
+    idx = np.concatenate([[0, s.n - 1], g.choice(s.n, 382, replace=False)])
+    want = oracle_lib.force_atoms(s.q, idx, 0.01, s.rc, s.box)
+    return s, idx, want
+
+
+@pytest.mark.parametrize("half", [True, False])
+def test_million_atoms_all_forms_sampled(cuda_lib, million, half):
+    """The benchmark's workload and launch configurations (the FP64 default
+    and the schedules the benchmark times for each form), on sampled atoms
+    against the oracle's per-atom sums."""
+    lj = cuda_lib
+    s, idx, want = million
+    q = to_dev(s.q)
+    pl = lj.lj_build_pairlist(q, s.box, s.rs, half)
+    scale = np.max(np.abs(want))
+    for prec, tpis, tol in ((0, (0, 2056, 2052, 1032), FP64_TOL), (1, (4, 8, 16), MIXED_TOL),
+                            (2, (132, 136, 144), FP64_TOL)):
+        for tpi in tpis:
+            p = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
+            lj.lj_force(q, p, pl, 0.01, s.rc, s.box, precision=prec, tpi=tpi)
+            torch.cuda.synchronize()
+            got = p[torch.from_numpy(idx).cuda(), :3].cpu().numpy()
+            assert np.max(np.abs(got - want)) <= tol * scale, (prec, tpi)
 
 
 @pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL), (2, FP64_TOL)])
