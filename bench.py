@@ -1,33 +1,41 @@
 #!/usr/bin/env python3
-"""LJ pair interactions/s on one GB300: FP64, mixed precision and double-float.
+"""LJ pair interactions/s on one GB300: FP64 vs mixed precision at stated error.
 
-Workload: the paper's benchmark (section "Benchmark Conditions"): an FCC
-crystal of N = 119,164 = 4*31^3 atoms at density 1.0, cutoff 3.0 sigma,
-search length 3.3 sigma (bookkeeping margin 0.3), jitter 0.05 sigma,
-particle order randomly permuted, half list (i < j), dt = 0.01.
+Headline workload (the precision configuration of this benchmark, the largest
+single system): an FCC crystal of N = 1,048,576 = 4*64^3 atoms at density
+1.0, cutoff 3.0 sigma, search length 3.3 sigma (bookkeeping margin 0.3),
+jitter 0.05 sigma, particle order randomly permuted, half list (i < j),
+dt = 0.01.  The FP64 kernel gives the headline value; the mixed and
+double-float forms are timed beside it and every form's force error is
+stated against the FP64 oracle.
 
-One step = one pass of the hot path: build the sorted CSR Verlet list on
-the GPU (cell binning, count, scan, fill) and then run the force 100 times
-on it, the paper's protocol ("the time to calculate the force 100 times").
-A pair interaction is one unique list entry processed in one force call,
-so each step credits 100 * nnz(half list).
+One step = one pass of the hot path, the paper's protocol (section
+"Benchmark Conditions": the force computed 100 times): build the sorted CSR
+Verlet list on the GPU (cell binning, scan, walk, row sort), then run the
+force 100 times on it.  A pair interaction is one unique half-list entry
+processed in one force call, so each step credits 100 * nnz(half list).
 
-Timing: inputs resident in HBM; L2 flushed (256 MiB write) before every
-step, outside the timed events; each step timed with CUDA events on the
-launching stream (three events a step: start, list built, end; the force
-call's duration is the span after the list over the 100 calls); W warm-up
-steps; the max over ranks of the summed step times.  `e2e` repeats the step with the positions and momenta copied from
-pinned host memory and the momenta copied back inside the timed region.
+Timing: inputs resident in HBM and larger than L2 (the list alone is
+~300 MB); L2 also flushed (256 MiB write) before every step, outside the
+timed events; each step timed with CUDA events on the launching stream; W
+warm-up steps; the max over ranks of the summed step times.  `e2e` repeats
+the step with positions and momenta copied from pinned host memory and the
+momenta copied back inside the timed region.
 
-`--impl reference` times the CPU oracle (the plain double-precision C
-implementation the tests compare against) on the same workload: each step
-is one oracle cell-list build plus 10 oracle force calls, single thread.
+The other configurations (the paper-size system in both orderings with
+half and full lists, the 4,000-atom system, 512 uneven systems in one
+persistent launch, the 64-replica adjoint) are reported in
+`other_configs`, each with its error against the oracle.  The CPU oracle,
+the plain double-precision C implementation the tests check against, is
+timed on the host's cores as `cpu_baseline` (one core, the paper's setting,
+and all cores).  `--impl reference` times the oracle alone on a bounded
+sample of the headline workload (the comparison arm).
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -44,29 +52,36 @@ import numpy as np  # noqa: E402
 METRIC = "LJ pair interactions/s on 1 GB300, FP64 vs mixed at stated error; % HBM roofline"
 UNIT = "pair interactions/s"
 FORCE_CALLS = 100
-DT, RC, MARGIN = 0.01, 3.0, 0.3
-CPU_FORCE_CALLS = 10
+DT, RC, MARGIN, RHO, JITTER = 0.01, 3.0, 0.3, 1.0, 0.05
+HEADLINE_K = 64          # 64^3 FCC cells: N = 1,048,576
+PAPER_K = 31             # 31^3 FCC cells: N = 119,164 (the paper's benchmark size)
 L2_FLUSH_BYTES = 256 << 20
-# FP64 peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM
-# (4 flop) x 2070 MHz (the nominal 1.25 TFLOP/s FP64 of GB300).
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per launch of the FP64 force kernel, by
-# schedule, from one ncu capture of the kernel as it stands on this workload
-# (profiles/force_fp64_images_tpi8_half_N119164.md); a schedule without an
-# entry reports null.
-# DRAM bytes (read + write) of one launch of the FP64 force kernel per
-# schedule, from ncu (cold cache), with the profile that records them.
-# L2 read and reduction sectors per launch of the FP64 force kernel from the
-# same ncu capture (the gathered-bytes view), per schedule.
-LTS_SECTORS_PER_LAUNCH = {
-    2056: (11254023, 24806804, "profiles/force_fp64_fixed_tpi8_half_N119164.md"),
+# The FP64 and FP32 ceilings derived from unit counts and the 2070 MHz clock
+# (152 SMs x 2 FP64 FMA/clk, x 128 FP32 FMA/clk); the bench reports the
+# measured ones (lj_measure_peak) and keeps these beside them.
+FP64_PEAK_DERIVED = 152 * 4 * 2.07e9 / 1e12
+FP32_PEAK_DERIVED = 152 * 256 * 2.07e9 / 1e12
+# CPU samples of the headline workload (bounded so the default run stays in
+# minutes): one core walks the middle block of rows of the half list; each
+# of the P all-core workers a block of rows of the full list.
+CPU_ROWS_ONE_CORE = 16384
+CPU_ROWS_PER_WORKER = 1024
+ORACLE_SAMPLE_ATOMS = 512
+# ncu counters per launch of the dominant kernel (the FP64 force kernel),
+# keyed by (schedule, list, atoms): DRAM bytes read + written, L2 read and
+# reduction sectors, and the summary that records them.  A schedule or
+# workload without an entry reports no traffic figure ("not profiled").
+PROFILED = {
+    (2056, "half", 119164): {"dram_bytes": 41910784.0 + 5632.0, "lts_read_sectors": 11254023,
+                             "lts_red_sectors": 24806804,
+                             "source": "profiles/force_fp64_fixed_tpi8_half_N119164.md"},
+    (2056, "half", 1048576): {"dram_bytes": 388423680.0 + 46345728.0,
+                              "lts_read_sectors": 100962352, "lts_red_sectors": 218370139,
+                              "source": "profiles/force_fp64_fixed_tpi8_half_N1048576.md"},
 }
-TRAFFIC_PER_LAUNCH = {
-    1032: (41903872.0 + 1280.0, "profiles/force_fp64_images_tpi8_half_N119164.md"),
-    2056: (41910784.0 + 5632.0, "profiles/force_fp64_fixed_tpi8_half_N119164.md"),
-    4104: (41915904.0, "profiles/force_fp64_compact_tpi8_half_N119164.md"),
-}
+ERROR_DEFINITION = ("max_err_rel = max |dp_gpu - dp_oracle| / max |dp_oracle|; rms_err_rel = "
+                    "RMS(dp_gpu - dp_oracle) / RMS(dp_oracle), over the x, y, z components of "
+                    "the atoms compared (dp = the momentum change of one call from p = 0)")
 
 
 def parse():
@@ -76,31 +91,232 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--order", choices=["random", "cell"], default="random")
-    ap.add_argument("--no-variants", action="store_true", help="skip the per-variant table")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline legs")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the other workloads (1M atoms, 512-system batch, 64-replica adjoint)")
-    ap.add_argument("--profile", choices=["fp64", "fp64-full", "mixed", "mixed-full", "dfloat",
-                                          "dfloat-full", "list", "vjp", "vjp-dfloat", "batched",
-                                          "batched-mixed", "batched-dfloat"],
-                    help="no timing: build the list and run a few calls of one kernel (for ncu)")
+                    help="skip the other configurations (paper size, 4,000 atoms, batch, adjoint, MD)")
+    ap.add_argument("--cpu-workers", type=int, default=0,
+                    help="processes for the oracle (0 = every core this process may use)")
     ap.add_argument("--schedule", type=int, default=0,
                     help="FP64 schedule for the timed steps (0 = the library's autotuner picks)")
     ap.add_argument("--peaks", action="store_true",
                     help="only measure the FP64 / FP32 / packed-FP32 / L2-read ceilings and print them")
-    ap.add_argument("--profile-atoms", choices=["paper", "million"], default="paper")
+    ap.add_argument("--profile", choices=["fp64", "fp64-full", "mixed", "mixed-full", "dfloat",
+                                          "dfloat-full", "list", "vjp", "vjp-dfloat", "batched",
+                                          "batched-mixed", "batched-dfloat"],
+                    help="no timing: build the list and run a few calls of one kernel (for ncu)")
+    ap.add_argument("--profile-atoms", choices=["paper", "million"], default="million")
     ap.add_argument("--profile-tpi", type=int, default=0, help="schedule for --profile (0 = auto)")
     return ap.parse_args()
 
 
-def measured_peaks():
+def cpu_count() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def measured_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json, STREAM-style copy)"
     except Exception:
         return 6800.0, "fallback (profiling recipe)"
 
+
+# ---------------------------------------------------------------------------
+# Workloads (regenerated from their seeds in every process that needs them)
+# ---------------------------------------------------------------------------
+
+_SYSTEMS: dict = {}
+
+
+def system_from_spec(spec):
+    """("fcc", k, rho, jitter, seed, order) | ("batch", nsys, seed, index) |
+    ("replica", replicas, k, seed, index) -> LJSystem (cached per process)."""
+    if spec in _SYSTEMS:
+        return _SYSTEMS[spec]
+    from paper_1806_05713_gb300 import inputs
+    kind = spec[0]
+    if kind == "fcc":
+        _, k, rho, jit, seed, order = spec
+        s = inputs.fcc_system(k, rho, jit, seed=seed, order=order, rc=RC, margin=MARGIN)
+    elif kind == "batch":
+        _, nsys, seed, idx = spec
+        key = ("batch-all", nsys, seed)
+        if key not in _SYSTEMS:
+            _SYSTEMS[key] = inputs.batched_systems(nsys=nsys, seed=seed)
+        s = _SYSTEMS[key][idx]
+    elif kind == "replica":
+        _, reps, k, seed, idx = spec
+        key = ("replica-all", reps, k, seed)
+        if key not in _SYSTEMS:
+            _SYSTEMS[key] = inputs.workload_replicas(reps, k, seed=seed)
+        s = _SYSTEMS[key][idx]
+    else:
+        raise ValueError(spec)
+    _SYSTEMS[spec] = s
+    return s
+
+
+def headline_spec(seed: int, order: str):
+    return ("fcc", HEADLINE_K, RHO, JITTER, seed, order)
+
+
+def headline_config(n_atoms: int, order: str) -> dict:
+    """The workload as both arms state it (same dict in both lines)."""
+    return {"workload": f"fcc-64^3 N={n_atoms} rho=1.0 rc=3.0 rs=3.3 jitter=0.05 {order}-order "
+                        f"half-list dt=0.01",
+            "n_atoms": n_atoms, "list": "half (i < j), CSR int32, rows sorted",
+            "force_calls_per_step": FORCE_CALLS, "list_builds_per_step": 1,
+            "l2": "inputs larger than the 129 MB L2 (list ~300 MB, q and p 33.5 MB each)"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: tasks for a process pool, and a team of timing processes
+# ---------------------------------------------------------------------------
+
+def _oracle_task(task):
+    """One oracle computation in a pool worker (spawned; loads no GPU code)."""
+    import oracle
+    kind = task[0]
+    if kind == "atoms":       # per-atom momentum change from the definition
+        _, spec, idx = task
+        s = system_from_spec(spec)
+        return oracle.force_atoms(s.q, idx, DT, s.rc, s.box)
+    if kind == "force":       # whole-system momentum change over the oracle's own list
+        _, spec = task
+        s = system_from_spec(spec)
+        rp, col = oracle.pairlist(s.q, s.box, s.rs, True)
+        return oracle.force(s.q, np.zeros((s.n, 3)), rp, col, True, DT, s.rc, s.box)
+    if kind == "grad":        # one replica's share of the force-matching gradient
+        _, spec, eps, sig, inv_count = task
+        s = system_from_spec(spec)
+        rp, col = oracle.pairlist(s.q, s.box, s.rs, False)
+        Ft = oracle.forces(s.q, rp, col, False, s.rc, s.box, 1.0, 1.0)
+        F = oracle.forces(s.q, rp, col, False, s.rc, s.box, eps, sig)
+        R = 2.0 * (F - Ft) * inv_count
+        gq, ge, gs = oracle.force_vjp(s.q, R, rp, col, False, s.rc, s.box, eps, sig)
+        return gq, ge, gs, float(np.sum((F - Ft) ** 2) * inv_count)
+    raise ValueError(kind)
+
+
+class OraclePool:
+    """A spawned process pool for the oracle (spawn: safe next to a CUDA
+    context, and the workers import no GPU code)."""
+
+    def __init__(self, workers: int):
+        import oracle
+        oracle.build()                      # compile once, before the workers load it
+        self.workers = workers
+        self.pool = mp.get_context("spawn").Pool(workers)
+
+    def submit(self, tasks):
+        return self.pool.map_async(_oracle_task, tasks, chunksize=1)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _team_worker(w, nworkers, spec, cmd_q, res_q, barrier):
+    import oracle
+    s = system_from_spec(spec)
+    oracle.force_rows(s.q, np.zeros((s.n, 3)), np.zeros(1, dtype=np.int32), np.zeros(0, np.int32),
+                      False, DT, s.rc, s.box, 0, 0)           # load the library before timing
+    while True:
+        msg = cmd_q.get()
+        if msg[0] == "stop":
+            return
+        _, i0, i1, half, calls = msg
+        a = i0 + (i1 - i0) * w // nworkers
+        b = i0 + (i1 - i0) * (w + 1) // nworkers
+        p = np.zeros((s.n, 3))
+        barrier.wait()
+        t0 = time.monotonic()
+        rp, col = oracle.pairlist_rows(s.q, s.box, s.rs, half, a, b)
+        for _ in range(calls):
+            oracle.force_rows(s.q, p, rp, col, half, DT, s.rc, s.box, a, b, inplace=True)
+        t1 = time.monotonic()
+        res_q.put((w, t0, t1, int(col.size)))
+
+
+class CpuTeam:
+    """P spawned processes that each time the oracle on their block of rows,
+    released together by a barrier: the all-cores leg of the CPU baseline.
+    Each worker builds its rows of the list and runs the force calls over
+    them (full list: a row updates only its own atom, so the workers share
+    nothing and need no reduction)."""
+
+    def __init__(self, workers: int, spec):
+        ctx = mp.get_context("spawn")
+        import oracle
+        oracle.build()
+        self.workers = workers
+        self.cmd = [ctx.Queue() for _ in range(workers)]
+        self.res = ctx.Queue()
+        self.barrier = ctx.Barrier(workers + 1)
+        self.procs = [ctx.Process(target=_team_worker,
+                                  args=(w, workers, spec, self.cmd[w], self.res, self.barrier),
+                                  daemon=True) for w in range(workers)]
+        for p in self.procs:
+            p.start()
+
+    def step(self, i0: int, i1: int, half: bool, calls: int):
+        """One timed step; returns (wall seconds, list entries walked)."""
+        for q in self.cmd:
+            q.put(("step", i0, i1, half, calls))
+        self.barrier.wait(timeout=900)
+        t0 = time.monotonic()
+        res = [self.res.get(timeout=900) for _ in range(self.workers)]
+        return max(r[2] for r in res) - t0, sum(r[3] for r in res)
+
+    def close(self):
+        for q in self.cmd:
+            q.put(("stop",))
+        for p in self.procs:
+            p.join(timeout=60)
+
+
+def cpu_one_core_leg(s, calls: int = FORCE_CALLS):
+    """One step of the paper's setting on one core: the oracle builds the
+    middle CPU_ROWS_ONE_CORE rows of the half list and runs `calls` force
+    calls over them.  Returns (pairs/s, seconds, entries, description)."""
+    import oracle
+    oracle.build()
+    i0 = s.n // 2 - CPU_ROWS_ONE_CORE // 2
+    i1 = i0 + CPU_ROWS_ONE_CORE
+    p = np.zeros((s.n, 3))
+    t0 = time.monotonic()
+    rp, col = oracle.pairlist_rows(s.q, s.box, s.rs, True, i0, i1)
+    for _ in range(calls):
+        oracle.force_rows(s.q, p, rp, col, True, DT, s.rc, s.box, i0, i1, inplace=True)
+    t = time.monotonic() - t0
+    desc = (f"1 core: oracle list rows {i0}..{i1 - 1} of the half list ({col.size} entries) "
+            f"built, then {calls} oracle force calls over them ({t:.1f} s)")
+    return calls * col.size / t, t, int(col.size), desc
+
+
+def cpu_all_cores_leg(team: CpuTeam, n: int, calls: int = FORCE_CALLS):
+    """One step on every core: P workers, each the oracle over its own block
+    of CPU_ROWS_PER_WORKER rows of the full list (list rows built, then
+    `calls` force calls).  A full-list entry is half a pair interaction, as
+    for the GPU's full-list kernels.  Returns (pairs/s, seconds, entries,
+    description)."""
+    rows = CPU_ROWS_PER_WORKER * team.workers
+    i0 = n // 2 - rows // 2
+    t, entries = team.step(i0, i0 + rows, False, calls)
+    desc = (f"{team.workers} processes (one per core): oracle list rows {i0}..{i0 + rows - 1} of "
+            f"the full list ({entries} entries = {entries // 2} pair interactions) built, then "
+            f"{calls} oracle force calls, each process over its {CPU_ROWS_PER_WORKER} rows "
+            f"({t:.2f} s wall)")
+    return calls * (entries / 2.0) / t, t, entries, desc
+
+
+# ---------------------------------------------------------------------------
+# Device-side helpers
+# ---------------------------------------------------------------------------
 
 def measure_ceilings(lj, dev, target_ms: float = 40.0, reps: int = 3):
     """The roofline denominators of the force kernels, measured on this GPU
@@ -130,21 +346,131 @@ def measure_ceilings(lj, dev, target_ms: float = 40.0, reps: int = 3):
     return out
 
 
-def run_peaks(args):
+def time_calls(fn, stream, flush, calls=20, warm=3):
+    """Median device time (ms) of fn over `calls` launches, L2 flushed before
+    each, CUDA events on the launching stream."""
     import torch
-    from paper_1806_05713_gb300 import build as lib_build
-    from paper_1806_05713_gb300 import lj
-    lib_build.build()
-    dev = torch.device("cuda", 0)
-    lj.load()
-    with ClockSampler(0) as clk:
-        res = measure_ceilings(lj, dev)
-    res["clocks"] = clk.summary()
-    res["sm_count"] = torch.cuda.get_device_properties(dev).multi_processor_count
-    res["derived_fp64_tflops"] = FP64_PEAK_TFLOPS
-    res["derived_fp32_tflops"] = FP32_PEAK_TFLOPS
-    print(json.dumps(res))
+    for _ in range(warm):
+        fn()
+    ms = []
+    for _ in range(calls):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
 
+
+def count_in_cutoff(q, pl, box, rc, chunk: int = 1 << 24):
+    """List entries with r < r_c (for the flop count), by the definition:
+    d = q_j - q_i, per axis the branchy minimum image (d > L/2: d - L;
+    d < -L/2: d + L), r^2 = (dx*dx + dy*dy) + dz*dz in separately rounded
+    double operations; torch elementwise ops at set-up time, not timed."""
+    import torch
+    rp = pl.row_ptr.long()
+    rows = torch.repeat_interleave(torch.arange(pl.n, device=q.device), rp[1:] - rp[:-1])
+    col = pl.col_view.long()
+    rc2 = float(rc) * float(rc)
+    total = 0
+    for k0 in range(0, col.numel(), chunk):
+        i, j = rows[k0:k0 + chunk], col[k0:k0 + chunk]
+        sq = []
+        for a in range(3):
+            L = float(box[a])
+            d = q[j, a] - q[i, a]
+            d = torch.where(d > 0.5 * L, d - L, torch.where(d < -0.5 * L, d + L, d))
+            sq.append(d * d)
+        r2 = (sq[0] + sq[1]) + sq[2]
+        total += int((r2 < rc2).sum().item())
+    return total
+
+
+def err_stats(got: np.ndarray, want: np.ndarray) -> dict:
+    d = got - want
+    return {"max_err_rel_vs_oracle": float(np.max(np.abs(d)) / np.max(np.abs(want))),
+            "rms_err_rel_vs_oracle": float(np.sqrt(np.mean(d ** 2)) / np.sqrt(np.mean(want ** 2)))}
+
+
+def schedule_name(tpi: int) -> str:
+    t = tpi & 63
+    name = f"{max(t, 1)} lanes/row"
+    if tpi & 128:
+        name += ", 2 entries/lane (software-pipelined)"
+    if tpi & 512:
+        name += ", rows by length"
+    if tpi & 1024:
+        name += ", image-selected displacement"
+    if tpi & 2048:
+        name += ", exact fixed-point displacement"
+    return name
+
+
+FORMS = (("fp64", 0), ("mixed", 1), ("dfloat", 2))
+FORM_CANDIDATES = {1: (4, 8, 16), 2: (132, 136, 144)}
+
+
+def best_form_call(lj, q, pl, box, rc, prec, tpis, stream, flush, dev, calls=10):
+    """Fastest schedule of one form on one list: (ms, tpi, dp of one call
+    from zero on the GPU)."""
+    import torch
+    best = None
+    for t in tpis:
+        pp = torch.zeros((pl.n, 4), dtype=torch.float64, device=dev)
+        fn = lj.lj_force_prepared(q, pp, pl, DT, rc, box, precision=prec, tpi=t)
+        ms = time_calls(fn, stream, flush, calls, 2)
+        if best is None or ms < best[0]:
+            best = (ms, t, fn, pp)
+    ms, t, fn, pp = best
+    pp.zero_()
+    fn()
+    torch.cuda.synchronize()
+    return ms, t, pp
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the oracle alone
+# ---------------------------------------------------------------------------
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    spec = headline_spec(0, args.order)
+    s = system_from_spec(spec)
+    workers = args.cpu_workers or cpu_count()
+    team = CpuTeam(workers, spec)
+    try:
+        for _ in range(max(0, args.warmup)):
+            cpu_all_cores_leg(team, s.n)
+        times, pairs, desc = [], [], ""
+        for _ in range(args.steps):
+            r, t, _, desc = cpu_all_cores_leg(team, s.n)
+            times.append(t)
+            pairs.append(r * t)
+    finally:
+        team.close()
+    one_rate, _, _, one_desc = cpu_one_core_leg(s)
+    value = sum(pairs) / sum(times)
+    sample = ("each step: " + desc + "; the same FP64 oracle the tests compare against, "
+              "unchanged, in spawned processes")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "ms_per_step_median": 1e3 * statistics.median(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": headline_config(s.n, args.order),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                         "sample": sample,
+                         "single_core": {"value": one_rate, "cores": 1, "sample": one_desc}},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+# Clocks and ranks
+# ---------------------------------------------------------------------------
 
 class ClockSampler:
     """nvidia-smi clock / throttle samples every 200 ms while running."""
@@ -228,73 +554,24 @@ def whole_job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
     return units_per_rank * world / (max_ms / 1e3)
 
 
-def workload(rank: int, order: str):
-    from paper_1806_05713_gb300 import inputs
-    return inputs.fcc_system(31, 1.0, 0.05, seed=rank, order=order, rc=RC, margin=MARGIN)
-
-
-def workload_name(order: str) -> str:
-    return f"fcc-31^3 N=119164 rho=1.0 rc=3.0 rs=3.3 jitter=0.05 {order}-order half-list dt=0.01"
-
-
 # ---------------------------------------------------------------------------
-# CPU oracle (baseline leg and --impl reference)
+# Profiling and peak modes
 # ---------------------------------------------------------------------------
 
-def oracle_sample(s, calls: int):
-    import oracle
-    oracle.build()
-    t0 = time.perf_counter()
-    rp, col = oracle.pairlist(s.q, s.box, s.rs, True, "cells")
-    p = np.zeros((s.n, 3))
-    for _ in range(calls):
-        p = oracle.force(s.q, p, rp, col, True, DT, s.rc, s.box)
-    dt = time.perf_counter() - t0
-    return dt, int(col.size)
-
-
-def run_reference(args, world, rank):
-    if rank != 0:
-        return
-    s = workload(0, args.order)
-    for _ in range(max(0, args.warmup)):
-        oracle_sample(s, 1)
-    times, nnz = [], 0
-    for _ in range(args.steps):
-        t, nnz = oracle_sample(s, CPU_FORCE_CALLS)
-        times.append(t)
-    total = sum(times)
-    value = args.steps * CPU_FORCE_CALLS * nnz / total
-    sample = (f"each step: 1 oracle cell-list build + {CPU_FORCE_CALLS} oracle force calls on "
-              f"N={s.n} ({nnz} half-list entries), single thread")
-    print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": workload_name(args.order), "n_atoms": s.n, "pairs_per_call": nnz,
-                   "force_calls_per_step": CPU_FORCE_CALLS, "list_builds_per_step": 1,
-                   "parallelism": "one CPU thread"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }))
-
-
-# ---------------------------------------------------------------------------
-# GPU arm
-# ---------------------------------------------------------------------------
-
-def count_in_cutoff(q, pl, box, rc):
-    """Entries with r < r_c (for the flop count), with torch on the GPU at
-    set-up time; not part of the timed path."""
+def run_peaks(args):
     import torch
-    rp = pl.row_ptr.long()
-    rows = torch.repeat_interleave(torch.arange(pl.n, device=q.device), rp[1:] - rp[:-1])
-    col = pl.col_view.long()
-    d = q[col, :3] - q[rows, :3]
-    L = torch.tensor(box, device=q.device, dtype=torch.float64)
-    d = d - L * torch.round(d / L)
-    return int(((d * d).sum(1) < rc * rc).sum().item())
+    from paper_1806_05713_gb300 import build as lib_build
+    from paper_1806_05713_gb300 import lj
+    lib_build.build()
+    dev = torch.device("cuda", 0)
+    lj.load()
+    with ClockSampler(0) as clk:
+        res = measure_ceilings(lj, dev)
+    res["clocks"] = clk.summary()
+    res["sm_count"] = torch.cuda.get_device_properties(dev).multi_processor_count
+    res["derived_fp64_tflops"] = FP64_PEAK_DERIVED
+    res["derived_fp32_tflops"] = FP32_PEAK_DERIVED
+    print(json.dumps(res))
 
 
 def run_profile(args):
@@ -304,8 +581,8 @@ def run_profile(args):
     from paper_1806_05713_gb300 import build as lib_build
     from paper_1806_05713_gb300 import inputs, lj
     lib_build.build()
-    k = 31 if args.profile_atoms == "paper" else 64
-    s = inputs.fcc_system(k, 1.0, 0.05, seed=0, order=args.order, rc=RC, margin=MARGIN)
+    k = PAPER_K if args.profile_atoms == "paper" else HEADLINE_K
+    s = inputs.fcc_system(k, RHO, JITTER, seed=0, order=args.order, rc=RC, margin=MARGIN)
     box = [float(x) for x in s.box]
     q = torch.from_numpy(s.q).cuda()
     p = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
@@ -336,13 +613,20 @@ def run_profile(args):
     else:
         prec = (lj.LJ_MIXED if args.profile.startswith("mixed") else
                 lj.LJ_DFLOAT if args.profile.startswith("dfloat") else lj.LJ_FP64)
-        tpi = args.profile_tpi
-        fn = lj.lj_force_prepared(q, p, pl, DT, s.rc, box, precision=prec, tpi=tpi)
+        fn = lj.lj_force_prepared(q, p, pl, DT, s.rc, box, precision=prec, tpi=args.profile_tpi)
         for _ in range(5):
             fn()
     torch.cuda.synchronize()
     print(json.dumps({"profile": args.profile, "n": s.n, "nnz": pl.nnz,
                       "launches": int(lj.load().lj_kernel_launch_count())}))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+BATCH_SAMPLE = tuple(range(0, 512, 32))   # 16 of the 512 systems checked against the oracle
+ADJ_REPLICAS, ADJ_K, ADJ_EPS, ADJ_SIGMA = 64, 16, 1.1, 0.97
 
 
 def main():
@@ -374,7 +658,8 @@ def main():
         dist.barrier()
     lib = lj.load()
 
-    s = workload(rank, args.order)
+    spec = headline_spec(rank, args.order)
+    s = system_from_spec(spec)
     box = [float(x) for x in s.box]
     q = torch.from_numpy(s.q).to(dev)
     p = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
@@ -382,7 +667,6 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     pl = lj.lj_build_pairlist(q, box, s.rs, True)
-    # schedule picked by the library's autotuner on this system and list
     if args.schedule:
         best_tpi, tune_table = args.schedule, {}
     else:
@@ -394,7 +678,7 @@ def main():
     def one_step(list_done):
         lj.lj_build_pairlist(q, box, s.rs, True, reuse=pl)
         list_done.record(stream)
-        for c in range(FORCE_CALLS):
+        for _ in range(FORCE_CALLS):
             force()
 
     def new_events():
@@ -458,179 +742,286 @@ def main():
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel (the FP64 force) -------------------
-    hbm_peak, hbm_src = measured_peaks()
+    workers = args.cpu_workers or cpu_count()
+    pool = OraclePool(workers)
+    sample = np.sort(np.random.default_rng(7).choice(s.n, ORACLE_SAMPLE_ATOMS, replace=False))
+    chunks = np.array_split(sample, workers)
+    jobs = {"headline_atoms": pool.submit([("atoms", spec, c) for c in chunks if c.size])}
+    if not args.no_extra:
+        jobs["paper"] = pool.submit([("force", ("fcc", PAPER_K, RHO, JITTER, 0, o))
+                                     for o in ("random", "cell")])
+        jobs["small"] = pool.submit([("force", ("fcc", 10, RHO, JITTER, 0, "random"))])
+        jobs["batch"] = pool.submit([("force", ("batch", 512, 0, int(k))) for k in BATCH_SAMPLE])
+        inv = 1.0 / (3.0 * ADJ_REPLICAS * 4 * ADJ_K ** 3)
+        jobs["adjoint"] = pool.submit([("grad", ("replica", ADJ_REPLICAS, ADJ_K, 0, r), ADJ_EPS,
+                                        ADJ_SIGMA, inv) for r in range(ADJ_REPLICAS)])
+
+    # ---- ceilings and the roofline of the dominant kernel ------------------
+    ceil = measure_ceilings(lj, dev)
+    hbm_peak, hbm_src = measured_hbm()
     t_force = statistics.mean(force_ms) / 1e3
     flops = 28.0 * n_cut + 8.0 * (nnz - n_cut)     # paper: 27 add/mul + 1 div per pair
     alg_bytes = 4.0 * nnz + 4.0 * (s.n + 1) + 32.0 * s.n + 64.0 * s.n
-    roof = {"bound": "alu", "achieved": flops / t_force / 1e12, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": flops / t_force / 1e12 / FP64_PEAK_TFLOPS,
-            "traffic": TRAFFIC_PER_LAUNCH.get(best_tpi, (None, None))[0],
-            "traffic_source": (TRAFFIC_PER_LAUNCH.get(best_tpi, (None, "not profiled"))[1] +
-                               " (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold cache)"),
+    achieved = flops / t_force / 1e12
+    prof = PROFILED.get((best_tpi, "half", s.n))
+    roof = {"bound": "alu", "achieved": achieved, "peak": ceil["fp64_fma_tflops"],
+            "unit": "TFLOP/s", "frac": achieved / ceil["fp64_fma_tflops"],
+            "traffic": None if prof is None else prof["dram_bytes"],
+            "traffic_note": ("not profiled: no ncu capture of this schedule on this workload"
+                             if prof is None else
+                             prof["source"] + " (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                              "one launch, cold cache)"),
             "kernel": f"FP64 force kernel, {schedule_name(best_tpi)}, half list",
-            "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
-            "flops_per_launch": flops, "launch_ms": t_force * 1e3}
+            "peak_source": ("measured live: lj_measure_peak DFMA probe (of measured; method and "
+                            "clocks in profiles/pipe_peaks_gb300.md)"),
+            "peak_derived": FP64_PEAK_DERIVED,
+            "frac_of_derived": achieved / FP64_PEAK_DERIVED,
+            "flops_per_launch": flops, "launch_ms": t_force * 1e3,
+            "flops_basis": "28 per in-cutoff entry (27 add/mul + 1 div), 8 per margin entry"}
     hbm_view = {"achieved": alg_bytes / t_force / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "frac": alg_bytes / t_force / 1e9 / hbm_peak, "peak_source": hbm_src,
                 "bytes_per_pair": alg_bytes / nnz}
-    # the gathered-bytes view: what the kernel asks of L2 -- per entry its
-    # column index and q_j record, per row its row pointers and q_i, and the
-    # FP64 reductions (p_j per interacting entry, p_i per lane and row)
     gathered_reads = 36.0 * nnz + 40.0 * s.n
     reductions = 3.0 * n_cut + 3.0 * 8 * s.n
-    lts = LTS_SECTORS_PER_LAUNCH.get(best_tpi)
     l2_view = {"gathered_read_bytes": gathered_reads, "reductions": reductions,
                "gathered_read_GBps": gathered_reads / t_force / 1e9,
+               "gathered_read_frac_of_l2_read_peak": gathered_reads / t_force / 1e9 / ceil["l2_read_gbs"],
                "reductions_per_s": reductions / t_force,
-               "lts_read_sectors": None if lts is None else lts[0],
-               "lts_red_sectors": None if lts is None else lts[1],
-               "lts_source": None if lts is None else lts[2]}
+               "lts_read_sectors": None if prof is None else prof["lts_read_sectors"],
+               "lts_red_sectors": None if prof is None else prof["lts_red_sectors"]}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "ms_per_step_median": statistics.median(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.order), "n_atoms": s.n, "pairs_per_call": nnz,
-                   "pairs_in_cutoff": n_cut, "force_calls_per_step": FORCE_CALLS,
-                   "list_builds_per_step": 1, "schedule": schedule_name(best_tpi),
-                   "l2": "flushed before every step (256 MiB write, outside the timed events)",
-                   "parallelism": f"replicas x{world}"},
+        "config": headline_config(s.n, args.order),
+        "l2_flush": "256 MiB write before every step, outside the timed events",
+        "parallelism": f"replicas x{world}",
+        "schedule": schedule_name(best_tpi), "pairs_per_call": nnz, "pairs_in_cutoff": n_cut,
         "list_build_ms": statistics.mean(list_ms),
         "force_ms_per_call": t_force * 1e3,
         "force_only_pairs_per_s": nnz / t_force,
         "roofline": roof, "hbm_roofline": hbm_view, "l2_gather_view": l2_view,
+        "ceilings_measured": ceil,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 32 * s.n,
                 "d2h_bytes_per_step": 32 * s.n},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
+        "error_definition": ERROR_DEFINITION,
+        "autotune_ms": {schedule_name(k): v for k, v in tune_table.items()},
     }
 
-    out["autotune_ms"] = {schedule_name(k): v for k, v in tune_table.items()}
-    out["forms"] = forms(lj, q, pl, box, s, best_tpi, flops, dev, stream, flush)
-    if not args.no_variants:
-        out["variants"] = variants(lj, s, q, pl, box, dev, stream, flush)
+    # ---- the three forms on the headline workload, errors vs the oracle ----
+    want_atoms = np.concatenate(jobs["headline_atoms"].get(timeout=1800))
+    out["forms"] = headline_forms(lj, q, pl, box, s, best_tpi, flops, dev, stream, flush, sample,
+                                  want_atoms, ceil)
+    del p, force
     if not args.no_extra:
-        del p, q, pl, force
-        torch.cuda.empty_cache()
-        out["other_configs"] = {
-            "million_fp64_vs_mixed": extra_million(lj, dev, stream, flush),
-            "batched_512_systems": extra_batched(lj, dev, stream, flush),
-            "adjoint_64_replicas": extra_adjoint(lj, dev, stream, flush),
-            "md_velocity_verlet": extra_md(lj, dev, stream),
-        }
+        oc = {}
+        oc["paper_119164"] = extra_paper(lj, dev, stream, flush, jobs["paper"].get(timeout=1800))
+        oc["small_4000"] = extra_small(lj, dev, stream, flush, jobs["small"].get(timeout=1800)[0])
+        oc["batched_512_systems"] = extra_batched(lj, dev, stream, flush,
+                                                  jobs["batch"].get(timeout=1800))
+        oc["adjoint_64_replicas"] = extra_adjoint(lj, dev, stream, flush,
+                                                  jobs["adjoint"].get(timeout=3600))
+        oc["md_velocity_verlet"] = extra_md(lj, dev, stream)
+        out["other_configs"] = oc
+    pool.close()
+
     if world == 1 and not args.no_cpu:
-        t, m = oracle_sample(s, CPU_FORCE_CALLS)
+        one_rate, _, _, one_desc = cpu_one_core_leg(s)
+        team = CpuTeam(workers, spec)
+        try:
+            cpu_all_cores_leg(team, s.n)               # warm-up step
+            all_rate, _, _, all_desc = cpu_all_cores_leg(team, s.n)
+        finally:
+            team.close()
         out["cpu_baseline"] = {
-            "value": CPU_FORCE_CALLS * m / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 oracle cell-list build + {CPU_FORCE_CALLS} oracle force calls on the "
-                      f"same N={s.n} system, single thread ({t:.1f} s)"}
+            "value": all_rate, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": all_desc + "; a bounded sample of the headline workload",
+            "single_core": {"value": one_rate, "unit": UNIT, "cores": 1, "sample": one_desc}}
     print(json.dumps(out))
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
 
 
-def schedule_name(tpi: int) -> str:
-    t = tpi & 63
-    name = f"{max(t, 1)} lanes/row"
-    if tpi & 256:
-        name = f"lane-queue, {name}"
-    if tpi & 64:
-        name = f"group-refill, {name}"
-    if tpi & 128:
-        name += ", 2 entries/lane (software-pipelined)"
-    if tpi & 512:
-        name += ", rows by length"
-    if tpi & 1024:
-        name += ", image-selected displacement"
-    if tpi & 2048:
-        name += ", exact fixed-point displacement"
-    if tpi & 4096:
-        name += ", exact fixed-point displacement, margin entries compacted away"
-    return name
-
-
-def extra_million(lj, dev, stream, flush):
-    """N = 1,048,576 (64^3 FCC): FP64 vs mixed, per call (L2 flushed), the
-    mixed error against the FP64 result."""
+def headline_forms(lj, q, pl, box, s, best_tpi, flops, dev, stream, flush, sample, want, ceil):
+    """FP64, mixed and double-float on the headline workload: time per call
+    (L2 flushed), pair interactions/s, and each form's error against the
+    oracle on the sampled atoms (the oracle's per-atom sums over all atoms);
+    then each form on the list layout chosen by measurement (half list with
+    p_j atomics or full list without), its pairs still counted as unique
+    half-list entries."""
     import torch
-    from paper_1806_05713_gb300 import inputs
-    s = inputs.workload_million()
-    box = [float(x) for x in s.box]
-    q = torch.from_numpy(s.q).to(dev)
-    t_list = time_calls(lambda: lj.lj_build_pairlist(q, box, s.rs, True), stream, flush, 3, 1)
-    pl = lj.lj_build_pairlist(q, box, s.rs, True)
-    res = {"n_atoms": s.n, "pairs_per_call": pl.nnz, "list_build_ms": t_list}
-    best, _, _ = lj.lj_autotune_force(q, pl, DT, s.rc, box, reps=3)
-    out = {}
-    for name, prec, tpis in (("fp64", lj.LJ_FP64, (best,)), ("mixed", lj.LJ_MIXED, (4, 8, 16)),
-                             ("dfloat", lj.LJ_DFLOAT, (136, 132))):
-        for t in tpis:
-            pp = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
-            fn = lj.lj_force_prepared(q, pp, pl, DT, s.rc, box, precision=prec, tpi=t)
-            ms = time_calls(fn, stream, flush, 10, 2)
-            pp.zero_()
-            fn()
-            out[(name, t)] = (ms, pp[:, :3].clone())
-    ms64, ref = out[("fp64", best)]
-    res["fp64"] = {"schedule": schedule_name(best), "ms": ms64, "pairs_per_s": pl.nnz / (ms64 / 1e3)}
-    mk = min((k for k in out if k[0] == "mixed"), key=lambda k: out[k][0])
-    msm, pm = out[mk]
-    err = pm - ref
-    res["mixed"] = {"schedule": schedule_name(mk[1]), "ms": msm, "pairs_per_s": pl.nnz / (msm / 1e3),
-                    "max_err_rel_vs_fp64": float(err.abs().max() / ref.abs().max()),
-                    "rms_err_rel_vs_fp64": float(err.pow(2).mean().sqrt() / ref.pow(2).mean().sqrt())}
-    res["speedup_mixed_vs_fp64"] = ms64 / msm
-    dk = min((k for k in out if k[0] == "dfloat"), key=lambda k: out[k][0])
-    msd, pd = out[dk]
-    err = pd - ref
-    res["dfloat"] = {"schedule": schedule_name(dk[1]), "ms": msd, "pairs_per_s": pl.nnz / (msd / 1e3),
-                     "max_err_rel_vs_fp64": float(err.abs().max() / ref.abs().max()),
-                     "rms_err_rel_vs_fp64": float(err.pow(2).mean().sqrt() / ref.pow(2).mean().sqrt())}
-    res["speedup_dfloat_vs_fp64"] = ms64 / msd
+    idx = torch.from_numpy(sample).to(dev)
+    res, fp64_ms = {}, None
+    for name, prec in FORMS:
+        tpis = (best_tpi,) if prec == 0 else FORM_CANDIDATES[prec]
+        ms, t, pp = best_form_call(lj, q, pl, box, s.rc, prec, tpis, stream, flush, dev)
+        got = pp[idx, :3].cpu().numpy()
+        r = {"schedule": schedule_name(t), "list": "half", "ms_per_call": ms,
+             "pairs_per_s": pl.nnz / (ms / 1e3),
+             "fp64_equivalent_tflops": flops / (ms / 1e3) / 1e12,
+             "oracle_atoms": int(sample.size), **err_stats(got, want)}
+        if prec == 0:
+            fp64_ms = ms
+        else:
+            r["speedup_vs_fp64"] = fp64_ms / ms
+        res[name] = r
+        del pp
+    for name, prec in FORMS:
+        plb, t, _, _ = lj.lj_autotune_layout(q, box, s.rs, DT, s.rc, precision=prec, reps=3)
+        ms, t, pp = best_form_call(lj, q, plb, box, s.rc, prec, (t,), stream, flush, dev)
+        got = pp[idx, :3].cpu().numpy()
+        res[name]["best_layout"] = {"list": "half" if plb.half else "full",
+                                    "schedule": schedule_name(t), "ms_per_call": ms,
+                                    "pairs_per_s": pl.nnz / (ms / 1e3), **err_stats(got, want)}
+        del plb, pp
+    res["note"] = ("fp64: IEEE double; mixed: FP32 pair arithmetic, FP64/compensated sums; "
+                   "dfloat: double-float pair arithmetic on the FP32 pipe, exact fixed-point "
+                   "displacement; all add into FP64 momenta.  Errors against the oracle on "
+                   f"{sample.size} sampled atoms (seeded choice); ceilings: FP32 FMA "
+                   f"{ceil['fp32_fma_tflops']:.1f} TFLOP/s, packed {ceil['fp32x2_fma_tflops']:.1f}, "
+                   f"L2 read {ceil['l2_read_gbs']:.0f} GB/s (measured)")
     return res
 
 
-def extra_batched(lj, dev, stream, flush):
-    """512 systems, N log-uniform in 500..32000, rho in 0.8..1.2, rc 2.5 or
-    3.0: one persistent launch replayed from a CUDA graph vs one launch per
-    system, FP64, mixed and double-float; the autotuner picks lanes per row,
-    rows per work item and the list layout (half list with atomics or full
-    list without)."""
+# ---------------------------------------------------------------------------
+# Other configurations
+# ---------------------------------------------------------------------------
+
+def extra_paper(lj, dev, stream, flush, oracle_dp):
+    """N = 119,164 (31^3 FCC, the paper's benchmark size): random and
+    cell-sorted particle order, half and full lists, list-build time, every
+    form's fastest schedule with its error against the oracle (whole
+    system); the FP64 schedules timed one by one; and the paper's layout
+    question (AoS4 / AoS8 / SoA)."""
     import torch
-    from paper_1806_05713_gb300 import inputs
+    res = {"n_atoms": 4 * PAPER_K ** 3, "schedules_fp64_ms": {}}
+    for order, want in zip(("random", "cell"), oracle_dp):
+        s = system_from_spec(("fcc", PAPER_K, RHO, JITTER, 0, order))
+        box = [float(x) for x in s.box]
+        q = torch.from_numpy(s.q).to(dev)
+        for half in (True, False):
+            kind = "half" if half else "full"
+            t_list = time_calls(lambda: lj.lj_build_pairlist(q, box, s.rs, half), stream, flush, 5, 1)
+            pl = lj.lj_build_pairlist(q, box, s.rs, half)
+            m_half = pl.nnz if half else pl.nnz // 2
+            entry = {"list_build_ms": t_list, "pairs_per_call": m_half}
+            for name, prec in FORMS:
+                tpis = (2056, 2052, 2064, 2568, 1032) if prec == 0 else FORM_CANDIDATES[prec]
+                if prec == 0:
+                    for t in tpis:
+                        pp = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
+                        fn = lj.lj_force_prepared(q, pp, pl, DT, s.rc, box, precision=0, tpi=t)
+                        res["schedules_fp64_ms"][f"{order}/{kind}/{schedule_name(t)}"] = \
+                            time_calls(fn, stream, flush, 10, 2)
+                        del pp
+                ms, t, pp = best_form_call(lj, q, pl, box, s.rc, prec, tpis, stream, flush, dev)
+                entry[name] = {"schedule": schedule_name(t), "ms_per_call": ms,
+                               "pairs_per_s": m_half / (ms / 1e3),
+                               **err_stats(pp[:, :3].cpu().numpy(), want)}
+                del pp
+            res[f"{order}/{kind}"] = entry
+            del pl
+    # the paper's layout question on GB300: AoS4 vs AoS8 vs SoA, FP64
+    s = system_from_spec(("fcc", PAPER_K, RHO, JITTER, 0, "random"))
+    box = [float(x) for x in s.box]
+    q = torch.from_numpy(s.q).to(dev)
+    for half in (True, False):
+        kind = "half" if half else "full"
+        pl = lj.lj_build_pairlist(q, box, s.rs, half)
+        m_half = pl.nnz if half else pl.nnz // 2
+        n = s.n
+        rec = torch.zeros((n, 8), dtype=torch.float64, device=dev)
+        rec[:, :3] = q[:, :3]
+        qs = q[:, :3].t().contiguous()
+        ps = torch.zeros_like(qs)
+        p4 = torch.zeros_like(q)
+        for name, fn in (("aos4", lambda: lj.lj_force_strided(q, p4, n, 4, 1, pl, DT, s.rc, box)),
+                         ("aos8", lambda: lj.lj_force_strided(rec, rec, n, 8, 1, pl, DT, s.rc, box,
+                                                              p_offset=4)),
+                         ("soa", lambda: lj.lj_force_strided(qs, ps, n, 1, n, pl, DT, s.rc, box))):
+            ms = time_calls(fn, stream, flush)
+            res[f"layout/fp64/random/{kind}/{name}"] = {"ms": ms, "pairs_per_s": m_half / (ms / 1e3)}
+    return res
+
+
+def extra_small(lj, dev, stream, flush, want):
+    """N = 4,000 (10^3 FCC): the parity configuration -- every form's error
+    against the oracle, and its time per call."""
+    import torch
+    s = system_from_spec(("fcc", 10, RHO, JITTER, 0, "random"))
+    box = [float(x) for x in s.box]
+    q = torch.from_numpy(s.q).to(dev)
+    pl = lj.lj_build_pairlist(q, box, s.rs, True)
+    res = {"n_atoms": s.n, "pairs_per_call": pl.nnz}
+    for name, prec in FORMS:
+        tpis = (2056,) if prec == 0 else FORM_CANDIDATES[prec]
+        ms, t, pp = best_form_call(lj, q, pl, box, s.rc, prec, tpis, stream, flush, dev)
+        res[name] = {"schedule": schedule_name(t), "ms_per_call": ms,
+                     **err_stats(pp[:, :3].cpu().numpy(), want)}
+    return res
+
+
+def extra_batched(lj, dev, stream, flush, oracle_dp):
+    """512 systems, N log-uniform in 500..32000, rho in 0.8..1.2, rc 2.5 or
+    3.0: one persistent launch replayed from a CUDA graph, against (a) one
+    lj_force call per system issued from the host and (b) the same per-system
+    calls replayed from one CUDA graph (no host work between launches, so
+    (b) against the persistent launch is the GPU-side difference and (a)
+    against (b) the host's).  FP64, mixed and double-float; the autotuner
+    picks lanes per row, rows per work item and the list layout.  Errors
+    against the oracle on 16 sampled systems."""
+    import torch
     from paper_1806_05713_gb300.batch import Batch
-    systems = inputs.batched_systems(nsys=512, seed=0)
-    res = {"n_systems": len(systems), "total_atoms": int(sum(s.n for s in systems))}
-    for name, prec in (("fp64", lj.LJ_FP64), ("mixed", lj.LJ_MIXED), ("dfloat", lj.LJ_DFLOAT)):
+    systems = [system_from_spec(("batch", 512, 0, k)) for k in range(512)]
+    res = {"n_systems": len(systems), "total_atoms": int(sum(x.n for x in systems)),
+           "oracle_systems": list(BATCH_SAMPLE)}
+    for name, prec in FORMS:
         b = Batch(systems, DT, prec, True, tpi=8, rows_per_item=64, plan_rows_min=16)
         tpi, rows, _ = b.autotune(tpis=(4, 8, 16), rows=(16, 32, 64, 128), reps=3,
                                   layouts=(True, False))
         g = b.capture_graph()
         t_graph = time_calls(g.replay, stream, flush, 10, 2)
-        t_sep = time_calls(lambda: b.force_per_system(tpi=lj.LJ_TPI_AUTO),
-                           stream, flush, 5, 1)
+        t_host = time_calls(lambda: b.force_per_system(tpi=lj.LJ_TPI_AUTO), stream, flush, 5, 1)
+        g_sep = b.capture_per_system_graph(tpi=lj.LJ_TPI_AUTO)
+        t_sep_graph = time_calls(g_sep.replay, stream, flush, 10, 2)
+        b.p4.zero_()
+        b.force()
+        torch.cuda.synchronize()
+        out_p = b.p4.cpu().numpy()
+        errs = [err_stats(out_p[int(b.atom_offset[k]):int(b.atom_offset[k]) + systems[k].n, :3], w)
+                for k, w in zip(BATCH_SAMPLE, oracle_dp)]
         res[name] = {"tpi": tpi, "rows_per_item": rows, "list": "half" if b.half else "full",
                      "pairs_per_call": b.pairs,
                      "graph_persistent_ms": t_graph,
                      "graph_persistent_pairs_per_s": b.pairs / (t_graph / 1e3),
-                     "per_system_launches_ms": t_sep,
-                     "per_system_pairs_per_s": b.pairs / (t_sep / 1e3),
-                     "speedup": t_sep / t_graph}
-        del b, g
+                     "per_system_graph_ms": t_sep_graph,
+                     "per_system_host_launches_ms": t_host,
+                     "speedup_persistent_vs_per_system_graph": t_sep_graph / t_graph,
+                     "speedup_per_system_graph_vs_host_launches": t_host / t_sep_graph,
+                     "max_err_rel_vs_oracle": max(e["max_err_rel_vs_oracle"] for e in errs),
+                     "rms_err_rel_vs_oracle": max(e["rms_err_rel_vs_oracle"] for e in errs),
+                     "error_note": "worst of the sampled systems, each relative to its own scale"}
+        del b, g, g_sep
     return res
 
 
-def extra_adjoint(lj, dev, stream, flush):
+def extra_adjoint(lj, dev, stream, flush, oracle_parts):
     """64 replicas of N = 16,384 (16^3 FCC, rho 1, jitter 0.1): forces with
-    (eps, sigma) = (1.1, 0.97) against targets at (1, 1), mean squared force
-    error, gradient w.r.t. positions, eps and sigma through the autograd
-    wrapper (forward kernel + hand-written adjoint kernel)."""
+    (eps, sigma) = (1.1, 0.97) against targets at (1, 1), loss = mean squared
+    force error over all replicas, atoms and components; gradient w.r.t.
+    positions, eps and sigma through the autograd wrapper (forward kernel +
+    hand-written adjoint kernel).  Each form's gradient against the oracle's
+    (its adjoint summed over replicas), and the FP64 adjoint against central
+    differences (h = 1e-6) of the FP64 loss for eps, sigma and four
+    coordinates."""
     import torch
-    from paper_1806_05713_gb300 import inputs
     from paper_1806_05713_gb300.autograd import lj_forces
-    reps = inputs.workload_replicas(64, 16, seed=0)
+    reps = [system_from_spec(("replica", ADJ_REPLICAS, ADJ_K, 0, r)) for r in range(ADJ_REPLICAS)]
     L = float(reps[0].box[0])
     box = [L, L, L]
     n1 = reps[0].n
@@ -645,21 +1036,66 @@ def extra_adjoint(lj, dev, stream, flush):
                       False, reps[0].rs, 0)
     Ft = torch.zeros_like(q)
     lj.lj_force(q, Ft, big, 1.0, reps[0].rc, box, 1.0, 1.0)
-    res = {"replicas": len(reps), "atoms": int(q.shape[0]), "pairs": off // 2}
-    for name, prec in (("fp64", lj.LJ_FP64), ("mixed", lj.LJ_MIXED), ("dfloat", lj.LJ_DFLOAT)):
-        eps = torch.tensor(1.1, dtype=torch.float64, device=dev, requires_grad=True)
-        sig = torch.tensor(0.97, dtype=torch.float64, device=dev, requires_grad=True)
+    want_q = np.concatenate([o[0] for o in oracle_parts])
+    want_e = float(sum(o[1] for o in oracle_parts))
+    want_s = float(sum(o[2] for o in oracle_parts))
+    want_loss = float(sum(o[3] for o in oracle_parts))
+    res = {"replicas": len(reps), "atoms": int(q.shape[0]), "pairs": off // 2,
+           "oracle_loss": want_loss, "oracle_grad_eps": want_e, "oracle_grad_sigma": want_s}
+
+    def loss_of(qq, e, sg, prec):
+        F = lj_forces(qq, e, sg, big, reps[0].rc, box, prec)
+        return ((F - Ft) ** 2)[:, :3].mean()
+
+    for name, prec in FORMS:
+        eps = torch.tensor(ADJ_EPS, dtype=torch.float64, device=dev, requires_grad=True)
+        sig = torch.tensor(ADJ_SIGMA, dtype=torch.float64, device=dev, requires_grad=True)
+        last = {}
 
         def step():
             qq = q.detach().requires_grad_(True)
             eps.grad = None
             sig.grad = None
-            F = lj_forces(qq, eps, sig, big, reps[0].rc, box, prec)
-            loss = ((F - Ft) ** 2)[:, :3].mean()
+            loss = loss_of(qq, eps, sig, prec)
             loss.backward()
+            last["q"], last["loss"] = qq.grad, loss
             return qq.grad
         ms = time_calls(step, stream, flush, 5, 1)
-        res[name] = {"forward_backward_ms": ms, "grad_eps": float(eps.grad), "grad_sigma": float(sig.grad)}
+        step()
+        gq = last["q"][:, :3].cpu().numpy()
+        d = gq - want_q
+        res[name] = {"forward_backward_ms": ms, "loss": float(last["loss"].detach()),
+                     "grad_eps": float(eps.grad), "grad_sigma": float(sig.grad),
+                     "grad_eps_rel_err_vs_oracle": abs(float(eps.grad) - want_e) / abs(want_e),
+                     "grad_sigma_rel_err_vs_oracle": abs(float(sig.grad) - want_s) / abs(want_s),
+                     "grad_q_max_err_rel_vs_oracle": float(np.max(np.abs(d)) / np.max(np.abs(want_q))),
+                     "grad_q_rms_err_rel_vs_oracle": float(np.sqrt(np.mean(d ** 2)) /
+                                                           np.sqrt(np.mean(want_q ** 2)))}
+    # central differences of the FP64 loss
+    h = 1e-6
+    coords = [(0, 0), (12345, 1), (n1 * 7 + 3, 2), (q.shape[0] - 1, 0)]
+    with torch.no_grad():
+        def loss64(qq=q, e=ADJ_EPS, sg=ADJ_SIGMA):
+            te = torch.tensor(e, dtype=torch.float64, device=dev)
+            ts = torch.tensor(sg, dtype=torch.float64, device=dev)
+            return float(loss_of(qq, te, ts, 0))
+        fd = {"eps": (loss64(e=ADJ_EPS + h) - loss64(e=ADJ_EPS - h)) / (2 * h),
+              "sigma": (loss64(sg=ADJ_SIGMA + h) - loss64(sg=ADJ_SIGMA - h)) / (2 * h)}
+        for (i, a) in coords:
+            qp, qm = q.clone(), q.clone()
+            qp[i, a] += h
+            qm[i, a] -= h
+            fd[f"q[{i},{a}]"] = (loss64(qq=qp) - loss64(qq=qm)) / (2 * h)
+    adj = {"eps": res["fp64"]["grad_eps"], "sigma": res["fp64"]["grad_sigma"]}
+    eps = torch.tensor(ADJ_EPS, dtype=torch.float64, device=dev, requires_grad=True)
+    sig = torch.tensor(ADJ_SIGMA, dtype=torch.float64, device=dev, requires_grad=True)
+    qq = q.detach().requires_grad_(True)
+    loss_of(qq, eps, sig, 0).backward()
+    for (i, a) in coords:
+        adj[f"q[{i},{a}]"] = float(qq.grad[i, a])
+    res["fp64_vs_central_differences"] = {
+        k: {"adjoint": adj[k], "central_difference": fd[k],
+            "rel_diff": abs(adj[k] - fd[k]) / max(abs(fd[k]), 1e-300)} for k in fd}
     return res
 
 
@@ -673,9 +1109,8 @@ def extra_md(lj, dev, stream):
     the displacement criterion (rebuild when 2 max |q - q_build| reaches the
     margin) beside the paper's fastest-atom bound."""
     import torch
-    from paper_1806_05713_gb300 import inputs
     from paper_1806_05713_gb300.md import VelocityVerlet
-    s = inputs.workload_paper()
+    s = system_from_spec(("fcc", PAPER_K, RHO, JITTER, 0, "random"))
     g = np.random.default_rng(0).normal(size=(s.n, 4))
     g[:, 3] = 0.0
     g[:, :3] -= g[:, :3].mean(axis=0)
@@ -705,131 +1140,6 @@ def extra_md(lj, dev, stream):
         res[name] = {"steps": steps, "ms_per_step": ms / steps, "list_rebuilds": vv.rebuilds - r0,
                      "pairs_per_s": vv.plist.nnz * steps / (ms / 1e3),
                      "energy_drift_rel": abs(e1 - e0) / abs(e0)}
-    return res
-
-
-FORM_NAMES = {0: "fp64", 1: "mixed", 2: "dfloat"}
-
-
-def forms(lj, q, pl, box, s, best_tpi, flops, dev, stream, flush):
-    """The three arithmetic forms on the headline workload (half list, one
-    force call, L2 flushed): time, pair interactions/s, FP64-equivalent
-    TFLOP/s (the paper's 28 flops per in-cutoff pair), error vs the FP64
-    kernel (itself within 1e-12 of the oracle in the tests); and each form
-    again with the list layout (half or full) chosen by measurement, its
-    pairs still counted as unique half-list entries."""
-    import torch
-    res, ref = {}, None
-    for name, prec, tpis in (("fp64", lj.LJ_FP64, (best_tpi,)), ("mixed", lj.LJ_MIXED, (8, 16)),
-                             ("dfloat", lj.LJ_DFLOAT, (136, 132))):
-        best = None
-        for t in tpis:
-            pp = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
-            fn = lj.lj_force_prepared(q, pp, pl, DT, s.rc, box, precision=prec, tpi=t)
-            ms = time_calls(fn, stream, flush)
-            if best is None or ms < best[0]:
-                best = (ms, t, fn, pp)
-        ms, t, fn, pp = best
-        pp.zero_()
-        fn()
-        torch.cuda.synchronize()
-        r = {"schedule": schedule_name(t), "ms_per_call": ms, "pairs_per_s": pl.nnz / (ms / 1e3),
-             "fp64_equivalent_tflops": flops / (ms / 1e3) / 1e12}
-        if ref is None:
-            ref = pp[:, :3].clone()
-        else:
-            err = pp[:, :3] - ref
-            r["max_err_rel_vs_fp64"] = float(err.abs().max() / ref.abs().max())
-            r["rms_err_rel_vs_fp64"] = float(err.pow(2).mean().sqrt() / ref.pow(2).mean().sqrt())
-            r["speedup_vs_fp64"] = res["fp64"]["ms_per_call"] / ms
-        res[name] = r
-    # each form with the list layout and schedule chosen by measurement
-    # (lj_autotune_layout: half list with p_j atomics, or full list)
-    for name, prec in (("fp64", lj.LJ_FP64), ("mixed", lj.LJ_MIXED), ("dfloat", lj.LJ_DFLOAT)):
-        plb, t, _, _ = lj.lj_autotune_layout(q, box, s.rs, DT, s.rc, precision=prec, reps=3)
-        pp = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
-        ms = time_calls(lj.lj_force_prepared(q, pp, plb, DT, s.rc, box, precision=prec, tpi=t),
-                        stream, flush)
-        res[name]["best_layout"] = {"list": "half" if plb.half else "full",
-                                    "schedule": schedule_name(t), "ms_per_call": ms,
-                                    "pairs_per_s": pl.nnz / (ms / 1e3)}
-        del plb, pp
-    res["note"] = ("dfloat: pair arithmetic in double-float on the FP32 pipe, exact fixed-point "
-                   "displacement; mixed: FP32 pair arithmetic; both add into FP64 momenta")
-    return res
-
-
-def time_calls(fn, stream, flush, calls=20, warm=3):
-    import torch
-    for _ in range(warm):
-        fn()
-    ms = []
-    for _ in range(calls):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        fn()
-        b.record(stream)
-        b.synchronize()
-        ms.append(a.elapsed_time(b))
-    return statistics.median(ms)
-
-
-def variants(lj, s, q, pl_half, box, dev, stream, flush):
-    """Force-only time per call of each schedule, list kind, precision and
-    particle order (config 'paper size: two orderings, half and full'), with
-    L2 flushed before each call, plus list-build times and mixed-form error."""
-    import torch
-    from paper_1806_05713_gb300 import inputs
-    res = {}
-    for order in ("random", "cell"):
-        if order == "random":
-            qq, sys_ = q, s
-        else:
-            sys_ = inputs.fcc_system(31, 1.0, 0.05, seed=0, order="cell", rc=RC, margin=MARGIN)
-            qq = torch.from_numpy(sys_.q).to(dev)
-        for half in (True, False):
-            kind = "half" if half else "full"
-            t_list = time_calls(lambda: lj.lj_build_pairlist(qq, box, sys_.rs, half), stream, flush, 5, 1)
-            pl = lj.lj_build_pairlist(qq, box, sys_.rs, half)
-            m_half = pl.nnz if half else pl.nnz // 2
-            res[f"list_build_ms/{order}/{kind}"] = t_list
-            ref = None
-            for prec, tpis in ((lj.LJ_FP64, (1032, 1028, 1544, 1160, 2056, 2052, 2568, 4104, 4100, 4112)),
-                               (lj.LJ_MIXED, (4, 8, 16)),
-                               (lj.LJ_DFLOAT, (136, 132, 144, 648, 8))):
-                for tpi in tpis:
-                    pp = torch.zeros((sys_.n, 4), dtype=torch.float64, device=dev)
-                    fn = lj.lj_force_prepared(qq, pp, pl, DT, sys_.rc, box, precision=prec, tpi=tpi)
-                    ms = time_calls(fn, stream, flush)
-                    name = f"{FORM_NAMES[prec]}/{order}/{kind}/tpi{tpi}"
-                    res[name] = {"ms": ms, "pairs_per_s": m_half / (ms / 1e3)}
-                    # error of one call vs the FP64 result (itself within 1e-12 of the oracle)
-                    pp.zero_()
-                    fn()
-                    if prec == lj.LJ_FP64 and ref is None:
-                        ref = pp[:, :3].clone()
-                    elif prec != lj.LJ_FP64 and ref is not None:
-                        err = pp[:, :3] - ref
-                        res[name]["max_err_rel"] = float(err.abs().max() / ref.abs().max())
-                        res[name]["rms_err_rel"] = float(err.pow(2).mean().sqrt() / ref.pow(2).mean().sqrt())
-    # the paper's layout question on GB300: AoS4 vs AoS8 vs SoA, FP64, 8 lanes/row
-    for half in (True, False):
-        kind = "half" if half else "full"
-        pl = lj.lj_build_pairlist(q, box, s.rs, half)
-        m_half = pl.nnz if half else pl.nnz // 2
-        n = s.n
-        rec = torch.zeros((n, 8), dtype=torch.float64, device=dev)
-        rec[:, :3] = q[:, :3]
-        qs = q[:, :3].t().contiguous()
-        ps = torch.zeros_like(qs)
-        p4 = torch.zeros_like(q)
-        for name, fn in (("aos4", lambda: lj.lj_force_strided(q, p4, n, 4, 1, pl, DT, s.rc, box)),
-                         ("aos8", lambda: lj.lj_force_strided(rec, rec, n, 8, 1, pl, DT, s.rc, box,
-                                                              p_offset=4)),
-                         ("soa", lambda: lj.lj_force_strided(qs, ps, n, 1, n, pl, DT, s.rc, box))):
-            ms = time_calls(fn, stream, flush)
-            res[f"layout/fp64/random/{kind}/{name}"] = {"ms": ms, "pairs_per_s": m_half / (ms / 1e3)}
     return res
 
 
