@@ -409,7 +409,7 @@ def schedule_name(tpi: int) -> str:
 
 
 FORMS = (("fp64", 0), ("mixed", 1), ("dfloat", 2))
-FORM_CANDIDATES = {1: (4, 8, 16), 2: (132, 136, 144)}
+FORM_CANDIDATES = {1: (4, 8, 16, 132, 136, 144), 2: (132, 136, 144)}
 
 
 def best_form_call(lj, q, pl, box, rc, prec, tpis, stream, flush, dev, calls=10):

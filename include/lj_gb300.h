@@ -78,9 +78,11 @@ extern "C" {
  * LJ_SCHED_SWP2 | 8). */
 #define LJ_TPI_AUTO 0
 /* LJ_SCHED_SWP2 | tpi (tpi = 4, 8 or 16; FP64 with the IEEE-bit-pattern
- * displacement, and LJ_DFLOAT): software pipelining, the paper's section
- * "Software Pipelining" -- each lane carries two independent entries per
- * iteration so that their dependency chains overlap. */
+ * displacement, LJ_MIXED and LJ_DFLOAT): software pipelining, the paper's
+ * section "Software Pipelining" -- each lane carries two independent
+ * entries per iteration so that their dependency chains overlap.  (The
+ * LJ_MIXED and LJ_DFLOAT rows also request the gathers of the next
+ * iteration before the arithmetic of the current one, in every schedule.) */
 #define LJ_SCHED_SWP2 128
 /* LJ_SCHED_SORTED | (a row-group schedule, FP64 or mixed): rows are walked
  * in order of decreasing length (a counting sort of the row lengths in the
@@ -218,7 +220,7 @@ size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
  *  eps, sigma       Eq. (1) parameters (> 0).
  *  precision        LJ_FP64, LJ_MIXED or LJ_DFLOAT.
  *  tpi              LJ_TPI_AUTO, 1..32 (power of two; LJ_DFLOAT: 4, 8, 16),
- *                   or LJ_SCHED_SWP2 | 4, 8, 16 (FP64 and LJ_DFLOAT).
+ *                   or LJ_SCHED_SWP2 | 4, 8, 16 (every form).
  *                   LJ_SCHED_SORTED may be or-ed into any of these,
  *                   LJ_SCHED_IMAGES into the FP64 4, 8, 16 and SWP2
  *                   schedules; LJ_SCHED_FIXED | 4, 8, 16 (FP64, optionally |

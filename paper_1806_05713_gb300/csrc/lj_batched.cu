@@ -163,9 +163,9 @@ batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ it
                     const uint4 *srel = rel + S.atom_off;
                     const MixedParams &P = S.mp;
                     if (half)
-                        mixed_row<TPI, true>(sq, srel, sp, srp, scol, r, P);
+                        mixed_row_pf<TPI, true, 1>(sq, srel, sp, srp, scol, r, P);
                     else
-                        mixed_row<TPI, false>(sq, srel, sp, srp, scol, r, P);
+                        mixed_row_pf<TPI, false, 1>(sq, srel, sp, srp, scol, r, P);
                 } else {
                     const longlong4 *sX = X + S.atom_off;
                     const Fp64Params &P = S.fp;

@@ -86,8 +86,9 @@ force_fixed_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ 
 }
 
 // MIXED form, 128-thread blocks (a finer last wave: the full list 2-4 %
-// faster than with 256).
-template <int TPI, bool HALF>
+// faster than with 256).  U = 1: one entry per lane and iteration, its
+// gathers one iteration ahead; U = 2 (LJ_SCHED_SWP2): two entries per lane.
+template <int TPI, bool HALF, int U>
 __global__ void __launch_bounds__(128)
 force_mixed_kernel(const double *__restrict__ q4, const uint4 *__restrict__ rel,
                    double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
@@ -96,7 +97,7 @@ force_mixed_kernel(const double *__restrict__ q4, const uint4 *__restrict__ rel,
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
     if (gid >= n) return;
     const int i = order ? order[gid] : gid;
-    mixed_row<TPI, HALF>(q4, rel, p4, row_ptr, col, i, P);
+    mixed_row_pf<TPI, HALF, U>(q4, rel, p4, row_ptr, col, i, P);
 }
 
 // Force and potential energy in one pass (FP64, 8 lanes per row, exact
@@ -296,16 +297,16 @@ int launch_fixed(const double *q4, const longlong4 *X, double *p4, int n, const 
     return LJ_OK;
 }
 
-template <int TPI>
+template <int TPI, int U = 1>
 int launch_mixed(const double *q4, const uint4 *rel, double *p4, int n, const int *rp,
                  const int *col, int half, const MixedParams &P, const int *order, cudaStream_t st)
 {
     const int64_t threads = int64_t(n) * TPI;
     const unsigned grid = unsigned((threads + 127) / 128);
     if (half)
-        force_mixed_kernel<TPI, true><<<grid, 128, 0, st>>>(q4, rel, p4, n, rp, col, P, order);
+        force_mixed_kernel<TPI, true, U><<<grid, 128, 0, st>>>(q4, rel, p4, n, rp, col, P, order);
     else
-        force_mixed_kernel<TPI, false><<<grid, 128, 0, st>>>(q4, rel, p4, n, rp, col, P, order);
+        force_mixed_kernel<TPI, false, U><<<grid, 128, 0, st>>>(q4, rel, p4, n, rp, col, P, order);
     LJ_TRY_LAUNCH("force_mixed_kernel");
     return LJ_OK;
 }
@@ -370,7 +371,7 @@ bool valid_schedule(int s, int precision)
     if (s & ~(LJ_SCHED_SORTED | LJ_SCHED_SWP2 | LJ_SCHED_IMAGES | 63)) return false;
     if (precision == LJ_DFLOAT) return (s & LJ_SCHED_IMAGES) == 0 && (t == 4 || t == 8 || t == 16);
     if (s & LJ_SCHED_IMAGES) return precision == LJ_FP64 && (t == 4 || t == 8 || t == 16);
-    if (s & LJ_SCHED_SWP2) return precision == LJ_FP64 && (t == 4 || t == 8 || t == 16);
+    if (s & LJ_SCHED_SWP2) return t == 4 || t == 8 || t == 16;
     return pow2;
 }
 
@@ -468,6 +469,9 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
     mixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4, ni, P, rel);
     LJ_TRY_LAUNCH("mixed_prepass_kernel");
     switch (tpi) {
+        case LJ_SCHED_SWP2 | 4: return launch_mixed<4, 2>(q4, rel, p4, ni, row_ptr, col, half, P, order, st);
+        case LJ_SCHED_SWP2 | 8: return launch_mixed<8, 2>(q4, rel, p4, ni, row_ptr, col, half, P, order, st);
+        case LJ_SCHED_SWP2 | 16: return launch_mixed<16, 2>(q4, rel, p4, ni, row_ptr, col, half, P, order, st);
         case 1: return launch_mixed<1>(q4, rel, p4, ni, row_ptr, col, half, P, order, st);
         case 2: return launch_mixed<2>(q4, rel, p4, ni, row_ptr, col, half, P, order, st);
         case 4: return launch_mixed<4>(q4, rel, p4, ni, row_ptr, col, half, P, order, st);

@@ -208,50 +208,83 @@ __device__ __forceinline__ void fp64_row(const double *__restrict__ q4, double *
     }
 }
 
-// One row i of the MIXED form (see lj_force.cu), walked by a TPI group;
-// rel holds the fixed-point positions of the system.
-template <int TPI, bool HALF>
-__device__ __forceinline__ void mixed_row(const double *__restrict__ q4,
-                                          const uint4 *__restrict__ rel, double *__restrict__ p4,
-                                          const int *__restrict__ row_ptr,
-                                          const int *__restrict__ col, int i, const MixedParams &P)
+// One row i of the MIXED form with its gathers software-pipelined (the
+// paper's section "Software Pipelining", applied to the loads): the lane's
+// entries are taken U at a time (k, k + TPI, ..., k + (U-1) TPI); the
+// fixed-point records of the next U entries and the column indices of the U
+// after those are requested before the arithmetic of the current ones, so
+// the two dependent L2 gathers of an entry (col[k], then rel[col[k]]) are in
+// flight while the lane computes.  Each lane adds its entries in increasing
+// k whatever U is, so the compensated sums do not depend on U.  rel holds
+// the fixed-point positions of the system (see lj_force.cu).
+template <int TPI, bool HALF, int U>
+__device__ __forceinline__ void mixed_row_pf(const double *__restrict__ q4,
+                                             const uint4 *__restrict__ rel, double *__restrict__ p4,
+                                             const int *__restrict__ row_ptr,
+                                             const int *__restrict__ col, int i,
+                                             const MixedParams &P)
 {
     const int sub = threadIdx.x & (TPI - 1);
-    const uint4 pi = rel[i];
+    const uint4 pi = __ldg(rel + i);
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     const int kb = row_ptr[i], ke = row_ptr[i + 1];
-    for (int k = kb + sub; k < ke; k += TPI) {
-        const int j = col[k];
-        const uint4 pj = rel[j];
-        const float dx = fixed_disp(pj.x, pi.x, P.scale[0]);
-        const float dy = fixed_disp(pj.y, pi.y, P.scale[1]);
-        const float dz = fixed_disp(pj.z, pi.z, P.scale[2]);
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        bool in = r2 < P.rc2f;
-        if (fabsf(r2 - P.rc2f) <= P.band) {
-            double xi, yi, zi, xj, yj, zj;
-            load_xyz(q4, i, xi, yi, zi);
-            load_xyz(q4, j, xj, yj, zj);
-            const double ex = min_image(__dsub_rn(xj, xi), P.L[0], P.half_bits[0]);
-            const double ey = min_image(__dsub_rn(yj, yi), P.L[1], P.half_bits[1]);
-            const double ez = min_image(__dsub_rn(zj, zi), P.L[2], P.half_bits[2]);
-            in = exact_in_cutoff(ex, ey, ez, P.rc2);
-        }
-        if (in) {
-            const float u = rcp_fp32(r2);
-            const float u2 = u * u;
-            const float u4 = u2 * u2;
-            const float u3 = u2 * u;
-            const float f = u4 * fmaf(-P.Bf, u3, P.Af);
-            const float fx = f * dx, fy = f * dy, fz = f * dz;
-            kahan_add(sx, cx, fx);
-            kahan_add(sy, cy, fy);
-            kahan_add(sz, cz, fz);
-            if (HALF) {
-                atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 0, f32_to_f64(-fx));
-                atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 1, f32_to_f64(-fy));
-                atomicAdd(p4 + 4 * static_cast<int64_t>(j) + 2, f32_to_f64(-fz));
+    // entries past the row end gather atom i itself (r^2 = 0, never used)
+    auto col_at = [&](int k) { return k < ke ? __ldg(col + k) : i; };
+    int j[U], jn[U];
+    uint4 r[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) j[u] = col_at(kb + sub + u * TPI);
+#pragma unroll
+    for (int u = 0; u < U; ++u) r[u] = __ldg(rel + j[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) jn[u] = col_at(kb + sub + (U + u) * TPI);
+    for (int k0 = kb; k0 < ke; k0 += U * TPI) {
+        uint4 rn[U];
+        int jnn[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) rn[u] = __ldg(rel + jn[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) jnn[u] = col_at(k0 + sub + (2 * U + u) * TPI);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool valid = k0 + sub + u * TPI < ke;
+            const float dx = fixed_disp(r[u].x, pi.x, P.scale[0]);
+            const float dy = fixed_disp(r[u].y, pi.y, P.scale[1]);
+            const float dz = fixed_disp(r[u].z, pi.z, P.scale[2]);
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            bool in = valid && r2 < P.rc2f;
+            if (valid && fabsf(r2 - P.rc2f) <= P.band) {
+                double xi, yi, zi, xj, yj, zj;
+                load_xyz(q4, i, xi, yi, zi);
+                load_xyz(q4, j[u], xj, yj, zj);
+                const double ex = min_image(__dsub_rn(xj, xi), P.L[0], P.half_bits[0]);
+                const double ey = min_image(__dsub_rn(yj, yi), P.L[1], P.half_bits[1]);
+                const double ez = min_image(__dsub_rn(zj, zi), P.L[2], P.half_bits[2]);
+                in = exact_in_cutoff(ex, ey, ez, P.rc2);
             }
+            if (in) {
+                const float w = rcp_fp32(r2);
+                const float w2 = w * w;
+                const float w4 = w2 * w2;
+                const float w3 = w2 * w;
+                const float f = w4 * fmaf(-P.Bf, w3, P.Af);
+                const float fx = f * dx, fy = f * dy, fz = f * dz;
+                kahan_add(sx, cx, fx);
+                kahan_add(sy, cy, fy);
+                kahan_add(sz, cz, fz);
+                if (HALF) {
+                    double *pj = p4 + 4 * static_cast<int64_t>(j[u]);
+                    atomicAdd(pj + 0, f32_to_f64(-fx));
+                    atomicAdd(pj + 1, f32_to_f64(-fy));
+                    atomicAdd(pj + 2, f32_to_f64(-fz));
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            r[u] = rn[u];
+            j[u] = jn[u];
+            jn[u] = jnn[u];
         }
     }
     if (TPI > 1) {
@@ -260,8 +293,6 @@ __device__ __forceinline__ void mixed_row(const double *__restrict__ q4,
         group_kahan<TPI>(sz, cz);
     }
     if (sub == 0) {
-        // p_i += s - c: the head and the compensation go to p as two FP64
-        // additions done in L2 (no FP64-pipe instruction in this kernel).
         double *pp = p4 + 4 * static_cast<int64_t>(i);
         atomicAdd(pp + 0, f32_to_f64(sx));
         atomicAdd(pp + 1, f32_to_f64(sy));

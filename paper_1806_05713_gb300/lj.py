@@ -385,7 +385,7 @@ def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float
                       if precision == LJ_FP64 else
                       [W | 8, W | 4, W | 16, S | W | 8, 4, 8, 16, S | 4, S | 8]
                       if precision == LJ_DFLOAT else
-                      [2, 4, 8, 16, S | 4, S | 8, S | 16])
+                      [4, 8, 16, W | 4, W | 8, W | 16, S | 8, S | W | 8])
     n = plist.n
     scratch = torch.zeros((n, 4), dtype=torch.float64, device=q4.device)
     ws = _workspace(lib.lj_force_workspace_bytes(n, _box3(box), int(precision)), q4.device)

@@ -55,7 +55,7 @@ def test_fp64_small_all_schedules(cuda_lib, oracle_lib, small, tpi, half):
     assert _relerr(got, want) <= FP64_TOL
 
 
-@pytest.mark.parametrize("tpi", [1, 4, 8, 32, 516, 520])
+@pytest.mark.parametrize("tpi", [1, 4, 8, 32, 516, 520, 132, 136, 144, 648])
 @pytest.mark.parametrize("half", [True, False])
 def test_mixed_small(cuda_lib, oracle_lib, small, tpi, half):
     got, _ = _run(cuda_lib, small, half, cuda_lib.LJ_MIXED, tpi)
@@ -239,10 +239,12 @@ def test_fp64_paper_size(cuda_lib, oracle_lib, order, half):
 def test_mixed_paper_size(cuda_lib, oracle_lib, half):
     s = inputs.workload_paper(order="cell")
     want = _oracle(oracle_lib, s, half)
-    got, _ = _run(cuda_lib, s, half, 1, 8)
-    err = got - want
-    assert np.max(np.abs(err)) / np.max(np.abs(want)) <= MIXED_TOL
-    assert np.sqrt(np.mean(err ** 2)) / np.sqrt(np.mean(want ** 2)) <= 2.5e-6
+    pl = None
+    for tpi in (8, 16, 136):
+        got, pl = _run(cuda_lib, s, half, 1, tpi, pl=pl)
+        err = got - want
+        assert np.max(np.abs(err)) / np.max(np.abs(want)) <= MIXED_TOL, tpi
+        assert np.sqrt(np.mean(err ** 2)) / np.sqrt(np.mean(want ** 2)) <= 2.5e-6, tpi
 
 
 @pytest.fixture(scope="module")
@@ -266,7 +268,7 @@ def test_million_atoms_all_forms_sampled(cuda_lib, million, half):
     q = to_dev(s.q)
     pl = lj.lj_build_pairlist(q, s.box, s.rs, half)
     scale = np.max(np.abs(want))
-    for prec, tpis, tol in ((0, (0, 2056, 2052, 1032), FP64_TOL), (1, (4, 8, 16), MIXED_TOL),
+    for prec, tpis, tol in ((0, (0, 2056, 2052, 1032), FP64_TOL), (1, (4, 8, 16, 136), MIXED_TOL),
                             (2, (132, 136, 144), FP64_TOL)):
         for tpi in tpis:
             p = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
