@@ -72,11 +72,11 @@ ORACLE_SAMPLE_ATOMS = 512
 # reduction sectors, and the summary that records them.  A schedule or
 # workload without an entry reports no traffic figure ("not profiled").
 PROFILED = {
-    (2056, "half", 119164): {"dram_bytes": 41910784.0 + 5632.0, "lts_read_sectors": 11254023,
-                             "lts_red_sectors": 24806804,
+    (2056, "half", 119164): {"dram_bytes": 41909760.0 + 0.0, "lts_read_sectors": 10610303,
+                             "lts_red_sectors": 24808185,
                              "source": "profiles/force_fp64_fixed_tpi8_half_N119164.md"},
-    (2056, "half", 1048576): {"dram_bytes": 388423680.0 + 46345728.0,
-                              "lts_read_sectors": 100962352, "lts_red_sectors": 218370139,
+    (2056, "half", 1048576): {"dram_bytes": 373012736.0 + 27113216.0,
+                              "lts_read_sectors": 96542789, "lts_red_sectors": 218289891,
                               "source": "profiles/force_fp64_fixed_tpi8_half_N1048576.md"},
 }
 ERROR_DEFINITION = ("max_err_rel = max |dp_gpu - dp_oracle| / max |dp_oracle|; rms_err_rel = "

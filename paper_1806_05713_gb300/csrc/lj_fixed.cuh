@@ -151,6 +151,59 @@ __device__ __forceinline__ double fixed128_to_f64(unsigned long long hi, unsigne
     return assemble_f64(round53(top, rem, half), n, k2, 0ull);
 }
 
+// fixed_to_f64 without branches: both the exact path (|v| < 2^53, shifted
+// up into the significand) and the rounded one (|v| >= 2^53, round to
+// nearest even) are computed and one is selected, so the lanes of a warp
+// never diverge on the magnitude of their displacement.  Same values as
+// fixed_to_f64.
+__device__ __forceinline__ double fixed_to_f64_sel(long long v, int k)
+{
+    const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned long long a = static_cast<unsigned long long>(v < 0 ? -v : v);
+    const int n = 64 - __clzll(static_cast<long long>(a));  // 0 for a = 0
+    const int up = max(53 - n, 0), sh = max(n - 53, 0);
+    const unsigned long long top = a >> sh;
+    const unsigned long long rem = a & ((1ull << sh) - 1ull);
+    const unsigned long long half = (1ull << sh) >> 1;       // 0 when sh = 0
+    const bool rnd = sh > 0 && (rem > half || (rem == half && (top & 1ull)));
+    const unsigned long long m = sh > 0 ? top + (rnd ? 1ull : 0ull) : a << up;
+    const double d = assemble_f64(m, n, k, sign);
+    return a == 0ull ? 0.0 : d;
+}
+
+// fixed128_to_f64 for hi != 0 (a value of 65 to 128 bits), without
+// branches: the 53 kept bits lie across hi and lo when the dropped count
+// sh = n - 53 is below 64, in hi alone when it is 64 or more; both results
+// are formed and one is selected, so a warp never diverges on the size of
+// a squared distance (the fixed-point scale k ties that size to the box:
+// in small boxes list entries fall on both sides).  `fast` is false for
+// hi = 0 (a squared distance below 2^(64-2k): coincident atoms, or an idle
+// lane), where the caller converts with fixed128_to_f64.  Same values as
+// fixed128_to_f64.
+__device__ __forceinline__ double fixed128_to_f64_hi(unsigned long long hi, unsigned long long lo,
+                                                     int k2, bool &fast)
+{
+    fast = hi != 0ull;
+    const int n = 128 - __clzll(static_cast<long long>(hi | 1ull));  // 65 .. 128 when fast
+    const int sh = n - 53;
+    // dropped bits all in lo (sh = 12 .. 63)
+    const int s1 = min(max(sh, 12), 63);
+    const unsigned long long top1 = (hi << (64 - s1)) | (lo >> s1);
+    const unsigned long long rem1 = lo & ((1ull << s1) - 1ull);
+    const unsigned long long half1 = 1ull << (s1 - 1);
+    const bool up1 = rem1 > half1 || (rem1 == half1 && (top1 & 1ull));
+    // dropped bits: all of lo and the low s2 bits of hi (sh = 64 .. 75)
+    const int s2 = min(max(sh - 64, 0), 11);
+    const unsigned long long top2 = hi >> s2;
+    const unsigned long long rhi = hi & ((1ull << s2) - 1ull);
+    const unsigned long long hh = (1ull << s2) >> 1;
+    const bool gt2 = s2 > 0 ? (rhi > hh || (rhi == hh && lo > 0ull)) : (lo > (1ull << 63));
+    const bool eq2 = s2 > 0 ? (rhi == hh && lo == 0ull) : (lo == (1ull << 63));
+    const bool up2 = gt2 || (eq2 && (top2 & 1ull));
+    const unsigned long long m = sh >= 64 ? top2 + (up2 ? 1ull : 0ull) : top1 + (up1 ? 1ull : 0ull);
+    return assemble_f64(m, n, k2, 0ull);
+}
+
 // 1/a in double for 2^-69 <= a < 2^120 from a seed good to ~2^-45 and one
 // Newton step (two FP64 instructions instead of rcp_fp64's three).  The
 // seed is built off the FP64 pipe: a split by its bits into a head float
@@ -291,6 +344,70 @@ __device__ __forceinline__ bool fixed_entry(const double *__restrict__ q4, long 
     return in;
 }
 
+// fixed_entry with one vote per entry instead of several: the common case
+// (a squared distance of at least 2^(64-2k), away from the cutoff band,
+// inside the range of the seeded reciprocal) is computed with selects only;
+// the rare lanes -- coincident or nearly coincident atoms, an entry
+// within 64 ulp of r_c^2 (the FP64 definition's decision), an r^2 outside
+// the reciprocal's range (a division) -- are handled under a single
+// group vote.  Returns whether the pair interacts; *w_div receives 1/r^2 by
+// division for the lanes that need it (and *use_div says which).  Same
+// values as fixed_entry followed by rcp_fp64_fixed.
+__device__ __forceinline__ bool fixed_entry_sel(const double *__restrict__ q4, long long xi,
+                                                long long yi, long long zi, long long xj,
+                                                long long yj, long long zj, bool valid, int i, int j,
+                                                const Fp64Params &P, const FixParams &F, unsigned gm,
+                                                double &dx, double &dy, double &dz, double &r2,
+                                                bool &use_div, double &w_div)
+{
+    const long long Dx = wrap_fixed(xj - xi, F.M[0], F.Mh[0]);
+    const long long Dy = wrap_fixed(yj - yi, F.M[1], F.Mh[1]);
+    const long long Dz = wrap_fixed(zj - zi, F.M[2], F.Mh[2]);
+    unsigned long long hi, lo;
+    norm2_fixed(Dx, Dy, Dz, hi, lo);
+    bool fast;
+    r2 = fixed128_to_f64_hi(hi, lo, 2 * F.k, fast);
+    dx = fixed_to_f64_sel(Dx, F.k);
+    dy = fixed_to_f64_sel(Dy, F.k);
+    dz = fixed_to_f64_sel(Dz, F.k);
+    long long rb = __double_as_longlong(r2);
+    bool in = valid && rb < P.rc2_bits;
+    bool near = static_cast<unsigned long long>(rb - P.rc2_bits + 64) < 128ull;
+    int ea = static_cast<int>((rb >> 52) & 0x7ff) - 1023;
+    bool rcp_ok = ea > -70 && ea < 120;
+    use_div = false;
+    w_div = 0.0;
+    const bool special = valid && (!fast || near || !rcp_ok);
+    if (__any_sync(gm, special)) {
+        if (special) {
+            if (!fast) {
+                r2 = fixed128_to_f64(hi, lo, 2 * F.k);
+                rb = __double_as_longlong(r2);
+                in = rb < P.rc2_bits;
+                near = static_cast<unsigned long long>(rb - P.rc2_bits + 64) < 128ull;
+            }
+            if (near) {
+                // the FP64 definition: its displacement, its decision
+                double qxi, qyi, qzi, qxj, qyj, qzj;
+                load_xyz(q4, i, qxi, qyi, qzi);
+                load_xyz(q4, j, qxj, qyj, qzj);
+                dx = min_image(__dsub_rn(qxj, qxi), P.L[0], P.half_bits[0]);
+                dy = min_image(__dsub_rn(qyj, qyi), P.L[1], P.half_bits[1]);
+                dz = min_image(__dsub_rn(qzj, qzi), P.L[2], P.half_bits[2]);
+                in = exact_in_cutoff(dx, dy, dz, P.rc2);
+                r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+            }
+            ea = static_cast<int>((__double_as_longlong(r2) >> 52) & 0x7ff) - 1023;
+            if (in && !(ea > -70 && ea < 120)) {
+                use_div = true;
+                w_div = 1.0 / r2;
+            }
+        }
+    }
+    if (!valid) r2 = 1.0;
+    return in;
+}
+
 // One row of the FP64 form with the exact fixed-point displacement (see the
 // header comment); the arithmetic after r^2 is fp64_row's.  EN: also sum the
 // pair energy 4 eps [(sigma/r)^12 - (sigma/r)^6] of every interacting entry
@@ -318,11 +435,17 @@ __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
         const int j = valid ? col[k] : i;
         long long xj, yj, zj;
         load_fixed(X, j, xj, yj, zj);
-        double dx, dy, dz, r2;
-        const bool in = fixed_entry(q4, xi, yi, zi, xj, yj, zj, valid, i, j, P, F, gm, dx, dy, dz, r2);
-        if (__any_sync(gm, in)) {
+        double dx, dy, dz, r2, w_div;
+        bool use_div;
+        const bool in = fixed_entry_sel(q4, xi, yi, zi, xj, yj, zj, valid, i, j, P, F, gm, dx, dy,
+                                        dz, r2, use_div, w_div);
+        // No vote on `in`: the FP64 chain runs for every lane (a group with
+        // no interacting entry at all is rare), lanes outside r_c on r^2 = 1.
+        {
             if (!in) r2 = 1.0;
-            const double w = rcp_fp64_fixed(r2, gm);
+            bool seed_ok;
+            double w = rcp_fp64_seeded(r2, seed_ok);
+            w = use_div ? w_div : w;
             const double w2 = w * w;
             const double w4 = w2 * w2;
             const double w3 = w2 * w;

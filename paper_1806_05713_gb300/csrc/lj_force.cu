@@ -68,12 +68,15 @@ force_fp64_kernel(const double *__restrict__ q4, double *__restrict__ p4, int n,
 
 // FP64 form with the exact fixed-point displacement (LJ_SCHED_FIXED).
 // 128-thread blocks (a finer last wave than 256 at the same occupancy,
-// about 1 % faster), twelve blocks an SM in 40 registers.  (Two entries per
-// lane -- the paper's software pipelining on this row -- needed 74
-// registers, six blocks an SM, and ran 0.298 ms against 0.263 at
-// N = 119,164: the occupancy hides the FP64 latency better.)
+// about 1 % faster).  At least eight blocks an SM: the row's selects (no
+// branch on the magnitude of a displacement) keep more values live, and
+// 64 registers hold them without spilling (twelve blocks in 40 registers
+// spilled and ran 0.6-0.8 % slower).  (Two entries per lane -- the paper's
+// software pipelining on this row -- needed 74 registers and ran 0.298 ms
+// against 0.263 at N = 119,164: the occupancy hides the FP64 latency
+// better.)
 template <int TPI, bool HALF>
-__global__ void __launch_bounds__(128, 12)
+__global__ void __launch_bounds__(128, 8)
 force_fixed_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
                    double *__restrict__ p4, int n, const int *__restrict__ row_ptr,
                    const int *__restrict__ col, Fp64Params P, FixParams F,
