@@ -104,7 +104,8 @@ def parse():
                                           "dfloat-full", "list", "vjp", "vjp-dfloat", "batched",
                                           "batched-mixed", "batched-dfloat"],
                     help="no timing: build the list and run a few calls of one kernel (for ncu)")
-    ap.add_argument("--profile-atoms", choices=["paper", "million"], default="million")
+    ap.add_argument("--profile-atoms", choices=["paper", "million"], default="paper",
+                    help="--profile workload: N = 119,164 (paper) or N = 1,048,576 (million)")
     ap.add_argument("--profile-tpi", type=int, default=0, help="schedule for --profile (0 = auto)")
     return ap.parse_args()
 

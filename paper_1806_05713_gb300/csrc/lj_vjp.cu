@@ -20,9 +20,9 @@
 //
 // Forms: FP64 (the displacement and s exact in integer fixed point and
 // rounded once to double, as lj_force's LJ_SCHED_FIXED; every later step
-// double), MIXED (fixed-point displacement rounded once to FP32, FP32 pair
-// arithmetic as in lj_force, Kahan-compensated FP32 row and scalar sums,
-// FP64 outputs).  Pairs within the error band of r_c^2 are
+// double), MIXED (fixed-point displacement rounded once to FP32, R rounded
+// to FP32 once per atom, FP32 pair arithmetic as in lj_force,
+// Kahan-compensated FP32 row and scalar sums, FP64 outputs).  Pairs within the error band of r_c^2 are
 // decided by the exact FP64 definition in both forms.
 #include <cmath>
 #include <cstring>
@@ -133,14 +133,16 @@ vjp_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
             const int k = base + sub;
             const bool valid = k < ke;
             const int j = valid ? col[k] : i;
-            double dx, dy, dz, s;
-            bool in;
+            double dx, dy, dz, s, w_div = 0.0;
+            bool in, use_div = false;
             if (FIX) {
                 // the exact fixed-point displacement and r^2 (the FP64
-                // definition within 64 ulp of r_c^2); s = 1 on an invalid lane
+                // definition within 64 ulp of r_c^2), with selects and one
+                // vote for the rare lanes; s = 1 on an invalid lane
                 long long fxj, fyj, fzj;
                 load_fixed(X, j, fxj, fyj, fzj);
-                in = fixed_entry(q4, fxi, fyi, fzi, fxj, fyj, fzj, valid, i, j, P, F, gm, dx, dy, dz, s);
+                in = fixed_entry_sel(q4, fxi, fyi, fzi, fxj, fyj, fzj, valid, i, j, P, F, gm, dx, dy,
+                                     dz, s, use_div, w_div);
             } else {
                 double cj[3];
                 load_q4_256(q4, j, cj[0], cj[1], cj[2]);
@@ -168,10 +170,20 @@ vjp_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
                 }
                 if (!valid) s = 1.0;
             }
-            if (__any_sync(gm, in)) {
+            // fixed point: no vote on `in` (every lane runs the chain, a lane
+            // outside r_c on its own r^2); image selection: skip groups with
+            // no interacting entry
+            if (FIX || __any_sync(gm, in)) {
                 double Rxj, Ryj, Rzj;
                 load_r3(R4, j, Rxj, Ryj, Rzj);
-                const double u = rcp_fp64(s, gm);
+                double u;
+                if (FIX) {
+                    bool seed_ok;
+                    u = rcp_fp64_seeded(s, seed_ok);
+                    u = use_div ? w_div : u;
+                } else {
+                    u = rcp_fp64(s, gm);
+                }
                 const double u2 = u * u, u3 = u2 * u, u4 = u2 * u2, u5 = u4 * u;
                 const double g = u4 * fma(C.G1, u3, -C.G2);
                 const double gp = u5 * fma(-C.H1, u3, C.H2);
@@ -215,13 +227,61 @@ vjp_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
     block_pair_sum(ge, gs, partial);
 }
 
+// MIXED form: one 32-byte record per atom, written by a pre-pass -- the
+// 32-bit fixed-point position {X, Y, Z} (as lj_force's mixed pre-pass) and
+// R = dLoss/dF rounded to FP32 -- so a gathered atom is one 256-bit load
+// (one sector) and no float/double conversion runs in the pair loop (those
+// run on GB300's FP64 pipe).
+__global__ void vjp_mixed_prepass_kernel(const double *__restrict__ q4,
+                                         const double *__restrict__ R4, int n, MixedParams P,
+                                         ulonglong4 *__restrict__ rec)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x, y, z, rx, ry, rz;
+    load_xyz(q4, i, x, y, z);
+    load_r3(R4, i, rx, ry, rz);
+    const unsigned X = __double2uint_rz(x * P.to_fixed[0]), Y = __double2uint_rz(y * P.to_fixed[1]),
+                   Z = __double2uint_rz(z * P.to_fixed[2]);
+    const unsigned fx = __float_as_uint(__double2float_rn(rx)),
+                   fy = __float_as_uint(__double2float_rn(ry)),
+                   fz = __float_as_uint(__double2float_rn(rz));
+    rec[i] = make_ulonglong4(static_cast<unsigned long long>(X) | (static_cast<unsigned long long>(Y) << 32),
+                             static_cast<unsigned long long>(Z),
+                             static_cast<unsigned long long>(fx) | (static_cast<unsigned long long>(fy) << 32),
+                             static_cast<unsigned long long>(fz));
+}
+
+struct MixedVjpRec {
+    unsigned X, Y, Z;
+    float rx, ry, rz;
+};
+
+__device__ __forceinline__ MixedVjpRec load_mixed_vjp_rec(const ulonglong4 *__restrict__ rec, int j)
+{
+    unsigned long long a, b, c, d;
+    asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(a), "=l"(b), "=l"(c), "=l"(d)
+        : "l"(rec + j));
+    MixedVjpRec r;
+    r.X = static_cast<unsigned>(a);
+    r.Y = static_cast<unsigned>(a >> 32);
+    r.Z = static_cast<unsigned>(b);
+    r.rx = __uint_as_float(static_cast<unsigned>(c));
+    r.ry = __uint_as_float(static_cast<unsigned>(c >> 32));
+    r.rz = __uint_as_float(static_cast<unsigned>(d));
+    return r;
+}
+
+// The row walk takes each lane's record one entry ahead and its column
+// index two ahead (software pipelining of the gathers, as lj_force's mixed
+// row); each lane adds its entries in increasing k as before.
 template <bool HALF>
 __global__ void __launch_bounds__(kVjpThreads)
-vjp_mixed_kernel(const double *__restrict__ q4, const uint4 *__restrict__ rel,
-                 const double *__restrict__ R4, int n, const int *__restrict__ row_ptr,
-                 const int *__restrict__ col, MixedParams P, float G1, float G2, float H1,
-                 float H2, float S1, float S2, double *__restrict__ gq4,
-                 double *__restrict__ partial)
+vjp_mixed_kernel(const double *__restrict__ q4, const ulonglong4 *__restrict__ rec, int n,
+                 const int *__restrict__ row_ptr, const int *__restrict__ col, MixedParams P,
+                 float G1, float G2, float H1, float H2, float S1, float S2,
+                 double *__restrict__ gq4, double *__restrict__ partial)
 {
     constexpr int TPI = kVjpTpi;
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / TPI;
@@ -230,21 +290,20 @@ vjp_mixed_kernel(const double *__restrict__ q4, const uint4 *__restrict__ rel,
     float es = 0.f, ec = 0.f, ss = 0.f, sc = 0.f;  // Kahan sums of g (d.w), dg/dsigma (d.w)
     if (gid < n) {
         const int i = gid;
-        const uint4 pi = rel[i];
-        double Rxd, Ryd, Rzd;
-        load_r3(R4, i, Rxd, Ryd, Rzd);
-        const float Rxi = static_cast<float>(Rxd), Ryi = static_cast<float>(Ryd),
-                    Rzi = static_cast<float>(Rzd);
+        const MixedVjpRec ri = load_mixed_vjp_rec(rec, i);
         float sx = 0.f, sy = 0.f, sz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
         const int kb = row_ptr[i], ke = row_ptr[i + 1];
+        auto col_at = [&](int k) { return k < ke ? __ldg(col + k) : i; };
+        int j = col_at(kb + sub);
+        MixedVjpRec rj = load_mixed_vjp_rec(rec, j);
+        int jn = col_at(kb + sub + TPI);
         for (int base = kb; base < ke; base += TPI) {
-            const int k = base + sub;
-            const bool valid = k < ke;
-            const int j = valid ? col[k] : i;
-            const uint4 pj = rel[j];
-            const float dx = fixed_disp(pj.x, pi.x, P.scale[0]);
-            const float dy = fixed_disp(pj.y, pi.y, P.scale[1]);
-            const float dz = fixed_disp(pj.z, pi.z, P.scale[2]);
+            const MixedVjpRec rn = load_mixed_vjp_rec(rec, jn);
+            const int jnn = col_at(base + sub + 2 * TPI);
+            const bool valid = base + sub < ke;
+            const float dx = fixed_disp(rj.X, ri.X, P.scale[0]);
+            const float dy = fixed_disp(rj.Y, ri.Y, P.scale[1]);
+            const float dz = fixed_disp(rj.Z, ri.Z, P.scale[2]);
             float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             bool in = valid && s < P.rc2f;
             const bool near = valid && fabsf(s - P.rc2f) <= P.band;
@@ -261,15 +320,12 @@ vjp_mixed_kernel(const double *__restrict__ q4, const uint4 *__restrict__ rel,
             }
             if (!valid) s = 1.0f;
             if (in) {
-                double Rxj, Ryj, Rzj;
-                load_r3(R4, j, Rxj, Ryj, Rzj);
                 const float u = rcp_fp32(s);
                 const float u2 = u * u, u3 = u2 * u, u4 = u2 * u2, u5 = u4 * u;
                 const float g = u4 * fmaf(G1, u3, -G2);
                 const float gp = u5 * fmaf(-H1, u3, H2);
                 const float dgs = u4 * fmaf(S1, u3, -S2);
-                const float wx = static_cast<float>(Rxj) - Rxi, wy = static_cast<float>(Ryj) - Ryi,
-                            wz = static_cast<float>(Rzj) - Rzi;
+                const float wx = rj.rx - ri.rx, wy = rj.ry - ri.ry, wz = rj.rz - ri.rz;
                 const float rw = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
                 const float t = 2.0f * gp * rw;
                 const float cx = fmaf(g, wx, t * dx), cy = fmaf(g, wy, t * dy), cz = fmaf(g, wz, t * dz);
@@ -279,19 +335,22 @@ vjp_mixed_kernel(const double *__restrict__ q4, const uint4 *__restrict__ rel,
                 kahan_add(es, ec, g * rw);
                 kahan_add(ss, sc, dgs * rw);
                 if (HALF) {
-                    atomicAdd(gq4 + 4 * static_cast<int64_t>(j) + 0, static_cast<double>(cx));
-                    atomicAdd(gq4 + 4 * static_cast<int64_t>(j) + 1, static_cast<double>(cy));
-                    atomicAdd(gq4 + 4 * static_cast<int64_t>(j) + 2, static_cast<double>(cz));
+                    atomicAdd(gq4 + 4 * static_cast<int64_t>(j) + 0, f32_to_f64(cx));
+                    atomicAdd(gq4 + 4 * static_cast<int64_t>(j) + 1, f32_to_f64(cy));
+                    atomicAdd(gq4 + 4 * static_cast<int64_t>(j) + 2, f32_to_f64(cz));
                 }
             }
+            rj = rn;
+            j = jn;
+            jn = jnn;
         }
         group_kahan<TPI>(sx, kx);
         group_kahan<TPI>(sy, ky);
         group_kahan<TPI>(sz, kz);
         if (sub == 0) {
-            const double ax = static_cast<double>(sx) - static_cast<double>(kx);
-            const double ay = static_cast<double>(sy) - static_cast<double>(ky);
-            const double az = static_cast<double>(sz) - static_cast<double>(kz);
+            const double ax = f32_to_f64(sx) - f32_to_f64(kx);
+            const double ay = f32_to_f64(sy) - f32_to_f64(ky);
+            const double az = f32_to_f64(sz) - f32_to_f64(kz);
             double *g = gq4 + 4 * static_cast<int64_t>(i);
             if (HALF) {
                 atomicAdd(g + 0, ax);
@@ -360,7 +419,7 @@ extern "C" size_t lj_force_vjp_workspace_bytes(int64_t n, int precision)
 {
     const size_t blocks = size_t(lj::vjp_blocks(n > 0 ? n : 1));
     size_t bytes = 2 * blocks * sizeof(double) + 256;
-    if (precision == LJ_MIXED) bytes += size_t(n > 0 ? n : 1) * sizeof(uint4) + 256;
+    if (precision == LJ_MIXED) bytes += size_t(n > 0 ? n : 1) * sizeof(ulonglong4) + 256;
     if (precision == LJ_FP64) bytes += size_t(n > 0 ? n : 1) * sizeof(longlong4) + 256;
     if (precision == LJ_DFLOAT) bytes += lj::vjp_dfloat_extra_bytes(n) + 256;
     return bytes;
@@ -423,17 +482,18 @@ extern "C" int lj_force_vjp(const double *q4_dev, const double *gradF4_dev, int6
     } else {
         const MixedParams P = make_mixed_params(box, 1.0, r_cut, eps, sigma);
         const VjpCoef C = make_coef(eps, sigma);
-        uint4 *rel = c.take<uint4>(size_t(n));
-        mixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, ni, P, rel);
-        LJ_TRY_LAUNCH("mixed_prepass_kernel");
+        ulonglong4 *rec = c.take<ulonglong4>(size_t(n));
+        vjp_mixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, gradF4_dev, ni,
+                                                                            P, rec);
+        LJ_TRY_LAUNCH("vjp_mixed_prepass_kernel");
         const float G1 = float(C.G1), G2 = float(C.G2), H1 = float(C.H1), H2 = float(C.H2),
                     S1 = float(C.S1), S2 = float(C.S2);
         if (half)
-            vjp_mixed_kernel<true><<<blocks, kVjpThreads, 0, st>>>(q4_dev, rel, gradF4_dev, ni, row_ptr_dev,
+            vjp_mixed_kernel<true><<<blocks, kVjpThreads, 0, st>>>(q4_dev, rec, ni, row_ptr_dev,
                                                                     col_dev, P, G1, G2, H1, H2, S1, S2,
                                                                     gradq4_dev, partial);
         else
-            vjp_mixed_kernel<false><<<blocks, kVjpThreads, 0, st>>>(q4_dev, rel, gradF4_dev, ni, row_ptr_dev,
+            vjp_mixed_kernel<false><<<blocks, kVjpThreads, 0, st>>>(q4_dev, rec, ni, row_ptr_dev,
                                                                      col_dev, P, G1, G2, H1, H2, S1, S2,
                                                                      gradq4_dev, partial);
         LJ_TRY_LAUNCH("vjp_mixed_kernel");

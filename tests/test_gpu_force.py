@@ -207,6 +207,30 @@ def test_fp64_box_wider_than_1024_cutoffs(cuda_lib, oracle_lib):
         assert _relerr(out[k * s.n:(k + 1) * s.n, :3], want) <= FP64_TOL
 
 
+@pytest.mark.parametrize("half", [True, False])
+@pytest.mark.parametrize("tpi", [2056, 2052, 2064])
+def test_fp64_rare_lanes(cuda_lib, oracle_lib, half, tpi):
+    """The fixed-point row's rare lanes: an extra atom 1e-11 from atom 0 (a
+    squared distance far below the branch-free conversion's range and below
+    the seeded reciprocal's, so the general conversion and a division serve
+    that pair), in a box of 8 sigma whose other entries fall on both sides of
+    the conversion's two paths.  The close pair's impulse (~1e142) is checked
+    on its two atoms, every other atom against its own scale."""
+    lj = cuda_lib
+    s = inputs.fcc_system(5, 1.0, 0.05, seed=21)      # L = 7.94, 500 atoms
+    q = np.vstack([s.q, s.q[:1]])
+    q[-1, 0] += 1e-11
+    c = inputs.LJSystem(q=q, box=s.box, rho=s.rho)
+    got, _ = _run(lj, c, half, 0, tpi)
+    want = _oracle(oracle_lib, c, half)
+    pair = [0, c.n - 1]
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got[pair] - want[pair])) <= FP64_TOL * np.max(np.abs(want[pair]))
+    rest = np.ones(c.n, dtype=bool)
+    rest[pair] = False
+    assert _relerr(got[rest], want[rest]) <= FP64_TOL
+
+
 def test_newton_third_law_half_list(cuda_lib, small):
     got, _ = _run(cuda_lib, small, True, 0, 2056)
     assert np.max(np.abs(got.sum(axis=0))) < 1e-12 * np.abs(got).sum()
