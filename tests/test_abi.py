@@ -181,3 +181,31 @@ def test_package_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
                 assert "lj_oracle" not in text, f
+
+
+def test_measurement_entry_points_check_arguments_without_gpu():
+    """lj_measure_peak and lj_eval_reciprocal refuse bad arguments before any
+    CUDA call (so these run on a machine without a GPU)."""
+    from paper_1806_05713_gb300 import lj
+    L = lj.load()
+    rate, ms = ctypes.c_double(-1.0), ctypes.c_double(-1.0)
+    peak = lambda kind=lj.LJ_PEAK_DFMA, buf=None, nb=0, work=1, r=True, m=True: L.lj_measure_peak(
+        kind, buf, nb, work, ctypes.byref(rate) if r else None, ctypes.byref(ms) if m else None, None)
+    assert peak(kind=-1) == lj.LJ_ERR_ARG
+    assert peak(kind=4) == lj.LJ_ERR_ARG
+    assert peak(work=0) == lj.LJ_ERR_ARG
+    assert peak(r=False) == lj.LJ_ERR_ARG
+    assert peak(m=False) == lj.LJ_ERR_ARG
+    # the L2 probe needs a 256-byte aligned buffer, a multiple of 4096 bytes
+    assert peak(kind=lj.LJ_PEAK_L2_READ) == lj.LJ_ERR_ARG
+    assert peak(kind=lj.LJ_PEAK_L2_READ, buf=ctypes.c_void_p(4096), nb=4000) == lj.LJ_ERR_ARG
+    assert peak(kind=lj.LJ_PEAK_L2_READ, buf=ctypes.c_void_p(4096 + 64), nb=8192) == lj.LJ_ERR_ARG
+    assert rate.value == 0.0 and ms.value == 0.0
+    fake = ctypes.c_void_p(4096)
+    assert L.lj_eval_reciprocal(-1, fake, 10, fake, None, None) == lj.LJ_ERR_ARG
+    assert L.lj_eval_reciprocal(6, fake, 10, fake, None, None) == lj.LJ_ERR_ARG
+    assert L.lj_eval_reciprocal(lj.LJ_RCP_FP32, fake, -1, fake, None, None) == lj.LJ_ERR_ARG
+    assert L.lj_eval_reciprocal(lj.LJ_RCP_FP32, None, 10, fake, None, None) == lj.LJ_ERR_ARG
+    assert L.lj_eval_reciprocal(lj.LJ_RCP_FP32, ctypes.c_void_p(4100), 10, fake, None, None) == \
+        lj.LJ_ERR_ARG
+    assert L.lj_eval_reciprocal(lj.LJ_RCP_DF2, None, 0, None, None, None) == lj.LJ_OK
