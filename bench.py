@@ -406,6 +406,8 @@ def schedule_name(tpi: int) -> str:
         name += ", image-selected displacement"
     if tpi & 2048:
         name += ", exact fixed-point displacement"
+    if tpi & 8192:
+        name = f"{max(t, 1)} rows/warp, their entries in one chunk per lane, exact fixed-point displacement"
     return name
 
 
@@ -912,7 +914,7 @@ def extra_paper(lj, dev, stream, flush, oracle_dp):
             m_half = pl.nnz if half else pl.nnz // 2
             entry = {"list_build_ms": t_list, "pairs_per_call": m_half}
             for name, prec in FORMS:
-                tpis = (2056, 2052, 2064, 2568, 1032) if prec == 0 else FORM_CANDIDATES[prec]
+                tpis = (10272, 10256, 10248, 2056, 2052, 2064, 2568, 1032) if prec == 0 else FORM_CANDIDATES[prec]
                 if prec == 0:
                     for t in tpis:
                         pp = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
@@ -960,7 +962,7 @@ def extra_small(lj, dev, stream, flush, want):
     pl = lj.lj_build_pairlist(q, box, s.rs, True)
     res = {"n_atoms": s.n, "pairs_per_call": pl.nnz}
     for name, prec in FORMS:
-        tpis = (2056,) if prec == 0 else FORM_CANDIDATES[prec]
+        tpis = (2056, 2052) if prec == 0 else FORM_CANDIDATES[prec]
         ms, t, pp = best_form_call(lj, q, pl, box, s.rc, prec, tpis, stream, flush, dev)
         res[name] = {"schedule": schedule_name(t), "ms_per_call": ms,
                      **err_stats(pp[:, :3].cpu().numpy(), want)}
@@ -983,7 +985,8 @@ def extra_batched(lj, dev, stream, flush, oracle_dp):
            "oracle_systems": list(BATCH_SAMPLE)}
     for name, prec in FORMS:
         b = Batch(systems, DT, prec, True, tpi=8, rows_per_item=64, plan_rows_min=16)
-        tpi, rows, _ = b.autotune(tpis=(4, 8, 16), rows=(16, 32, 64, 128), reps=3,
+        tpis = (4, 8, 16, lj.LJ_SCHED_STREAM) if prec == lj.LJ_FP64 else (4, 8, 16)
+        tpi, rows, _ = b.autotune(tpis=tpis, rows=(16, 32, 64, 128), reps=3,
                                   layouts=(True, False))
         g = b.capture_graph()
         t_graph = time_calls(g.replay, stream, flush, 10, 2)
@@ -996,7 +999,8 @@ def extra_batched(lj, dev, stream, flush, oracle_dp):
         out_p = b.p4.cpu().numpy()
         errs = [err_stats(out_p[int(b.atom_offset[k]):int(b.atom_offset[k]) + systems[k].n, :3], w)
                 for k, w in zip(BATCH_SAMPLE, oracle_dp)]
-        res[name] = {"tpi": tpi, "rows_per_item": rows, "list": "half" if b.half else "full",
+        res[name] = {"tpi": "stream" if tpi == lj.LJ_SCHED_STREAM else tpi,
+                     "rows_per_item": rows, "list": "half" if b.half else "full",
                      "pairs_per_call": b.pairs,
                      "graph_persistent_ms": t_graph,
                      "graph_persistent_pairs_per_s": b.pairs / (t_graph / 1e3),

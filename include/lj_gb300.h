@@ -74,8 +74,10 @@ extern "C" {
 /* ---- schedules ---------------------------------------------------------- */
 /* `tpi` = threads per i-row: 1, 2, 4, 8, 16 or 32 lanes of one warp walk one
  * row and reduce their partial sums with warp shuffles; 0 = library default
- * (FP64: LJ_SCHED_FIXED | 8; mixed: 8 lanes per row; double-float:
- * LJ_SCHED_SWP2 | 8). */
+ * (FP64: LJ_SCHED_FIXED | LJ_SCHED_STREAM | 32 for a half list of at least
+ * 524,288 rows, else LJ_SCHED_FIXED | 8 -- image selection instead of the
+ * fixed point for boxes wider than 1024 r_c; mixed: 8 lanes per row;
+ * double-float: LJ_SCHED_SWP2 | 8). */
 #define LJ_TPI_AUTO 0
 /* LJ_SCHED_SWP2 | tpi (tpi = 4, 8 or 16; FP64 with the IEEE-bit-pattern
  * displacement, LJ_MIXED and LJ_DFLOAT): software pipelining, the paper's
@@ -103,6 +105,14 @@ extern "C" {
  * boxes return LJ_ERR_ARG, and the default schedule, lj_force_energy,
  * lj_force_vjp and lj_force_batched use image selection there. */
 #define LJ_SCHED_FIXED 2048
+/* LJ_SCHED_FIXED | LJ_SCHED_STREAM | r (r = 4, 8, 16 or 32; FP64 only): the
+ * fixed-point rows above, but a warp owns r consecutive rows and cuts their
+ * entries (contiguous in CSR) into 32 equal chunks, one per lane, each lane
+ * moving forward through the row boundaries of its chunk; lanes idle only
+ * in the padding of the last chunk instead of at the end of every row.
+ * p_i is added with FP64 atomics by every lane whose chunk meets the row,
+ * so full lists are not deterministic under this schedule. */
+#define LJ_SCHED_STREAM 8192
 
 const char *lj_status_string(int status);
 /* Text of the last CUDA error seen by this library in this thread. */
@@ -224,12 +234,13 @@ size_t lj_force_workspace_bytes(int64_t n, const double box[3], int precision);
  *                   LJ_SCHED_SORTED may be or-ed into any of these,
  *                   LJ_SCHED_IMAGES into the FP64 4, 8, 16 and SWP2
  *                   schedules; LJ_SCHED_FIXED | 4, 8, 16 (FP64, optionally |
- *                   LJ_SCHED_SORTED).
+ *                   LJ_SCHED_SORTED); LJ_SCHED_FIXED | LJ_SCHED_STREAM | 4,
+ *                   8, 16, 32 (FP64).
  *  workspace_dev    scratch of lj_force_workspace_bytes() (NULL if 0).
  * Half lists add p_j with FP64 atomics, so their rounding order (not their
  * value beyond the last bits) varies between calls; full lists are
- * deterministic (except, for LJ_DFLOAT, rows with two or more pairs that
- * take the FP64 formula).
+ * deterministic (except under LJ_SCHED_STREAM and, for LJ_DFLOAT, rows with
+ * two or more pairs that take the FP64 formula).
  * LJ_DFLOAT agrees with LJ_FP64 to ~1e-14 of max |dp|; it returns
  * LJ_ERR_ARG if 24 eps sigma^6 dt / r_c^7 is outside 2^-690 .. 2^690.
  * Asynchronous.  Errors: LJ_ERR_ARG, LJ_ERR_BOX, LJ_ERR_CAPACITY (workspace
@@ -448,7 +459,8 @@ typedef struct lj_batch {
     double dt;
     int32_t nsys;
     int32_t precision;
-    int32_t tpi;           /* lanes per row: 1, 2, 4, 8, 16, 32 */
+    int32_t tpi;           /* lanes per row: 1, 2, 4, 8, 16, 32; or LJ_SCHED_STREAM
+                              (FP64): each work item's rows walked as one stream */
     int32_t rows_per_item; /* rows per work item (>= 1) */
     int32_t blocks;        /* persistent grid size */
     int32_t flags;         /* bit 0: every system has a cubic box */
@@ -462,7 +474,9 @@ size_t lj_batch_plan_bytes(const lj_system *systems, int nsys, int rows_per_item
  * (items of at most rows_per_item rows of one system, ordered by decreasing
  * estimated cost nnz/n * rows, the longest-first rule), and copy it and the
  * per-system constants of Algorithm 1 (dt, eps, sigma, cutoff, box) to
- * plan_dev.  precision: LJ_FP64, LJ_MIXED or LJ_DFLOAT (tpi 4, 8 or 16; two
+ * plan_dev.  precision: LJ_FP64 (tpi 1 .. 32, or LJ_SCHED_STREAM: the warp
+ * that takes an item walks its rows' entries as one stream, as lj_force's
+ * LJ_SCHED_STREAM), LJ_MIXED (tpi 1 .. 32) or LJ_DFLOAT (tpi 4, 8 or 16; two
  * entries per lane in packed f32x2 registers).  Blocks until the copy is
  * done.  Errors: LJ_ERR_ARG, LJ_ERR_BOX, LJ_ERR_CAPACITY (plan_bytes too
  * small), LJ_ERR_CUDA.
@@ -511,7 +525,8 @@ int lj_autotune_force(const double *q4_dev, double *p4_scratch_dev, int64_t n,
  * candidate lists (re-initialising the plan in plan_dev for each), `reps`
  * times each, on p4_scratch_dev; return the fastest pair and its median
  * time.  plan_bytes must hold the plan for the smallest rows_per_item and
- * the workspace must be sized for the batch.  Synchronous.
+ * the workspace must be sized for the batch.  Candidates the precision does
+ * not accept are skipped (LJ_ERR_ARG if none is left).  Synchronous.
  */
 int lj_autotune_batched(const lj_system *systems, int nsys, double dt, int precision,
                         const int *tpis, int n_tpi, const int *rows_per_item, int n_rpi,

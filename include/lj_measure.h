@@ -64,10 +64,9 @@ int lj_measure_peak(int kind, void *buf_dev, size_t buf_bytes, int64_t work, dou
 /* ======================================================================== */
 
 /* Kinds for lj_eval_reciprocal.  Each evaluates, element by element, the
- * very device function the force kernels inline. */
-#define LJ_RCP_FP64_SEEDED 0 /* 1/a: double-float seed on the FP32 pipe + one FP64
-                                Newton step (the default FP64 kernel); defined for
-                                2^-69 <= a < 2^120 */
+ * very device function the force kernels inline.  Kind 0 (a double-float
+ * seed with one FP64 Newton step, replaced by LJ_RCP_FP64_INT) is retired
+ * and refused. */
 #define LJ_RCP_FP64_FAST 1   /* 1/a: FP32 seed + one third-order FP64 correction
                                 (the image-selected FP64 kernels); defined for
                                 2^-126 <= a < 2^126 */
@@ -80,6 +79,10 @@ int lj_measure_peak(int kind, void *buf_dev, size_t buf_bytes, int64_t work, dou
                                 lane (the DFLOAT kernels' default) */
 #define LJ_RCP_FP32 5        /* 1/a in FP32: hardware approximation + one Newton
                                 step (the mixed kernels) */
+#define LJ_RCP_FP64_INT 6    /* 1/a: FP32 seed + one second-order Newton step in
+                                integer arithmetic, no FP64 instruction (the
+                                fixed-point FP64 kernels); within 0.5 + 2^-12 ulp
+                                for 2^-119 <= a < 2^120 */
 
 /*
  * The paper proposes, as future work for its AVX-512 kernels, replacing the

@@ -184,7 +184,9 @@ class Batch:
 
     def _autotune_layout(self, tpis, rows, reps):
         if tpis is None:
-            tpis = (4, 8, 16) if self.precision == lj.LJ_DFLOAT else (2, 4, 8, 16)
+            tpis = ((4, 8, 16) if self.precision == lj.LJ_DFLOAT else
+                    (2, 4, 8, 16, lj.LJ_SCHED_STREAM) if self.precision == lj.LJ_FP64 else
+                    (2, 4, 8, 16))
         scratch = torch.zeros_like(self.p4)
         ta = (ctypes.c_int * len(tpis))(*tpis)
         ra = (ctypes.c_int * len(rows))(*rows)

@@ -172,8 +172,8 @@ extern "C" int lj_md_steps(double *q4_dev, double *p4_dev, int64_t n, int32_t *r
         return LJ_ERR_ARG;
     if (energies_dev && precision != LJ_FP64) return LJ_ERR_ARG;
     int t = tpi;
-    const int rc = force_check(q4_dev, p4_dev, n, row_ptr_dev, col_dev, nnz, dt, r_cut, box, eps,
-                               sigma, precision, &t, workspace_dev, workspace_bytes);
+    const int rc = force_check(q4_dev, p4_dev, n, row_ptr_dev, col_dev, nnz, half, dt, r_cut, box,
+                               eps, sigma, precision, &t, workspace_dev, workspace_bytes);
     if (rc != LJ_OK) return rc;
     if (energies_dev && workspace_bytes < lj_force_energy_workspace_bytes(n)) return LJ_ERR_CAPACITY;
     if (n == 0 || steps == 0) return LJ_OK;

@@ -13,12 +13,15 @@
 //   r^2 = (D_x^2 + D_y^2 + D_z^2) 2^-2k exact in 128-bit integers,
 // each rounded once to double with integer instructions.  The FP64
 // definition rounds d = x_j - x_i (and the wrap) and the three products and
-// sums of r^2; these values are at least as accurate.  Everything after --
-// 1/r^2, the powers, df, df d and the momentum sums -- is the FP64 form's
-// IEEE double arithmetic, unchanged: 14 FP64 instructions per entry (half
-// list).  Entries whose r^2 lies within 64 ulp of r_c^2 take the FP64
-// definition for the decision and the displacement, so the interacting set
-// and every pair near the cutoff are the oracle's.
+// sums of r^2; these values are at least as accurate.  1/r^2 is formed
+// with integer instructions too (rcp_fp64_int: within 0.5 + 2^-12 ulp), and
+// the rest -- the powers, df, df d and the momentum sums -- is the FP64
+// form's IEEE double arithmetic: 11 FP64 instructions per entry of a half
+// list (3 powers, 2 for df, 3 for df d, 3 for the row's sum; 8 for a full
+// list, whose products df d fuse into the sum).  Entries whose r^2 lies
+// within 64 ulp of r_c^2 take the FP64 definition for the decision and the
+// displacement, so the interacting set and every pair near the cutoff are
+// the oracle's.
 #pragma once
 
 #include <cmath>
@@ -104,18 +107,6 @@ __device__ __forceinline__ unsigned long long round53(unsigned long long top, un
     return top + ((rem > half || (rem == half && (top & 1ull))) ? 1ull : 0ull);
 }
 
-// v 2^-k rounded to the nearest double (|v| < 2^63), integer instructions.
-__device__ __forceinline__ double fixed_to_f64(long long v, int k)
-{
-    if (v == 0) return 0.0;
-    const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
-    const unsigned long long a = static_cast<unsigned long long>(v < 0 ? -v : v);
-    const int n = 64 - __clzll(static_cast<long long>(a));
-    if (n <= 53) return assemble_f64(a << (53 - n), n, k, sign);
-    const int sh = n - 53;
-    return assemble_f64(round53(a >> sh, a & ((1ull << sh) - 1ull), 1ull << (sh - 1)), n, k, sign);
-}
-
 // (hi 2^64 + lo) 2^-k2 rounded to the nearest double, integer instructions.
 __device__ __forceinline__ double fixed128_to_f64(unsigned long long hi, unsigned long long lo, int k2)
 {
@@ -151,11 +142,11 @@ __device__ __forceinline__ double fixed128_to_f64(unsigned long long hi, unsigne
     return assemble_f64(round53(top, rem, half), n, k2, 0ull);
 }
 
-// fixed_to_f64 without branches: both the exact path (|v| < 2^53, shifted
-// up into the significand) and the rounded one (|v| >= 2^53, round to
-// nearest even) are computed and one is selected, so the lanes of a warp
-// never diverge on the magnitude of their displacement.  Same values as
-// fixed_to_f64.
+// v 2^-k rounded to the nearest double (|v| < 2^63) with integer
+// instructions and no branch: both the exact path (|v| < 2^53, shifted up
+// into the significand) and the rounded one (|v| >= 2^53, round to nearest
+// even) are computed and one is selected, so the lanes of a warp never
+// diverge on the magnitude of their displacement.
 __device__ __forceinline__ double fixed_to_f64_sel(long long v, int k)
 {
     const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
@@ -204,58 +195,67 @@ __device__ __forceinline__ double fixed128_to_f64_hi(unsigned long long hi, unsi
     return assemble_f64(m, n, k2, 0ull);
 }
 
-// 1/a in double for 2^-69 <= a < 2^120 from a seed good to ~2^-45 and one
-// Newton step (two FP64 instructions instead of rcp_fp64's three).  The
-// seed is built off the FP64 pipe: a split by its bits into a head float
-// (24 leading bits) and a tail float (the next 29 bits, rounded), the
-// head's FP32 reciprocal y refined on the FP32 pipe to y + y (t + t^2) with
-// t = 1 - a y (the reciprocal of a double-float number), and y and its
-// correction joined into one double with integer instructions.  Outside
-// the range the caller divides (a warp-uniform branch).
-__device__ __forceinline__ double rcp_fp64_seeded(double a, bool &ok)
+// The range of rcp_fp64_int: 2^kRcpIntLo <= a < 2^kRcpIntHi.
+constexpr int kRcpIntLo = -119;
+constexpr int kRcpIntHi = 120;
+
+// 1/a in double for 2^-119 <= a < 2^120 without an FP64 instruction: one
+// Newton step, carried to second order, in integer arithmetic on the
+// significands.  The seed y is the FP32 approximate reciprocal of a's
+// leading 24 bits, so r = 1 - a y is about 2^-22 in magnitude.  With
+// a = A 2^(ea-52) and y = Y 2^(ey-23) (A, Y the integer significands),
+// a y = A Y 2^-S with S = 75 - ea - ey (75 or 76), and the residual
+// E = 2^S - A Y = 2^S r is below 2^57 in magnitude: it is the low 64 bits
+// of -A Y read as a signed number, exactly.  Then
+// 1/a = y / (1 - r) = y (1 + r + r^2 + r^3 + ...); the terms
+// z1 = Y 2^29 r, z2 = z1 r and z3 = z2 r are formed in integers in units of
+// 2^-14 of the ulp of Y 2^29 (z1 from the exact product Y E, z2 and z3 from
+// E's leading bits), and u = Y 2^29 + z1 + z2 + z3 is rounded to 53 bits in
+// the binade it falls in.  The truncations and the dropped r^4 term leave u
+// within about 2^-12 ulp of 1/a, so the result is within 0.5 + 2^-12 ulp
+// (and correctly rounded unless 1/a lies that close to a midpoint).  It
+// takes a few dozen integer instructions where an FP64 Newton step takes
+// two FP64 ones, and leaves the FP64 pipe -- the limit of the FP64 force
+// kernels -- to the force arithmetic.  `ok` is false outside the range.
+__device__ __forceinline__ double rcp_fp64_int(double a, bool &ok)
 {
     const long long b = __double_as_longlong(a);
-    const int ea = static_cast<int>((b >> 52) & 0x7ff) - 1023;  // a in [2^ea, 2^(ea+1))
-    ok = ea > -70 && ea < 120;  // head, tail and y stay normal floats
+    const int ea = static_cast<int>((b >> 52) & 0x7ff) - 1023;
+    ok = ea >= kRcpIntLo && ea < kRcpIntHi;  // the head and y stay normal floats
     const int e = ok ? ea : 0;
-    const unsigned long long mant = static_cast<unsigned long long>(b) & 0xfffffffffffffull;
-    // head: 1.m[51:29] 2^e exactly; tail: m[28:0] 2^(e-52)
+    const unsigned long long A =
+        (static_cast<unsigned long long>(b) & 0xfffffffffffffull) | 0x10000000000000ull;
     const float head = __uint_as_float(static_cast<unsigned>((e + 127) << 23) |
-                                       static_cast<unsigned>(mant >> 29));
-    const float tail = __fmul_rn(__uint2float_rn(static_cast<unsigned>(mant & 0x1fffffffull)),
-                                 __uint_as_float(static_cast<unsigned>((e - 52 + 127) << 23)));
+                                       static_cast<unsigned>((A >> 29) & 0x7fffffull));
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(head));
-    float t = __fmaf_rn(-head, y, 1.0f);
-    t = __fmaf_rn(-tail, y, t);
-    const float q = __fmul_rn(y, t);
-    const float l = __fmaf_rn(q, t, q);  // 1/a ~ y + l, |l| < 2^-21 y
-    // y + l as a double: y's 24-bit significand at bit 52, l added at its
-    // binary point (integer add of the two aligned significands).  For large
-    // a the correction l is a subnormal float (|l| ~ 2^-22 / a falls below
-    // 2^-126 once a passes ~2^104, earlier when y is already close): it then
-    // has no implicit bit and the exponent of the smallest normal, and its
-    // absolute resolution 2^-149 still leaves the seed within 2^-31 of 1/a
-    // up to a < 2^120, which the Newton step squares to below an ulp.
-    const unsigned uy = __float_as_uint(y), ul = __float_as_uint(l);
-    const int ey = static_cast<int>((uy >> 23) & 0xff);
-    const int el = static_cast<int>((ul >> 23) & 0xff);
-    long long my = static_cast<long long>((uy & 0x7fffffu) | 0x800000u) << 29;
-    const int sh = 29 - (ey - (el ? el : 1));  // where l's significand lands
-    long long ml = static_cast<long long>((ul & 0x7fffffu) | (el ? 0x800000u : 0u));
-    ml = sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> -sh) : 0);
-    my += (ul >> 31) ? -ml : ml;
-    long long eb = static_cast<long long>(ey) - 127 + 1023;
-    if (my >= (1ll << 53)) {
-        my >>= 1;
-        ++eb;
-    } else if (my < (1ll << 52)) {
-        my <<= 1;
-        --eb;
-    }
-    const double x0 = __longlong_as_double((eb << 52) | (my & 0xfffffffffffffll));
-    const double r = fma(-a, x0, 1.0);
-    return fma(x0, r, x0);
+    const unsigned uy = __float_as_uint(y);
+    const int ey = static_cast<int>((uy >> 23) & 0xff) - 127;
+    const unsigned Y = (uy & 0x7fffffu) | 0x800000u;
+    const int S = 75 - e - ey;
+    const long long E = -static_cast<long long>(A * static_cast<unsigned long long>(Y));
+    // Q = floor(Y E / 2^32) = 2^(S-61) z1, from two 32 x 32 -> 64-bit products
+    const long long Q = static_cast<long long>(Y) * (E >> 32) +
+                        static_cast<long long>((static_cast<unsigned long long>(Y) *
+                                                (static_cast<unsigned long long>(E) & 0xffffffffull)) >> 32);
+    const long long z1 = Q >> (S - 75);  // 2^14 z1 (Q carries S - 61 = 14 or 15 fraction bits)
+    const int Qh = static_cast<int>(Q >> 18);
+    const int Eh = static_cast<int>(E >> 26);
+    const long long z2 = (static_cast<long long>(Qh) * Eh) >> (2 * S - 119);       // 2^14 z2
+    const long long z3 = (static_cast<long long>(static_cast<int>(z2)) * Eh) >> (S - 26);  // 2^14 z3
+    const long long D = z1 + z2 + z3;
+    const long long base = static_cast<long long>(Y) << 29;
+    const long long fl = base + (D >> 14);  // floor(u)
+    long long m = base + ((D + (1ll << 13)) >> 14);
+    int ed = ey;
+    const bool up = fl >= (1ll << 53), lo = fl < (1ll << 52);
+    m = up ? (base >> 1) + ((D + (1ll << 14)) >> 15) : m;  // u in [2^53, 2^54): round u / 2
+    m = lo ? 2 * base + ((D + (1ll << 12)) >> 13) : m;     // u below 2^52: round 2 u
+    ed += up ? 1 : (lo ? -1 : 0);
+    const bool carry = m == (1ll << 53);
+    m = carry ? (1ll << 52) : m;
+    ed += carry ? 1 : 0;
+    return __longlong_as_double((static_cast<long long>(ed + 1023) << 52) | (m & 0xfffffffffffffll));
 }
 
 // 1/sqrt(a) in double for 2^-120 < a < 2^120: the FP32 approximation of the
@@ -275,16 +275,6 @@ __device__ __forceinline__ double rsqrt_fp64(double a)
 #pragma unroll
     for (int it = 0; it < 2; ++it) y = fma(y, fma(-h, y * y, 0.5), y);
     return y;
-}
-
-__device__ __forceinline__ double rcp_fp64_fixed(double a, unsigned mask)
-{
-    bool ok;
-    double x = rcp_fp64_seeded(a, ok);
-    if (__any_sync(mask, !ok)) {
-        if (!ok) x = 1.0 / a;
-    }
-    return x;
 }
 
 // |D|^2 summed over three axes as a 128-bit integer (|D| <= 2^60 each).
@@ -309,50 +299,13 @@ __device__ __forceinline__ void norm2_fixed(long long dx, long long dy, long lon
 // The exact fixed-point displacement of entry j of row i (see the header
 // comment): d in double, r^2 in double (1.0 for an invalid lane), and the
 // FP64 definition's d, r^2 and decision for entries within 64 ulp of r_c^2.
-// Returns whether the pair interacts.  Every lane of gm calls it.
-__device__ __forceinline__ bool fixed_entry(const double *__restrict__ q4, long long xi, long long yi,
-                                            long long zi, long long xj, long long yj, long long zj,
-                                            bool valid, int i, int j, const Fp64Params &P,
-                                            const FixParams &F, unsigned gm, double &dx, double &dy,
-                                            double &dz, double &r2)
-{
-    const long long Dx = wrap_fixed(xj - xi, F.M[0], F.Mh[0]);
-    const long long Dy = wrap_fixed(yj - yi, F.M[1], F.Mh[1]);
-    const long long Dz = wrap_fixed(zj - zi, F.M[2], F.Mh[2]);
-    unsigned long long hi, lo;
-    norm2_fixed(Dx, Dy, Dz, hi, lo);
-    r2 = valid ? fixed128_to_f64(hi, lo, 2 * F.k) : 1.0;
-    dx = fixed_to_f64(Dx, F.k);
-    dy = fixed_to_f64(Dy, F.k);
-    dz = fixed_to_f64(Dz, F.k);
-    const long long rb = __double_as_longlong(r2);
-    bool in = valid && rb < P.rc2_bits;
-    const bool near = valid && static_cast<unsigned long long>(rb - P.rc2_bits + 64) < 128ull;
-    if (__any_sync(gm, near)) {
-        if (near) {
-            // the FP64 definition: its displacement, its decision
-            double qxi, qyi, qzi, qxj, qyj, qzj;
-            load_xyz(q4, i, qxi, qyi, qzi);
-            load_xyz(q4, j, qxj, qyj, qzj);
-            dx = min_image(__dsub_rn(qxj, qxi), P.L[0], P.half_bits[0]);
-            dy = min_image(__dsub_rn(qyj, qyi), P.L[1], P.half_bits[1]);
-            dz = min_image(__dsub_rn(qzj, qzi), P.L[2], P.half_bits[2]);
-            in = exact_in_cutoff(dx, dy, dz, P.rc2);
-            r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-        }
-    }
-    return in;
-}
-
-// fixed_entry with one vote per entry instead of several: the common case
-// (a squared distance of at least 2^(64-2k), away from the cutoff band,
-// inside the range of the seeded reciprocal) is computed with selects only;
-// the rare lanes -- coincident or nearly coincident atoms, an entry
-// within 64 ulp of r_c^2 (the FP64 definition's decision), an r^2 outside
-// the reciprocal's range (a division) -- are handled under a single
-// group vote.  Returns whether the pair interacts; *w_div receives 1/r^2 by
-// division for the lanes that need it (and *use_div says which).  Same
-// values as fixed_entry followed by rcp_fp64_fixed.
+// The common case (a squared distance of at least 2^(64-2k), away from the
+// cutoff band, inside the range of rcp_fp64_int) is computed with selects
+// only; the rare lanes -- coincident or nearly coincident atoms, an entry
+// within 64 ulp of r_c^2, an r^2 outside the reciprocal's range (a
+// division) -- are handled under one vote of the group gm (every lane of
+// gm calls it).  Returns whether the pair interacts; *w_div receives 1/r^2
+// by division for the lanes that need it (and *use_div says which).
 __device__ __forceinline__ bool fixed_entry_sel(const double *__restrict__ q4, long long xi,
                                                 long long yi, long long zi, long long xj,
                                                 long long yj, long long zj, bool valid, int i, int j,
@@ -374,7 +327,7 @@ __device__ __forceinline__ bool fixed_entry_sel(const double *__restrict__ q4, l
     bool in = valid && rb < P.rc2_bits;
     bool near = static_cast<unsigned long long>(rb - P.rc2_bits + 64) < 128ull;
     int ea = static_cast<int>((rb >> 52) & 0x7ff) - 1023;
-    bool rcp_ok = ea > -70 && ea < 120;
+    bool rcp_ok = ea >= kRcpIntLo && ea < kRcpIntHi;
     use_div = false;
     w_div = 0.0;
     const bool special = valid && (!fast || near || !rcp_ok);
@@ -398,7 +351,7 @@ __device__ __forceinline__ bool fixed_entry_sel(const double *__restrict__ q4, l
                 r2 = fma(dz, dz, fma(dy, dy, dx * dx));
             }
             ea = static_cast<int>((__double_as_longlong(r2) >> 52) & 0x7ff) - 1023;
-            if (in && !(ea > -70 && ea < 120)) {
+            if (in && !(ea >= kRcpIntLo && ea < kRcpIntHi)) {
                 use_div = true;
                 w_div = 1.0 / r2;
             }
@@ -443,8 +396,8 @@ __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
         // no interacting entry at all is rare), lanes outside r_c on r^2 = 1.
         {
             if (!in) r2 = 1.0;
-            bool seed_ok;
-            double w = rcp_fp64_seeded(r2, seed_ok);
+            bool rcp_ok;
+            double w = rcp_fp64_int(r2, rcp_ok);
             w = use_div ? w_div : w;
             const double w2 = w * w;
             const double w4 = w2 * w2;
@@ -500,6 +453,135 @@ __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
             atomicAdd(pi + 1, ay);
             atomicAdd(pi + 2, az);
         }
+    }
+}
+
+
+// LJ_SCHED_FIXED | LJ_SCHED_STREAM | R: a warp owns R consecutive rows and
+// walks their entries as one range -- the rows of a CSR list are
+// contiguous, so entries row_ptr[i0] .. row_ptr[i0 + R] are one range --
+// cut into 32 contiguous chunks of C entries, one per lane (C a multiple of
+// 4 and the chunks aligned to 16 bytes of col, so that a lane reads four
+// column indices with one load).  Lanes idle only in the padding of the
+// range, not at the end of every row (with 8 lanes per row about 15 % of
+// the FP64 instruction slots of a random-order half list went to idle
+// lanes).  A lane finds the row of its first entry by a binary search over
+// the row pointers and then moves forward through the row boundaries; it
+// keeps the partial sum of the row it is in and adds it to p_i with FP64
+// atomics when it moves on.  A row is split over the one to three lanes
+// whose chunks it spans, so full lists are not deterministic.
+// Rows i0 .. i1-1 (i0 < i1) of the calling warp; every lane of the warp calls it.
+template <bool HALF>
+__device__ __forceinline__ void fp64_fixed_stream(const double *__restrict__ q4,
+                                                  const longlong4 *__restrict__ X,
+                                                  double *__restrict__ p4,
+                                                  const int *__restrict__ row_ptr,
+                                                  const int *__restrict__ col, int i0, int i1,
+                                                  const Fp64Params &P, const FixParams &F)
+{
+    const int lane = threadIdx.x & 31;
+    const int e0 = row_ptr[i0], e1 = row_ptr[i1];
+    if (e0 >= e1) return;  // no entries (warp-uniform)
+    // chunks start at a0 <= e0, where col + a0 is 16-byte aligned
+    const int a0 = e0 - static_cast<int>((reinterpret_cast<uintptr_t>(col + e0) >> 2) & 3u);
+    const int C = ((e1 - a0 + 127) >> 7) << 2;  // entries per lane: 32 C >= e1 - a0
+    const int s = a0 + lane * C;                // this lane's entries: [s, s + C) within [e0, e1)
+    // the row of the lane's first entry: the last row r < i1 with row_ptr[r] <= max(s, e0)
+    int row = i0;
+    {
+        const int first = max(s, e0);
+        int hi = i1;
+        while (hi - row > 1) {
+            const int mid = (row + hi) >> 1;
+            if (row_ptr[mid] <= first)
+                row = mid;
+            else
+                hi = mid;
+        }
+    }
+    int row_end = row_ptr[row + 1];
+    long long xi = 0, yi = 0, zi = 0;
+    bool loaded = false, touched = false;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    int c0 = 0, c1 = 0, c2 = 0, c3 = 0;  // the column indices of entries e .. e + 3
+    for (int k = 0; k < C; ++k) {
+        const int e = s + k;
+        if ((k & 3) == 0) {
+            if (e >= e0 && e + 4 <= e1) {
+                const int4 v = __ldg(reinterpret_cast<const int4 *>(col + e));
+                c0 = v.x;
+                c1 = v.y;
+                c2 = v.z;
+                c3 = v.w;
+            } else {
+                // the range's ends: only the indices inside [e0, e1) are read
+                c0 = (e >= e0 && e < e1) ? __ldg(col + e) : 0;
+                c1 = (e + 1 >= e0 && e + 1 < e1) ? __ldg(col + e + 1) : 0;
+                c2 = (e + 2 >= e0 && e + 2 < e1) ? __ldg(col + e + 2) : 0;
+                c3 = (e + 3 >= e0 && e + 3 < e1) ? __ldg(col + e + 3) : 0;
+            }
+        }
+        const bool valid = e >= e0 && e < e1;
+        // move to the row that holds entry e (rows may be empty)
+        while (valid && e >= row_end) {
+            if (touched) {
+                double *pr = p4 + 4 * static_cast<int64_t>(row);
+                atomicAdd(pr + 0, ax);
+                atomicAdd(pr + 1, ay);
+                atomicAdd(pr + 2, az);
+                ax = ay = az = 0.0;
+                touched = false;
+            }
+            ++row;
+            row_end = row_ptr[row + 1];
+            loaded = false;
+        }
+        if (valid && !loaded) {
+            load_fixed(X, row, xi, yi, zi);
+            loaded = true;
+        }
+        const int i = row;
+        const int j = valid ? c0 : i;
+        c0 = c1;
+        c1 = c2;
+        c2 = c3;
+        long long xj, yj, zj;
+        load_fixed(X, j, xj, yj, zj);
+        double dx, dy, dz, r2, w_div;
+        bool use_div;
+        const bool in = fixed_entry_sel(q4, xi, yi, zi, xj, yj, zj, valid, i, j, P, F, 0xffffffffu,
+                                        dx, dy, dz, r2, use_div, w_div);
+        if (!in) r2 = 1.0;
+        bool rcp_ok;
+        double w = rcp_fp64_int(r2, rcp_ok);
+        w = use_div ? w_div : w;
+        const double w2 = w * w;
+        const double w4 = w2 * w2;
+        const double w3 = w2 * w;
+        const double fn = w4 * fma(P.B, w3, -P.A);  // -df: p_i -= fn d, p_j += fn d
+        if (in) {
+            touched = true;
+            if (HALF) {
+                const double fx = fn * dx, fy = fn * dy, fz = fn * dz;
+                double *pj = p4 + 4 * static_cast<int64_t>(j);
+                atomicAdd(pj + 0, fx);
+                atomicAdd(pj + 1, fy);
+                atomicAdd(pj + 2, fz);
+                ax -= fx;
+                ay -= fy;
+                az -= fz;
+            } else {
+                ax = fma(-fn, dx, ax);
+                ay = fma(-fn, dy, ay);
+                az = fma(-fn, dz, az);
+            }
+        }
+    }
+    if (touched) {
+        double *pr = p4 + 4 * static_cast<int64_t>(row);
+        atomicAdd(pr + 0, ax);
+        atomicAdd(pr + 1, ay);
+        atomicAdd(pr + 2, az);
     }
 }
 

@@ -39,10 +39,12 @@ void count_launch();
 int check_box(const double box[3], double r_search);
 
 // Every host-side check lj_force makes before it launches (LJ_TPI_AUTO is
-// resolved into *tpi); LJ_OK or the status lj_force would return.
+// resolved into *tpi, which may depend on the list kind `half`); LJ_OK or
+// the status lj_force would return.
 int force_check(const double *q4, const double *p4, int64_t n, const int32_t *row_ptr,
-                const int32_t *col, int64_t nnz, double dt, double rc, const double box[3],
-                double eps, double sigma, int precision, int *tpi, const void *ws, size_t ws_bytes);
+                const int32_t *col, int64_t nnz, int half, double dt, double rc,
+                const double box[3], double eps, double sigma, int precision, int *tpi,
+                const void *ws, size_t ws_bytes);
 
 // Workspace carving: successive 256-byte-aligned sub-buffers of one block.
 struct Carver {

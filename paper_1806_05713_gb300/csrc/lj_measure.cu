@@ -167,9 +167,6 @@ __global__ void eval_reciprocal_kernel(int kind, const double *__restrict__ a, l
     double v = 0.0, w = 0.0;
     bool in_range = true;
     switch (kind) {
-        case LJ_RCP_FP64_SEEDED:
-            v = rcp_fp64_seeded(x, in_range);
-            break;
         case LJ_RCP_FP64_FAST:
             v = rcp_fp64_fast(x, in_range);
             break;
@@ -189,6 +186,9 @@ __global__ void eval_reciprocal_kernel(int kind, const double *__restrict__ a, l
         }
         case LJ_RCP_FP32:
             v = static_cast<double>(rcp_fp32(__double2float_rn(x)));
+            break;
+        case LJ_RCP_FP64_INT:
+            v = rcp_fp64_int(x, in_range);
             break;
         default:
             break;
@@ -260,7 +260,7 @@ extern "C" int lj_eval_reciprocal(int kind, const double *a_dev, int64_t n, doub
                                   uint8_t *ok_dev, void *stream)
 {
     using namespace lj;
-    if (kind < LJ_RCP_FP64_SEEDED || kind > LJ_RCP_FP32 || n < 0) return LJ_ERR_ARG;
+    if (kind < LJ_RCP_FP64_FAST || kind > LJ_RCP_FP64_INT || n < 0) return LJ_ERR_ARG;
     if (n == 0) return LJ_OK;
     if (!a_dev || !out_dev) return LJ_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(a_dev) | reinterpret_cast<uintptr_t>(out_dev)) & 7u)

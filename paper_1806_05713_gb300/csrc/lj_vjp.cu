@@ -178,8 +178,8 @@ vjp_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
                 load_r3(R4, j, Rxj, Ryj, Rzj);
                 double u;
                 if (FIX) {
-                    bool seed_ok;
-                    u = rcp_fp64_seeded(s, seed_ok);
+                    bool rcp_ok;
+                    u = rcp_fp64_int(s, rcp_ok);
                     u = use_div ? w_div : u;
                 } else {
                     u = rcp_fp64(s, gm);

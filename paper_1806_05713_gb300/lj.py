@@ -32,17 +32,18 @@ LJ_SCHED_SWP2 = 128
 LJ_SCHED_SORTED = 512
 LJ_SCHED_IMAGES = 1024
 LJ_SCHED_FIXED = 2048
+LJ_SCHED_STREAM = 8192
 LJ_MD_LAST_HALF_KICK = 1
 LJ_PEAK_DFMA = 0
 LJ_PEAK_FFMA = 1
 LJ_PEAK_FFMA2 = 2
 LJ_PEAK_L2_READ = 3
-LJ_RCP_FP64_SEEDED = 0
 LJ_RCP_FP64_FAST = 1
 LJ_RSQRT_FP64 = 2
 LJ_RCP_DF = 3
 LJ_RCP_DF2 = 4
 LJ_RCP_FP32 = 5
+LJ_RCP_FP64_INT = 6
 LJ_STATIC_MAX_ATOMS = 131072
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liblj_gb300.so")
@@ -381,7 +382,9 @@ def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float
         S, W, I, F = LJ_SCHED_SORTED, LJ_SCHED_SWP2, LJ_SCHED_IMAGES, LJ_SCHED_FIXED
         # the fixed-point schedules are refused (and skipped) for boxes wider
         # than 1024 r_c, where the image-selected ones take over
-        candidates = ([F | 4, F | 8, F | 16, S | F | 8, I | 4, I | 8, I | 16, I | W | 8]
+        R = LJ_SCHED_STREAM
+        candidates = ([F | 4, F | 8, F | 16, S | F | 8, F | R | 8, F | R | 16, F | R | 32, I | 4,
+                       I | 8, I | 16, I | W | 8]
                       if precision == LJ_FP64 else
                       [W | 8, W | 4, W | 16, S | W | 8, 4, 8, 16, S | 4, S | 8]
                       if precision == LJ_DFLOAT else

@@ -203,7 +203,9 @@ def test_measurement_entry_points_check_arguments_without_gpu():
     assert rate.value == 0.0 and ms.value == 0.0
     fake = ctypes.c_void_p(4096)
     assert L.lj_eval_reciprocal(-1, fake, 10, fake, None, None) == lj.LJ_ERR_ARG
-    assert L.lj_eval_reciprocal(6, fake, 10, fake, None, None) == lj.LJ_ERR_ARG
+    # kind 0 (a double-float seed with an FP64 Newton step) is retired
+    assert L.lj_eval_reciprocal(0, fake, 10, fake, None, None) == lj.LJ_ERR_ARG
+    assert L.lj_eval_reciprocal(7, fake, 10, fake, None, None) == lj.LJ_ERR_ARG
     assert L.lj_eval_reciprocal(lj.LJ_RCP_FP32, fake, -1, fake, None, None) == lj.LJ_ERR_ARG
     assert L.lj_eval_reciprocal(lj.LJ_RCP_FP32, None, 10, fake, None, None) == lj.LJ_ERR_ARG
     assert L.lj_eval_reciprocal(lj.LJ_RCP_FP32, ctypes.c_void_p(4100), 10, fake, None, None) == \

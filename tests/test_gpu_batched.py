@@ -39,6 +39,30 @@ def test_batched_matches_oracle_per_system(cuda_lib, oracle_lib, systems, precis
         assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
 
 
+@pytest.mark.parametrize("half", [True, False])
+@pytest.mark.parametrize("rows", [8, 64])
+def test_batched_stream_walk_matches_oracle(cuda_lib, oracle_lib, systems, half, rows):
+    """FP64 batch with each work item's rows walked as one stream of entries
+    (tpi = LJ_SCHED_STREAM) against the oracle, per system."""
+    from paper_1806_05713_gb300.batch import Batch
+    lj = cuda_lib
+    b = Batch(systems, 0.01, lj.LJ_FP64, half, tpi=lj.LJ_SCHED_STREAM, rows_per_item=rows,
+              plan_rows_min=8)
+    b.force()
+    torch.cuda.synchronize()
+    for s, got in zip(systems, _per_system(b, b.p4)):
+        want = _oracle_dp(oracle_lib, s, 0.01, half)
+        assert np.max(np.abs(got - want)) <= FP64_TOL * np.max(np.abs(want))
+
+
+def test_batched_stream_walk_refused_for_other_forms(cuda_lib, systems):
+    from paper_1806_05713_gb300.batch import Batch
+    lj = cuda_lib
+    for prec in (lj.LJ_MIXED, lj.LJ_DFLOAT):
+        with pytest.raises(lj.LJError):
+            Batch(systems, 0.01, prec, True, tpi=lj.LJ_SCHED_STREAM, rows_per_item=16)
+
+
 def test_batched_equals_per_system_launches_full_list(cuda_lib, systems):
     """Full lists are deterministic: the persistent launch gives the same bits
     as one lj_force call per system with the same row arithmetic (8 lanes

@@ -14,10 +14,11 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-12
 MIXED_TOL = 1e-5
 SCHEDULES = [1, 2, 4, 8, 16, 32, 132, 136, 144, 520, 644, 648, 656, 1028, 1032, 1040, 1156, 1160,
-             1168, 1544, 1672, 2052, 2056, 2064, 2568]
+             1168, 1544, 1672, 2052, 2056, 2064, 2568, 10244, 10248, 10256]
 # t lanes per row; 128|t two entries per lane (software-pipelined); 512|...
 # length-sorted rows; 1024|... image-selected displacement; 2048|... exact
-# fixed-point displacement (the default)
+# fixed-point displacement (the default); 8192|2048|r the fixed-point rows,
+# r rows per warp walked as one stream of entries
 
 
 def _run(lj, s, half, precision, tpi, dt=0.01, eps=1.0, sigma=1.0, p0=None, rc=None, pl=None):
@@ -116,7 +117,7 @@ def test_small_box_mixed_image_choice(cuda_lib, oracle_lib):
         assert _relerr(got, want) <= MIXED_TOL
 
 
-@pytest.mark.parametrize("tpi", [1032, 2056, 2568])
+@pytest.mark.parametrize("tpi", [1032, 2056, 2568, 10248])
 def test_fp64_pairs_on_the_cutoff(cuda_lib, oracle_lib, tpi):
     """Pairs at r_c and one ulp either side, along an axis and a diagonal:
     the FP64 schedules interact exactly the oracle's pairs."""
@@ -158,7 +159,7 @@ def test_fp64_fixed_point_box_sizes(cuda_lib, oracle_lib, scale):
             assert _relerr(got - p0[:, :3], want - p0[:, :3]) <= FP64_TOL
 
 
-@pytest.mark.parametrize("tpi", [2052, 2056, 2064])
+@pytest.mark.parametrize("tpi", [2052, 2056, 2064, 10244, 10256])
 def test_fp64_long_rows(cuda_lib, oracle_lib, tpi):
     """r_c = 4, full list: ~330 entries a row, many strides of every group
     size of the fixed-point schedule."""
@@ -208,14 +209,14 @@ def test_fp64_box_wider_than_1024_cutoffs(cuda_lib, oracle_lib):
 
 
 @pytest.mark.parametrize("half", [True, False])
-@pytest.mark.parametrize("tpi", [2056, 2052, 2064])
+@pytest.mark.parametrize("tpi", [2056, 2052, 2064, 10244, 10256])
 def test_fp64_rare_lanes(cuda_lib, oracle_lib, half, tpi):
     """The fixed-point row's rare lanes: an extra atom 1e-11 from atom 0 (a
-    squared distance far below the branch-free conversion's range and below
-    the seeded reciprocal's, so the general conversion and a division serve
-    that pair), in a box of 8 sigma whose other entries fall on both sides of
-    the conversion's two paths.  The close pair's impulse (~1e142) is checked
-    on its two atoms, every other atom against its own scale."""
+    squared distance far below the branch-free conversion's range, so the
+    general conversion serves that pair), in a box of 8 sigma whose other
+    entries fall on both sides of the conversion's two paths.  The close
+    pair's impulse (~1e142) is checked on its two atoms, every other atom
+    against its own scale."""
     lj = cuda_lib
     s = inputs.fcc_system(5, 1.0, 0.05, seed=21)      # L = 7.94, 500 atoms
     q = np.vstack([s.q, s.q[:1]])
@@ -229,6 +230,28 @@ def test_fp64_rare_lanes(cuda_lib, oracle_lib, half, tpi):
     rest = np.ones(c.n, dtype=bool)
     rest[pair] = False
     assert _relerr(got[rest], want[rest]) <= FP64_TOL
+
+
+@pytest.mark.parametrize("half", [True, False])
+@pytest.mark.parametrize("tpi", [2056, 10256])
+def test_fp64_scaled_system_divides(cuda_lib, oracle_lib, half, tpi):
+    """Every length (positions, box, r_c, r_s, sigma) times 2^-64: each r^2
+    then lies below 2^-119, outside the integer reciprocal's range, so every
+    pair takes the division path.  (The other end, r^2 >= 2^120, cannot
+    occur: lj_force refuses r_c^2 > 1e30.)  Scaling by a power of two is
+    exact in binary arithmetic, so the oracle runs on the scaled system
+    unchanged."""
+    lj = cuda_lib
+    f = 2.0 ** -64
+    s = inputs.fcc_system(6, 1.0, 0.05, seed=4)
+    c = inputs.LJSystem(q=s.q * f, box=s.box * f, rho=s.rho, rc=s.rc * f, margin=s.margin * f)
+    got, _ = _run(lj, c, half, 0, tpi, sigma=f)
+    want = _oracle(oracle_lib, c, half, sigma=f)
+    assert np.all(np.isfinite(got))
+    assert _relerr(got, want) <= FP64_TOL
+    # and it is the unscaled result, scaled
+    base, _ = _run(lj, s, half, 0, tpi)
+    assert _relerr(got * f, base) <= FP64_TOL
 
 
 def test_newton_third_law_half_list(cuda_lib, small):
@@ -254,7 +277,7 @@ def test_fp64_paper_size(cuda_lib, oracle_lib, order, half):
     s = inputs.workload_paper(order=order)
     want = _oracle(oracle_lib, s, half)
     pl = None
-    for tpi in (8, 32, 136, 648, 1032, 1160, 1672, 2052, 2056, 2064, 2568):
+    for tpi in (8, 32, 136, 648, 1032, 1160, 1672, 2052, 2056, 2064, 2568, 10244, 10248, 10256):
         got, pl = _run(cuda_lib, s, half, 0, tpi, pl=pl)
         assert _relerr(got, want) <= FP64_TOL, tpi
 
@@ -292,7 +315,8 @@ def test_million_atoms_all_forms_sampled(cuda_lib, million, half):
     q = to_dev(s.q)
     pl = lj.lj_build_pairlist(q, s.box, s.rs, half)
     scale = np.max(np.abs(want))
-    for prec, tpis, tol in ((0, (0, 2056, 2052, 1032), FP64_TOL), (1, (4, 8, 16, 136), MIXED_TOL),
+    for prec, tpis, tol in ((0, (0, 2056, 2052, 1032, 10248, 10256), FP64_TOL),
+                            (1, (4, 8, 16, 136), MIXED_TOL),
                             (2, (132, 136, 144), FP64_TOL)):
         for tpi in tpis:
             p = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
