@@ -72,12 +72,12 @@ ORACLE_SAMPLE_ATOMS = 512
 # reduction sectors, and the summary that records them.  A schedule or
 # workload without an entry reports no traffic figure ("not profiled").
 PROFILED = {
-    (2056, "half", 119164): {"dram_bytes": 41909760.0 + 0.0, "lts_read_sectors": 10610303,
-                             "lts_red_sectors": 24808185,
+    (2056, "half", 119164): {"dram_bytes": 41910784.0 + 768.0, "lts_read_sectors": 10565312,
+                             "lts_red_sectors": 24809860,
                              "source": "profiles/force_fp64_fixed_tpi8_half_N119164.md"},
-    (2056, "half", 1048576): {"dram_bytes": 373012736.0 + 27113216.0,
-                              "lts_read_sectors": 96542789, "lts_red_sectors": 218289891,
-                              "source": "profiles/force_fp64_fixed_tpi8_half_N1048576.md"},
+    (10272, "half", 1048576): {"dram_bytes": 493294848.0 + 56002304.0,
+                               "lts_read_sectors": 106330976, "lts_red_sectors": 199349072,
+                               "source": "profiles/force_fp64_stream_r32_half_N1048576.md"},
 }
 ERROR_DEFINITION = ("max_err_rel = max |dp_gpu - dp_oracle| / max |dp_oracle|; rms_err_rel = "
                     "RMS(dp_gpu - dp_oracle) / RMS(dp_oracle), over the x, y, z components of "
@@ -101,7 +101,8 @@ def parse():
     ap.add_argument("--peaks", action="store_true",
                     help="only measure the FP64 / FP32 / packed-FP32 / L2-read ceilings and print them")
     ap.add_argument("--profile", choices=["fp64", "fp64-full", "mixed", "mixed-full", "dfloat",
-                                          "dfloat-full", "list", "vjp", "vjp-dfloat", "batched",
+                                          "dfloat-full", "list", "vjp", "vjp-half", "vjp-dfloat",
+                                          "batched",
                                           "batched-mixed", "batched-dfloat"],
                     help="no timing: build the list and run a few calls of one kernel (for ncu)")
     ap.add_argument("--profile-atoms", choices=["paper", "million"], default="paper",
@@ -595,14 +596,16 @@ def run_profile(args):
         systems = inputs.batched_systems(nsys=64, seed=0)
         prec = {"batched": lj.LJ_FP64, "batched-mixed": lj.LJ_MIXED,
                 "batched-dfloat": lj.LJ_DFLOAT}[args.profile]
-        b = Batch(systems, DT, prec, True, tpi=8 if prec == lj.LJ_FP64 else 4, rows_per_item=16)
+        tpi = args.profile_tpi or (8 if prec == lj.LJ_FP64 else 4)
+        b = Batch(systems, DT, prec, True, tpi=tpi,
+                  rows_per_item=64 if tpi == lj.LJ_SCHED_STREAM else 16)
         for _ in range(5):
             b.force()
         torch.cuda.synchronize()
         print(json.dumps({"profile": args.profile, "systems": len(systems), "atoms": b.total_atoms}))
         return
     if args.profile.startswith("vjp"):
-        half = False
+        half = args.profile == "vjp-half"
     pl = lj.lj_build_pairlist(q, box, s.rs, half)
     pl = lj.lj_build_pairlist(q, box, s.rs, half, reuse=pl)
     if args.profile.startswith("vjp"):
@@ -785,7 +788,12 @@ def main():
                 "frac": alg_bytes / t_force / 1e9 / hbm_peak, "peak_source": hbm_src,
                 "bytes_per_pair": alg_bytes / nnz}
     gathered_reads = 36.0 * nnz + 40.0 * s.n
-    reductions = 3.0 * n_cut + 3.0 * 8 * s.n
+    # p_i partial sums: one per lane and row for a grid over rows (t lanes);
+    # for r rows per warp in 32 per-lane chunks, one per row plus one per
+    # chunk boundary (32 per r rows)
+    t_lanes = best_tpi & 63
+    flushes = (s.n + 32.0 * s.n / t_lanes) if best_tpi & 8192 else float(t_lanes * s.n)
+    reductions = 3.0 * n_cut + 3.0 * flushes
     l2_view = {"gathered_read_bytes": gathered_reads, "reductions": reductions,
                "gathered_read_GBps": gathered_reads / t_force / 1e9,
                "gathered_read_frac_of_l2_read_peak": gathered_reads / t_force / 1e9 / ceil["l2_read_gbs"],
@@ -1031,14 +1039,19 @@ def extra_adjoint(lj, dev, stream, flush, oracle_parts):
     box = [L, L, L]
     n1 = reps[0].n
     q = torch.from_numpy(np.concatenate([r.q for r in reps])).to(dev)
-    rows, cols, off = [torch.zeros(1, dtype=torch.int32, device=dev)], [], 0
-    for k, r in enumerate(reps):  # block-diagonal list over replicas sharing one box size
-        pl = lj.lj_build_pairlist(q[k * n1:(k + 1) * n1].contiguous(), box, r.rs, False)
-        rows.append(pl.row_ptr[1:] + off)
-        cols.append(pl.col_view + k * n1)
-        off += pl.nnz
-    big = lj.PairList(torch.cat(rows).contiguous(), torch.cat(cols).contiguous(), q.shape[0], off,
-                      False, reps[0].rs, 0)
+
+    def block_list(half):  # block-diagonal list over replicas sharing one box size
+        rows, cols, off = [torch.zeros(1, dtype=torch.int32, device=dev)], [], 0
+        for k, r in enumerate(reps):
+            pl = lj.lj_build_pairlist(q[k * n1:(k + 1) * n1].contiguous(), box, r.rs, half)
+            rows.append(pl.row_ptr[1:] + off)
+            cols.append(pl.col_view + k * n1)
+            off += pl.nnz
+        return lj.PairList(torch.cat(rows).contiguous(), torch.cat(cols).contiguous(), q.shape[0],
+                           off, half, reps[0].rs, 0)
+    lists = {"full": block_list(False), "half": block_list(True)}
+    big = lists["full"]
+    off = big.nnz
     Ft = torch.zeros_like(q)
     lj.lj_force(q, Ft, big, 1.0, reps[0].rc, box, 1.0, 1.0)
     want_q = np.concatenate([o[0] for o in oracle_parts])
@@ -1048,8 +1061,8 @@ def extra_adjoint(lj, dev, stream, flush, oracle_parts):
     res = {"replicas": len(reps), "atoms": int(q.shape[0]), "pairs": off // 2,
            "oracle_loss": want_loss, "oracle_grad_eps": want_e, "oracle_grad_sigma": want_s}
 
-    def loss_of(qq, e, sg, prec):
-        F = lj_forces(qq, e, sg, big, reps[0].rc, box, prec)
+    def loss_of(qq, e, sg, prec, plist=big):
+        F = lj_forces(qq, e, sg, plist, reps[0].rc, box, prec)
         return ((F - Ft) ** 2)[:, :3].mean()
 
     for name, prec in FORMS:
@@ -1057,19 +1070,24 @@ def extra_adjoint(lj, dev, stream, flush, oracle_parts):
         sig = torch.tensor(ADJ_SIGMA, dtype=torch.float64, device=dev, requires_grad=True)
         last = {}
 
-        def step():
+        def step(plist):
             qq = q.detach().requires_grad_(True)
             eps.grad = None
             sig.grad = None
-            loss = loss_of(qq, eps, sig, prec)
+            loss = loss_of(qq, eps, sig, prec, plist)
             loss.backward()
             last["q"], last["loss"] = qq.grad, loss
             return qq.grad
-        ms = time_calls(step, stream, flush, 5, 1)
-        step()
+        # half list (atomics) or full list (gathers), chosen by measurement
+        layout_ms = {k: time_calls(lambda: step(pl), stream, flush, 5, 1) for k, pl in lists.items()}
+        layout = min(layout_ms, key=layout_ms.get)
+        ms = layout_ms[layout]
+        step(lists[layout])
         gq = last["q"][:, :3].cpu().numpy()
         d = gq - want_q
-        res[name] = {"forward_backward_ms": ms, "loss": float(last["loss"].detach()),
+        res[name] = {"forward_backward_ms": ms, "list": layout,
+                     "forward_backward_ms_by_list": layout_ms,
+                     "loss": float(last["loss"].detach()),
                      "grad_eps": float(eps.grad), "grad_sigma": float(sig.grad),
                      "grad_eps_rel_err_vs_oracle": abs(float(eps.grad) - want_e) / abs(want_e),
                      "grad_sigma_rel_err_vs_oracle": abs(float(sig.grad) - want_s) / abs(want_s),

@@ -39,6 +39,7 @@ constexpr int kVjpThreads = 256;
 struct VjpCoef {
     double G1, G2;  // g      = u^4 (G1 u^3 - G2)
     double H1, H2;  // g'     = u^5 (H2 - H1 u^3)
+    double T1, T2;  // 2 g'   = u^5 (T2 - T1 u^3): 2 H1, 2 H2 (exact)
     double S1, S2;  // dg/ds  = u^4 (S1 u^3 - S2)   (s = sigma)
     double inv_eps;
 };
@@ -52,6 +53,8 @@ VjpCoef make_coef(double eps, double sigma)
     C.G2 = 24.0 * eps * s6;
     C.H1 = 336.0 * eps * s12;
     C.H2 = 96.0 * eps * s6;
+    C.T1 = 2.0 * C.H1;
+    C.T2 = 2.0 * C.H2;
     C.S1 = 576.0 * eps * s11;
     C.S2 = 144.0 * eps * s5;
     C.inv_eps = 1.0 / eps;
@@ -186,11 +189,11 @@ vjp_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
                 }
                 const double u2 = u * u, u3 = u2 * u, u4 = u2 * u2, u5 = u4 * u;
                 const double g = u4 * fma(C.G1, u3, -C.G2);
-                const double gp = u5 * fma(-C.H1, u3, C.H2);
+                const double gp2 = u5 * fma(-C.T1, u3, C.T2);  // 2 g', bit for bit
                 const double dgs = u4 * fma(C.S1, u3, -C.S2);
                 const double wx = Rxj - Rxi, wy = Ryj - Ryi, wz = Rzj - Rzi;
                 const double rw = fma(dz, wz, fma(dy, wy, dx * wx));
-                const double t = 2.0 * gp * rw;
+                const double t = gp2 * rw;
                 const double cx = fma(g, wx, t * dx), cy = fma(g, wy, t * dy),
                              cz = fma(g, wz, t * dz);
                 if (in) {
