@@ -555,7 +555,10 @@ size_t lj_force_vjp_workspace_bytes(int64_t n, int precision);
  *                       dLoss/deps = sum (g/eps)(d.w),
  *                       dLoss/dsigma = sum dg/dsigma (d.w).
  * Full lists gather per row without atomics (deterministic); half lists
- * scatter dLoss/dq_j with FP64 atomics.  The scalar sums use a fixed-order
+ * scatter dLoss/dq_j with FP64 atomics (LJ_FP64 half lists of at least
+ * 524,288 rows with a box up to 1024 r_cut wide: each warp takes 32 rows and
+ * cuts their entries into one chunk per lane, as LJ_SCHED_STREAM, adding
+ * dLoss/dq_i with atomics too).  The scalar sums use a fixed-order
  * reduction.  precision: LJ_FP64, LJ_MIXED (FP32 pair arithmetic,
  * compensated FP32 sums, FP64 outputs) or LJ_DFLOAT (double-float pair
  * arithmetic on the FP32 pipe, FP64-class results; needs |dLoss/dF| within

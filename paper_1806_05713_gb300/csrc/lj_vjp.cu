@@ -230,6 +230,142 @@ vjp_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
     block_pair_sum(ge, gs, partial);
 }
 
+// Half lists of at least kVjpStreamRows rows (fixed point): a warp owns
+// kVjpStreamR consecutive rows and cuts their entries into one contiguous
+// chunk per lane, as lj_force's LJ_SCHED_STREAM (fp64_fixed_stream): lanes
+// idle only in the padding of the last chunk instead of at the end of every
+// row, and a lane adds its partial dLoss/dq_i with FP64 atomics when it
+// leaves a row.  The pair arithmetic is vjp_fp64_kernel's.
+constexpr int kVjpStreamR = 32;
+constexpr int64_t kVjpStreamRows = 524288;
+
+__device__ __forceinline__ void vjp_fp64_stream_walk(
+    const double *__restrict__ q4, const longlong4 *__restrict__ X, const double *__restrict__ R4,
+    const int *__restrict__ row_ptr, const int *__restrict__ col, int i0, int i1, const Fp64Params &P,
+    const FixParams &F, const VjpCoef &C, double *__restrict__ gq4, double &ge, double &gs)
+{
+    const int lane = threadIdx.x & 31;
+    const int e0 = row_ptr[i0], e1 = row_ptr[i1];
+    if (e0 >= e1) return;  // no entries (warp-uniform)
+    // chunks start at a0 <= e0, where col + a0 is 16-byte aligned
+    const int a0 = e0 - static_cast<int>((reinterpret_cast<uintptr_t>(col + e0) >> 2) & 3u);
+    const int CH = ((e1 - a0 + 127) >> 7) << 2;  // entries per lane: 32 CH >= e1 - a0
+    const int s0 = a0 + lane * CH;
+    int row = i0;  // the last row r < i1 with row_ptr[r] <= max(s0, e0)
+    {
+        const int first = max(s0, e0);
+        int hi = i1;
+        while (hi - row > 1) {
+            const int mid = (row + hi) >> 1;
+            if (row_ptr[mid] <= first)
+                row = mid;
+            else
+                hi = mid;
+        }
+    }
+    int row_end = row_ptr[row + 1];
+    long long fxi = 0, fyi = 0, fzi = 0;
+    double Rxi = 0.0, Ryi = 0.0, Rzi = 0.0;
+    bool loaded = false, touched = false;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    int c0 = 0, c1 = 0, c2 = 0, c3 = 0;  // the column indices of entries e .. e + 3
+    for (int k = 0; k < CH; ++k) {
+        const int e = s0 + k;
+        if ((k & 3) == 0) {
+            if (e >= e0 && e + 4 <= e1) {
+                const int4 v = __ldg(reinterpret_cast<const int4 *>(col + e));
+                c0 = v.x;
+                c1 = v.y;
+                c2 = v.z;
+                c3 = v.w;
+            } else {
+                // the range's ends: only the indices inside [e0, e1) are read
+                c0 = (e >= e0 && e < e1) ? __ldg(col + e) : 0;
+                c1 = (e + 1 >= e0 && e + 1 < e1) ? __ldg(col + e + 1) : 0;
+                c2 = (e + 2 >= e0 && e + 2 < e1) ? __ldg(col + e + 2) : 0;
+                c3 = (e + 3 >= e0 && e + 3 < e1) ? __ldg(col + e + 3) : 0;
+            }
+        }
+        const bool valid = e >= e0 && e < e1;
+        while (valid && e >= row_end) {
+            if (touched) {
+                double *g = gq4 + 4 * static_cast<int64_t>(row);
+                atomicAdd(g + 0, ax);
+                atomicAdd(g + 1, ay);
+                atomicAdd(g + 2, az);
+                ax = ay = az = 0.0;
+                touched = false;
+            }
+            ++row;
+            row_end = row_ptr[row + 1];
+            loaded = false;
+        }
+        if (valid && !loaded) {
+            load_fixed(X, row, fxi, fyi, fzi);
+            load_r3(R4, row, Rxi, Ryi, Rzi);
+            loaded = true;
+        }
+        const int i = row;
+        const int j = valid ? c0 : i;
+        c0 = c1;
+        c1 = c2;
+        c2 = c3;
+        long long fxj, fyj, fzj;
+        load_fixed(X, j, fxj, fyj, fzj);
+        double dx, dy, dz, sq, w_div;
+        bool use_div;
+        const bool in = fixed_entry_sel(q4, fxi, fyi, fzi, fxj, fyj, fzj, valid, i, j, P, F,
+                                        0xffffffffu, dx, dy, dz, sq, use_div, w_div);
+        double Rxj, Ryj, Rzj;
+        load_r3(R4, j, Rxj, Ryj, Rzj);
+        bool rcp_ok;
+        double u = rcp_fp64_int(sq, rcp_ok);
+        u = use_div ? w_div : u;
+        const double u2 = u * u, u3 = u2 * u, u4 = u2 * u2, u5 = u4 * u;
+        const double g = u4 * fma(C.G1, u3, -C.G2);
+        const double gp2 = u5 * fma(-C.T1, u3, C.T2);  // 2 g'
+        const double dgs = u4 * fma(C.S1, u3, -C.S2);
+        const double wx = Rxj - Rxi, wy = Ryj - Ryi, wz = Rzj - Rzi;
+        const double rw = fma(dz, wz, fma(dy, wy, dx * wx));
+        const double t = gp2 * rw;
+        const double cx = fma(g, wx, t * dx), cy = fma(g, wy, t * dy), cz = fma(g, wz, t * dz);
+        if (in) {
+            touched = true;
+            ax -= cx;
+            ay -= cy;
+            az -= cz;
+            ge = fma(g, rw, ge);
+            gs = fma(dgs, rw, gs);
+            double *gj = gq4 + 4 * static_cast<int64_t>(j);
+            atomicAdd(gj + 0, cx);
+            atomicAdd(gj + 1, cy);
+            atomicAdd(gj + 2, cz);
+        }
+    }
+    if (touched) {
+        double *g = gq4 + 4 * static_cast<int64_t>(row);
+        atomicAdd(g + 0, ax);
+        atomicAdd(g + 1, ay);
+        atomicAdd(g + 2, az);
+    }
+}
+
+__global__ void __launch_bounds__(kVjpThreads, 4)
+vjp_fp64_stream_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
+                       const double *__restrict__ R4, int n, const int *__restrict__ row_ptr,
+                       const int *__restrict__ col, Fp64Params P, FixParams F, VjpCoef C,
+                       double *__restrict__ gq4, double *__restrict__ partial)
+{
+    const long long w = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    double ge = 0.0, gs = 0.0;
+    if (w * kVjpStreamR < n) {
+        const int i0 = static_cast<int>(w * kVjpStreamR);
+        vjp_fp64_stream_walk(q4, X, R4, row_ptr, col, i0, min(i0 + kVjpStreamR, n), P, F, C, gq4,
+                             ge, gs);
+    }
+    block_pair_sum(ge, gs, partial);
+}
+
 // MIXED form: one 32-byte record per atom, written by a pre-pass -- the
 // 32-bit fixed-point position {X, Y, Z} (as lj_force's mixed pre-pass) and
 // R = dLoss/dF rounded to FP32 -- so a gathered atom is one 256-bit load
@@ -450,6 +586,7 @@ extern "C" int lj_force_vjp(const double *q4_dev, const double *gradF4_dev, int6
         return LJ_ERR_CAPACITY;
     const int ni = static_cast<int>(n);
     const int blocks = vjp_blocks(n);
+    int used_blocks = blocks;  // blocks that write a partial sum (the stream walk uses fewer)
     Carver c(workspace_dev);
     double *partial = c.take<double>(2 * size_t(blocks));
     if (half || nnz == 0)
@@ -467,12 +604,18 @@ extern "C" int lj_force_vjp(const double *q4_dev, const double *gradF4_dev, int6
         if (fixed_point_ok(box, r_cut)) {
             fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, ni, F, X);
             LJ_TRY_LAUNCH("fixed_prepass_kernel");
-            if (half)
+            if (half && n >= kVjpStreamRows) {
+                const int64_t warps = (n + kVjpStreamR - 1) / kVjpStreamR;
+                used_blocks = static_cast<int>((warps * 32 + kVjpThreads - 1) / kVjpThreads);
+                vjp_fp64_stream_kernel<<<used_blocks, kVjpThreads, 0, st>>>(
+                    q4_dev, X, gradF4_dev, ni, row_ptr_dev, col_dev, P, F, C, gradq4_dev, partial);
+            } else if (half) {
                 vjp_fp64_kernel<true, true><<<blocks, kVjpThreads, 0, st>>>(
                     q4_dev, X, gradF4_dev, ni, row_ptr_dev, col_dev, P, F, C, gradq4_dev, partial);
-            else
+            } else {
                 vjp_fp64_kernel<false, true><<<blocks, kVjpThreads, 0, st>>>(
                     q4_dev, X, gradF4_dev, ni, row_ptr_dev, col_dev, P, F, C, gradq4_dev, partial);
+            }
         } else {
             if (half)
                 vjp_fp64_kernel<true, false><<<blocks, kVjpThreads, 0, st>>>(
@@ -502,7 +645,7 @@ extern "C" int lj_force_vjp(const double *q4_dev, const double *gradF4_dev, int6
         LJ_TRY_LAUNCH("vjp_mixed_kernel");
     }
     const double scale = half ? 1.0 : 0.5;
-    vjp_final_kernel<<<1, 1024, 0, st>>>(partial, blocks, scale, 1.0 / eps, grad_eps_sigma_dev);
+    vjp_final_kernel<<<1, 1024, 0, st>>>(partial, used_blocks, scale, 1.0 / eps, grad_eps_sigma_dev);
     LJ_TRY_LAUNCH("vjp_final_kernel");
     return LJ_OK;
 }

@@ -199,3 +199,37 @@ def test_autograd_dfloat_vs_oracle(cuda_lib, oracle_lib):
     assert abs(loss - np.mean((Fm - Ft) ** 2)) <= 1e-11 * loss
     assert np.max(np.abs(gq - oq)) <= 1e-10 * np.max(np.abs(oq))
     assert abs(ge - oe) <= 1e-9 * abs(oe) and abs(gs - os_) <= 1e-9 * abs(os_)
+
+
+def test_vjp_fp64_million_half_list_sampled(cuda_lib, oracle_lib):
+    """N = 1,048,576 on a half list, the adjoint benchmark's size and layout
+    (large half lists take the walk with one chunk of entries per lane):
+    dLoss/dq on sampled atoms against the oracle's per-atom sums (each atom's
+    full row from the oracle's list, processed alone), and dLoss/deps against
+    the identity dL/deps = sum_i R_i . F_i(q; eps, sigma) / eps, with F from
+    lj_force (itself checked against the oracle)."""
+    lj = cuda_lib
+    s = inputs.workload_million()
+    q = to_dev(s.q)
+    pl = lj.lj_build_pairlist(q, s.box, s.rs, True)
+    g = np.random.default_rng(21)
+    R = g.normal(size=(s.n, 4))
+    R[:, 3] = 0.0
+    gq, ges = lj.lj_force_vjp(q, to_dev(R), pl, s.rc, s.box, EPS_M, SIG_M, lj.LJ_FP64)
+    F = torch.zeros_like(q)
+    lj.lj_force(q, F, pl, 1.0, s.rc, s.box, EPS_M, SIG_M, lj.LJ_FP64)
+    torch.cuda.synchronize()
+    got = gq.cpu().numpy()[:, :3]
+    assert np.all(np.isfinite(got))
+    idx = np.concatenate([[0, s.n - 1], g.choice(s.n, 126, replace=False)])
+    want = np.empty((idx.size, 3))
+    for m, a in enumerate(idx):
+        rp_a, col_a = oracle_lib.pairlist_rows(s.q, s.box, s.rs, False, int(a), int(a) + 1)
+        row_ptr = np.zeros(s.n + 1, dtype=np.int32)
+        row_ptr[a + 1:] = col_a.size
+        wq, _, _ = oracle_lib.force_vjp(s.q, R, row_ptr, col_a, True, s.rc, s.box, EPS_M, SIG_M)
+        want[m] = wq[a]
+    assert np.max(np.abs(got[idx] - want)) <= 1e-11 * np.max(np.abs(want))
+    e = float(ges.cpu().numpy()[0])
+    want_e = float(np.sum(R[:, :3] * F.cpu().numpy()[:, :3])) / EPS_M
+    assert abs(e - want_e) <= 1e-10 * abs(want_e)
