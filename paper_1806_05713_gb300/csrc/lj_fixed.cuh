@@ -163,16 +163,20 @@ __device__ __forceinline__ double fixed_to_f64_sel(long long v, int k)
 }
 
 // fixed128_to_f64 for hi != 0 (a value of 65 to 128 bits), without
-// branches: the 53 kept bits lie across hi and lo when the dropped count
-// sh = n - 53 is below 64, in hi alone when it is 64 or more; both results
-// are formed and one is selected, so a warp never diverges on the size of
-// a squared distance (the fixed-point scale k ties that size to the box:
-// in small boxes list entries fall on both sides).  `fast` is false for
+// divergence: the 53 kept bits lie across hi and lo when the dropped count
+// sh = n - 53 is below 64, in hi alone when it is 64 or more; both forms are
+// computed and one is selected, so a warp never diverges on the size of a
+// squared distance (the fixed-point scale k ties that size to the box: in
+// small boxes list entries fall on both sides).  VOTE: the second form only
+// when a lane of the group gm needs it (every lane of gm calls it) -- a gain
+// for the whole-warp stream walk, a loss for the 4-16-lane groups, whose
+// extra registers cost occupancy.  `fast` is false for
 // hi = 0 (a squared distance below 2^(64-2k): coincident atoms, or an idle
 // lane), where the caller converts with fixed128_to_f64.  Same values as
 // fixed128_to_f64.
+template <bool VOTE>
 __device__ __forceinline__ double fixed128_to_f64_hi(unsigned long long hi, unsigned long long lo,
-                                                     int k2, bool &fast)
+                                                     int k2, bool &fast, unsigned gm)
 {
     fast = hi != 0ull;
     const int n = 128 - __clzll(static_cast<long long>(hi | 1ull));  // 65 .. 128 when fast
@@ -183,6 +187,11 @@ __device__ __forceinline__ double fixed128_to_f64_hi(unsigned long long hi, unsi
     const unsigned long long rem1 = lo & ((1ull << s1) - 1ull);
     const unsigned long long half1 = 1ull << (s1 - 1);
     const bool up1 = rem1 > half1 || (rem1 == half1 && (top1 & 1ull));
+    // the second form only when a lane of the group needs it (in a box
+    // whose squared distances stay below 2^(117 - 2k), none does)
+    if constexpr (VOTE) {
+        if (__all_sync(gm, sh < 64)) return assemble_f64(top1 + (up1 ? 1ull : 0ull), n, k2, 0ull);
+    }
     // dropped bits: all of lo and the low s2 bits of hi (sh = 64 .. 75)
     const int s2 = min(max(sh - 64, 0), 11);
     const unsigned long long top2 = hi >> s2;
@@ -217,7 +226,9 @@ constexpr int kRcpIntHi = 120;
 // takes a few dozen integer instructions where an FP64 Newton step takes
 // two FP64 ones, and leaves the FP64 pipe -- the limit of the FP64 force
 // kernels -- to the force arithmetic.  `ok` is false outside the range.
-__device__ __forceinline__ double rcp_fp64_int(double a, bool &ok)
+// VOTE as fixed128_to_f64_hi (every lane of gm calls it; gm unused without).
+template <bool VOTE>
+__device__ __forceinline__ double rcp_fp64_int(double a, bool &ok, unsigned gm)
 {
     const long long b = __double_as_longlong(a);
     const int ea = static_cast<int>((b >> 52) & 0x7ff) - 1023;
@@ -249,9 +260,13 @@ __device__ __forceinline__ double rcp_fp64_int(double a, bool &ok)
     long long m = base + ((D + (1ll << 13)) >> 14);
     int ed = ey;
     const bool up = fl >= (1ll << 53), lo = fl < (1ll << 52);
-    m = up ? (base >> 1) + ((D + (1ll << 14)) >> 15) : m;  // u in [2^53, 2^54): round u / 2
-    m = lo ? 2 * base + ((D + (1ll << 12)) >> 13) : m;     // u below 2^52: round 2 u
-    ed += up ? 1 : (lo ? -1 : 0);
+    // u outside Y's binade (1/a and the seed on either side of a power of
+    // two: rare); VOTE: under one vote of the group gm
+    if (!VOTE || __any_sync(gm, up || lo)) {
+        m = up ? (base >> 1) + ((D + (1ll << 14)) >> 15) : m;  // u in [2^53, 2^54): round u / 2
+        m = lo ? 2 * base + ((D + (1ll << 12)) >> 13) : m;     // u below 2^52: round 2 u
+        ed += up ? 1 : (lo ? -1 : 0);
+    }
     const bool carry = m == (1ll << 53);
     m = carry ? (1ll << 52) : m;
     ed += carry ? 1 : 0;
@@ -305,7 +320,9 @@ __device__ __forceinline__ void norm2_fixed(long long dx, long long dy, long lon
 // within 64 ulp of r_c^2, an r^2 outside the reciprocal's range (a
 // division) -- are handled under one vote of the group gm (every lane of
 // gm calls it).  Returns whether the pair interacts; *w_div receives 1/r^2
-// by division for the lanes that need it (and *use_div says which).
+// by division for the lanes that need it (and *use_div says which).  VOTE:
+// see fixed128_to_f64_hi.
+template <bool VOTE = false>
 __device__ __forceinline__ bool fixed_entry_sel(const double *__restrict__ q4, long long xi,
                                                 long long yi, long long zi, long long xj,
                                                 long long yj, long long zj, bool valid, int i, int j,
@@ -319,7 +336,7 @@ __device__ __forceinline__ bool fixed_entry_sel(const double *__restrict__ q4, l
     unsigned long long hi, lo;
     norm2_fixed(Dx, Dy, Dz, hi, lo);
     bool fast;
-    r2 = fixed128_to_f64_hi(hi, lo, 2 * F.k, fast);
+    r2 = fixed128_to_f64_hi<VOTE>(hi, lo, 2 * F.k, fast, gm);
     dx = fixed_to_f64_sel(Dx, F.k);
     dy = fixed_to_f64_sel(Dy, F.k);
     dz = fixed_to_f64_sel(Dz, F.k);
@@ -397,7 +414,7 @@ __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
         {
             if (!in) r2 = 1.0;
             bool rcp_ok;
-            double w = rcp_fp64_int(r2, rcp_ok);
+            double w = rcp_fp64_int<false>(r2, rcp_ok, gm);
             w = use_div ? w_div : w;
             const double w2 = w * w;
             const double w4 = w2 * w2;
@@ -549,11 +566,11 @@ __device__ __forceinline__ void fp64_fixed_stream(const double *__restrict__ q4,
         load_fixed(X, j, xj, yj, zj);
         double dx, dy, dz, r2, w_div;
         bool use_div;
-        const bool in = fixed_entry_sel(q4, xi, yi, zi, xj, yj, zj, valid, i, j, P, F, 0xffffffffu,
+        const bool in = fixed_entry_sel<true>(q4, xi, yi, zi, xj, yj, zj, valid, i, j, P, F, 0xffffffffu,
                                         dx, dy, dz, r2, use_div, w_div);
         if (!in) r2 = 1.0;
         bool rcp_ok;
-        double w = rcp_fp64_int(r2, rcp_ok);
+        double w = rcp_fp64_int<true>(r2, rcp_ok, 0xffffffffu);
         w = use_div ? w_div : w;
         const double w2 = w * w;
         const double w4 = w2 * w2;

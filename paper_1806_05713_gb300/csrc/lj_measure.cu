@@ -188,7 +188,7 @@ __global__ void eval_reciprocal_kernel(int kind, const double *__restrict__ a, l
             v = static_cast<double>(rcp_fp32(__double2float_rn(x)));
             break;
         case LJ_RCP_FP64_INT:
-            v = rcp_fp64_int(x, in_range);
+            v = rcp_fp64_int<false>(x, in_range, 0u);
             break;
         default:
             break;

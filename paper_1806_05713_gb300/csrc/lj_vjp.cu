@@ -182,7 +182,7 @@ vjp_fp64_kernel(const double *__restrict__ q4, const longlong4 *__restrict__ X,
                 double u;
                 if (FIX) {
                     bool rcp_ok;
-                    u = rcp_fp64_int(s, rcp_ok);
+                    u = rcp_fp64_int<false>(s, rcp_ok, gm);
                     u = use_div ? w_div : u;
                 } else {
                     u = rcp_fp64(s, gm);
@@ -314,12 +314,12 @@ __device__ __forceinline__ void vjp_fp64_stream_walk(
         load_fixed(X, j, fxj, fyj, fzj);
         double dx, dy, dz, sq, w_div;
         bool use_div;
-        const bool in = fixed_entry_sel(q4, fxi, fyi, fzi, fxj, fyj, fzj, valid, i, j, P, F,
-                                        0xffffffffu, dx, dy, dz, sq, use_div, w_div);
+        const bool in = fixed_entry_sel<true>(q4, fxi, fyi, fzi, fxj, fyj, fzj, valid, i, j, P, F,
+                                              0xffffffffu, dx, dy, dz, sq, use_div, w_div);
         double Rxj, Ryj, Rzj;
         load_r3(R4, j, Rxj, Ryj, Rzj);
         bool rcp_ok;
-        double u = rcp_fp64_int(sq, rcp_ok);
+        double u = rcp_fp64_int<true>(sq, rcp_ok, 0xffffffffu);
         u = use_div ? w_div : u;
         const double u2 = u * u, u3 = u2 * u, u4 = u2 * u2, u5 = u4 * u;
         const double g = u4 * fma(C.G1, u3, -C.G2);
