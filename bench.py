@@ -75,8 +75,8 @@ PROFILED = {
     (2056, "half", 119164): {"dram_bytes": 41910784.0 + 768.0, "lts_read_sectors": 10565312,
                              "lts_red_sectors": 24809860,
                              "source": "profiles/force_fp64_fixed_tpi8_half_N119164.md"},
-    (10272, "half", 1048576): {"dram_bytes": 493294848.0 + 56002304.0,
-                               "lts_read_sectors": 106330976, "lts_red_sectors": 199349072,
+    (10272, "half", 1048576): {"dram_bytes": 488836608.0 + 55444224.0,
+                               "lts_read_sectors": 106171089, "lts_red_sectors": 199342661,
                                "source": "profiles/force_fp64_stream_r32_half_N1048576.md"},
 }
 ERROR_DEFINITION = ("max_err_rel = max |dp_gpu - dp_oracle| / max |dp_oracle|; rms_err_rel = "
