@@ -1,6 +1,6 @@
 /*
  * lj_measure.h -- measurement and self-check entry points of the GB300 LJ
- * library: the throughput ceilings the force kernels are judged against,
+ * library: the throughput ceilings the force kernels are measured against,
  * and direct evaluation of the reciprocal approximations the kernels use.
  *
  * Conventions are those of lj_gb300.h (device pointers end in _dev, LJ_OK or
@@ -29,7 +29,7 @@ extern "C" {
 /*
  * The paper states the cost of one pair as 27 additions or multiplications,
  * one division, 48 bytes read and 24 written (section "Lennard-Jones
- * Potential"), and judges its kernels by how close they come to the
+ * Potential"), and rates its kernels by how close they come to the
  * machine's limits.  On GB300 the FP64 force kernel is bound by the FP64
  * pipe, the mixed kernel by the FP32 pipe and by L2 gathers, so the
  * ceilings these kernels are compared with are measured here rather than
