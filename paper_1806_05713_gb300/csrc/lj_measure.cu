@@ -188,7 +188,9 @@ __global__ void eval_reciprocal_kernel(int kind, const double *__restrict__ a, l
             v = static_cast<double>(rcp_fp32(__double2float_rn(x)));
             break;
         case LJ_RCP_FP64_INT:
-            v = rcp_fp64_int<false>(x, in_range, 0u);
+            // the form with the rare binade cases under a vote of the active
+            // lanes (the arithmetic of the select-only form, gated)
+            v = rcp_fp64_int<true>(x, in_range, __activemask());
             break;
         default:
             break;

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-12
 MIXED_TOL = 1e-5
 SCHEDULES = [1, 2, 4, 8, 16, 32, 132, 136, 144, 520, 644, 648, 656, 1028, 1032, 1040, 1156, 1160,
-             1168, 1544, 1672, 2052, 2056, 2064, 2568, 10244, 10248, 10256]
+             1168, 1544, 1672, 2052, 2056, 2064, 2568, 10244, 10248, 10256, 10272]
 # t lanes per row; 128|t two entries per lane (software-pipelined); 512|...
 # length-sorted rows; 1024|... image-selected displacement; 2048|... exact
 # fixed-point displacement (the default); 8192|2048|r the fixed-point rows,
@@ -87,12 +87,30 @@ def test_two_body_closed_form(cuda_lib, precision):
         q[1, 0] += r
         s = inputs.LJSystem(q=q, box=np.array([20.0] * 3), rho=0.0)
         for half in (True, False):
-            for tpi in (1, 32) + ((2056,) if precision == 0 else ()):
+            for tpi in (1, 32) + ((2056, 10244, 10272) if precision == 0 else ()):
                 got, _ = _run(lj, s, half, precision, tpi, dt=dt)
                 tol = 1e-15 if precision == 0 else 1e-6
                 assert abs(got[1, 0] - want) <= tol * 24 * dt + 1e-14 * 48 * dt
                 assert abs(got[0, 0] + want) <= tol * 24 * dt + 1e-14 * 48 * dt
                 assert np.all(got[:, 1:] == 0.0)
+
+
+@pytest.mark.parametrize("half", [True, False])
+def test_fp64_stream_sparse_rows(cuda_lib, oracle_lib, half):
+    """A dilute gas (rho = 0.002, 1,000 atoms): most rows are empty and whole
+    windows of 4-32 rows hold no entry, the last window is ragged (1,000 is
+    no multiple of 32 or 16); the stream walks against the oracle."""
+    lj = cuda_lib
+    g = np.random.default_rng(31)
+    n, L = 1000, (1000 / 0.002) ** (1 / 3)
+    q = np.zeros((n, 4))
+    q[:, :3] = g.uniform(0.0, L, size=(n, 3))
+    s = inputs.LJSystem(q=q, box=np.array([L] * 3), rho=0.002)
+    want = _oracle(oracle_lib, s, half)
+    assert np.count_nonzero(np.any(want != 0.0, axis=1)) < n // 2
+    for tpi in (10244, 10248, 10256, 10272, 2056):
+        got, _ = _run(lj, s, half, 0, tpi)
+        assert _relerr(got, want) <= FP64_TOL, tpi
 
 
 def test_wrap_across_boundary(cuda_lib):
@@ -277,7 +295,8 @@ def test_fp64_paper_size(cuda_lib, oracle_lib, order, half):
     s = inputs.workload_paper(order=order)
     want = _oracle(oracle_lib, s, half)
     pl = None
-    for tpi in (8, 32, 136, 648, 1032, 1160, 1672, 2052, 2056, 2064, 2568, 10244, 10248, 10256):
+    for tpi in (8, 32, 136, 648, 1032, 1160, 1672, 2052, 2056, 2064, 2568, 10244, 10248, 10256,
+                10272):
         got, pl = _run(cuda_lib, s, half, 0, tpi, pl=pl)
         assert _relerr(got, want) <= FP64_TOL, tpi
 
