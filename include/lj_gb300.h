@@ -113,6 +113,14 @@ extern "C" {
  * p_i is added with FP64 atomics by every lane whose chunk meets the row,
  * so full lists are not deterministic under this schedule. */
 #define LJ_SCHED_STREAM 8192
+/* LJ_SCHED_CELLS | (a row-group schedule, any form; not with LJ_SCHED_SORTED
+ * or LJ_SCHED_STREAM): the rows are walked in space-filling order -- counting-
+ * sorted per call (three small kernels) by the Morton index of their atom's
+ * cell, at most 32 cells per axis of side >= r_cut / 2 -- so that the warps
+ * of an SM take nearby atoms, whose neighbour sets overlap, and the gathered
+ * q_j records come from L1 when the atoms are numbered in random order.  The
+ * results do not depend on the order (each row keeps its own sum). */
+#define LJ_SCHED_CELLS 16384
 
 const char *lj_status_string(int status);
 /* Text of the last CUDA error seen by this library in this thread. */

@@ -178,7 +178,6 @@ batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ it
                      unsigned long long *__restrict__ counter)
 {
     const int lane = threadIdx.x & 31;
-    {
     const unsigned gm = group_mask<TPI>();
     constexpr int kGroups = 32 / TPI;
     while (true) {
@@ -228,7 +227,6 @@ batched_force_kernel(const SysDev *__restrict__ sys, const Item *__restrict__ it
                 }
             }
         }
-    }
     }
 }
 

@@ -281,6 +281,112 @@ int sort_rows_by_length(const int *row_ptr, int n, int *hist, int *slot, int *or
     return LJ_OK;
 }
 
+// Rows in space-filling order (LJ_SCHED_CELLS): the box is cut into at most
+// 32 cells per axis of side >= r_c / 2, and the rows are counting-sorted by
+// the Morton (bit-interleaved) index of their atom's cell.  The warps of an
+// SM then walk rows of nearby atoms, whose neighbour sets overlap, so the
+// gathered q_j records are reused from L1 instead of L2 when the atoms are
+// numbered in random order.  The order within a cell is the atomic slot
+// order; the rows' results do not depend on it.
+constexpr int kCellBits = 5;
+constexpr int kCellKeys = 1 << (3 * kCellBits);
+
+struct CellGrid {
+    double inv[3];  // cells per unit length
+    int nc[3];      // cells per axis (1 .. 32)
+};
+
+CellGrid make_cell_grid(const double box[3], double rc)
+{
+    CellGrid g{};
+    for (int a = 0; a < 3; ++a) {
+        const int c = static_cast<int>(box[a] / (0.5 * rc));
+        g.nc[a] = c < 1 ? 1 : (c > (1 << kCellBits) ? (1 << kCellBits) : c);
+        g.inv[a] = g.nc[a] / box[a];
+    }
+    return g;
+}
+
+__device__ __forceinline__ unsigned spread3(unsigned v)  // b4..b0 -> b12 b9 b6 b3 b0
+{
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ int cell_key(const double *__restrict__ q4, int i, const CellGrid &g)
+{
+    double x, y, z;
+    load_xyz(q4, i, x, y, z);
+    const int cx = min(max(static_cast<int>(x * g.inv[0]), 0), g.nc[0] - 1);
+    const int cy = min(max(static_cast<int>(y * g.inv[1]), 0), g.nc[1] - 1);
+    const int cz = min(max(static_cast<int>(z * g.inv[2]), 0), g.nc[2] - 1);
+    return static_cast<int>(spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2));
+}
+
+__global__ void cell_hist_kernel(const double *__restrict__ q4, int n, CellGrid g,
+                                 int *__restrict__ hist, int *__restrict__ slot)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    slot[i] = atomicAdd(&hist[cell_key(q4, i, g)], 1);
+}
+
+// Exclusive prefix sum of the kCellKeys counts in place: one block of 1024
+// threads, 32 counts each.
+__global__ void cell_scan_kernel(int *__restrict__ hist)
+{
+    constexpr int kPer = kCellKeys / 1024;
+    __shared__ int part[1024];
+    const int t = threadIdx.x;
+    int v[kPer];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        v[k] = hist[t * kPer + k];
+        sum += v[k];
+    }
+    part[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int u = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += u;
+        __syncthreads();
+    }
+    int run = part[t] - sum;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        hist[t * kPer + k] = run;
+        run += v[k];
+    }
+}
+
+__global__ void cell_scatter_kernel(const double *__restrict__ q4, int n, CellGrid g,
+                                    const int *__restrict__ start, const int *__restrict__ slot,
+                                    int *__restrict__ order)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    order[start[cell_key(q4, i, g)] + slot[i]] = i;
+}
+
+int sort_rows_by_cell(const double *q4, int n, const double box[3], double rc, int *hist,
+                      int *slot, int *order, cudaStream_t st)
+{
+    const CellGrid g = make_cell_grid(box, rc);
+    LJ_TRY_CUDA(cudaMemsetAsync(hist, 0, sizeof(int) * kCellKeys, st));
+    const unsigned b = unsigned((n + 255) / 256);
+    cell_hist_kernel<<<b, 256, 0, st>>>(q4, n, g, hist, slot);
+    LJ_TRY_LAUNCH("cell_hist_kernel");
+    cell_scan_kernel<<<1, 1024, 0, st>>>(hist);
+    LJ_TRY_LAUNCH("cell_scan_kernel");
+    cell_scatter_kernel<<<b, 256, 0, st>>>(q4, n, g, hist, slot, order);
+    LJ_TRY_LAUNCH("cell_scatter_kernel");
+    return LJ_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -368,8 +474,8 @@ int check_force_args(const double *q4, const double *p4, int64_t n, const int32_
     return check_box(box, r_cut);
 }
 
-// Workspace: [order: n int][slot: n int][length histogram] (the
-// length-sorted row order of LJ_SCHED_SORTED) and the fixed-point positions
+// Workspace: [order: n int][slot: n int][histogram] (the row order of
+// LJ_SCHED_SORTED or LJ_SCHED_CELLS) and the fixed-point positions
 // of the form (LJ_FP64: 64-bit integers; LJ_MIXED: 32-bit; LJ_DFLOAT:
 // chunks).
 struct ForceWs {
@@ -385,7 +491,7 @@ ForceWs carve_force_ws(void *base, int64_t n, int precision)
     const size_t nn = size_t(n > 0 ? n : 1);
     w.order = c.take<int>(nn);
     w.slot = c.take<int>(nn);
-    w.hist = c.take<int>(kLenBuckets);
+    w.hist = c.take<int>(kCellKeys);  // the larger of the two counting sorts
     w.rel = precision == LJ_MIXED ? c.take<uint4>(nn) : nullptr;
     w.rec = precision == LJ_DFLOAT ? static_cast<void *>(c.take<char>(dfloat_record_bytes(n)))
             : precision == LJ_FP64 ? static_cast<void *>(c.take<longlong4>(nn))
@@ -395,6 +501,12 @@ ForceWs carve_force_ws(void *base, int64_t n, int precision)
 
 bool valid_schedule(int s, int precision)
 {
+    // the space-filling row order goes with every row-group schedule (as the
+    // length-sorted one does, which it excludes)
+    if (s & LJ_SCHED_CELLS) {
+        if (s & (LJ_SCHED_SORTED | LJ_SCHED_STREAM)) return false;
+        s = (s & ~LJ_SCHED_CELLS) | LJ_SCHED_SORTED;
+    }
     const int t = s & 63;
     const bool pow2 = t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32;
     if (s & LJ_SCHED_STREAM)  // rows per warp; implies the fixed-point rows, not length-sorted
@@ -416,7 +528,7 @@ size_t force_workspace_bytes_impl(int64_t n, int precision)
     const size_t nn = size_t(n > 0 ? n : 1);
     c.take<int>(nn);
     c.take<int>(nn);
-    c.take<int>(kLenBuckets);
+    c.take<int>(kCellKeys);
     if (precision == LJ_MIXED) c.take<uint4>(nn);
     if (precision == LJ_DFLOAT) c.take<char>(dfloat_record_bytes(n));
     if (precision == LJ_FP64) c.take<longlong4>(nn);
@@ -474,6 +586,11 @@ int force_impl(const double *q4, double *p4, int64_t n, const int32_t *row_ptr, 
         if (rc2 != LJ_OK) return rc2;
         order = W.order;
         tpi &= ~LJ_SCHED_SORTED;
+    } else if (tpi & LJ_SCHED_CELLS) {
+        const int rc2 = sort_rows_by_cell(q4, ni, box, rc, W.hist, W.slot, W.order, st);
+        if (rc2 != LJ_OK) return rc2;
+        order = W.order;
+        tpi &= ~LJ_SCHED_CELLS;
     }
     if (precision == LJ_DFLOAT)
         return force_dfloat(q4, p4, ni, row_ptr, col, half, box, dt, rc, eps, sigma, tpi, order,

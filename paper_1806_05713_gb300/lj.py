@@ -33,6 +33,7 @@ LJ_SCHED_SORTED = 512
 LJ_SCHED_IMAGES = 1024
 LJ_SCHED_FIXED = 2048
 LJ_SCHED_STREAM = 8192
+LJ_SCHED_CELLS = 16384
 LJ_MD_LAST_HALF_KICK = 1
 LJ_PEAK_DFMA = 0
 LJ_PEAK_FFMA = 1
@@ -382,13 +383,13 @@ def lj_autotune_force(q4: torch.Tensor, plist: PairList, dt: float, r_cut: float
         S, W, I, F = LJ_SCHED_SORTED, LJ_SCHED_SWP2, LJ_SCHED_IMAGES, LJ_SCHED_FIXED
         # the fixed-point schedules are refused (and skipped) for boxes wider
         # than 1024 r_c, where the image-selected ones take over
-        R = LJ_SCHED_STREAM
+        R, C = LJ_SCHED_STREAM, LJ_SCHED_CELLS
         candidates = ([F | 4, F | 8, F | 16, S | F | 8, F | R | 8, F | R | 16, F | R | 32, I | 4,
                        I | 8, I | 16, I | W | 8]
                       if precision == LJ_FP64 else
                       [W | 8, W | 4, W | 16, S | W | 8, 4, 8, 16, S | 4, S | 8]
                       if precision == LJ_DFLOAT else
-                      [4, 8, 16, W | 4, W | 8, W | 16, S | 8, S | W | 8])
+                      [4, 8, 16, W | 4, W | 8, W | 16, S | 8, S | W | 8, C | 8, C | W | 4, C | W | 8])
     n = plist.n
     scratch = torch.zeros((n, 4), dtype=torch.float64, device=q4.device)
     ws = _workspace(lib.lj_force_workspace_bytes(n, _box3(box), int(precision)), q4.device)

@@ -94,6 +94,11 @@ def test_host_argument_checks_without_gpu():
     # 4096, two entries per lane on the fixed-point rows) are refused
     for retired in (64 | 8, 256 | 8, 4096 | 8, lj.LJ_SCHED_FIXED | lj.LJ_SCHED_SWP2 | 8):
         assert force(prec=0, tpi=retired, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG
+    # the space-filling row order excludes the length-sorted one and the
+    # stream walk
+    C = lj.LJ_SCHED_CELLS
+    for bad in (C | lj.LJ_SCHED_SORTED | 8, C | lj.LJ_SCHED_FIXED | lj.LJ_SCHED_STREAM | 8):
+        assert force(prec=0, tpi=bad, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG
     # mixed precision, or the FP64 fixed-point schedule, without a workspace
     assert force(prec=1, tpi=8) == lj.LJ_ERR_CAPACITY
     assert force(prec=0, tpi=lj.LJ_SCHED_FIXED | 8) == lj.LJ_ERR_CAPACITY

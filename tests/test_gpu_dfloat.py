@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 DF = 2
-TPIS = [4, 8, 16, 132, 136, 144, 516, 520, 528, 648]
+TPIS = [4, 8, 16, 132, 136, 144, 516, 520, 528, 648, 16516]  # 16384: LJ_SCHED_CELLS
 # 128|t: two entries per lane in packed f32x2 registers; 512|t: rows in order of
 # decreasing length
 

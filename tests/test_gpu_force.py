@@ -14,11 +14,12 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-12
 MIXED_TOL = 1e-5
 SCHEDULES = [1, 2, 4, 8, 16, 32, 132, 136, 144, 520, 644, 648, 656, 1028, 1032, 1040, 1156, 1160,
-             1168, 1544, 1672, 2052, 2056, 2064, 2568, 10244, 10248, 10256, 10272]
+             1168, 1544, 1672, 2052, 2056, 2064, 2568, 10244, 10248, 10256, 10272, 17416, 18440]
 # t lanes per row; 128|t two entries per lane (software-pipelined); 512|...
 # length-sorted rows; 1024|... image-selected displacement; 2048|... exact
 # fixed-point displacement (the default); 8192|2048|r the fixed-point rows,
-# r rows per warp walked as one stream of entries
+# r rows per warp cut into one chunk of entries per lane; 16384|... rows in
+# space-filling (cell) order
 
 
 def _run(lj, s, half, precision, tpi, dt=0.01, eps=1.0, sigma=1.0, p0=None, rc=None, pl=None):
@@ -56,7 +57,7 @@ def test_fp64_small_all_schedules(cuda_lib, oracle_lib, small, tpi, half):
     assert _relerr(got, want) <= FP64_TOL
 
 
-@pytest.mark.parametrize("tpi", [1, 4, 8, 32, 516, 520, 132, 136, 144, 648])
+@pytest.mark.parametrize("tpi", [1, 4, 8, 32, 516, 520, 132, 136, 144, 648, 16392, 16516, 16520])
 @pytest.mark.parametrize("half", [True, False])
 def test_mixed_small(cuda_lib, oracle_lib, small, tpi, half):
     got, _ = _run(cuda_lib, small, half, cuda_lib.LJ_MIXED, tpi)
@@ -111,6 +112,24 @@ def test_fp64_stream_sparse_rows(cuda_lib, oracle_lib, half):
     for tpi in (10244, 10248, 10256, 10272, 2056):
         got, _ = _run(lj, s, half, 0, tpi)
         assert _relerr(got, want) <= FP64_TOL, tpi
+
+
+@pytest.mark.parametrize("precision,tpi", [(0, 2056), (0, 1032), (1, 8), (1, 132), (2, 136)])
+def test_cell_order_full_list_bitwise(cuda_lib, precision, tpi):
+    """LJ_SCHED_CELLS only changes which warp walks which row: on a full list
+    (each row's sum kept by its own group, no atomics) the momenta are
+    bit-identical with and without it (N = 119,164, random order)."""
+    lj = cuda_lib
+    s = inputs.workload_paper()
+    q = to_dev(s.q)
+    pl = lj.lj_build_pairlist(q, s.box, s.rs, False)
+    out = []
+    for t in (tpi, lj.LJ_SCHED_CELLS | tpi):
+        p = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
+        lj.lj_force(q, p, pl, 0.01, s.rc, s.box, precision=precision, tpi=t)
+        torch.cuda.synchronize()
+        out.append(p.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
 
 
 def test_wrap_across_boundary(cuda_lib):
@@ -296,7 +315,7 @@ def test_fp64_paper_size(cuda_lib, oracle_lib, order, half):
     want = _oracle(oracle_lib, s, half)
     pl = None
     for tpi in (8, 32, 136, 648, 1032, 1160, 1672, 2052, 2056, 2064, 2568, 10244, 10248, 10256,
-                10272):
+                10272, 18440):
         got, pl = _run(cuda_lib, s, half, 0, tpi, pl=pl)
         assert _relerr(got, want) <= FP64_TOL, tpi
 
@@ -335,7 +354,7 @@ def test_million_atoms_all_forms_sampled(cuda_lib, million, half):
     pl = lj.lj_build_pairlist(q, s.box, s.rs, half)
     scale = np.max(np.abs(want))
     for prec, tpis, tol in ((0, (0, 2056, 2052, 1032, 10248, 10256), FP64_TOL),
-                            (1, (4, 8, 16, 136), MIXED_TOL),
+                            (1, (4, 8, 16, 136, 16516), MIXED_TOL),
                             (2, (132, 136, 144), FP64_TOL)):
         for tpi in tpis:
             p = torch.zeros((s.n, 4), dtype=torch.float64, device="cuda")
