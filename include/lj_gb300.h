@@ -116,7 +116,7 @@ extern "C" {
 /* LJ_SCHED_CELLS | (a row-group schedule, any form; not with LJ_SCHED_SORTED
  * or LJ_SCHED_STREAM): the rows are walked in space-filling order -- counting-
  * sorted per call (three small kernels) by the Morton index of their atom's
- * cell, at most 32 cells per axis of side >= r_cut / 2 -- so that the warps
+ * cell, at most 16 cells per axis of side >= r_cut / 2 -- so that the warps
  * of an SM take nearby atoms, whose neighbour sets overlap, and the gathered
  * q_j records come from L1 when the atoms are numbered in random order.  The
  * results do not depend on the order (each row keeps its own sum). */

@@ -282,18 +282,19 @@ int sort_rows_by_length(const int *row_ptr, int n, int *hist, int *slot, int *or
 }
 
 // Rows in space-filling order (LJ_SCHED_CELLS): the box is cut into at most
-// 32 cells per axis of side >= r_c / 2, and the rows are counting-sorted by
+// 16 cells per axis of side >= r_c / 2, and the rows are counting-sorted by
 // the Morton (bit-interleaved) index of their atom's cell.  The warps of an
 // SM then walk rows of nearby atoms, whose neighbour sets overlap, so the
 // gathered q_j records are reused from L1 instead of L2 when the atoms are
 // numbered in random order.  The order within a cell is the atomic slot
 // order; the rows' results do not depend on it.
-constexpr int kCellBits = 5;
+constexpr int kCellBits = 4;
 constexpr int kCellKeys = 1 << (3 * kCellBits);
+static_assert(kCellKeys % 1024 == 0, "cell_scan_kernel gives each of 1024 threads whole counts");
 
 struct CellGrid {
     double inv[3];  // cells per unit length
-    int nc[3];      // cells per axis (1 .. 32)
+    int nc[3];      // cells per axis (1 .. 16)
 };
 
 CellGrid make_cell_grid(const double box[3], double rc)
@@ -307,7 +308,7 @@ CellGrid make_cell_grid(const double box[3], double rc)
     return g;
 }
 
-__device__ __forceinline__ unsigned spread3(unsigned v)  // b4..b0 -> b12 b9 b6 b3 b0
+__device__ __forceinline__ unsigned spread3(unsigned v)  // bit b of v -> bit 3 b
 {
     v = (v | (v << 8)) & 0x0300f00fu;
     v = (v | (v << 4)) & 0x030c30c3u;
@@ -334,7 +335,7 @@ __global__ void cell_hist_kernel(const double *__restrict__ q4, int n, CellGrid 
 }
 
 // Exclusive prefix sum of the kCellKeys counts in place: one block of 1024
-// threads, 32 counts each.
+// threads, kCellKeys / 1024 counts each.
 __global__ void cell_scan_kernel(int *__restrict__ hist)
 {
     constexpr int kPer = kCellKeys / 1024;
