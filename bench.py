@@ -403,6 +403,8 @@ def schedule_name(tpi: int) -> str:
         name += ", 2 entries/lane (software-pipelined)"
     if tpi & 512:
         name += ", rows by length"
+    if tpi & 16384:
+        name += ", rows in cell order"
     if tpi & 1024:
         name += ", image-selected displacement"
     if tpi & 2048:
