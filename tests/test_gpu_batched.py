@@ -191,11 +191,15 @@ def test_full_batch_sampled_systems(cuda_lib, oracle_lib):
     """512 systems (N log-uniform 500..32000): the bench's batch, checked on
     sampled systems against the oracle."""
     from paper_1806_05713_gb300.batch import Batch
+    lj = cuda_lib
     systems = inputs.batched_systems(nsys=512, seed=0)
-    b = Batch(systems, 0.01, 0, True, tpi=8, rows_per_item=64)
-    b.force()
-    torch.cuda.synchronize()
-    got = _per_system(b, b.p4)
-    for k in (0, 1, 97, 255, 300, 511):
-        want = _oracle_dp(oracle_lib, systems[k], 0.01, True)
-        assert np.max(np.abs(got[k] - want)) <= FP64_TOL * np.max(np.abs(want))
+    want = {k: _oracle_dp(oracle_lib, systems[k], 0.01, True) for k in (0, 1, 97, 255, 300, 511)}
+    # 8 lanes per row, and the autotuner's pick there: 64-row items walked in
+    # per-lane chunks (lj_batch.tpi = LJ_SCHED_STREAM)
+    for tpi in (8, lj.LJ_SCHED_STREAM):
+        b = Batch(systems, 0.01, 0, True, tpi=tpi, rows_per_item=64)
+        b.force()
+        torch.cuda.synchronize()
+        got = _per_system(b, b.p4)
+        for k, w in want.items():
+            assert np.max(np.abs(got[k] - w)) <= FP64_TOL * np.max(np.abs(w)), (tpi, k)
