@@ -111,7 +111,8 @@ extern "C" {
  * moving forward through the row boundaries of its chunk; lanes idle only
  * in the padding of the last chunk instead of at the end of every row.
  * p_i is added with FP64 atomics by every lane whose chunk meets the row,
- * so full lists are not deterministic under this schedule. */
+ * so full lists are not deterministic under this schedule.  Lists of more
+ * than 2^31 - 257 entries are refused (LJ_ERR_CAPACITY). */
 #define LJ_SCHED_STREAM 8192
 /* LJ_SCHED_CELLS | (a row-group schedule, any form; not with LJ_SCHED_SORTED
  * or LJ_SCHED_STREAM): the rows are walked in space-filling order -- counting-

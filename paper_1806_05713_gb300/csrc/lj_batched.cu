@@ -332,6 +332,7 @@ extern "C" int lj_batch_init(lj_batch *batch, const lj_system *systems, int nsys
         if (y.n < 0 || y.nnz < 0 || y.atom_offset < 0 || y.row_offset < 0 || y.entry_offset < 0)
             return LJ_ERR_ARG;
         if (y.n >= (int64_t(1) << 31) - 1) return LJ_ERR_CAPACITY;
+        if (tpi == LJ_SCHED_STREAM && y.nnz > kStreamMaxEntries) return LJ_ERR_CAPACITY;
         const double *fake = reinterpret_cast<const double *>(256);
         const int32_t *fakei = reinterpret_cast<const int32_t *>(256);
         const int rc = check_force_args(fake, fake, y.n, fakei, fakei, y.nnz, y.r_cut, y.box, y.eps,

@@ -488,6 +488,11 @@ __device__ __forceinline__ void fp64_fixed_row(const double *__restrict__ q4,
 // atomics when it moves on.  A row is split over the one to three lanes
 // whose chunks it spans, so full lists are not deterministic.
 // Rows i0 .. i1-1 (i0 < i1) of the calling warp; every lane of the warp calls it.
+// The stream walk indexes entries with 32-bit ints up to 128 past the end of
+// a warp's range (the padding of the last chunk), so its callers keep a list
+// (a system's, in a batch) at or below this many entries.
+constexpr long long kStreamMaxEntries = 2147483647LL - 256;
+
 template <bool HALF>
 __device__ __forceinline__ void fp64_fixed_stream(const double *__restrict__ q4,
                                                   const longlong4 *__restrict__ X,

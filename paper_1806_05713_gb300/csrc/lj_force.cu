@@ -558,13 +558,15 @@ int force_check(const double *q4, const double *p4, int64_t n, const int32_t *ro
     if (t == LJ_TPI_AUTO) {
         if (precision == LJ_FP64)
             t = !fixed_point_ok(box, rc) ? (LJ_SCHED_IMAGES | 8)
-                : (half && n >= kStreamDefaultRows) ? (LJ_SCHED_FIXED | LJ_SCHED_STREAM | 32)
+                : (half && n >= kStreamDefaultRows && nnz <= kStreamMaxEntries)
+                    ? (LJ_SCHED_FIXED | LJ_SCHED_STREAM | 32)
                                                      : (LJ_SCHED_FIXED | 8);
         else
             t = precision == LJ_DFLOAT ? (LJ_SCHED_SWP2 | 8) : 8;
     }
     if ((t & LJ_SCHED_FIXED) && !fixed_point_ok(box, rc)) return LJ_ERR_ARG;
     if (!valid_schedule(t, precision)) return LJ_ERR_ARG;
+    if ((t & LJ_SCHED_STREAM) && nnz > kStreamMaxEntries) return LJ_ERR_CAPACITY;
     if (!ws || ws_bytes < force_workspace_bytes_impl(n, precision)) return LJ_ERR_CAPACITY;
     if (precision == LJ_DFLOAT && !dfloat_params_ok(box, dt, rc, eps, sigma)) return LJ_ERR_ARG;
     *tpi = t;

@@ -604,7 +604,7 @@ extern "C" int lj_force_vjp(const double *q4_dev, const double *gradF4_dev, int6
         if (fixed_point_ok(box, r_cut)) {
             fixed_prepass_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(q4_dev, ni, F, X);
             LJ_TRY_LAUNCH("fixed_prepass_kernel");
-            if (half && n >= kVjpStreamRows) {
+            if (half && n >= kVjpStreamRows && nnz <= kStreamMaxEntries) {
                 const int64_t warps = (n + kVjpStreamR - 1) / kVjpStreamR;
                 used_blocks = static_cast<int>((warps * 32 + kVjpThreads - 1) / kVjpThreads);
                 vjp_fp64_stream_kernel<<<used_blocks, kVjpThreads, 0, st>>>(

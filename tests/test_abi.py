@@ -94,6 +94,11 @@ def test_host_argument_checks_without_gpu():
     # 4096, two entries per lane on the fixed-point rows) are refused
     for retired in (64 | 8, 256 | 8, 4096 | 8, lj.LJ_SCHED_FIXED | lj.LJ_SCHED_SWP2 | 8):
         assert force(prec=0, tpi=retired, ws=fake, wsb=1 << 40) == lj.LJ_ERR_ARG
+    # the stream walk indexes entries in 32 bits with up to 128 of padding:
+    # lists within 256 of 2^31 entries are refused before any launch
+    stream32 = lj.LJ_SCHED_FIXED | lj.LJ_SCHED_STREAM | 32
+    assert force(prec=0, tpi=stream32, nnz=(1 << 31) - 200, ws=fake, wsb=1 << 40) == \
+        lj.LJ_ERR_CAPACITY
     # the space-filling row order excludes the length-sorted one and the
     # stream walk
     C = lj.LJ_SCHED_CELLS
